@@ -1,0 +1,356 @@
+"""FP64 CPU oracle for Cherenkov bunch generation and propagation.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product library
+never imports this package and shares no code with it.
+
+The arithmetic lives in ``cher_oracle.c`` (plain C, FP64, no fused
+multiply-add); this module compiles it with gcc and marshals numpy arrays
+through ctypes.  Every function cites the paper section it follows in the C
+source.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cher_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+
+ST_GROUND, ST_UPWARD, ST_BELOW_OBS, ST_ABOVE_MAX, ST_ANGLE = 0, 1, 2, 3, 4
+MAX_HITS = 4
+
+
+def build(force: bool = False) -> str:
+    """Compile cher_oracle.c into liboracle.so (gcc, -O2, no FMA contraction)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+            "-std=c11", _SRC, "-o", _LIB_PATH + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Atm(ctypes.Structure):
+    _fields_ = [("h_bound", ctypes.c_double * 6), ("a", ctypes.c_double * 5),
+                ("b", ctypes.c_double * 5), ("c", ctypes.c_double * 5),
+                ("n0_minus_1", ctypes.c_double)]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [("atm", _Atm), ("h_obs", ctypes.c_double), ("h_max", ctypes.c_double),
+                ("n_fine", ctypes.c_int), ("eta_tab", _dp),
+                ("H", ctypes.c_int), ("Z", ctypes.c_int), ("theta_max", ctypes.c_double),
+                ("ax", _dp), ("al", _dp),
+                ("bunch_size", ctypes.c_double), ("lambda1_nm", ctypes.c_double),
+                ("lambda2_nm", ctypes.c_double),
+                ("n_tel", ctypes.c_int), ("tel", _dp),
+                ("t_ref", _dp), ("n_showers", ctypes.c_int), ("bf_tol", ctypes.c_double)]
+
+
+class _Tracks(ctypes.Structure):
+    _fields_ = [("x0", _dp), ("y0", _dp), ("z0", _dp), ("t0", _dp), ("len", _dp),
+                ("ekin", _dp), ("ux", _dp), ("uy", _dp), ("uz", _dp),
+                ("shower", _u32p), ("n", ctypes.c_int64), ("track_base", ctypes.c_int64)]
+
+
+class _Out(ctypes.Structure):
+    _fields_ = [("status", _i32p), ("xe", _dp), ("ye", _dp), ("he", _dp), ("te", _dp),
+                ("px", _dp), ("py", _dp), ("pz", _dp), ("X", _dp), ("Y", _dp), ("t", _dp),
+                ("cx", _dp), ("cy", _dp), ("cz", _dp), ("lam", _dp), ("w", _dp),
+                ("nhit", _i32p), ("hit_tel", _i32p), ("hit_x", _dp), ("hit_y", _dp),
+                ("hit_t", _dp)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = ctypes.CDLL(path)
+        L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.orc_thickness.argtypes = [ctypes.POINTER(_Atm), ctypes.c_double]
+        L.orc_thickness.restype = ctypes.c_double
+        L.orc_rho.argtypes = [ctypes.POINTER(_Atm), ctypes.c_double]
+        L.orc_rho.restype = ctypes.c_double
+        L.orc_eta_exact.argtypes = [ctypes.POINTER(_Atm), ctypes.c_double]
+        L.orc_eta_exact.restype = ctypes.c_double
+        L.orc_build_eta_table.argtypes = [ctypes.POINTER(_Atm), ctypes.c_double,
+                                          ctypes.c_int, _dp]
+        L.orc_eta_lookup.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.orc_eta_lookup.restype = ctypes.c_double
+        L.orc_segment_yield.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int64, _dp, _dp,
+                                        _dp, _dp, _i32p, _dp, _dp, _i32p]
+        L.orc_brute_ray.argtypes = [ctypes.POINTER(_Atm), ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double, _dp, _dp]
+        L.orc_build_refraction_tables.argtypes = [ctypes.POINTER(_Atm), ctypes.c_double,
+                                                  ctypes.c_double, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_double,
+                                                  ctypes.c_double, _dp, _dp]
+        L.orc_propagate_photon.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int] + \
+            [ctypes.c_double] * 7 + [_dp]
+        L.orc_bunches.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Tracks),
+                                  ctypes.c_uint64, _i64p, ctypes.c_int,
+                                  ctypes.POINTER(_Out)]
+        L.orc_num_threads.restype = ctypes.c_int
+        L.orc_philox_fill.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                      ctypes.c_int64, _u32p]
+        _lib = L
+    return _lib
+
+
+def _ptr(a, ctype=ctypes.c_double):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# Atmosphere
+# --------------------------------------------------------------------------
+def _atm(atm: dict) -> _Atm:
+    A = _Atm()
+    A.h_bound[:] = list(map(float, atm["h_bound"]))
+    A.a[:] = list(map(float, atm["a"]))
+    A.b[:] = list(map(float, atm["b"]))
+    A.c[:] = list(map(float, atm["c"]))
+    A.n0_minus_1 = float(atm["n0_minus_1"])
+    return A
+
+
+def philox4x32_10(ctr, key):
+    """One Philox4x32-10 block: ctr (4 x u32), key (2 x u32) -> 4 x u32."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c, ctypes.c_uint32), _ptr(k, ctypes.c_uint32),
+                            _ptr(o, ctypes.c_uint32))
+    return o
+
+
+def philox_stream(seed: int, track: int, j0: int, n: int):
+    """n Philox blocks (4 words each) for counters (track, j0 + m, 0)."""
+    o = np.zeros((n, 4), dtype=np.uint32)
+    lib().orc_philox_fill(ctypes.c_uint64(seed), ctypes.c_uint64(track),
+                          ctypes.c_uint32(j0), int(n), _ptr(o, ctypes.c_uint32))
+    return o
+
+
+def eta_lookup(tab, h_max, h):
+    """Fine-table lookup of eta = n - 1 (clamped to [0, h_max])."""
+    t = _f64(tab)
+    return np.array([lib().orc_eta_lookup(_ptr(t), len(t), float(h_max), float(x))
+                     for x in np.atleast_1d(h)])
+
+
+def thickness(atm, h):
+    A = _atm(atm)
+    return np.array([lib().orc_thickness(ctypes.byref(A), float(x))
+                     for x in np.atleast_1d(h)])
+
+
+def rho(atm, h):
+    A = _atm(atm)
+    return np.array([lib().orc_rho(ctypes.byref(A), float(x)) for x in np.atleast_1d(h)])
+
+
+def eta_exact(atm, h):
+    A = _atm(atm)
+    return np.array([lib().orc_eta_exact(ctypes.byref(A), float(x))
+                     for x in np.atleast_1d(h)])
+
+
+def eta_table(atm, h_max, n_fine):
+    A = _atm(atm)
+    t = np.zeros(n_fine)
+    if lib().orc_build_eta_table(ctypes.byref(A), float(h_max), int(n_fine), _ptr(t)) != 0:
+        raise ValueError("bad eta table arguments")
+    return t
+
+
+def refraction_tables(atm, h_obs, h_max, H, Z, theta_max_rad, tol=1e-13):
+    A = _atm(atm)
+    ax = np.zeros((H, Z))
+    al = np.zeros((H, Z))
+    rc = lib().orc_build_refraction_tables(ctypes.byref(A), float(h_obs), float(h_max),
+                                           int(H), int(Z), float(theta_max_rad),
+                                           float(tol), _ptr(ax), _ptr(al))
+    if rc != 0:
+        raise ValueError("bad refraction table arguments")
+    return ax, al
+
+
+def brute_ray(atm, h_obs, h_e, sin_obs, tol=1e-12):
+    """(B): horizontal displacement x and optical path l from h_obs to h_e."""
+    A = _atm(atm)
+    x = ctypes.c_double()
+    l_ = ctypes.c_double()
+    rc = lib().orc_brute_ray(ctypes.byref(A), float(h_obs), float(h_e), float(sin_obs),
+                             float(tol), ctypes.byref(x), ctypes.byref(l_))
+    if rc != 0:
+        raise ValueError("bad ray")
+    return x.value, l_.value
+
+
+# --------------------------------------------------------------------------
+# A configured model: atmosphere + tables + telescopes + band
+# --------------------------------------------------------------------------
+@dataclass
+class Model:
+    atm: dict
+    h_obs: float
+    telescopes: np.ndarray               # (n_tel, 4): x, y, z, r
+    h_max: float = 60000.0
+    n_fine: int = 10000
+    H: int = 1000
+    Z: int = 64
+    theta_max_deg: float = 70.0
+    bunch_size: float = 5.0
+    lambda1_nm: float = 300.0
+    lambda2_nm: float = 600.0
+    t_ref: np.ndarray | None = None
+    table_tol: float = 1e-13
+    bf_tol: float = 1e-12
+    eta_tab: np.ndarray = field(init=False, repr=False)
+    ax: np.ndarray = field(init=False, repr=False)
+    al: np.ndarray = field(init=False, repr=False)
+
+    def __post_init__(self):
+        self.telescopes = _f64(np.asarray(self.telescopes).reshape(-1, 4))
+        self.eta_tab = eta_table(self.atm, self.h_max, self.n_fine)
+        self.ax, self.al = refraction_tables(self.atm, self.h_obs, self.h_max, self.H,
+                                             self.Z, np.radians(self.theta_max_deg),
+                                             self.table_tol)
+        if self.t_ref is not None:
+            self.t_ref = _f64(np.atleast_1d(self.t_ref))
+
+    def _cfg(self) -> _Cfg:
+        C = _Cfg()
+        C.atm = _atm(self.atm)
+        C.h_obs = self.h_obs
+        C.h_max = self.h_max
+        C.n_fine = self.n_fine
+        C.eta_tab = _ptr(self.eta_tab)
+        C.H, C.Z = self.H, self.Z
+        C.theta_max = float(np.radians(self.theta_max_deg))
+        C.ax, C.al = _ptr(self.ax), _ptr(self.al)
+        C.bunch_size = self.bunch_size
+        C.lambda1_nm, C.lambda2_nm = self.lambda1_nm, self.lambda2_nm
+        C.n_tel = self.telescopes.shape[0]
+        C.tel = _ptr(self.telescopes)
+        if self.t_ref is not None:
+            C.t_ref = _ptr(self.t_ref)
+            C.n_showers = self.t_ref.shape[0]
+        else:
+            C.t_ref = None
+            C.n_showers = 0
+        C.bf_tol = self.bf_tol
+        return C
+
+    # ---- a1: per-step yield ------------------------------------------------
+    def segment_yield(self, tracks: dict):
+        n = len(tracks["z0"])
+        z0, ln, ek, uz = (_f64(tracks[k]) for k in ("z0", "len", "ekin", "uz"))
+        nb = np.zeros(n, np.int32)
+        w = np.zeros(n)
+        s2 = np.zeros(n)
+        valid = np.zeros(n, np.int32)
+        C = self._cfg()
+        lib().orc_segment_yield(ctypes.byref(C), n, _ptr(z0), _ptr(ln), _ptr(ek), _ptr(uz),
+                                _ptr(nb, ctypes.c_int32), _ptr(w), _ptr(s2),
+                                _ptr(valid, ctypes.c_int32))
+        return nb, w, s2, valid.astype(bool)
+
+    # ---- a2..a5: every bunch ----------------------------------------------
+    def bunches(self, tracks: dict, seed: int, variant: int = 0, track_base: int = 0):
+        nb, _, _, _ = self.segment_yield(tracks)
+        off = np.zeros(len(nb) + 1, np.int64)
+        np.cumsum(nb, out=off[1:])
+        nbt = int(off[-1])
+        arr = {k: _f64(tracks[k]) for k in
+               ("x0", "y0", "z0", "t0", "len", "ekin", "ux", "uy", "uz")}
+        T = _Tracks()
+        for k, v in arr.items():
+            setattr(T, k, _ptr(v))
+        shower = tracks.get("shower")
+        if shower is not None:
+            shower = np.ascontiguousarray(shower, dtype=np.uint32)
+            T.shower = _ptr(shower, ctypes.c_uint32)
+        else:
+            T.shower = None
+        T.n = len(nb)
+        T.track_base = int(track_base)
+        out = {k: np.zeros(nbt) for k in ("xe", "ye", "he", "te", "px", "py", "pz", "X", "Y",
+                                          "t", "cx", "cy", "cz", "lam", "w")}
+        out["status"] = np.zeros(nbt, np.int32)
+        out["nhit"] = np.zeros(nbt, np.int32)
+        out["hit_tel"] = np.full((nbt, MAX_HITS), -1, np.int32)
+        for k in ("hit_x", "hit_y", "hit_t"):
+            out[k] = np.zeros((nbt, MAX_HITS))
+        O = _Out()
+        for k, v in out.items():
+            setattr(O, k, _ptr(v, ctypes.c_int32 if v.dtype == np.int32 else ctypes.c_double))
+        C = self._cfg()
+        rc = lib().orc_bunches(ctypes.byref(C), ctypes.byref(T), ctypes.c_uint64(seed),
+                               _ptr(off, ctypes.c_int64), int(variant), ctypes.byref(O))
+        if rc != 0:
+            raise ValueError("orc_bunches failed")
+        seg = np.repeat(np.arange(len(nb), dtype=np.int64), nb)
+        out["seg"] = seg
+        out["j"] = np.arange(nbt, dtype=np.int64) - off[seg]
+        out["nb"] = nb
+        out["off"] = off
+        return out
+
+    def propagate_photon(self, xe, ye, he, te, px, py, pz, variant=0):
+        r = np.zeros(6)
+        C = self._cfg()
+        st = lib().orc_propagate_photon(ctypes.byref(C), int(variant), xe, ye, he, te,
+                                        px, py, pz, _ptr(r))
+        return st, r
+
+
+def hit_records(out: dict, track_base: int = 0):
+    """Flatten the per-bunch hit lists into records sorted by (tel, key)."""
+    nh = np.minimum(out["nhit"], MAX_HITS)
+    if np.any(out["nhit"] > MAX_HITS):
+        raise RuntimeError("a bunch crossed more telescopes than the oracle records")
+    b = np.repeat(np.arange(len(nh)), nh)
+    slot = np.concatenate([np.arange(m) for m in nh]) if len(nh) else np.zeros(0, int)
+    slot = slot.astype(np.int64)
+    tel = out["hit_tel"][b, slot]
+    key = ((out["seg"][b] + track_base).astype(np.uint64) << np.uint64(32)) | \
+        out["j"][b].astype(np.uint64)
+    rec = dict(tel=tel.astype(np.int64), key=key, bunch=b,
+               x=out["hit_x"][b, slot], y=out["hit_y"][b, slot], t=out["hit_t"][b, slot],
+               cx=out["cx"][b], cy=out["cy"][b], zem=out["he"][b], w=out["w"][b],
+               lam=out["lam"][b])
+    order = np.lexsort((rec["key"], rec["tel"]))
+    return {k: v[order] for k, v in rec.items()}
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())

@@ -1,0 +1,676 @@
+/*
+ * cher_oracle.c -- plain, slow FP64 CPU oracle for Cherenkov photon-bunch
+ * generation and propagation (Arrabito et al., "Optimizing Cherenkov photons
+ * generation and propagation in CORSIKA for CTA Monte-Carlo simulations").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes or
+ * calls this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark load it.  It shares no code, header, table or constant with
+ * the CUDA path.
+ *
+ * What it computes, in the order the paper describes it (Appendix A):
+ *   per track step   : Cherenkov yield (CERENK, paper section 3.2), split
+ *                      into sub-steps, one bunch of about five photons each;
+ *   per bunch        : emission point, azimuth and wavelength from a
+ *                      counter-based Philox4x32-10 stream keyed by
+ *                      (seed, track, bunch), so every code version draws the
+ *                      same random sequence (paper section 5.2);
+ *                      refraction and propagation to the observation level
+ *                      (RAYBND, paper section 3.2 and the Appendix B listing:
+ *                      the horizontal direction is rescaled by
+ *                      sin(theta_obs)/sin(theta_em), the vertical cosine is
+ *                      recomputed from sin(theta_obs), the ground point moves
+ *                      by the horizontal offset along the horizontal
+ *                      direction and the travel time is added);
+ *                      atmosphere lookups through uniform fine tables built
+ *                      once (fast interpolation, paper section 3.3.2, 10000
+ *                      points for the index of refraction);
+ *                      the fiducial-sphere test of every telescope (paper
+ *                      section 2: only photons crossing a sphere are kept).
+ * The paper prints no formulas; the physics is textbook (Frank-Tamm yield,
+ * Cherenkov angle cos(theta_c) = 1/(beta n), Snell's law in a flat layered
+ * atmosphere) and every choice the paper leaves open is listed, as a
+ * "reading", in the design notes of the repository.
+ *
+ * Two propagation variants:
+ *   (T) table variant: refraction corrections interpolated bilinearly from
+ *       tables over (height, squared sine of the observation zenith angle)
+ *       that this file builds by numerical integration.  This is the parity
+ *       reference.
+ *   (B) brute-force variant: the ray integral itself, with no tables, used to
+ *       pin (T) on tiny inputs.
+ *
+ * Floating point: FP64 throughout, compiled with -ffp-contract=off so that no
+ * multiply-add is fused; the photon-yield chain and the index-of-refraction
+ * table lookup are written one IEEE operation per statement because the
+ * integer bunch count nb = ceil(N/B) depends on their exact rounding.
+ *
+ * Units: lengths in m, heights above sea level with z up, times in ns,
+ * energies in MeV, wavelengths in nm.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ----------------------------------------------------------------------- */
+/* Physical constants (CODATA 2018 / SI definition)                         */
+/* ----------------------------------------------------------------------- */
+#define ORC_C_M_PER_NS 0.299792458       /* speed of light, m/ns (exact)     */
+#define ORC_ME_MEV 0.51099895000         /* electron mass, MeV               */
+#define ORC_ALPHA 7.2973525693e-3        /* fine-structure constant          */
+#define ORC_PI 3.14159265358979323846
+
+/* drop / status codes of a bunch (paper Alg. 1: the rare branches) */
+#define ORC_ST_GROUND 0      /* reached the observation level               */
+#define ORC_ST_UPWARD 1      /* photon direction not downward               */
+#define ORC_ST_BELOW_OBS 2   /* emitted below the observation level         */
+#define ORC_ST_ABOVE_MAX 3   /* emitted above the top of the tables         */
+#define ORC_ST_ANGLE 4       /* zenith at the observation level > table max */
+
+#define ORC_MAX_HITS 4       /* telescopes recorded per bunch               */
+
+/* Layered atmosphere: thickness T(h) = a_i + b_i exp(-h/c_i) in layer i,
+ * h in [h_bound[i], h_bound[i+1]); density rho = -dT/dh; above h_bound[5]
+ * there is no air.  n(h) - 1 = n0_minus_1 * rho(h) / rho(0). */
+typedef struct {
+    double h_bound[6];
+    double a[5], b[5], c[5];
+    double n0_minus_1;
+} orc_atm;
+
+/* Everything the per-bunch computation needs, set up by the caller. */
+typedef struct {
+    orc_atm atm;
+    double h_obs;            /* observation level, m a.s.l.                */
+    double h_max;            /* top of the tables, m a.s.l.                */
+    /* fine table of eta = n - 1 on [0, h_max], n_fine points              */
+    int n_fine;
+    const double *eta_tab;
+    /* refraction tables [H][Z]: h in [h_obs, h_max], sin^2 in [0, sin^2 tmax] */
+    int H, Z;
+    double theta_max;        /* rad                                        */
+    const double *ax, *al;
+    /* bunching and wavelength band                                        */
+    double bunch_size;
+    double lambda1_nm, lambda2_nm;
+    /* telescopes: x, y, z (relative to h_obs), r                          */
+    int n_tel;
+    const double *tel;
+    /* per-shower reference time (ns); NULL means zero                      */
+    const double *t_ref;
+    int n_showers;
+    double bf_tol;           /* absolute tolerance of the (B) integrals    */
+} orc_cfg;
+
+typedef struct {
+    const double *x0, *y0, *z0, *t0, *len, *ekin;
+    const double *ux, *uy, *uz;
+    const uint32_t *shower;  /* NULL: every track belongs to shower 0      */
+    int64_t n;
+    int64_t track_base;      /* global index of track 0 (Philox counter)   */
+} orc_tracks;
+
+/* One entry per bunch, indexed by bunch_off[i] + j. */
+typedef struct {
+    int32_t *status;
+    double *xe, *ye, *he, *te;        /* emission point and time           */
+    double *px, *py, *pz;             /* emission direction                */
+    double *X, *Y, *t;                /* ground point and arrival time     */
+    double *cx, *cy, *cz;             /* direction at the observation level */
+    double *lam, *w;                  /* wavelength (nm), photons          */
+    int32_t *nhit;                    /* telescopes crossed                */
+    int32_t *hit_tel;                 /* [ORC_MAX_HITS] per bunch          */
+    double *hit_x, *hit_y, *hit_t;    /* record in the telescope frame     */
+} orc_bunch_out;
+
+/* ======================================================================= */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel random      */
+/* numbers: as easy as 1, 2, 3").  Each round multiplies counter words 0   */
+/* and 2 by the two round multipliers, takes the 64-bit products apart and */
+/* mixes the high halves with the other counter words and the key; the key */
+/* is advanced by the two Weyl constants between rounds.                   */
+/* ======================================================================= */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* n consecutive blocks for counters (lo(i), hi(i), j0 + m, 0), m < n, under
+ * the key (lo(seed), hi(seed)): 4 n words into out. */
+void orc_philox_fill(uint64_t seed, uint64_t i, uint32_t j0, int64_t n, uint32_t *out)
+{
+    uint32_t key[2] = { (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) };
+    for (int64_t m = 0; m < n; ++m) {
+        uint32_t ctr[4] = { (uint32_t)(i & 0xffffffffu), (uint32_t)(i >> 32),
+                            j0 + (uint32_t)m, 0u };
+        orc_philox4x32_10(ctr, key, out + 4 * m);
+    }
+}
+
+/* A 32-bit word to a uniform deviate in (0, 1): (x + 1/2) / 2^32, exact. */
+static double orc_u01(uint32_t x)
+{
+    return ((double)x + 0.5) * (1.0 / 4294967296.0);
+}
+
+/* ======================================================================= */
+/* Atmosphere (paper section 3.3.1: density, thickness and refractive index */
+/* as functions of altitude)                                                */
+/* ======================================================================= */
+static int orc_layer(const orc_atm *A, double h)
+{
+    int i = 0;
+    while (i < 4 && h >= A->h_bound[i + 1]) ++i;
+    return i;
+}
+
+double orc_thickness(const orc_atm *A, double h)
+{
+    if (h >= A->h_bound[5]) return 0.0;
+    int i = orc_layer(A, h);
+    return A->a[i] + A->b[i] * exp(-(h / A->c[i]));
+}
+
+double orc_rho(const orc_atm *A, double h)
+{
+    if (h >= A->h_bound[5]) return 0.0;
+    int i = orc_layer(A, h);
+    double r = A->b[i] / A->c[i];
+    double e = exp(-(h / A->c[i]));
+    return r * e;
+}
+
+/* eta(h) = n(h) - 1 = n0_minus_1 * rho(h) / rho(0), from the formula. */
+double orc_eta_exact(const orc_atm *A, double h)
+{
+    double rho0 = orc_rho(A, 0.0);
+    double rho = orc_rho(A, h);
+    double q = rho / rho0;
+    return A->n0_minus_1 * q;
+}
+
+/* Fine table (fast interpolation, paper section 3.3.2): eta at the
+ * n uniformly spaced heights h_k = k * dh, dh = h_max / (n - 1). */
+int orc_build_eta_table(const orc_atm *A, double h_max, int n, double *tab)
+{
+    if (n < 2 || !(h_max > 0.0)) return -1;
+    double dh = h_max / (double)(n - 1);
+    for (int k = 0; k < n; ++k) {
+        double h = (double)k * dh;
+        tab[k] = orc_eta_exact(A, h);
+    }
+    return 0;
+}
+
+/* Lookup in the fine table: no search, index from the uniform step; the
+ * height is clamped to [0, h_max].  One IEEE operation per statement. */
+double orc_eta_lookup(const double *tab, int n, double h_max, double h)
+{
+    double dh = h_max / (double)(n - 1);
+    double inv_dh = 1.0 / dh;
+    double hc = h;
+    if (hc < 0.0) hc = 0.0;
+    if (hc > h_max) hc = h_max;
+    double x = hc * inv_dh;
+    int k = (int)x;
+    if (k > n - 2) k = n - 2;
+    double f = x - (double)k;
+    double d = tab[k + 1] - tab[k];
+    double fd = f * d;
+    return tab[k] + fd;
+}
+
+/* ======================================================================= */
+/* Per-step photon yield (CERENK, paper section 3.2 and Appendix A)         */
+/* ======================================================================= */
+/* Frank-Tamm for a singly charged particle with n independent of the
+ * wavelength: dN/dL = 2 pi alpha sin^2(theta_c) (1/lambda1 - 1/lambda2).
+ * sin^2(theta_c) = 1 - 1/(beta n)^2 is written without cancellation using
+ * g = E_kin / m_e (gamma = 1 + g, beta^2 gamma^2 = g (2 + g)):
+ *     sin^2 = [eta (2 + eta) gamma^2 - (1 + eta)^2] / [g (2 + g) (1 + eta)^2].
+ * n is taken at the midpoint of the step.  nb = ceil(N / B) bunches share
+ * the photons equally: w = N / nb. */
+typedef struct {
+    int64_t nb;
+    double w, N, s2, beta, eta;
+} orc_yield;
+
+static double orc_band_factor(const orc_cfg *C)
+{
+    /* 2 pi alpha (1/lambda1 - 1/lambda2), lambda in m */
+    double two_pi_alpha = (2.0 * ORC_PI) * ORC_ALPHA;
+    double inv1 = 1.0e9 / C->lambda1_nm;
+    double inv2 = 1.0e9 / C->lambda2_nm;
+    double dinv = inv1 - inv2;
+    return two_pi_alpha * dinv;
+}
+
+static int orc_finite(double v) { return v == v && v - v == 0.0; }
+
+/* returns 0 for a valid step, -1 for an invalid one (nb = 0 then) */
+static int orc_step_yield(const orc_cfg *C, double z0, double len, double ekin,
+                          double uz, orc_yield *Y)
+{
+    Y->nb = 0; Y->w = 0.0; Y->N = 0.0; Y->s2 = 0.0; Y->beta = 0.0; Y->eta = 0.0;
+    if (!orc_finite(z0) || !orc_finite(len) || !orc_finite(ekin) || !orc_finite(uz)
+        || len < 0.0 || ekin <= 0.0)
+        return -1;
+    double inv_me = 1.0 / ORC_ME_MEV;
+    double K = orc_band_factor(C);
+    double inv_B = 1.0 / C->bunch_size;
+
+    double g = ekin * inv_me;               /* gamma - 1                   */
+    double gam = 1.0 + g;
+    double gam2 = gam * gam;
+    double half_len = 0.5 * len;
+    double dz = half_len * uz;
+    double hm = z0 + dz;                    /* midpoint height             */
+    double eta = orc_eta_lookup(C->eta_tab, C->n_fine, C->h_max, hm);
+    double np1 = 1.0 + eta;
+    double np1sq = np1 * np1;
+    double two_eta = 2.0 + eta;
+    double a = eta * two_eta;
+    double b = a * gam2;
+    double num = b - np1sq;                 /* (beta n)^2 gamma^2 - gamma^2 ... */
+    double two_g = 2.0 + g;
+    double bg2 = g * two_g;                 /* beta^2 gamma^2              */
+    double den = bg2 * np1sq;
+    double s2 = num / den;
+    Y->eta = eta;
+    Y->beta = sqrt(bg2) / gam;
+    if (!(s2 > 0.0)) return 0;              /* below threshold             */
+    double Ks2 = K * s2;
+    double N = len * Ks2;
+    double q = N * inv_B;
+    if (!(q < 2147483647.0)) return -1;
+    double nbd = ceil(q);
+    Y->s2 = s2;
+    Y->N = N;
+    Y->nb = (int64_t)nbd;
+    Y->w = (Y->nb > 0) ? N / nbd : 0.0;
+    return 0;
+}
+
+/* Per-step yield for n steps: nb (bunches), w (photons per bunch),
+ * s2 (sin^2 of the Cherenkov angle) and a validity flag (1 valid). */
+void orc_segment_yield(const orc_cfg *C, int64_t n, const double *z0,
+                       const double *len, const double *ekin, const double *uz,
+                       int32_t *nb, double *w, double *s2, int32_t *valid)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        orc_yield Y;
+        int ok = orc_step_yield(C, z0[i], len[i], ekin[i], uz[i], &Y);
+        nb[i] = (int32_t)Y.nb;
+        if (w) w[i] = Y.w;
+        if (s2) s2[i] = Y.s2;
+        if (valid) valid[i] = (ok == 0);
+    }
+}
+
+/* ======================================================================= */
+/* Ray integrals in a flat layered atmosphere (RAYBND's refraction,        */
+/* paper section 3.2).  With n(h) sin(theta(h)) = n_obs sin(theta_obs)     */
+/* (Snell), a ray seen at zenith theta_obs at the observation level has    */
+/*   horizontal displacement x(h) = int_{h_obs}^{h} tan(theta(h')) dh'     */
+/*   optical path            l(h) = int_{h_obs}^{h} n(h') / cos(theta(h')) dh' */
+/* The integrands are smooth inside a layer and jump at layer boundaries,   */
+/* so every integral is split there and done by adaptive Simpson.          */
+/* ======================================================================= */
+typedef struct {
+    const orc_atm *A;
+    double np1_obs;   /* n at the observation level                        */
+    double s_obs;     /* sin(theta_obs)                                    */
+    double c_obs;     /* cos(theta_obs)                                    */
+    int which;        /* integrand selector                                */
+} orc_ray;
+
+enum { F_TAN = 0, F_OPT = 1, F_TAN_CORR = 2, F_OPT_CORR = 3, F_RATIO = 4 };
+
+static double orc_integrand(const orc_ray *R, double h)
+{
+    double eta = orc_eta_exact(R->A, h);
+    double np1 = 1.0 + eta;
+    double s = R->np1_obs * R->s_obs / np1;
+    double c = sqrt(1.0 - s * s);
+    switch (R->which) {
+    case F_TAN: return s / c;
+    case F_OPT: return np1 / c;
+    case F_TAN_CORR: return s / c - R->s_obs / R->c_obs;
+    case F_OPT_CORR: return np1 / c - 1.0 / R->c_obs;
+    case F_RATIO: return R->np1_obs / np1 - 1.0;
+    }
+    return 0.0;
+}
+
+static double orc_simpson_rec(const orc_ray *R, double a, double b, double fa,
+                              double fm, double fb, double whole, double tol,
+                              int depth)
+{
+    double m = 0.5 * (a + b);
+    double lm = 0.5 * (a + m), rm = 0.5 * (m + b);
+    double flm = orc_integrand(R, lm), frm = orc_integrand(R, rm);
+    double left = (m - a) / 6.0 * (fa + 4.0 * flm + fm);
+    double right = (b - m) / 6.0 * (fm + 4.0 * frm + fb);
+    double delta = left + right - whole;
+    if (depth <= 0 || fabs(delta) <= 15.0 * tol)
+        return left + right + delta / 15.0;
+    return orc_simpson_rec(R, a, m, fa, flm, fm, left, 0.5 * tol, depth - 1)
+         + orc_simpson_rec(R, m, b, fm, frm, fb, right, 0.5 * tol, depth - 1);
+}
+
+static double orc_simpson(const orc_ray *R, double a, double b, double tol)
+{
+    if (b <= a) return 0.0;
+    double fa = orc_integrand(R, a), fb = orc_integrand(R, b);
+    double m = 0.5 * (a + b), fm = orc_integrand(R, m);
+    double whole = (b - a) / 6.0 * (fa + 4.0 * fm + fb);
+    return orc_simpson_rec(R, a, b, fa, fm, fb, whole, tol, 48);
+}
+
+/* integral over [lo, hi] split at the layer boundaries inside it */
+static double orc_integrate(const orc_ray *R, double lo, double hi, double tol)
+{
+    double sum = 0.0, a = lo;
+    for (int i = 1; i <= 5; ++i) {
+        double hb = R->A->h_bound[i];
+        if (hb > a && hb < hi) {
+            sum += orc_simpson(R, a, hb, tol);
+            a = hb;
+        }
+    }
+    sum += orc_simpson(R, a, hi, tol);
+    return sum;
+}
+
+/* (B): x and l of the ray that arrives at zenith asin(sin_obs), from the
+ * observation level up to h_e, with the exact n(h). */
+int orc_brute_ray(const orc_atm *A, double h_obs, double h_e, double sin_obs,
+                  double tol, double *x_out, double *l_out)
+{
+    if (!(sin_obs >= 0.0 && sin_obs < 1.0) || h_e < h_obs) return -1;
+    orc_ray R;
+    R.A = A;
+    R.np1_obs = 1.0 + orc_eta_exact(A, h_obs);
+    R.s_obs = sin_obs;
+    R.c_obs = sqrt(1.0 - sin_obs * sin_obs);
+    R.which = F_TAN;
+    *x_out = orc_integrate(&R, h_obs, h_e, tol);
+    R.which = F_OPT;
+    *l_out = orc_integrate(&R, h_obs, h_e, tol);
+    return 0;
+}
+
+/* Refraction tables over heights h_j = h_obs + j dht (j < H, dht =
+ * (h_max - h_obs)/(H-1)) and observation-level zeniths theta_k whose squared
+ * sines are uniform: sin^2(theta_k) = k dq (k < Z, dq = sin^2(theta_max)/(Z-1)).
+ * They hold the corrections to the straight line at theta_k,
+ *     dx = x(h_j) - (h_j - h_obs) tan(theta_k),
+ *     dl = l(h_j) - (h_j - h_obs) / cos(theta_k),
+ * divided by their leading angular dependence so that interpolation stays
+ * accurate at large zenith angles (to first order in n - 1, ax does not
+ * depend on the angle and al is linear in sin^2(theta)):
+ *     ax[j][k] = dx cos^3(theta_k) / sin(theta_k)   (k > 0),
+ *     ax[j][0] = int (n_obs / n(h') - 1) dh'         (the limit theta -> 0),
+ *     al[j][k] = dl cos^3(theta_k).
+ * Each column is accumulated interval by interval. */
+int orc_build_refraction_tables(const orc_atm *A, double h_obs, double h_max,
+                                int H, int Z, double theta_max, double tol,
+                                double *ax, double *al)
+{
+    if (H < 2 || Z < 2 || !(h_max > h_obs) || !(theta_max > 0.0)
+        || !(theta_max < 0.5 * ORC_PI))
+        return -1;
+    double dht = (h_max - h_obs) / (double)(H - 1);
+    double smax = sin(theta_max);
+    double dq = smax * smax / (double)(Z - 1);
+    double np1_obs = 1.0 + orc_eta_exact(A, h_obs);
+    for (int k = 0; k < Z; ++k) {
+        double q = (double)k * dq;
+        double so = sqrt(q), co = sqrt(1.0 - so * so);
+        orc_ray R;
+        R.A = A; R.np1_obs = np1_obs; R.s_obs = so; R.c_obs = co;
+        double dx = 0.0, dl = 0.0;
+        ax[(size_t)0 * Z + k] = 0.0;
+        al[(size_t)0 * Z + k] = 0.0;
+        for (int j = 1; j < H; ++j) {
+            double lo = h_obs + (double)(j - 1) * dht;
+            double hi = h_obs + (double)j * dht;
+            R.which = (k == 0) ? F_RATIO : F_TAN_CORR;
+            dx += orc_integrate(&R, lo, hi, tol);
+            R.which = F_OPT_CORR;
+            dl += orc_integrate(&R, lo, hi, tol);
+            double c3 = co * co * co;
+            ax[(size_t)j * Z + k] = (k == 0) ? dx : dx * c3 / so;
+            al[(size_t)j * Z + k] = dl * c3;
+        }
+    }
+    return 0;
+}
+
+/* bilinear interpolation in a [H][Z] table at fractional indices */
+static double orc_bilinear(const double *T, int Z, int j, int k, double a, double b)
+{
+    double t00 = T[(size_t)j * Z + k], t01 = T[(size_t)j * Z + k + 1];
+    double t10 = T[(size_t)(j + 1) * Z + k], t11 = T[(size_t)(j + 1) * Z + k + 1];
+    double v0 = t00 + a * (t10 - t00);
+    double v1 = t01 + a * (t11 - t01);
+    return v0 + b * (v1 - v0);
+}
+
+/* ======================================================================= */
+/* Propagation of one photon bunch to the observation level (RAYBND).      */
+/* variant 0 = (T) tables, 1 = (B) brute force.                             */
+/* out: X, Y, t, cx, cy, cz.  Returns the status code.                      */
+/* ======================================================================= */
+int orc_propagate_photon(const orc_cfg *C, int variant, double xe, double ye,
+                         double he, double te, double px, double py, double pz,
+                         double *out)
+{
+    /* rare conditions first (paper Alg. 2), each a counted drop */
+    if (pz >= 0.0) return ORC_ST_UPWARD;
+    if (he < C->h_obs) return ORC_ST_BELOW_OBS;
+    if (he > C->h_max) return ORC_ST_ABOVE_MAX;
+
+    double sin_em = sqrt(px * px + py * py);
+    double eta_e, eta_o;
+    if (variant == 0) {
+        eta_e = orc_eta_lookup(C->eta_tab, C->n_fine, C->h_max, he);
+        eta_o = orc_eta_lookup(C->eta_tab, C->n_fine, C->h_max, C->h_obs);
+    } else {
+        eta_e = orc_eta_exact(&C->atm, he);
+        eta_o = orc_eta_exact(&C->atm, C->h_obs);
+    }
+    /* Snell in flat layers: n(h_e) sin(theta_em) = n_obs sin(theta_obs) */
+    double sin_obs = sin_em * (1.0 + eta_e) / (1.0 + eta_o);
+    double q = sin_obs * sin_obs;
+    double smax = sin(C->theta_max);
+    double q_max = smax * smax;
+    if (q > q_max) return ORC_ST_ANGLE;
+    double cos_obs = sqrt(1.0 - q);
+    double dH = he - C->h_obs;
+
+    double hx = 0.0, hy = 0.0;        /* horizontal unit direction        */
+    if (sin_em > 0.0) { hx = px / sin_em; hy = py / sin_em; }
+
+    double D, L;                      /* horizontal offset, optical path  */
+    if (variant == 0) {
+        double dht = (C->h_max - C->h_obs) / (double)(C->H - 1);
+        double dq = q_max / (double)(C->Z - 1);
+        double fj = dH / dht;
+        int j = (int)fj;
+        if (j > C->H - 2) j = C->H - 2;
+        double a = fj - (double)j;
+        double fk = q / dq;
+        int k = (int)fk;
+        if (k > C->Z - 2) k = C->Z - 2;
+        double b = fk - (double)k;
+        double Ax = orc_bilinear(C->ax, C->Z, j, k, a, b);
+        double Al = orc_bilinear(C->al, C->Z, j, k, a, b);
+        /* dx = Ax tan sec^2, dl = Al sec^3 (see the table definition) */
+        double sec = 1.0 / cos_obs;
+        double tn = sin_obs * sec;
+        double sec2 = sec * sec;
+        D = dH * tn + Ax * tn * sec2;
+        L = dH * sec + Al * sec2 * sec;
+    } else {
+        if (orc_brute_ray(&C->atm, C->h_obs, he, sin_obs, C->bf_tol, &D, &L) != 0)
+            return ORC_ST_ANGLE;
+    }
+    out[0] = xe + D * hx;
+    out[1] = ye + D * hy;
+    out[2] = te + L / ORC_C_M_PER_NS;
+    out[3] = sin_obs * hx;
+    out[4] = sin_obs * hy;
+    out[5] = -cos_obs;
+    return ORC_ST_GROUND;
+}
+
+/* ======================================================================= */
+/* Fiducial telescope spheres (TELOUT, paper sections 2 and Appendix A).    */
+/* The line through the ground point along the arrival direction crosses   */
+/* sphere k iff |(C_k - P0) x D|^2 <= R_k^2 (inclusive).  The record is    */
+/* taken where the line crosses the horizontal plane through the centre,   */
+/* relative to the centre; its time moves at c/n_obs along the line.       */
+/* ======================================================================= */
+static int orc_telescopes(const orc_cfg *C, double X, double Y, double t,
+                          double cx, double cy, double cz, double np1_obs,
+                          int32_t *tel, double *rx, double *ry, double *rt)
+{
+    int nh = 0;
+    for (int k = 0; k < C->n_tel; ++k) {
+        double tx = C->tel[4 * k + 0], ty = C->tel[4 * k + 1];
+        double tz = C->tel[4 * k + 2], tr = C->tel[4 * k + 3];
+        double dx = tx - X, dy = ty - Y, dz = tz;
+        double q0 = dy * cz - dz * cy;
+        double q1 = dz * cx - dx * cz;
+        double q2 = dx * cy - dy * cx;
+        double d2 = q0 * q0 + q1 * q1 + q2 * q2;
+        if (d2 <= tr * tr) {
+            if (nh < ORC_MAX_HITS) {
+                double s = tz / cz;
+                tel[nh] = k;
+                rx[nh] = X + s * cx - tx;
+                ry[nh] = Y + s * cy - ty;
+                rt[nh] = t + s * np1_obs / ORC_C_M_PER_NS;
+            }
+            ++nh;
+        }
+    }
+    return nh;
+}
+
+/* ======================================================================= */
+/* Whole path for a set of steps: every bunch of every step.               */
+/* bunch_off[i] is the index of the first bunch of step i (a prefix sum of */
+/* nb from orc_segment_yield).  variant 0 = (T), 1 = (B).                  */
+/* Returns 0, or -1 on bad arguments.                                       */
+/* ======================================================================= */
+int orc_bunches(const orc_cfg *C, const orc_tracks *Tk, uint64_t seed,
+                const int64_t *bunch_off, int variant, orc_bunch_out *O)
+{
+    if (!C || !Tk || !bunch_off || !O) return -1;
+    uint32_t key[2] = { (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) };
+    double inv1 = 1.0 / C->lambda1_nm, inv2 = 1.0 / C->lambda2_nm;
+    double np1_obs_T = 1.0 + orc_eta_lookup(C->eta_tab, C->n_fine, C->h_max, C->h_obs);
+    double np1_obs_B = 1.0 + orc_eta_exact(&C->atm, C->h_obs);
+    double np1_obs = (variant == 0) ? np1_obs_T : np1_obs_B;
+
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < Tk->n; ++i) {
+        orc_yield Y;
+        if (orc_step_yield(C, Tk->z0[i], Tk->len[i], Tk->ekin[i], Tk->uz[i], &Y) != 0)
+            continue;
+        if (Y.nb == 0) continue;
+        double ux = Tk->ux[i], uy = Tk->uy[i], uz = Tk->uz[i];
+        double cos_c = 1.0 / (Y.beta * (1.0 + Y.eta));
+        double sin_c = sqrt(Y.s2);
+        /* azimuth basis around the step direction */
+        double e1x, e1y, e1z = 0.0;
+        double rho2 = ux * ux + uy * uy;
+        if (rho2 > 1e-20) {
+            double r = sqrt(rho2);
+            e1x = -uy / r; e1y = ux / r;
+        } else {
+            e1x = 1.0; e1y = 0.0;
+        }
+        double e2x = uy * e1z - uz * e1y;
+        double e2y = uz * e1x - ux * e1z;
+        double e2z = ux * e1y - uy * e1x;
+        uint32_t sh = Tk->shower ? Tk->shower[i] : 0u;
+        double t_ref = (C->t_ref && (int)sh < C->n_showers) ? C->t_ref[sh] : 0.0;
+        int64_t gi = Tk->track_base + i;
+        double inv_bc = 1.0 / (Y.beta * ORC_C_M_PER_NS);
+        for (int64_t j = 0; j < Y.nb; ++j) {
+            int64_t bidx = bunch_off[i] + j;
+            uint32_t ctr[4] = { (uint32_t)((uint64_t)gi & 0xffffffffu),
+                                (uint32_t)((uint64_t)gi >> 32), (uint32_t)j, 0u };
+            uint32_t x[4];
+            orc_philox4x32_10(ctr, key, x);
+            double u0 = orc_u01(x[0]), u1 = orc_u01(x[1]), u2 = orc_u01(x[2]);
+            /* sub-step j, emission point uniform inside it */
+            double f = ((double)j + u0) / (double)Y.nb;
+            double phi = 2.0 * ORC_PI * u1;
+            /* 1/lambda^2 spectrum on [lambda1, lambda2] by inversion */
+            double lam = 1.0 / (inv1 - u2 * (inv1 - inv2));
+            double cp = cos(phi), sp = sin(phi);
+            double px = cos_c * ux + sin_c * (cp * e1x + sp * e2x);
+            double py = cos_c * uy + sin_c * (cp * e1y + sp * e2y);
+            double pz = cos_c * uz + sin_c * (cp * e1z + sp * e2z);
+            double fl = f * Tk->len[i];
+            double xe = Tk->x0[i] + fl * ux;
+            double ye = Tk->y0[i] + fl * uy;
+            double he = Tk->z0[i] + fl * uz;
+            double te = Tk->t0[i] + fl * inv_bc;
+            O->xe[bidx] = xe; O->ye[bidx] = ye; O->he[bidx] = he; O->te[bidx] = te;
+            O->px[bidx] = px; O->py[bidx] = py; O->pz[bidx] = pz;
+            O->lam[bidx] = lam; O->w[bidx] = Y.w;
+            double r[6];
+            int st = orc_propagate_photon(C, variant, xe, ye, he, te, px, py, pz, r);
+            O->status[bidx] = st;
+            O->nhit[bidx] = 0;
+            if (st != ORC_ST_GROUND) {
+                O->X[bidx] = O->Y[bidx] = O->t[bidx] = 0.0;
+                O->cx[bidx] = O->cy[bidx] = O->cz[bidx] = 0.0;
+                continue;
+            }
+            double t = r[2] - t_ref;
+            O->X[bidx] = r[0]; O->Y[bidx] = r[1]; O->t[bidx] = t;
+            O->cx[bidx] = r[3]; O->cy[bidx] = r[4]; O->cz[bidx] = r[5];
+            O->nhit[bidx] = orc_telescopes(C, r[0], r[1], t, r[3], r[4], r[5], np1_obs,
+                                           O->hit_tel + ORC_MAX_HITS * bidx,
+                                           O->hit_x + ORC_MAX_HITS * bidx,
+                                           O->hit_y + ORC_MAX_HITS * bidx,
+                                           O->hit_t + ORC_MAX_HITS * bidx);
+        }
+    }
+    return 0;
+}
+
+int orc_max_hits(void) { return ORC_MAX_HITS; }
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
