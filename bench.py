@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Throughput of the Cherenkov bunch hot path: bunches generated and
+propagated per second.
+
+Workload (default): one 1 TeV vertical gamma-like shower, 2e6 e+- steps,
+19 telescope spheres, refraction tables 1000 x 64 up to 70 deg (seeded,
+synthetic: see workloads/).  A step of the benchmark is one call of
+cher_generate_propagate over all 2e6 steps: every bunch generated, refracted,
+propagated, tested against the spheres and the crossings compacted.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank simulates its own shower (independent
+showers: weak scaling, no collective on the data path); the value is the
+bunches of all ranks over the slowest rank's time.  `--impl reference`
+times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Cherenkov bunches generated+propagated/s (FP32 vs FP64 path), % of roofline"
+UNIT = "bunches/s"
+WORKLOAD = "vertical_1tev"
+
+# ---------------------------------------------------------------------------
+# Algorithmic operation counts (derivation in DESIGN.md, "Roofline").
+# Per bunch, FP32/INT32 lane operations of the single-precision path, by
+# stage; per emitting step, the FP64 operations of the yield.
+# ---------------------------------------------------------------------------
+OPS_PER_BUNCH_FP32 = {
+    "philox4x32_10": 98,        # 10 x (2 mul.lo + 2 mul.hi + 4 xor) + 9 x 2 key adds
+    "deviates": 9,              # 3 x (shift, convert, fma)
+    "emission": 33,             # sub-step fraction, sincospi(2u), cone rotation, lambda
+    "drops_and_snell": 26,      # height, checks, n(h) lookup, ratio, sin^2, sqrt
+    "tables": 22,               # two indices, two fractions, 2 x 3 lerps
+    "ground_point_time": 24,    # sec, tan, offsets, X, Y, t, direction cosines
+    "grid_and_spheres": 24,     # cell index + bounds, one sphere test (cross product)
+    "bunch_slot": 20,           # binary search over 256 tile offsets
+}
+OPS_PER_BUNCH = sum(OPS_PER_BUNCH_FP32.values())
+FP64_OPS_PER_STEP = 34          # yield chain: 24 mul/add + 1 division (~10 ops)
+FP32_LANES_PER_SM = 128
+FP64_FMA_PER_SM_CLK = 2         # GB300: about 1/64 of the FP32 rate (1.25 TFLOP/s)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the
+    timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t_load=None):
+        rows = []
+        try:
+            for ln in open(self.path):
+                f = [x.strip() for x in ln.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on a bounded sample of the same workload."""
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    import oracle
+    import workloads
+    oracle.build()
+    sample_steps = 20_000
+    sc = workloads.vertical_1tev(n=sample_steps)
+    M = oracle.Model(sc["atm"], sc["h_obs"], sc["telescopes"], t_ref=sc["t_ref"])
+    tr = sc["tracks"]
+    for _ in range(args.warmup):
+        M.bunches(tr, 7)
+    t0 = time.perf_counter()
+    nb = 0
+    for _ in range(args.steps):
+        o = M.bunches(tr, 7)
+        nb += len(o["status"])
+    dt = time.perf_counter() - t0
+    v = nb / dt
+    cores = oracle.num_threads()
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{WORKLOAD} sample: first {sample_steps} of 2e6 steps",
+                       "precision": "fp64 oracle (table variant)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{sample_steps} steps ({nb // args.steps} bunches) "
+                                       f"of the 1 TeV vertical shower per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2006_14927_gb300 as P
+    import workloads
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    P.build()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- workload (each rank its own shower: weak scaling) ----------------
+    sc = workloads.vertical_1tev(seed=2 + rank)
+    n = len(sc["tracks"]["x0"])
+    track_base = rank * n
+    t0 = time.perf_counter()
+    ctx = P.Context(sc["atm"], sc["h_obs"], sc["telescopes"])
+    ctx.build_refraction_tables(sc["H"], sc["Z"], sc["theta_max_deg"], sc["h_max"])
+    table_s = time.perf_counter() - t0
+    cap = 600_000
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def measure(prec, steps, warmup, autotune):
+        dtr = P.device_tracks(sc["tracks"], prec, device=dev, t_ref=sc["t_ref"])
+        out = ctx.alloc_hits(cap, prec, device=dev)
+        if autotune:
+            ctx.autotune(dtr, 11, prec, out)
+        for _ in range(warmup):
+            ctx.generate_propagate(dtr, 11, prec, out, track_base=track_base)
+        code, stats = ctx.sync_status(out)
+        if code != 0:
+            raise RuntimeError(f"status {code} in warm-up")
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        barrier()
+        w0 = time.perf_counter()
+        for k in range(steps):
+            flush.fill_(k & 0xff)                   # evict L2 between timed steps
+            ev[k][0].record(stream)
+            ctx.generate_propagate(dtr, 11, prec, out, track_base=track_base)
+            ev[k][1].record(stream)
+        barrier()
+        wall = time.perf_counter() - w0
+        ms = [a.elapsed_time(b) for a, b in ev]
+        code, stats = ctx.sync_status(out)
+        return dict(ms=ms, wall=wall, stats=stats, dtr=dtr, out=out, code=code)
+
+    steps, warmup = args.steps, args.warmup
+    with ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+                      if os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0].isdigit()
+                      else 0) as clk:
+        r32 = measure(P.CHER_FP32_BULK, steps, warmup, autotune=True)
+    clocks = clk.summary()
+    launch = ctx.get_launch()
+    r64 = measure(P.CHER_FP64, max(3, steps // 4), max(3, min(warmup, 3)), autotune=False)
+
+    def total(r):
+        t = sum(r["ms"]) / 1e3
+        b = float(r["stats"][3]) * len(r["ms"])
+        if world > 1:
+            tt = torch.tensor([t, b], dtype=torch.float64, device=dev)
+            tmax = tt[:1].clone()
+            torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+            torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
+            return float(tmax.item()), float(tt[1].item())
+        return t, b
+
+    t32, b32 = total(r32)
+    t64, b64 = total(r64)
+    v32, v64 = b32 / t32, b64 / t64
+
+    # ---- end to end: host buffers through the C ABI ---------------------
+    prec = P.CHER_FP32_BULK
+    host = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory()
+            for k, v in sc["tracks"].items() if k != "shower"}
+    host["ux"], host["uy"], host["uz"] = (host[k].to(torch.float32).pin_memory()
+                                          for k in ("ux", "uy", "uz"))
+    dtr = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    dtr["t_ref"] = torch.as_tensor(sc["t_ref"], dtype=torch.float64, device=dev)
+    out = r32["out"]
+    n_tel = ctx.n_tel
+    h_cnt = torch.empty(n_tel, dtype=torch.int64).pin_memory()
+    h_st = torch.empty(P.NSTATS, dtype=torch.int64).pin_memory()
+    h_pos = torch.empty((n_tel, cap, 4), dtype=torch.float32).pin_memory()
+    h_tim = torch.empty((n_tel, cap, 4), dtype=torch.float32).pin_memory()
+    h_key = torch.empty((n_tel, cap), dtype=torch.int64).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+
+    def e2e_step():
+        for k, v in host.items():
+            dtr[k].copy_(v, non_blocking=True)
+        ctx.generate_propagate(dtr, 11, prec, out, track_base=track_base)
+        h_cnt.copy_(out.count, non_blocking=True)
+        h_st.copy_(out.stats, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        d2h = h_cnt.numel() * 8 + h_st.numel() * 8
+        for k_ in range(n_tel):
+            c = min(int(h_cnt[k_]), cap)
+            if c:
+                h_pos[k_, :c].copy_(out.pos[k_, :c], non_blocking=True)
+                h_tim[k_, :c].copy_(out.tim[k_, :c], non_blocking=True)
+                h_key[k_, :c].copy_(out.key[k_, :c], non_blocking=True)
+                d2h += c * 40
+        torch.cuda.current_stream().synchronize()
+        return d2h
+
+    for _ in range(max(1, warmup // 2)):
+        e2e_step()
+    barrier()
+    e0 = time.perf_counter()
+    d2h = 0
+    for _ in range(steps):
+        d2h = e2e_step()
+    barrier()
+    te = time.perf_counter() - e0
+    if world > 1:
+        tt = torch.tensor([te], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        te = float(tt.item())
+    e2e_value = b32 / len(r32["ms"]) * steps / te
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (ALU bound) ----------------------
+    peaks, src = _peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = sm_count * FP32_LANES_PER_SM * mhz * 1e6          # lane ops/s
+    fp64_peak = sm_count * FP64_FMA_PER_SM_CLK * mhz * 1e6
+    st = r32["stats"]
+    bunches = float(st[3])
+    emitting = float(st[1])
+    per_launch_s = statistics.mean(r32["ms"]) / 1e3
+    ops = bunches * OPS_PER_BUNCH
+    achieved = ops / per_launch_s
+    t_alu = ops / alu_peak
+    t_fp64 = emitting * FP64_OPS_PER_STEP / fp64_peak
+    cpu = cpu_baseline() if world == 1 else None
+    line = {
+        "metric": METRIC, "value": v32, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": 1e3 * t32 / len(r32["ms"]),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "vertical_1tev: 1 TeV vertical gamma-like shower, 2e6 e+- "
+                               "steps per GPU, 19 spheres (R 6-12 m, hex 120 m), tables "
+                               "1000 x 64 to 70 deg, h_obs 2.2 km",
+                   "precision": "fp32_bulk (FP64 yield)", "bunches_per_step": int(bunches),
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "launch": {"block": launch[0], "ctas_per_sm": launch[1],
+                              "persistent": launch[1] > 0},
+                   "table_build_s": table_s},
+        "fp64": {"value": v64, "unit": UNIT, "ms_per_step": 1e3 * t64 / len(r64["ms"]),
+                 "steps": len(r64["ms"])},
+        "fp32_over_fp64": v32 / v64,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
+                     "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None,
+                     "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32/INT32 lanes x "
+                                    f"{mhz:.0f} MHz ({src} max clock)",
+                     "ops_per_bunch": OPS_PER_BUNCH,
+                     "roofline_ms": 1e3 * max(t_alu, t_fp64),
+                     "fp64_yield_ms_at_peak": 1e3 * t_fp64,
+                     "launch_ms": 1e3 * per_launch_s},
+        "gpu_launches": len(r32["ms"]),
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline():
+    """The oracle as it stands on this host's cores, bounded sample."""
+    import oracle
+    import workloads
+    oracle.build()
+    n = 20_000
+    sc = workloads.vertical_1tev(n=n)
+    M = oracle.Model(sc["atm"], sc["h_obs"], sc["telescopes"], t_ref=sc["t_ref"])
+    M.bunches(sc["tracks"], 7)
+    t0 = time.perf_counter()
+    reps, nb = 0, 0
+    while time.perf_counter() - t0 < 10.0 or reps < 2:
+        o = M.bunches(sc["tracks"], 7)
+        nb += len(o["status"])
+        reps += 1
+    dt = time.perf_counter() - t0
+    return {"value": nb / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {n} of the 2e6 steps ({nb // reps} bunches), repeated "
+                      f"{reps} times, FP64 table variant, OpenMP over steps"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

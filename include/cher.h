@@ -1,0 +1,277 @@
+/*
+ * cher.h -- C ABI of the GB300 (sm_103a) Cherenkov bunch library.
+ *
+ * The library runs the data-parallel hot path of air-shower Cherenkov light
+ * simulation that Arrabito et al. profile and optimise for CORSIKA/iact
+ * ("Optimizing Cherenkov photons generation and propagation in CORSIKA for
+ * CTA Monte-Carlo simulations"):
+ *
+ *   a0  atmosphere tables, built once: the index of refraction on a uniform
+ *       fine grid (the paper's "fast interpolation", section 3.3.2) and
+ *       refraction-correction tables over height and zenith angle (the
+ *       "coefficients for air refraction correction" of section 3.3.1);
+ *   a1  per track step: Cherenkov angle and Frank-Tamm photon yield, split
+ *       into bunches of about five photons, one per sub-step (CERENK,
+ *       section 3.2 and Appendix A);
+ *   a2  per bunch: emission point, azimuth and wavelength from a
+ *       counter-based Philox4x32-10 stream keyed by (seed, track, bunch), so
+ *       that every run and every code version draws the same randoms
+ *       (section 5.2);
+ *   a3  per bunch: refraction and propagation to the observation level
+ *       (RAYBND, section 3.2 and the Appendix B listing), rare conditions
+ *       tested first (Algorithms 1-2);
+ *   a4  per bunch: fiducial telescope spheres (TELOUT, section 2 and
+ *       Appendix A), candidates found through a ground grid;
+ *   a5  compaction of the bunches that cross a sphere into per-telescope
+ *       record buffers.
+ * All steps a1-a5 run in the library's CUDA kernels; a0 runs on the host
+ * once per context.
+ *
+ * Conventions.  Lengths in m, heights above sea level with z pointing up,
+ * times in ns, kinetic energies in MeV, wavelengths in nm.  Every function
+ * returns a cher_status and never aborts, traps or prints.  Pointers marked
+ * "device" must be CUDA device memory (for example from PyTorch) and stay
+ * owned by the caller; the context owns only its tables, its telescope grid
+ * and a few bytes of scratch.  Functions taking a stream are asynchronous
+ * on that stream (NULL = legacy default stream) and do not synchronise.
+ * A context is not thread safe: calls on one context must be serialised by
+ * the caller; distinct contexts are independent.
+ */
+#ifndef CHER_H
+#define CHER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum cher_status {
+    CHER_OK = 0,
+    CHER_EINVAL = 1,     /* a NULL pointer, a bad size or a bad parameter   */
+    CHER_ENOMEM = 2,     /* host or device allocation failed                */
+    CHER_ECUDA = 3,      /* a CUDA runtime call failed                      */
+    CHER_ESTATE = 4,     /* refraction tables not built yet                 */
+    CHER_ERANGE = 5,     /* a size exceeds what the library supports        */
+    CHER_EOVERFLOW = 6,  /* a telescope buffer ran out of capacity          */
+    CHER_ETIMEOUT = 7    /* a bounded device-side wait gave up              */
+} cher_status;
+
+/* Text for a status code (static storage, never NULL). */
+const char *cher_status_string(cher_status s);
+
+typedef enum cher_precision {
+    CHER_FP64 = 0,       /* everything in double precision                  */
+    CHER_FP32_BULK = 1   /* per-bunch arithmetic in single precision; the
+                            photon yield (hence the bunch count) and the
+                            per-step reference times stay in double         */
+} cher_precision;
+
+/* Layered atmosphere: thickness T(h) = a[i] + b[i] exp(-h / c[i]) (g/cm^2,
+ * c in m) in layer i, h in [h_bound[i], h_bound[i+1]); the lowest layer
+ * extends below h_bound[0] and there is no air above h_bound[5].  The
+ * density is rho = -dT/dh and n(h) - 1 = n0_minus_1 rho(h) / rho(0)
+ * (section 3.3.1: density, thickness and refractive index versus altitude).
+ * Requires c[i] > 0, b[i] >= 0, increasing h_bound, 0 <= n0_minus_1 < 0.01. */
+typedef struct cher_atmosphere {
+    double h_bound[6];
+    double a[5], b[5], c[5];
+    double n0_minus_1;
+} cher_atmosphere;
+
+/* A fiducial sphere: centre (x, y, h_obs + z), radius r > 0 (section 2). */
+typedef struct cher_telescope {
+    double x, y, z, r;
+} cher_telescope;
+
+/* Options fixed at creation.  Zero fields take the defaults in brackets. */
+typedef struct cher_options {
+    double bunch_size;       /* photons per bunch at most [5] (Appendix A)   */
+    double lambda_min_nm;    /* wavelength band [300, 600] nm               */
+    double lambda_max_nm;
+    int32_t n_fine;          /* points of the fine n(h) table [10000]
+                                (section 3.3.2), 2..1048576                 */
+} cher_options;
+
+typedef struct cher_ctx cher_ctx;
+
+/* Create a context on the current CUDA device.
+ *   atm       atmosphere (host, copied)
+ *   h_obs     observation level, m a.s.l., inside the atmosphere
+ *   tel       n_tel telescopes (host, copied); 1 <= n_tel <= 4096
+ *   opt       options (host, copied) or NULL for the defaults
+ *   out       receives the new context
+ * Errors: CHER_EINVAL for bad arguments, CHER_ENOMEM. */
+cher_status cher_create(const cher_atmosphere *atm, double h_obs,
+                        const cher_telescope *tel, int32_t n_tel,
+                        const cher_options *opt, cher_ctx **out);
+
+/* Build (or rebuild) all atmosphere tables on the host in double precision
+ * and upload them (one blocking copy per table):
+ *   - eta = n - 1 at n_fine uniform heights on [0, h_max];
+ *   - refraction tables over n_heights uniform heights on [h_obs, h_max]
+ *     and n_zenith observation-level zenith angles whose squared sines are
+ *     uniform on [0, sin^2(zenith_max_deg)], holding the horizontal offset
+ *     and optical path of the refracted ray minus those of the straight line
+ *     at the same observation zenith, each divided by its leading angular
+ *     factor (sin/cos^3 and 1/cos^3); a photon arriving steeper than
+ *     zenith_max_deg, or emitted above h_max, is counted and dropped;
+ *   - the ground grid of telescope candidates.
+ * Requires 2 <= n_heights <= 65536, 2 <= n_zenith <= 4096,
+ * 0 < zenith_max_deg < 85, h_obs < h_max <= h_bound[5].
+ * Errors: CHER_EINVAL, CHER_ERANGE (table too large), CHER_ENOMEM,
+ * CHER_ECUDA. */
+cher_status cher_build_refraction_tables(cher_ctx *ctx, int32_t n_heights,
+                                         int32_t n_zenith,
+                                         double zenith_max_deg, double h_max);
+
+/* Release everything the context owns (NULL is accepted). */
+cher_status cher_destroy(cher_ctx *ctx);
+
+/* Track steps, structure of arrays, all device pointers with n elements.
+ * Step i starts at (x0, y0, z0) at time t0, runs len along the unit
+ * direction (ux, uy, uz), for an e+- of kinetic energy ekin.  The direction
+ * arrays are float for CHER_FP32_BULK and double for CHER_FP64.
+ * shower (optional, NULL = all 0) indexes t_ref (optional, NULL = 0): the
+ * arrival times are reported relative to t_ref[shower[i]].
+ * track_base is the global index of step 0: the Philox counter of bunch j
+ * of step i is (track_base + i, j), so any split of a track list into calls
+ * reproduces the same bunches. */
+typedef struct cher_tracks {
+    const double *x0, *y0, *z0, *t0, *len, *ekin;
+    const void *ux, *uy, *uz;
+    const uint32_t *shower;
+    const double *t_ref;
+    int32_t n_showers;
+    int64_t n;
+    int64_t track_base;
+} cher_tracks;
+
+/* Number of counters in cher_output.stats and their meaning. */
+#define CHER_NSTATS 16
+enum {
+    CHER_STAT_STEPS = 0,        /* steps processed                          */
+    CHER_STAT_EMITTING = 1,     /* steps above the Cherenkov threshold      */
+    CHER_STAT_INVALID = 2,      /* steps with a non-finite or negative field */
+    CHER_STAT_BUNCHES = 3,      /* bunches generated (sum of nb)            */
+    CHER_STAT_UPWARD = 4,       /* dropped: not travelling downward         */
+    CHER_STAT_BELOW_OBS = 5,    /* dropped: emitted below h_obs             */
+    CHER_STAT_ABOVE_MAX = 6,    /* dropped: emitted above h_max             */
+    CHER_STAT_ANGLE = 7,        /* dropped: zenith beyond the tables        */
+    CHER_STAT_GROUND = 8,       /* reached the observation level            */
+    CHER_STAT_HITS = 9,         /* (bunch, telescope) crossings found       */
+    CHER_STAT_OVERFLOW = 10     /* crossings not stored (buffer full)       */
+};
+
+/* Per-telescope output buffers (device).  Telescope k owns records
+ * [k * cap_per_tel, (k + 1) * cap_per_tel).  Record r holds
+ *   pos[4 r + 0..3] = x, y, cx, cy
+ *   tim[4 r + 0..3] = t, z_emit, photons, lambda_nm
+ *   key[r]          = (track_base + i) << 32 | j
+ * where (x, y) is where the arrival line crosses the horizontal plane
+ * through the sphere centre, relative to the centre; (cx, cy) are the
+ * direction cosines at the observation level; t is the arrival time at
+ * that plane minus t_ref; z_emit the emission height.  pos and tim are
+ * float for CHER_FP32_BULK and double for CHER_FP64, 16-byte (32-byte for
+ * double) aligned.  The order of records inside a telescope is not
+ * deterministic: sort by key.  count[k] receives the number of crossings
+ * found for telescope k, which may exceed cap_per_tel (then only
+ * cap_per_tel are stored and the rest counted in stats[OVERFLOW]).
+ * count and stats are cleared by every call. */
+typedef struct cher_output {
+    void *pos;
+    void *tim;
+    uint64_t *key;
+    int64_t cap_per_tel;
+    unsigned long long *count;   /* [n_tel]       */
+    unsigned long long *stats;   /* [CHER_NSTATS] */
+} cher_output;
+
+/* The whole hot path (a1-a5) for n steps in one launch: a persistent,
+ * tile-scheduled kernel whose CTAs pull tiles of steps from an atomic queue
+ * in the context's scratch word.  Asynchronous on `stream`; the return value
+ * reports argument checks and the launch only.  Errors: CHER_EINVAL,
+ * CHER_ESTATE, CHER_ERANGE (n > 2^40), CHER_ECUDA. */
+cher_status cher_generate_propagate(cher_ctx *ctx, const cher_tracks *tracks,
+                                    uint64_t seed, cher_precision prec,
+                                    const cher_output *out, void *stream);
+
+/* Synchronise `stream`, read out->stats and report CHER_EOVERFLOW if a
+ * telescope buffer overflowed during the last call, else CHER_OK (or
+ * CHER_ECUDA if the stream reports an error).  stats_host (optional,
+ * CHER_NSTATS entries) receives the counters. */
+cher_status cher_sync_status(cher_ctx *ctx, const cher_output *out,
+                             unsigned long long *stats_host, void *stream);
+
+/* Launch shape of cher_generate_propagate.  block_threads in {128, 256,
+ * 512} is also the number of steps per tile; ctas_per_sm in 1..8 sets the
+ * persistent grid (0 = one CTA per tile, no persistence).  The defaults
+ * come from cher_autotune or are 256 / 3.  Errors: CHER_EINVAL. */
+cher_status cher_set_launch(cher_ctx *ctx, int32_t block_threads,
+                            int32_t ctas_per_sm);
+cher_status cher_get_launch(const cher_ctx *ctx, int32_t *block_threads,
+                            int32_t *ctas_per_sm);
+
+/* ---- inspection entry points (same device code, for validation) ------- */
+
+/* a1 only: per-step bunch count nb[i] (int32) and photons per bunch w[i]
+ * (double), device outputs of n elements.  Errors as above. */
+cher_status cher_segment_yield(cher_ctx *ctx, const cher_tracks *tracks,
+                               cher_precision prec, int32_t *nb, double *w,
+                               void *stream);
+
+/* a2-a4 for every bunch, not only the crossing ones.  bunch_off (device,
+ * n + 1 entries) is the exclusive prefix sum of nb from
+ * cher_segment_yield; bunch b = bunch_off[i] + j is written at index b of
+ *   pos[4 b ..] = X, Y, cx, cy   (ground point at h_obs, direction)
+ *   tim[4 b ..] = t, z_emit, photons, lambda_nm
+ *   status[b]   = 0 ground, 1 upward, 2 below h_obs, 3 above h_max,
+ *                 4 beyond the zenith range
+ *   nhit[b], first_hit[b] = number of spheres crossed, lowest index or -1.
+ * pos/tim are float (CHER_FP32_BULK) or double (CHER_FP64). */
+typedef struct cher_trace {
+    void *pos;
+    void *tim;
+    int32_t *status;
+    int32_t *nhit;
+    int32_t *first_hit;
+    int64_t n_bunches;
+} cher_trace;
+
+cher_status cher_trace_bunches(cher_ctx *ctx, const cher_tracks *tracks,
+                               uint64_t seed, cher_precision prec,
+                               const int64_t *bunch_off, const cher_trace *out,
+                               void *stream);
+
+/* Copy the double-precision tables of the context to host arrays:
+ * eta[n_fine], ax[n_heights * n_zenith], al[n_heights * n_zenith]
+ * (row-major, height first); any pointer may be NULL.  Errors:
+ * CHER_ESTATE before cher_build_refraction_tables. */
+cher_status cher_get_tables(const cher_ctx *ctx, double *eta, double *ax,
+                            double *al);
+
+/* The host table builder on its own (no CUDA call): fills eta[n_fine],
+ * ax[n_heights * n_zenith], al[n_heights * n_zenith] exactly as
+ * cher_build_refraction_tables does.  Errors: CHER_EINVAL. */
+cher_status cher_build_tables_host(const cher_atmosphere *atm, double h_obs,
+                                   int32_t n_fine, int32_t n_heights,
+                                   int32_t n_zenith, double zenith_max_deg,
+                                   double h_max, double *eta, double *ax,
+                                   double *al);
+
+/* Measure a few launch shapes of cher_generate_propagate on the given
+ * input (which must already be resident) and keep the fastest; if
+ * cache_path is not NULL the choice is read from / appended to that file
+ * (one line per device name, precision and tile count).  Writes into `out`
+ * while measuring.  Errors as cher_generate_propagate, plus CHER_EINVAL if
+ * the cache file is unreadable garbage. */
+cher_status cher_autotune(cher_ctx *ctx, const cher_tracks *tracks,
+                          uint64_t seed, cher_precision prec,
+                          const cher_output *out, const char *cache_path,
+                          void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHER_H */

@@ -98,8 +98,8 @@ def lib():
                                           ctypes.c_int, _dp]
         L.orc_eta_lookup.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
         L.orc_eta_lookup.restype = ctypes.c_double
-        L.orc_segment_yield.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int64, _dp, _dp,
-                                        _dp, _dp, _i32p, _dp, _dp, _i32p]
+        L.orc_segment_yield.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Tracks), _i32p,
+                                        _dp, _dp, _i32p]
         L.orc_brute_ray.argtypes = [ctypes.POINTER(_Atm), ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double, _dp, _dp]
         L.orc_build_refraction_tables.argtypes = [ctypes.POINTER(_Atm), ctypes.c_double,
@@ -242,10 +242,13 @@ class Model:
         self.telescopes = _f64(np.asarray(self.telescopes).reshape(-1, 4))
         self.eta_tab = eta_table(self.atm, self.h_max, self.n_fine)
         self.ax, self.al = refraction_tables(self.atm, self.h_obs, self.h_max, self.H,
-                                             self.Z, np.radians(self.theta_max_deg),
-                                             self.table_tol)
+                                             self.Z, self.theta_max_rad, self.table_tol)
         if self.t_ref is not None:
             self.t_ref = _f64(np.atleast_1d(self.t_ref))
+
+    @property
+    def theta_max_rad(self) -> float:
+        return float(self.theta_max_deg) * 3.14159265358979323846 / 180.0
 
     def _cfg(self) -> _Cfg:
         C = _Cfg()
@@ -255,7 +258,7 @@ class Model:
         C.n_fine = self.n_fine
         C.eta_tab = _ptr(self.eta_tab)
         C.H, C.Z = self.H, self.Z
-        C.theta_max = float(np.radians(self.theta_max_deg))
+        C.theta_max = self.theta_max_rad
         C.ax, C.al = _ptr(self.ax), _ptr(self.al)
         C.bunch_size = self.bunch_size
         C.lambda1_nm, C.lambda2_nm = self.lambda1_nm, self.lambda2_nm
@@ -272,17 +275,38 @@ class Model:
 
     # ---- a1: per-step yield ------------------------------------------------
     def segment_yield(self, tracks: dict):
-        n = len(tracks["z0"])
-        z0, ln, ek, uz = (_f64(tracks[k]) for k in ("z0", "len", "ekin", "uz"))
+        T, keep = self._tracks(tracks)
+        n = T.n
         nb = np.zeros(n, np.int32)
         w = np.zeros(n)
         s2 = np.zeros(n)
         valid = np.zeros(n, np.int32)
         C = self._cfg()
-        lib().orc_segment_yield(ctypes.byref(C), n, _ptr(z0), _ptr(ln), _ptr(ek), _ptr(uz),
-                                _ptr(nb, ctypes.c_int32), _ptr(w), _ptr(s2),
-                                _ptr(valid, ctypes.c_int32))
+        lib().orc_segment_yield(ctypes.byref(C), ctypes.byref(T), _ptr(nb, ctypes.c_int32),
+                                _ptr(w), _ptr(s2), _ptr(valid, ctypes.c_int32))
+        del keep
         return nb, w, s2, valid.astype(bool)
+
+    def _tracks(self, tracks: dict, track_base: int = 0):
+        """ctypes view of a track dict; the second value keeps the arrays alive."""
+        n = len(tracks["z0"])
+        arr = {}
+        for k in ("x0", "y0", "z0", "t0", "len", "ekin", "ux", "uy", "uz"):
+            v = tracks.get(k)
+            arr[k] = _f64(v) if v is not None else np.zeros(n)
+        T = _Tracks()
+        for k, v in arr.items():
+            setattr(T, k, _ptr(v))
+        shower = tracks.get("shower")
+        if shower is not None:
+            shower = np.ascontiguousarray(shower, dtype=np.uint32)
+            arr["shower"] = shower
+            T.shower = _ptr(shower, ctypes.c_uint32)
+        else:
+            T.shower = None
+        T.n = n
+        T.track_base = int(track_base)
+        return T, arr
 
     # ---- a2..a5: every bunch ----------------------------------------------
     def bunches(self, tracks: dict, seed: int, variant: int = 0, track_base: int = 0):
@@ -290,19 +314,7 @@ class Model:
         off = np.zeros(len(nb) + 1, np.int64)
         np.cumsum(nb, out=off[1:])
         nbt = int(off[-1])
-        arr = {k: _f64(tracks[k]) for k in
-               ("x0", "y0", "z0", "t0", "len", "ekin", "ux", "uy", "uz")}
-        T = _Tracks()
-        for k, v in arr.items():
-            setattr(T, k, _ptr(v))
-        shower = tracks.get("shower")
-        if shower is not None:
-            shower = np.ascontiguousarray(shower, dtype=np.uint32)
-            T.shower = _ptr(shower, ctypes.c_uint32)
-        else:
-            T.shower = None
-        T.n = len(nb)
-        T.track_base = int(track_base)
+        T, keep = self._tracks(tracks, track_base)
         out = {k: np.zeros(nbt) for k in ("xe", "ye", "he", "te", "px", "py", "pz", "X", "Y",
                                           "t", "cx", "cy", "cz", "lam", "w")}
         out["status"] = np.zeros(nbt, np.int32)

@@ -264,14 +264,10 @@ static double orc_band_factor(const orc_cfg *C)
 
 static int orc_finite(double v) { return v == v && v - v == 0.0; }
 
-/* returns 0 for a valid step, -1 for an invalid one (nb = 0 then) */
-static int orc_step_yield(const orc_cfg *C, double z0, double len, double ekin,
-                          double uz, orc_yield *Y)
+/* the yield of a step whose fields are all valid */
+static int orc_step_yield_valid(const orc_cfg *C, double z0, double len, double ekin,
+                                double uz, orc_yield *Y)
 {
-    Y->nb = 0; Y->w = 0.0; Y->N = 0.0; Y->s2 = 0.0; Y->beta = 0.0; Y->eta = 0.0;
-    if (!orc_finite(z0) || !orc_finite(len) || !orc_finite(ekin) || !orc_finite(uz)
-        || len < 0.0 || ekin <= 0.0)
-        return -1;
     double inv_me = 1.0 / ORC_ME_MEV;
     double K = orc_band_factor(C);
     double inv_B = 1.0 / C->bunch_size;
@@ -288,10 +284,10 @@ static int orc_step_yield(const orc_cfg *C, double z0, double len, double ekin,
     double two_eta = 2.0 + eta;
     double a = eta * two_eta;
     double b = a * gam2;
-    double num = b - np1sq;                 /* (beta n)^2 gamma^2 - gamma^2 ... */
+    double num = b - np1sq;                 /* gamma^2 ((beta n)^2 - 1)   */
     double two_g = 2.0 + g;
     double bg2 = g * two_g;                 /* beta^2 gamma^2              */
-    double den = bg2 * np1sq;
+    double den = bg2 * np1sq;               /* gamma^2 (beta n)^2         */
     double s2 = num / den;
     Y->eta = eta;
     Y->beta = sqrt(bg2) / gam;
@@ -308,15 +304,32 @@ static int orc_step_yield(const orc_cfg *C, double z0, double len, double ekin,
     return 0;
 }
 
-/* Per-step yield for n steps: nb (bunches), w (photons per bunch),
- * s2 (sin^2 of the Cherenkov angle) and a validity flag (1 valid). */
-void orc_segment_yield(const orc_cfg *C, int64_t n, const double *z0,
-                       const double *len, const double *ekin, const double *uz,
-                       int32_t *nb, double *w, double *s2, int32_t *valid)
+/* A step is valid when every field is finite, its length is not negative
+ * and its kinetic energy is positive; an invalid step emits nothing. */
+static int orc_step_valid(const orc_tracks *T, int64_t i)
 {
-    for (int64_t i = 0; i < n; ++i) {
+    return orc_finite(T->x0[i]) && orc_finite(T->y0[i]) && orc_finite(T->z0[i])
+        && orc_finite(T->t0[i]) && orc_finite(T->len[i]) && orc_finite(T->ekin[i])
+        && orc_finite(T->ux[i]) && orc_finite(T->uy[i]) && orc_finite(T->uz[i])
+        && T->len[i] >= 0.0 && T->ekin[i] > 0.0;
+}
+
+/* returns 0 for a valid step, -1 for an invalid one (nb = 0 then) */
+static int orc_step_yield(const orc_cfg *C, const orc_tracks *T, int64_t i, orc_yield *Y)
+{
+    Y->nb = 0; Y->w = 0.0; Y->N = 0.0; Y->s2 = 0.0; Y->beta = 0.0; Y->eta = 0.0;
+    if (!orc_step_valid(T, i)) return -1;
+    return orc_step_yield_valid(C, T->z0[i], T->len[i], T->ekin[i], T->uz[i], Y);
+}
+
+/* Per-step yield for every step: nb (bunches), w (photons per bunch),
+ * s2 (sin^2 of the Cherenkov angle) and a validity flag (1 valid). */
+void orc_segment_yield(const orc_cfg *C, const orc_tracks *T, int32_t *nb, double *w,
+                       double *s2, int32_t *valid)
+{
+    for (int64_t i = 0; i < T->n; ++i) {
         orc_yield Y;
-        int ok = orc_step_yield(C, z0[i], len[i], ekin[i], uz[i], &Y);
+        int ok = orc_step_yield(C, T, i, &Y);
         nb[i] = (int32_t)Y.nb;
         if (w) w[i] = Y.w;
         if (s2) s2[i] = Y.s2;
@@ -595,7 +608,7 @@ int orc_bunches(const orc_cfg *C, const orc_tracks *Tk, uint64_t seed,
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < Tk->n; ++i) {
         orc_yield Y;
-        if (orc_step_yield(C, Tk->z0[i], Tk->len[i], Tk->ekin[i], Tk->uz[i], &Y) != 0)
+        if (orc_step_yield(C, Tk, i, &Y) != 0)
             continue;
         if (Y.nb == 0) continue;
         double ux = Tk->ux[i], uy = Tk->uy[i], uz = Tk->uz[i];

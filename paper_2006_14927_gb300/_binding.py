@@ -1,0 +1,352 @@
+"""ctypes binding of libcher.so: argument marshalling only.
+
+Every step of the photon-bunch path runs in the library's CUDA kernels (or,
+for the one-off table build, in its C++ host code).  PyTorch supplies device
+memory and streams.  If the library has not been built, importing works but
+every call raises: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcher.so")
+
+CHER_FP64 = 0
+CHER_FP32_BULK = 1
+NSTATS = 16
+STAT_NAMES = ["steps", "emitting", "invalid", "bunches", "upward", "below_obs", "above_max",
+              "angle", "ground", "hits", "overflow"]
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
+                4: "tables not built", 5: "out of range", 6: "overflow", 7: "timeout"}
+
+
+class CherError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS_NAMES.get(code, code)} (status {code})")
+        self.code = code
+
+
+class Atmosphere(ctypes.Structure):
+    _fields_ = [("h_bound", ctypes.c_double * 6), ("a", ctypes.c_double * 5),
+                ("b", ctypes.c_double * 5), ("c", ctypes.c_double * 5),
+                ("n0_minus_1", ctypes.c_double)]
+
+
+class Telescope(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_double), ("y", ctypes.c_double), ("z", ctypes.c_double),
+                ("r", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("bunch_size", ctypes.c_double), ("lambda_min_nm", ctypes.c_double),
+                ("lambda_max_nm", ctypes.c_double), ("n_fine", ctypes.c_int32)]
+
+
+class Tracks(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_void_p), ("y0", ctypes.c_void_p), ("z0", ctypes.c_void_p),
+                ("t0", ctypes.c_void_p), ("len", ctypes.c_void_p), ("ekin", ctypes.c_void_p),
+                ("ux", ctypes.c_void_p), ("uy", ctypes.c_void_p), ("uz", ctypes.c_void_p),
+                ("shower", ctypes.c_void_p), ("t_ref", ctypes.c_void_p),
+                ("n_showers", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("track_base", ctypes.c_int64)]
+
+
+class Output(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_void_p), ("tim", ctypes.c_void_p), ("key", ctypes.c_void_p),
+                ("cap_per_tel", ctypes.c_int64), ("count", ctypes.c_void_p),
+                ("stats", ctypes.c_void_p)]
+
+
+class Trace(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_void_p), ("tim", ctypes.c_void_p), ("status", ctypes.c_void_p),
+                ("nhit", ctypes.c_void_p), ("first_hit", ctypes.c_void_p),
+                ("n_bunches", ctypes.c_int64)]
+
+
+_S = ctypes.c_int
+_P = ctypes.c_void_p
+_lib = None
+
+# name -> (restype, argtypes): every symbol of include/cher.h
+SIGNATURES = {
+    "cher_status_string": (ctypes.c_char_p, [_S]),
+    "cher_create": (_S, [ctypes.POINTER(Atmosphere), ctypes.c_double, ctypes.POINTER(Telescope),
+                         ctypes.c_int32, ctypes.POINTER(Options), ctypes.POINTER(_P)]),
+    "cher_build_refraction_tables": (_S, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                          ctypes.c_double]),
+    "cher_destroy": (_S, [_P]),
+    "cher_generate_propagate": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
+                                     ctypes.POINTER(Output), _P]),
+    "cher_sync_status": (_S, [_P, ctypes.POINTER(Output), ctypes.POINTER(ctypes.c_ulonglong), _P]),
+    "cher_set_launch": (_S, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "cher_get_launch": (_S, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "cher_segment_yield": (_S, [_P, ctypes.POINTER(Tracks), _S, _P, _P, _P]),
+    "cher_trace_bunches": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S, _P,
+                                ctypes.POINTER(Trace), _P]),
+    "cher_get_tables": (_S, [_P, _P, _P, _P]),
+    "cher_build_tables_host": (_S, [ctypes.POINTER(Atmosphere), ctypes.c_double, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                    ctypes.c_double, _P, _P, _P]),
+    "cher_autotune": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
+                           ctypes.POINTER(Output), ctypes.c_char_p, _P]),
+}
+
+
+def lib():
+    """Load libcher.so; raise if it has not been built (no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_2006_14927_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise CherError(code, what)
+
+
+def atmosphere_struct(atm: dict) -> Atmosphere:
+    A = Atmosphere()
+    A.h_bound[:] = [float(v) for v in atm["h_bound"]]
+    A.a[:] = [float(v) for v in atm["a"]]
+    A.b[:] = [float(v) for v in atm["b"]]
+    A.c[:] = [float(v) for v in atm["c"]]
+    A.n0_minus_1 = float(atm["n0_minus_1"])
+    return A
+
+
+def build_tables_host(atm: dict, h_obs: float, n_fine: int, n_heights: int, n_zenith: int,
+                      zenith_max_deg: float, h_max: float):
+    """The library's host table builder on its own (no CUDA call)."""
+    eta = np.zeros(n_fine)
+    ax = np.zeros((n_heights, n_zenith))
+    al = np.zeros((n_heights, n_zenith))
+    A = atmosphere_struct(atm)
+    _check(lib().cher_build_tables_host(ctypes.byref(A), float(h_obs), int(n_fine),
+                                        int(n_heights), int(n_zenith), float(zenith_max_deg),
+                                        float(h_max), eta.ctypes.data, ax.ctypes.data,
+                                        al.ctypes.data), "cher_build_tables_host")
+    return eta, ax, al
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def device_tracks(tracks: dict, precision: int, device="cuda", t_ref=None, pin=False):
+    """Copy a track dict (numpy or torch) to device tensors of the ABI's dtypes."""
+    torch = _torch()
+    ddir = torch.float32 if precision == CHER_FP32_BULK else torch.float64
+    out = {}
+    for k in ("x0", "y0", "z0", "t0", "len", "ekin"):
+        out[k] = torch.as_tensor(tracks[k]).to(device=device, dtype=torch.float64).contiguous()
+    for k in ("ux", "uy", "uz"):
+        out[k] = torch.as_tensor(tracks[k]).to(device=device, dtype=ddir).contiguous()
+    if tracks.get("shower") is not None:
+        sh = np.asarray(tracks["shower"]).astype(np.uint32).view(np.int32) \
+            if not hasattr(tracks["shower"], "device") else tracks["shower"]
+        out["shower"] = torch.as_tensor(sh).to(device=device, dtype=torch.int32).contiguous()
+    if t_ref is not None:
+        out["t_ref"] = torch.as_tensor(np.atleast_1d(t_ref) if not hasattr(t_ref, "device")
+                                       else t_ref).to(device=device,
+                                                      dtype=torch.float64).contiguous()
+    return out
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return _torch().cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+@dataclass
+class HitBuffers:
+    """Per-telescope record buffers (device tensors) plus counters."""
+    pos: object      # (n_tel, cap, 4): x, y, cx, cy
+    tim: object      # (n_tel, cap, 4): t, z_emit, photons, lambda_nm
+    key: object      # (n_tel, cap) int64 holding the u64 key bits
+    count: object    # (n_tel,) int64 holding u64 counts
+    stats: object    # (16,) int64
+    cap: int
+    precision: int
+
+    def struct(self) -> Output:
+        o = Output()
+        o.pos = self.pos.data_ptr()
+        o.tim = self.tim.data_ptr()
+        o.key = self.key.data_ptr()
+        o.cap_per_tel = self.cap
+        o.count = self.count.data_ptr()
+        o.stats = self.stats.data_ptr()
+        return o
+
+    def records(self):
+        """Host numpy records of every telescope, sorted by (telescope, key)."""
+        cnt = np.minimum(self.count.cpu().numpy(), self.cap)
+        pos, tim, key = self.pos.cpu().numpy(), self.tim.cpu().numpy(), self.key.cpu().numpy()
+        tel = np.concatenate([np.full(c, k, np.int64) for k, c in enumerate(cnt)]) \
+            if len(cnt) else np.zeros(0, np.int64)
+        sel = (tel, np.concatenate([np.arange(c) for c in cnt]).astype(np.int64))
+        rec = dict(tel=tel, key=key[sel].view(np.uint64), x=pos[sel][:, 0], y=pos[sel][:, 1],
+                   cx=pos[sel][:, 2], cy=pos[sel][:, 3], t=tim[sel][:, 0], zem=tim[sel][:, 1],
+                   w=tim[sel][:, 2], lam=tim[sel][:, 3])
+        order = np.lexsort((rec["key"], rec["tel"]))
+        return {k: v[order] for k, v in rec.items()}
+
+
+class Context:
+    """A cher_ctx: atmosphere, observation level, telescopes and tables."""
+
+    def __init__(self, atm: dict, h_obs: float, telescopes, bunch_size=5.0,
+                 lambda_min_nm=300.0, lambda_max_nm=600.0, n_fine=10000):
+        tel = np.asarray(telescopes, dtype=np.float64).reshape(-1, 4)
+        self.n_tel = tel.shape[0]
+        T = (Telescope * self.n_tel)(*[Telescope(*map(float, r)) for r in tel])
+        O = Options(float(bunch_size), float(lambda_min_nm), float(lambda_max_nm), int(n_fine))
+        A = atmosphere_struct(atm)
+        h = ctypes.c_void_p()
+        _check(lib().cher_create(ctypes.byref(A), float(h_obs), T, self.n_tel, ctypes.byref(O),
+                                 ctypes.byref(h)), "cher_create")
+        self._h = h
+        self.h_obs = float(h_obs)
+        self.n_fine = int(n_fine)
+        self.H = self.Z = 0
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().cher_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_refraction_tables(self, n_heights=1000, n_zenith=64, zenith_max_deg=70.0,
+                                h_max=60000.0):
+        _check(lib().cher_build_refraction_tables(self._h, int(n_heights), int(n_zenith),
+                                                  float(zenith_max_deg), float(h_max)),
+               "cher_build_refraction_tables")
+        self.H, self.Z = int(n_heights), int(n_zenith)
+
+    def set_launch(self, block_threads=256, ctas_per_sm=3):
+        _check(lib().cher_set_launch(self._h, int(block_threads), int(ctas_per_sm)),
+               "cher_set_launch")
+
+    def get_launch(self):
+        b, c = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().cher_get_launch(self._h, ctypes.byref(b), ctypes.byref(c)),
+               "cher_get_launch")
+        return b.value, c.value
+
+    def get_tables(self):
+        eta = np.zeros(self.n_fine)
+        ax = np.zeros((self.H, self.Z))
+        al = np.zeros((self.H, self.Z))
+        _check(lib().cher_get_tables(self._h, eta.ctypes.data, ax.ctypes.data, al.ctypes.data),
+               "cher_get_tables")
+        return eta, ax, al
+
+    @staticmethod
+    def tracks_struct(dev: dict, track_base: int = 0) -> Tracks:
+        t = Tracks()
+        for k in ("x0", "y0", "z0", "t0", "len", "ekin", "ux", "uy", "uz"):
+            setattr(t, k, dev[k].data_ptr())
+        t.shower = dev["shower"].data_ptr() if "shower" in dev else None
+        if "t_ref" in dev:
+            t.t_ref = dev["t_ref"].data_ptr()
+            t.n_showers = int(dev["t_ref"].numel())
+        else:
+            t.t_ref = None
+            t.n_showers = 0
+        t.n = int(dev["x0"].numel())
+        t.track_base = int(track_base)
+        return t
+
+    def alloc_hits(self, cap_per_tel: int, precision: int, device="cuda") -> HitBuffers:
+        torch = _torch()
+        dt = torch.float32 if precision == CHER_FP32_BULK else torch.float64
+        n = self.n_tel
+        return HitBuffers(pos=torch.zeros((n, cap_per_tel, 4), dtype=dt, device=device),
+                          tim=torch.zeros((n, cap_per_tel, 4), dtype=dt, device=device),
+                          key=torch.zeros((n, cap_per_tel), dtype=torch.int64, device=device),
+                          count=torch.zeros(n, dtype=torch.int64, device=device),
+                          stats=torch.zeros(NSTATS, dtype=torch.int64, device=device),
+                          cap=int(cap_per_tel), precision=precision)
+
+    def generate_propagate(self, dev_tracks: dict, seed: int, precision: int,
+                           out: HitBuffers, stream=None, track_base: int = 0):
+        t = self.tracks_struct(dev_tracks, track_base)
+        o = out.struct()
+        _check(lib().cher_generate_propagate(self._h, ctypes.byref(t), ctypes.c_uint64(seed),
+                                             int(precision), ctypes.byref(o),
+                                             ctypes.c_void_p(_stream_ptr(stream))),
+               "cher_generate_propagate")
+
+    def sync_status(self, out: HitBuffers, stream=None):
+        st = (ctypes.c_ulonglong * NSTATS)()
+        o = out.struct()
+        code = lib().cher_sync_status(self._h, ctypes.byref(o), st,
+                                      ctypes.c_void_p(_stream_ptr(stream)))
+        if code not in (0, 6):
+            raise CherError(code, "cher_sync_status")
+        return code, np.array(st[:], dtype=np.uint64)
+
+    def segment_yield(self, dev_tracks: dict, precision: int, stream=None):
+        torch = _torch()
+        n = int(dev_tracks["x0"].numel())
+        dev = dev_tracks["x0"].device
+        nb = torch.zeros(n, dtype=torch.int32, device=dev)
+        w = torch.zeros(n, dtype=torch.float64, device=dev)
+        t = self.tracks_struct(dev_tracks)
+        _check(lib().cher_segment_yield(self._h, ctypes.byref(t), int(precision), nb.data_ptr(),
+                                        w.data_ptr(), ctypes.c_void_p(_stream_ptr(stream))),
+               "cher_segment_yield")
+        return nb, w
+
+    def trace_bunches(self, dev_tracks: dict, seed: int, precision: int, bunch_off,
+                      stream=None, track_base: int = 0):
+        torch = _torch()
+        nbt = int(bunch_off[-1].item())
+        dev = dev_tracks["x0"].device
+        dt = torch.float32 if precision == CHER_FP32_BULK else torch.float64
+        pos = torch.zeros((nbt, 4), dtype=dt, device=dev)
+        tim = torch.zeros((nbt, 4), dtype=dt, device=dev)
+        status = torch.full((nbt,), -1, dtype=torch.int32, device=dev)
+        nhit = torch.zeros(nbt, dtype=torch.int32, device=dev)
+        first = torch.zeros(nbt, dtype=torch.int32, device=dev)
+        tr = Trace(pos.data_ptr(), tim.data_ptr(), status.data_ptr(), nhit.data_ptr(),
+                   first.data_ptr(), nbt)
+        t = self.tracks_struct(dev_tracks, track_base)
+        _check(lib().cher_trace_bunches(self._h, ctypes.byref(t), ctypes.c_uint64(seed),
+                                        int(precision), bunch_off.data_ptr(), ctypes.byref(tr),
+                                        ctypes.c_void_p(_stream_ptr(stream))),
+               "cher_trace_bunches")
+        return dict(pos=pos, tim=tim, status=status, nhit=nhit, first_hit=first)
+
+    def autotune(self, dev_tracks: dict, seed: int, precision: int, out: HitBuffers,
+                 cache_path: str | None = None, stream=None):
+        t = self.tracks_struct(dev_tracks)
+        o = out.struct()
+        _check(lib().cher_autotune(self._h, ctypes.byref(t), ctypes.c_uint64(seed),
+                                   int(precision), ctypes.byref(o),
+                                   cache_path.encode() if cache_path else None,
+                                   ctypes.c_void_p(_stream_ptr(stream))), "cher_autotune")
+        return self.get_launch()

@@ -1,0 +1,503 @@
+// cher_api.cu -- the C ABI declared in include/cher.h: context lifetime,
+// argument checks, table upload, launch configuration and the autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "cher_internal.h"
+
+struct cher_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cher_atmosphere atm{};
+    double h_obs = 0;
+    std::vector<cher_telescope> tel;
+    cher_options opt{};
+    // constants of the yield, computed once in double (same rounding as the
+    // per-step statements of the kernel)
+    double inv_me = 0, K = 0, inv_B = 0, lam_inv1 = 0, lam_dinv = 0;
+    // tables
+    bool built = false;
+    cher::HostTables T;
+    cher::HostGrid G;
+    double eta_obs = 0;
+    double *d_eta64 = nullptr;
+    float *d_eta32 = nullptr;
+    void *d_tab64 = nullptr, *d_tab32 = nullptr;
+    void *d_tel64 = nullptr, *d_tel32 = nullptr;
+    int32_t *d_cell_start = nullptr, *d_cell_tel = nullptr;
+    // scratch: the persistent kernel's tile counter
+    unsigned long long *d_scratch = nullptr;
+    // launch shape
+    int block = 256;
+    int ctas_per_sm = 3;
+};
+
+namespace {
+
+bool bad_ptr(const void *p) { return p == nullptr; }
+
+void free_tables(cher_ctx *c) {
+    cudaFree(c->d_eta64);
+    cudaFree(c->d_eta32);
+    cudaFree(c->d_tab64);
+    cudaFree(c->d_tab32);
+    cudaFree(c->d_tel64);
+    cudaFree(c->d_tel32);
+    cudaFree(c->d_cell_start);
+    cudaFree(c->d_cell_tel);
+    c->d_eta64 = nullptr;
+    c->d_eta32 = nullptr;
+    c->d_tab64 = c->d_tab32 = nullptr;
+    c->d_tel64 = c->d_tel32 = nullptr;
+    c->d_cell_start = c->d_cell_tel = nullptr;
+    c->built = false;
+}
+
+template <class T>
+cher_status upload(T **dst, const T *src, size_t n) {
+    if (cudaMalloc(reinterpret_cast<void **>(dst), n * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return CHER_ENOMEM;
+    }
+    if (cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return CHER_ECUDA;
+    return CHER_OK;
+}
+
+bool tracks_ok(const cher_tracks *t) {
+    if (!t) return false;
+    if (t->n < 0 || t->n > (int64_t(1) << 40)) return false;
+    if (t->track_base < 0 || t->track_base > (int64_t(1) << 40)) return false;
+    if (t->n == 0) return true;
+    if (bad_ptr(t->x0) || bad_ptr(t->y0) || bad_ptr(t->z0) || bad_ptr(t->t0) ||
+        bad_ptr(t->len) || bad_ptr(t->ekin) || bad_ptr(t->ux) || bad_ptr(t->uy) ||
+        bad_ptr(t->uz))
+        return false;
+    if (t->t_ref && t->n_showers < 1) return false;
+    return true;
+}
+
+cher::KParams base_params(const cher_ctx *c, const cher_tracks *t, uint64_t seed, bool fp32) {
+    cher::KParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.x0 = t->x0; p.y0 = t->y0; p.z0 = t->z0; p.t0 = t->t0; p.len = t->len; p.ekin = t->ekin;
+    p.ux = t->ux; p.uy = t->uy; p.uz = t->uz;
+    p.shower = t->shower;
+    p.t_ref = t->t_ref;
+    p.n_showers = t->n_showers;
+    p.n = t->n;
+    p.track_base = t->track_base;
+    p.key0 = static_cast<uint32_t>(seed & 0xffffffffu);
+    p.key1 = static_cast<uint32_t>(seed >> 32);
+    p.inv_me = c->inv_me;
+    p.K = c->K;
+    p.inv_B = c->inv_B;
+    p.n_fine = c->T.n_fine;
+    p.h_max = c->T.h_max;
+    p.inv_dh = c->T.inv_dh;
+    p.eta64 = c->d_eta64;
+    p.eta32 = c->d_eta32;
+    p.eta_in_smem = (fp32 && c->T.n_fine <= 16384) ? 1 : 0;
+    p.h_obs = c->h_obs;
+    p.eta_obs = c->eta_obs;
+    p.H = c->T.H;
+    p.Z = c->T.Z;
+    p.inv_dht = c->T.inv_dht;
+    p.inv_dq = c->T.inv_dq;
+    p.q_max = c->T.q_max;
+    p.tab = fp32 ? c->d_tab32 : c->d_tab64;
+    p.lam_inv1 = c->lam_inv1;
+    p.lam_dinv = c->lam_dinv;
+    p.n_tel = static_cast<int32_t>(c->tel.size());
+    p.tel = fp32 ? c->d_tel32 : c->d_tel64;
+    p.gnx = c->G.nx;
+    p.gny = c->G.ny;
+    p.gx0 = c->G.x0;
+    p.gy0 = c->G.y0;
+    p.inv_gcs = c->G.inv_cs;
+    p.cell_start = c->d_cell_start;
+    p.cell_tel = c->d_cell_tel;
+    return p;
+}
+
+cher_status launch(cher_ctx *c, cher::KParams &p, bool fp32, int mode, bool persistent,
+                   void *stream) {
+    const int block = c->block;
+    p.n_tiles = (p.n + block - 1) / block;
+    if (p.n_tiles == 0) return CHER_OK;
+    const size_t smem = cher::kernel_smem_bytes(fp32, block, p);
+    if (cher::kernel_prepare(fp32, block, mode, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return CHER_ERANGE;
+    }
+    int grid;
+    if (persistent && c->ctas_per_sm > 0) {
+        const int fit = cher::kernel_max_ctas_per_sm(fp32, block, mode, smem);
+        const int per_sm = std::max(1, std::min(c->ctas_per_sm, fit));
+        grid = static_cast<int>(std::min<int64_t>(p.n_tiles, int64_t(per_sm) * c->num_sms));
+        p.tile_counter = c->d_scratch;
+        if (cudaMemsetAsync(c->d_scratch, 0, sizeof(unsigned long long),
+                            static_cast<cudaStream_t>(stream)) != cudaSuccess)
+            return CHER_ECUDA;
+    } else {
+        if (p.n_tiles > 0x7fffffff) return CHER_ERANGE;
+        grid = static_cast<int>(p.n_tiles);
+        p.tile_counter = nullptr;
+    }
+    if (cher::kernel_launch(fp32, block, mode, grid, smem, p, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return CHER_ECUDA;
+    }
+    return CHER_OK;
+}
+
+bool check_device(const cher_ctx *c) {
+    int d = -1;
+    return cudaGetDevice(&d) == cudaSuccess && d == c->device;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cher_status_string(cher_status s) {
+    switch (s) {
+    case CHER_OK: return "ok";
+    case CHER_EINVAL: return "invalid argument";
+    case CHER_ENOMEM: return "out of memory";
+    case CHER_ECUDA: return "CUDA runtime error";
+    case CHER_ESTATE: return "refraction tables not built";
+    case CHER_ERANGE: return "size out of supported range";
+    case CHER_EOVERFLOW: return "telescope buffer overflow";
+    case CHER_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+cher_status cher_create(const cher_atmosphere *atm, double h_obs, const cher_telescope *tel,
+                        int32_t n_tel, const cher_options *opt, cher_ctx **out) {
+    if (!atm || !tel || !out || n_tel < 1 || n_tel > 4096 || !std::isfinite(h_obs))
+        return CHER_EINVAL;
+    *out = nullptr;
+    for (int k = 0; k < n_tel; ++k)
+        if (!(tel[k].r > 0.0) || !std::isfinite(tel[k].x) || !std::isfinite(tel[k].y) ||
+            !std::isfinite(tel[k].z) || !std::isfinite(tel[k].r))
+            return CHER_EINVAL;
+    cher_options o{5.0, 300.0, 600.0, 10000};
+    if (opt) {
+        if (opt->bunch_size != 0.0) o.bunch_size = opt->bunch_size;
+        if (opt->lambda_min_nm != 0.0) o.lambda_min_nm = opt->lambda_min_nm;
+        if (opt->lambda_max_nm != 0.0) o.lambda_max_nm = opt->lambda_max_nm;
+        if (opt->n_fine != 0) o.n_fine = opt->n_fine;
+    }
+    if (!(o.bunch_size > 0.0) || !(o.lambda_min_nm > 0.0) ||
+        !(o.lambda_max_nm > o.lambda_min_nm) || o.n_fine < 2 || o.n_fine > (1 << 20))
+        return CHER_EINVAL;
+    cher_ctx *c = new (std::nothrow) cher_ctx;
+    if (!c) return CHER_ENOMEM;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return CHER_ECUDA;
+    }
+    c->atm = *atm;
+    c->h_obs = h_obs;
+    c->tel.assign(tel, tel + n_tel);
+    c->opt = o;
+    // yield constants: K = 2 pi alpha (1/lambda1 - 1/lambda2), lambda in m
+    c->inv_me = 1.0 / cher::kMe;
+    const double two_pi_alpha = (2.0 * cher::kPi) * cher::kAlpha;
+    const double inv1 = 1.0e9 / o.lambda_min_nm;
+    const double inv2 = 1.0e9 / o.lambda_max_nm;
+    const double dinv = inv1 - inv2;
+    c->K = two_pi_alpha * dinv;
+    c->inv_B = 1.0 / o.bunch_size;
+    c->lam_inv1 = 1.0 / o.lambda_min_nm;
+    c->lam_dinv = 1.0 / o.lambda_min_nm - 1.0 / o.lambda_max_nm;
+    if (cudaMalloc(reinterpret_cast<void **>(&c->d_scratch), 256) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return CHER_ENOMEM;
+    }
+    *out = c;
+    return CHER_OK;
+}
+
+cher_status cher_build_refraction_tables(cher_ctx *c, int32_t n_heights, int32_t n_zenith,
+                                         double zenith_max_deg, double h_max) {
+    if (!c) return CHER_EINVAL;
+    if (!check_device(c)) return CHER_EINVAL;
+    cher::HostTables T;
+    const double th = zenith_max_deg * cher::kPi / 180.0;
+    cher_status s = cher::build_tables(c->atm, c->h_obs, c->opt.n_fine, n_heights, n_zenith, th,
+                                       h_max, T);
+    if (s != CHER_OK) return s;
+    cher::HostGrid G;
+    s = cher::build_grid(c->tel.data(), static_cast<int32_t>(c->tel.size()), th, G);
+    if (s != CHER_OK) return s;
+    if (static_cast<double>(n_heights) * n_zenith * 32.0 > 4.0e9) return CHER_ERANGE;
+    free_tables(c);
+    c->T = std::move(T);
+    c->G = std::move(G);
+    c->eta_obs = cher::eta_lookup(c->T, c->h_obs);
+
+    const int H = c->T.H, Z = c->T.Z;
+    std::vector<double> t64(static_cast<size_t>(H) * (Z - 1) * 4);
+    std::vector<float> t32(t64.size());
+    for (int j = 0; j < H; ++j)
+        for (int k = 0; k < Z - 1; ++k) {
+            const size_t e = (static_cast<size_t>(j) * (Z - 1) + k) * 4;
+            const size_t a = static_cast<size_t>(j) * Z + k;
+            t64[e + 0] = c->T.ax[a];
+            t64[e + 1] = c->T.al[a];
+            t64[e + 2] = c->T.ax[a + 1];
+            t64[e + 3] = c->T.al[a + 1];
+            for (int q = 0; q < 4; ++q) t32[e + q] = static_cast<float>(t64[e + q]);
+        }
+    std::vector<float> e32(c->T.eta.begin(), c->T.eta.end());
+    const size_t nt = c->tel.size();
+    std::vector<double> tel64(nt * 4);
+    std::vector<float> tel32(nt * 4);
+    for (size_t k = 0; k < nt; ++k) {
+        const cher_telescope &q = c->tel[k];
+        const double v[4] = {q.x, q.y, q.z, q.r * q.r};
+        for (int m = 0; m < 4; ++m) {
+            tel64[4 * k + m] = v[m];
+            tel32[4 * k + m] = static_cast<float>(v[m]);
+        }
+    }
+    cher_status r;
+    double *d_tab64 = nullptr;
+    float *d_tab32 = nullptr, *d_tel32 = nullptr;
+    double *d_tel64 = nullptr;
+    if ((r = upload(&c->d_eta64, c->T.eta.data(), c->T.eta.size())) != CHER_OK ||
+        (r = upload(&c->d_eta32, e32.data(), e32.size())) != CHER_OK ||
+        (r = upload(&d_tab64, t64.data(), t64.size())) != CHER_OK ||
+        (r = upload(&d_tab32, t32.data(), t32.size())) != CHER_OK ||
+        (r = upload(&d_tel64, tel64.data(), tel64.size())) != CHER_OK ||
+        (r = upload(&d_tel32, tel32.data(), tel32.size())) != CHER_OK ||
+        (r = upload(&c->d_cell_start, c->G.cell_start.data(), c->G.cell_start.size())) != CHER_OK ||
+        (r = upload(&c->d_cell_tel, c->G.cell_tel.data(), c->G.cell_tel.size())) != CHER_OK) {
+        c->d_tab64 = d_tab64;
+        c->d_tab32 = d_tab32;
+        c->d_tel64 = d_tel64;
+        c->d_tel32 = d_tel32;
+        free_tables(c);
+        return r;
+    }
+    c->d_tab64 = d_tab64;
+    c->d_tab32 = d_tab32;
+    c->d_tel64 = d_tel64;
+    c->d_tel32 = d_tel32;
+    c->built = true;
+    return CHER_OK;
+}
+
+cher_status cher_destroy(cher_ctx *c) {
+    if (!c) return CHER_OK;
+    free_tables(c);
+    cudaFree(c->d_scratch);
+    delete c;
+    return CHER_OK;
+}
+
+cher_status cher_set_launch(cher_ctx *c, int32_t block_threads, int32_t ctas_per_sm) {
+    if (!c) return CHER_EINVAL;
+    if (block_threads != 128 && block_threads != 256 && block_threads != 512) return CHER_EINVAL;
+    if (ctas_per_sm < 0 || ctas_per_sm > 8) return CHER_EINVAL;
+    c->block = block_threads;
+    c->ctas_per_sm = ctas_per_sm;
+    return CHER_OK;
+}
+
+cher_status cher_get_launch(const cher_ctx *c, int32_t *block_threads, int32_t *ctas_per_sm) {
+    if (!c) return CHER_EINVAL;
+    if (block_threads) *block_threads = c->block;
+    if (ctas_per_sm) *ctas_per_sm = c->ctas_per_sm;
+    return CHER_OK;
+}
+
+cher_status cher_generate_propagate(cher_ctx *c, const cher_tracks *t, uint64_t seed,
+                                    cher_precision prec, const cher_output *out, void *stream) {
+    if (!c || !out || !tracks_ok(t)) return CHER_EINVAL;
+    if (prec != CHER_FP64 && prec != CHER_FP32_BULK) return CHER_EINVAL;
+    if (!c->built) return CHER_ESTATE;
+    if (!check_device(c)) return CHER_EINVAL;
+    if (bad_ptr(out->count) || bad_ptr(out->stats)) return CHER_EINVAL;
+    if (out->cap_per_tel < 0) return CHER_EINVAL;
+    if (out->cap_per_tel > 0 && (bad_ptr(out->pos) || bad_ptr(out->tim) || bad_ptr(out->key)))
+        return CHER_EINVAL;
+    const size_t al = prec == CHER_FP32_BULK ? 16 : 16;
+    if (reinterpret_cast<uintptr_t>(out->pos) % al || reinterpret_cast<uintptr_t>(out->tim) % al)
+        return CHER_EINVAL;
+    const bool fp32 = prec == CHER_FP32_BULK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(out->count, 0, c->tel.size() * sizeof(unsigned long long), s) !=
+            cudaSuccess ||
+        cudaMemsetAsync(out->stats, 0, CHER_NSTATS * sizeof(unsigned long long), s) != cudaSuccess)
+        return CHER_ECUDA;
+    cher::KParams p = base_params(c, t, seed, fp32);
+    p.pos = out->pos;
+    p.tim = out->tim;
+    p.key = out->key;
+    p.cap = out->cap_per_tel;
+    p.count = out->count;
+    p.stats = out->stats;
+    return launch(c, p, fp32, cher::MODE_HITS, true, stream);
+}
+
+cher_status cher_sync_status(cher_ctx *c, const cher_output *out, unsigned long long *stats_host,
+                             void *stream) {
+    if (!c || !out || !out->stats) return CHER_EINVAL;
+    unsigned long long st[CHER_NSTATS];
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CHER_ECUDA;
+    if (cudaMemcpy(st, out->stats, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CHER_ECUDA;
+    if (stats_host) std::memcpy(stats_host, st, sizeof(st));
+    return st[CHER_STAT_OVERFLOW] ? CHER_EOVERFLOW : CHER_OK;
+}
+
+cher_status cher_segment_yield(cher_ctx *c, const cher_tracks *t, cher_precision prec, int32_t *nb,
+                               double *w, void *stream) {
+    if (!c || !tracks_ok(t) || (t->n > 0 && (!nb || !w))) return CHER_EINVAL;
+    if (prec != CHER_FP64 && prec != CHER_FP32_BULK) return CHER_EINVAL;
+    if (!c->built) return CHER_ESTATE;
+    if (!check_device(c)) return CHER_EINVAL;
+    const bool fp32 = prec == CHER_FP32_BULK;
+    cher::KParams p = base_params(c, t, 0, fp32);
+    p.y_nb = nb;
+    p.y_w = w;
+    return launch(c, p, fp32, cher::MODE_YIELD, false, stream);
+}
+
+cher_status cher_trace_bunches(cher_ctx *c, const cher_tracks *t, uint64_t seed,
+                               cher_precision prec, const int64_t *bunch_off,
+                               const cher_trace *out, void *stream) {
+    if (!c || !tracks_ok(t) || !out) return CHER_EINVAL;
+    if (prec != CHER_FP64 && prec != CHER_FP32_BULK) return CHER_EINVAL;
+    if (!c->built) return CHER_ESTATE;
+    if (!check_device(c)) return CHER_EINVAL;
+    if (t->n > 0 && (!bunch_off || !out->pos || !out->tim || !out->status || !out->nhit ||
+                     !out->first_hit))
+        return CHER_EINVAL;
+    const bool fp32 = prec == CHER_FP32_BULK;
+    cher::KParams p = base_params(c, t, seed, fp32);
+    p.pos = out->pos;
+    p.tim = out->tim;
+    p.bunch_off = bunch_off;
+    p.t_status = out->status;
+    p.t_nhit = out->nhit;
+    p.t_first = out->first_hit;
+    return launch(c, p, fp32, cher::MODE_TRACE, false, stream);
+}
+
+cher_status cher_get_tables(const cher_ctx *c, double *eta, double *ax, double *al) {
+    if (!c) return CHER_EINVAL;
+    if (!c->built) return CHER_ESTATE;
+    if (eta) std::copy(c->T.eta.begin(), c->T.eta.end(), eta);
+    if (ax) std::copy(c->T.ax.begin(), c->T.ax.end(), ax);
+    if (al) std::copy(c->T.al.begin(), c->T.al.end(), al);
+    return CHER_OK;
+}
+
+cher_status cher_build_tables_host(const cher_atmosphere *atm, double h_obs, int32_t n_fine,
+                                   int32_t n_heights, int32_t n_zenith, double zenith_max_deg,
+                                   double h_max, double *eta, double *ax, double *al) {
+    if (!atm || !eta || !ax || !al) return CHER_EINVAL;
+    cher::HostTables T;
+    const cher_status s = cher::build_tables(*atm, h_obs, n_fine, n_heights, n_zenith,
+                                             zenith_max_deg * cher::kPi / 180.0, h_max, T);
+    if (s != CHER_OK) return s;
+    std::copy(T.eta.begin(), T.eta.end(), eta);
+    std::copy(T.ax.begin(), T.ax.end(), ax);
+    std::copy(T.al.begin(), T.al.end(), al);
+    return CHER_OK;
+}
+
+cher_status cher_autotune(cher_ctx *c, const cher_tracks *t, uint64_t seed, cher_precision prec,
+                          const cher_output *out, const char *cache_path, void *stream) {
+    if (!c || !tracks_ok(t) || !out) return CHER_EINVAL;
+    if (!c->built) return CHER_ESTATE;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) return CHER_ECUDA;
+    char tag[256];
+    const long long tiles_bucket = static_cast<long long>(std::log2(double(t->n) + 1.0));
+    std::snprintf(tag, sizeof(tag), "%s|%d|%lld|%d|%d", prop.name, static_cast<int>(prec),
+                  tiles_bucket, static_cast<int>(c->tel.size()), c->T.Z);
+    for (char *q = tag; *q; ++q)
+        if (*q == ' ') *q = '_';
+    if (cache_path) {
+        if (FILE *f = std::fopen(cache_path, "r")) {
+            char line[512];
+            while (std::fgets(line, sizeof(line), f)) {
+                char key[300];
+                int b, cps;
+                if (std::sscanf(line, "%299s %d %d", key, &b, &cps) == 3 &&
+                    std::strcmp(key, tag) == 0) {
+                    std::fclose(f);
+                    return cher_set_launch(c, b, cps);
+                }
+            }
+            std::fclose(f);
+        }
+    }
+    const int blocks[] = {128, 256, 512};
+    const int ctas[] = {0, 1, 2, 3, 4, 6, 8};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return CHER_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float best = 1e30f;
+    int best_b = c->block, best_c = c->ctas_per_sm;
+    cher_status rc = CHER_OK;
+    for (int b : blocks)
+        for (int cps : ctas) {
+            if (b == 512 && cps > 4) continue;
+            c->block = b;
+            c->ctas_per_sm = cps;
+            float tsum = 0.0f;
+            bool ok = true;
+            for (int rep = 0; rep < 4 && ok; ++rep) {
+                cudaEventRecord(e0, s);
+                rc = cher_generate_propagate(c, t, seed, prec, out, stream);
+                cudaEventRecord(e1, s);
+                if (rc != CHER_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                    ok = false;
+                    break;
+                }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tsum += ms;   // first run warms up
+            }
+            if (ok && tsum < best) {
+                best = tsum;
+                best_b = b;
+                best_c = cps;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->block = best_b;
+    c->ctas_per_sm = best_c;
+    if (best >= 1e30f) return rc != CHER_OK ? rc : CHER_ECUDA;
+    if (cache_path) {
+        if (FILE *f = std::fopen(cache_path, "a")) {
+            std::fprintf(f, "%s %d %d\n", tag, best_b, best_c);
+            std::fclose(f);
+        }
+    }
+    return CHER_OK;
+}
+
+}  // extern "C"

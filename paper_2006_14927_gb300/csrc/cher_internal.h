@@ -1,0 +1,113 @@
+// cher_internal.h -- private structures shared by the library's translation
+// units (host table builder, C ABI, CUDA kernels).  Not installed, not part
+// of the ABI.
+#pragma once
+
+#include <cuda_runtime_api.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/cher.h"
+
+namespace cher {
+
+// Physical constants (CODATA 2018; c exact by the SI definition).
+constexpr double kC = 0.299792458;          // m/ns
+constexpr double kMe = 0.51099895000;       // electron mass, MeV
+constexpr double kAlpha = 7.2973525693e-3;  // fine-structure constant
+constexpr double kPi = 3.14159265358979323846;
+
+// Bunch status codes (the rare branches of the paper's Algorithm 1).
+enum : int32_t { ST_GROUND = 0, ST_UPWARD = 1, ST_BELOW = 2, ST_ABOVE = 3, ST_ANGLE = 4 };
+
+constexpr int kMaxCandPerCell = 32;   // telescope candidates in one grid cell
+
+// Host-side tables, all FP64 (step a0).
+struct HostTables {
+    int32_t n_fine = 0;
+    double h_max = 0, dh = 0, inv_dh = 0;
+    std::vector<double> eta;             // [n_fine]
+    int32_t H = 0, Z = 0;
+    double theta_max = 0, dht = 0, inv_dht = 0, q_max = 0, dq = 0, inv_dq = 0;
+    std::vector<double> ax, al;          // [H][Z]
+};
+
+// Ground grid of telescope candidates (step a4).
+struct HostGrid {
+    double x0 = 0, y0 = 0, cs = 1, inv_cs = 1;
+    int32_t nx = 1, ny = 1;
+    std::vector<int32_t> cell_start;     // [nx * ny + 1]
+    std::vector<int32_t> cell_tel;       // candidates
+};
+
+// Build eta, ax, al (table definitions in cher_tables.cpp).
+cher_status build_tables(const cher_atmosphere &atm, double h_obs, int32_t n_fine,
+                         int32_t H, int32_t Z, double theta_max, double h_max,
+                         HostTables &out);
+// Eta lookup in the fine table, one IEEE operation per statement (the same
+// rounding as the device lookup that decides the bunch count).
+double eta_lookup(const HostTables &t, double h);
+cher_status build_grid(const cher_telescope *tel, int32_t n_tel, double theta_max,
+                       HostGrid &g);
+
+// Everything a kernel launch needs, passed by value.
+struct KParams {
+    // tracks
+    const double *x0, *y0, *z0, *t0, *len, *ekin;
+    const void *ux, *uy, *uz;
+    const uint32_t *shower;
+    const double *t_ref;
+    int32_t n_showers;
+    int64_t n, track_base;
+    uint32_t key0, key1;
+    // yield constants (FP64, same rounding as the host)
+    double inv_me, K, inv_B;
+    // fine eta table
+    int32_t n_fine;
+    double h_max, inv_dh;
+    const double *eta64;
+    const float *eta32;
+    int32_t eta_in_smem;
+    // observation level
+    double h_obs, eta_obs;
+    // refraction tables, pair-interleaved: entry (j, k), k < Z-1, holds
+    // {ax[j][k], al[j][k], ax[j][k+1], al[j][k+1]}
+    int32_t H, Z;
+    double inv_dht, inv_dq, q_max;
+    const void *tab;                      // float4 or double4 [H][Z-1]
+    // wavelength band in 1/nm
+    double lam_inv1, lam_dinv;
+    // telescopes and grid
+    int32_t n_tel;
+    const void *tel;                      // float4 / double4: x, y, z, r^2
+    int32_t gnx, gny;
+    double gx0, gy0, inv_gcs;
+    const int32_t *cell_start, *cell_tel;
+    // outputs
+    void *pos, *tim;
+    uint64_t *key;
+    int64_t cap;
+    unsigned long long *count, *stats;
+    // trace mode
+    const int64_t *bunch_off;
+    int32_t *t_status, *t_nhit, *t_first;
+    // yield-only mode
+    int32_t *y_nb;
+    double *y_w;
+    // scheduling
+    unsigned long long *tile_counter;     // NULL: one CTA per tile
+    int64_t n_tiles;
+};
+
+enum Mode : int { MODE_HITS = 0, MODE_TRACE = 1, MODE_YIELD = 2 };
+
+// Launchers (cher_kernels.cu).  fp32 selects CHER_FP32_BULK.
+size_t kernel_smem_bytes(bool fp32, int block, const KParams &p);
+cudaError_t kernel_prepare(bool fp32, int block, int mode, size_t smem);
+cudaError_t kernel_launch(bool fp32, int block, int mode, int grid, size_t smem,
+                          const KParams &p, void *stream);
+int kernel_max_ctas_per_sm(bool fp32, int block, int mode, size_t smem);
+
+}  // namespace cher

@@ -1,0 +1,683 @@
+// cher_kernels.cu -- the hot path (steps a1-a5) as one fused kernel per tile
+// of track steps, in FP64 and in FP32-bulk precision.
+//
+// A CTA owns a tile of `BLOCK` consecutive steps:
+//   phase A  one thread per step: Cherenkov yield in FP64 (CERENK, paper
+//            section 3.2), bunch count nb = ceil(N / B), per-step constants
+//            staged in shared memory; a CTA-wide exclusive scan of nb gives
+//            every bunch of the tile a slot;
+//   phase B  the CTA's threads stride over the tile's bunches (the paper's
+//            sub-step loop, Appendix A, unrolled across threads): Philox
+//            randoms, emission point / azimuth / wavelength, the rare
+//            conditions first (Algorithm 2's hoisting becomes a per-lane
+//            predicate), Snell + one fine-table index for n(h) and one
+//            (height, sin^2) cell for both refraction corrections (the
+//            single-search refactor of section 3.3.1 and the repeated-call
+//            hoisting of Algorithm 3), the ground point and arrival time
+//            (RAYBND, Appendix B listing), candidate spheres from the ground
+//            grid, and warp-aggregated compaction of the crossings (TELOUT).
+// In the persistent variant CTAs pull tiles from an atomic queue, so showers
+// of very uneven size share one launch (the paper's independent-shower
+// parallelism, section 2, inside one GPU).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "cher_internal.h"
+
+namespace cher {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11).  Counter (lo(i), hi(i), j, 0), key
+// (lo(seed), hi(seed)).
+// ------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// uniform deviates in (0, 1)
+__device__ __forceinline__ double u01d(uint32_t x) {
+    return (static_cast<double>(x) + 0.5) * (1.0 / 4294967296.0);
+}
+__device__ __forceinline__ float u01f(uint32_t x) {
+    // top 24 bits, centred: exactly representable, never 0 or 1
+    return __uint2float_rz(x >> 8) * (1.0f / 16777216.0f) + (1.0f / 33554432.0f);
+}
+
+// ------------------------------------------------------------------------
+// a1: per-step yield, FP64, one IEEE operation per statement in a fixed
+// order (the bunch count must not depend on the precision of the rest).
+// ------------------------------------------------------------------------
+struct Yield {
+    int nb;
+    bool valid;
+    double N, s2, g, gam, eta;
+};
+
+__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
+
+__device__ __forceinline__ double eta_exact_lookup(const KParams &p, double h) {
+    double hc = h;
+    if (hc < 0.0) hc = 0.0;
+    if (hc > p.h_max) hc = p.h_max;
+    const double x = __dmul_rn(hc, p.inv_dh);
+    int k = static_cast<int>(x);
+    if (k > p.n_fine - 2) k = p.n_fine - 2;
+    const double f = __dsub_rn(x, static_cast<double>(k));
+    const double t0 = __ldg(p.eta64 + k), t1 = __ldg(p.eta64 + k + 1);
+    const double d = __dsub_rn(t1, t0);
+    const double fd = __dmul_rn(f, d);
+    return __dadd_rn(t0, fd);
+}
+
+// A step emits only if every field is finite, len >= 0 and ekin > 0.
+template <class R>
+__device__ __forceinline__ bool step_valid(const KParams &p, int64_t i) {
+    return finite_d(__ldg(p.x0 + i)) && finite_d(__ldg(p.y0 + i)) && finite_d(__ldg(p.t0 + i)) &&
+           finite_d(static_cast<double>(__ldg(static_cast<const R *>(p.ux) + i))) &&
+           finite_d(static_cast<double>(__ldg(static_cast<const R *>(p.uy) + i)));
+}
+
+__device__ __forceinline__ void step_yield(const KParams &p, bool others_valid, double z0,
+                                           double len, double ekin, double uz, Yield &y) {
+    y.nb = 0;
+    y.valid = false;
+    y.N = y.s2 = y.g = y.gam = y.eta = 0.0;
+    if (!others_valid || !finite_d(z0) || !finite_d(len) || !finite_d(ekin) || !finite_d(uz) ||
+        len < 0.0 || ekin <= 0.0)
+        return;
+    const double g = __dmul_rn(ekin, p.inv_me);
+    const double gam = __dadd_rn(1.0, g);
+    const double gam2 = __dmul_rn(gam, gam);
+    const double half_len = __dmul_rn(0.5, len);
+    const double dz = __dmul_rn(half_len, uz);
+    const double hm = __dadd_rn(z0, dz);
+    const double eta = eta_exact_lookup(p, hm);
+    const double np1 = __dadd_rn(1.0, eta);
+    const double np1sq = __dmul_rn(np1, np1);
+    const double two_eta = __dadd_rn(2.0, eta);
+    const double a = __dmul_rn(eta, two_eta);
+    const double b = __dmul_rn(a, gam2);
+    const double num = __dsub_rn(b, np1sq);
+    const double two_g = __dadd_rn(2.0, g);
+    const double bg2 = __dmul_rn(g, two_g);
+    const double den = __dmul_rn(bg2, np1sq);
+    const double s2 = __ddiv_rn(num, den);
+    y.g = g;
+    y.gam = gam;
+    y.eta = eta;
+    y.valid = true;
+    if (!(s2 > 0.0)) return;
+    const double Ks2 = __dmul_rn(p.K, s2);
+    const double N = __dmul_rn(len, Ks2);
+    const double q = __dmul_rn(N, p.inv_B);
+    if (!(q < 2147483647.0)) {
+        y.valid = false;
+        return;
+    }
+    y.nb = static_cast<int>(ceil(q));
+    y.N = N;
+    y.s2 = s2;
+}
+
+// ------------------------------------------------------------------------
+// Per-step constants staged in shared memory for the bunch loop.
+// ------------------------------------------------------------------------
+template <class R>
+struct alignas(16) Seg {
+    R ux, uy, uz, L;
+    R e1x, e1y, e2x, e2y;
+    R e2z, cosc, sinc, inv_nb;
+    R x0, y0, dz0, tseg;   // dz0 = z0 - h_obs, tseg = t0 - t_ref (FP64 differences)
+    R inv_bc, w;
+    int nb, pad;
+};
+
+template <class R>
+__device__ __forceinline__ R load_dir(const void *p, int64_t i) {
+    return __ldg(static_cast<const R *>(p) + i);
+}
+
+template <class R>
+__device__ __forceinline__ void prep_step(const KParams &p, int64_t i, const Yield &y, Seg<R> &S) {
+    const double ux = static_cast<double>(load_dir<R>(p.ux, i));
+    const double uy = static_cast<double>(load_dir<R>(p.uy, i));
+    const double uz = static_cast<double>(load_dir<R>(p.uz, i));
+    const double len = __ldg(p.len + i);
+    double t_ref = 0.0;
+    if (p.t_ref) {
+        const uint32_t sh = p.shower ? __ldg(p.shower + i) : 0u;
+        if (static_cast<int32_t>(sh) < p.n_showers) t_ref = __ldg(p.t_ref + sh);
+    }
+    S.nb = y.nb;
+    S.pad = 0;
+    S.ux = static_cast<R>(ux);
+    S.uy = static_cast<R>(uy);
+    S.uz = static_cast<R>(uz);
+    S.L = static_cast<R>(len);
+    S.x0 = static_cast<R>(__ldg(p.x0 + i));
+    S.y0 = static_cast<R>(__ldg(p.y0 + i));
+    S.dz0 = static_cast<R>(__ldg(p.z0 + i) - p.h_obs);
+    S.tseg = static_cast<R>(__ldg(p.t0 + i) - t_ref);
+    // azimuth basis around the step: e1 horizontal, e2 = d x e1
+    R e1x, e1y;
+    const R rho2 = S.ux * S.ux + S.uy * S.uy;
+    if (rho2 > R(1e-20)) {
+        const R inv = R(1) / sqrt(rho2);
+        e1x = -S.uy * inv;
+        e1y = S.ux * inv;
+    } else {
+        e1x = R(1);
+        e1y = R(0);
+    }
+    S.e1x = e1x;
+    S.e1y = e1y;
+    S.e2x = -S.uz * e1y;
+    S.e2y = S.uz * e1x;
+    S.e2z = S.ux * e1y - S.uy * e1x;
+    if (y.nb > 0) {
+        // beta = sqrt(g (2 + g)) / gamma ; cos = 1 / (beta n) ; sin = sqrt(s2)
+        const R bg = sqrt(static_cast<R>(y.g * (2.0 + y.g)));
+        const R beta = bg / static_cast<R>(y.gam);
+        S.cosc = R(1) / (beta * static_cast<R>(1.0 + y.eta));
+        S.sinc = sqrt(static_cast<R>(y.s2));
+        S.inv_nb = R(1) / static_cast<R>(y.nb);
+        S.inv_bc = R(1) / (beta * R(kC));
+        S.w = static_cast<R>(y.N / static_cast<double>(y.nb));
+    } else {
+        S.cosc = S.sinc = S.inv_nb = S.inv_bc = S.w = R(0);
+    }
+}
+
+// ------------------------------------------------------------------------
+// a2 + a3: one bunch, from the Philox block to the ground.
+// ------------------------------------------------------------------------
+template <class R>
+struct BunchOut {
+    R X, Y, cx, cy, cz, t, he, lam;
+    int status;
+};
+
+template <class R>
+struct Consts {
+    R h_obs, dH_max, eta_o, inv_np1o, q_max, inv_dht, inv_dq, inv_dh, lam_inv1, lam_dinv;
+    int H, Z, n_fine;
+};
+
+template <class R>
+__device__ __forceinline__ R eta_at(const KParams &p, const Consts<R> &c, const R *eta_s, R h) {
+    R x = h * c.inv_dh;
+    x = x < R(0) ? R(0) : x;
+    int k = static_cast<int>(x);
+    k = k > c.n_fine - 2 ? c.n_fine - 2 : k;
+    const R f = x - static_cast<R>(k);
+    R t0, t1;
+    if constexpr (std::is_same<R, float>::value) {
+        if (eta_s) {
+            t0 = eta_s[k];
+            t1 = eta_s[k + 1];
+        } else {
+            t0 = __ldg(p.eta32 + k);
+            t1 = __ldg(p.eta32 + k + 1);
+        }
+    } else {
+        t0 = __ldg(p.eta64 + k);
+        t1 = __ldg(p.eta64 + k + 1);
+    }
+    return t0 + f * (t1 - t0);
+}
+
+template <class R>
+__device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, const R *eta_s,
+                                      const Seg<R> &S, int64_t gi, int j, BunchOut<R> &o) {
+    const uint4 x = philox4x32_10(
+        make_uint4(static_cast<uint32_t>(gi), static_cast<uint32_t>(static_cast<uint64_t>(gi) >> 32),
+                   static_cast<uint32_t>(j), 0u),
+        p.key0, p.key1);
+    R u0, u1, u2;
+    if constexpr (std::is_same<R, float>::value) {
+        u0 = u01f(x.x);
+        u1 = u01f(x.y);
+        u2 = u01f(x.z);
+    } else {
+        u0 = u01d(x.x);
+        u1 = u01d(x.y);
+        u2 = u01d(x.z);
+    }
+    // sub-step j, emission point uniform inside it
+    const R f = (static_cast<R>(j) + u0) * S.inv_nb;
+    const R fl = f * S.L;
+    R sp, cp;
+    if constexpr (std::is_same<R, float>::value)
+        sincospif(2.0f * u1, &sp, &cp);
+    else
+        sincospi(2.0 * u1, &sp, &cp);
+    const R px = S.cosc * S.ux + S.sinc * (cp * S.e1x + sp * S.e2x);
+    const R py = S.cosc * S.uy + S.sinc * (cp * S.e1y + sp * S.e2y);
+    const R pz = S.cosc * S.uz + S.sinc * (sp * S.e2z);
+    // 1/lambda^2 spectrum by inversion
+    o.lam = R(1) / (c.lam_inv1 - u2 * c.lam_dinv);
+    const R dH = S.dz0 + fl * S.uz;                 // h_e - h_obs
+    o.he = c.h_obs + dH;
+    // rare conditions first (paper Alg. 2)
+    if (!(pz < R(0))) { o.status = ST_UPWARD; return; }
+    if (!(dH >= R(0))) { o.status = ST_BELOW; return; }
+    if (!(dH <= c.dH_max)) { o.status = ST_ABOVE; return; }
+    // Snell: sin_obs = sin_em (1 + eta_e) / (1 + eta_o)
+    const R eta_e = eta_at<R>(p, c, eta_s, o.he);
+    const R rat = R(1) + (eta_e - c.eta_o) * c.inv_np1o;
+    const R se2 = px * px + py * py;
+    const R q = se2 * rat * rat;                    // sin^2(theta_obs)
+    if (!(q <= c.q_max)) { o.status = ST_ANGLE; return; }
+    const R co = sqrt(R(1) - q);
+    // one cell of the (height, sin^2) tables serves both corrections
+    const R fj = dH * c.inv_dht;
+    int jj = static_cast<int>(fj);
+    jj = jj > c.H - 2 ? c.H - 2 : jj;
+    const R a = fj - static_cast<R>(jj);
+    const R fk = q * c.inv_dq;
+    int kk = static_cast<int>(fk);
+    kk = kk > c.Z - 2 ? c.Z - 2 : kk;
+    const R b = fk - static_cast<R>(kk);
+    R Ax, Al;
+    {
+        const size_t e0 = static_cast<size_t>(jj) * (c.Z - 1) + kk;
+        const size_t e1 = e0 + (c.Z - 1);
+        if constexpr (std::is_same<R, float>::value) {
+            const float4 *T = static_cast<const float4 *>(p.tab);
+            const float4 t0 = __ldg(T + e0), t1 = __ldg(T + e1);
+            const float x0 = t0.x + a * (t1.x - t0.x), x1 = t0.z + a * (t1.z - t0.z);
+            const float l0 = t0.y + a * (t1.y - t0.y), l1 = t0.w + a * (t1.w - t0.w);
+            Ax = x0 + b * (x1 - x0);
+            Al = l0 + b * (l1 - l0);
+        } else {
+            const double2 *T = static_cast<const double2 *>(p.tab);
+            const double2 t0a = __ldg(T + 2 * e0), t0b = __ldg(T + 2 * e0 + 1);
+            const double2 t1a = __ldg(T + 2 * e1), t1b = __ldg(T + 2 * e1 + 1);
+            const double x0 = t0a.x + a * (t1a.x - t0a.x), x1 = t0b.x + a * (t1b.x - t0b.x);
+            const double l0 = t0a.y + a * (t1a.y - t0a.y), l1 = t0b.y + a * (t1b.y - t0b.y);
+            Ax = x0 + b * (x1 - x0);
+            Al = l0 + b * (l1 - l0);
+        }
+    }
+    const R sec = R(1) / co;
+    const R sec2 = sec * sec;
+    R hx = R(0), hy = R(0), so = R(0);
+    if (se2 > R(0)) {
+        const R rse = R(1) / sqrt(se2);
+        hx = px * rse;
+        hy = py * rse;
+        so = se2 * rse * rat;
+    }
+    const R tn = so * sec;
+    const R D = tn * (dH + Ax * sec2);              // horizontal offset
+    const R Lp = sec * (dH + Al * sec2);            // optical path
+    o.X = S.x0 + fl * S.ux + D * hx;
+    o.Y = S.y0 + fl * S.uy + D * hy;
+    o.t = S.tseg + fl * S.inv_bc + Lp * R(1.0 / kC);
+    o.cx = so * hx;
+    o.cy = so * hy;
+    o.cz = -co;
+    o.status = ST_GROUND;
+}
+
+// Candidate spheres of the bunch's grid cell: bit m of the mask is cell
+// entry s0 + m.
+template <class R>
+__device__ __forceinline__ unsigned sphere_hits(const KParams &p, const BunchOut<R> &o, int &s0) {
+    s0 = 0;
+    if (o.status != ST_GROUND) return 0u;
+    const R gx = (o.X - static_cast<R>(p.gx0)) * static_cast<R>(p.inv_gcs);
+    const R gy = (o.Y - static_cast<R>(p.gy0)) * static_cast<R>(p.inv_gcs);
+    if (!(gx >= R(0)) || !(gy >= R(0)) || !(gx < static_cast<R>(p.gnx)) ||
+        !(gy < static_cast<R>(p.gny)))
+        return 0u;
+    const int cell = static_cast<int>(gy) * p.gnx + static_cast<int>(gx);
+    s0 = __ldg(p.cell_start + cell);
+    const int s1 = __ldg(p.cell_start + cell + 1);
+    unsigned mask = 0u;
+    for (int m = s0; m < s1; ++m) {
+        const int k = __ldg(p.cell_tel + m);
+        R tx, ty, tz, r2;
+        if constexpr (std::is_same<R, float>::value) {
+            const float4 T = __ldg(static_cast<const float4 *>(p.tel) + k);
+            tx = T.x; ty = T.y; tz = T.z; r2 = T.w;
+        } else {
+            const double2 *T = static_cast<const double2 *>(p.tel);
+            const double2 A = __ldg(T + 2 * k), B = __ldg(T + 2 * k + 1);
+            tx = A.x; ty = A.y; tz = B.x; r2 = B.y;
+        }
+        const R dx = tx - o.X, dy = ty - o.Y, dz = tz;
+        const R q0 = dy * o.cz - dz * o.cy;
+        const R q1 = dz * o.cx - dx * o.cz;
+        const R q2 = dx * o.cy - dy * o.cx;
+        const R d2 = q0 * q0 + q1 * q1 + q2 * q2;
+        if (d2 <= r2) mask |= 1u << (m - s0);
+    }
+    return mask;
+}
+
+template <class R>
+__device__ __forceinline__ void tel_xyz(const KParams &p, int k, R &tx, R &ty, R &tz) {
+    if constexpr (std::is_same<R, float>::value) {
+        const float4 T = __ldg(static_cast<const float4 *>(p.tel) + k);
+        tx = T.x; ty = T.y; tz = T.z;
+    } else {
+        const double2 *T = static_cast<const double2 *>(p.tel);
+        const double2 A = __ldg(T + 2 * k), B = __ldg(T + 2 * k + 1);
+        tx = A.x; ty = A.y; tz = B.x;
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void store4(void *base, int64_t r, R a, R b, R c, R d) {
+    if constexpr (std::is_same<R, float>::value) {
+        static_cast<float4 *>(base)[r] = make_float4(a, b, c, d);
+    } else {
+        double2 *q = static_cast<double2 *>(base) + 2 * r;
+        q[0] = make_double2(a, b);
+        q[1] = make_double2(c, d);
+    }
+}
+
+// warp-wide sum of a counter, one atomic per warp
+__device__ __forceinline__ void flush_stat(unsigned long long *stats, int idx, unsigned v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(stats + idx, static_cast<unsigned long long>(v));
+}
+
+// ------------------------------------------------------------------------
+// The fused kernel.
+// ------------------------------------------------------------------------
+template <class R, int BLOCK, int MODE>
+__global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    Seg<R> *seg = reinterpret_cast<Seg<R> *>(smem);
+    int *off = reinterpret_cast<int *>(seg + BLOCK);          // BLOCK + 1
+    int *wsum = off + BLOCK + 1;                                // BLOCK / 32
+    __shared__ unsigned long long s_tile;
+    R *eta_s = nullptr;
+    if constexpr (std::is_same<R, float>::value) {
+        if (p.eta_in_smem) {
+            eta_s = reinterpret_cast<R *>(wsum + 32);
+            for (int k = threadIdx.x; k < p.n_fine; k += BLOCK) eta_s[k] = __ldg(p.eta32 + k);
+        }
+    }
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    Consts<R> c;
+    c.h_obs = static_cast<R>(p.h_obs);
+    c.dH_max = static_cast<R>(p.h_max - p.h_obs);
+    c.eta_o = static_cast<R>(p.eta_obs);
+    c.inv_np1o = static_cast<R>(1.0 / (1.0 + p.eta_obs));
+    c.q_max = static_cast<R>(p.q_max);
+    c.inv_dht = static_cast<R>(p.inv_dht);
+    c.inv_dq = static_cast<R>(p.inv_dq);
+    c.inv_dh = static_cast<R>(p.inv_dh);
+    c.lam_inv1 = static_cast<R>(p.lam_inv1);
+    c.lam_dinv = static_cast<R>(p.lam_dinv);
+    c.H = p.H;
+    c.Z = p.Z;
+    c.n_fine = p.n_fine;
+    const R np1o = static_cast<R>(1.0 + p.eta_obs);
+
+    unsigned st_steps = 0, st_emit = 0, st_inval = 0, st_bunch = 0, st_up = 0, st_below = 0,
+             st_above = 0, st_angle = 0, st_ground = 0, st_hits = 0, st_over = 0;
+
+    int64_t tile = blockIdx.x;
+    for (;;) {
+        if (p.tile_counter) {
+            __syncthreads();
+            if (tid == 0) s_tile = atomicAdd(p.tile_counter, 1ull);
+            __syncthreads();
+            tile = static_cast<int64_t>(s_tile);
+        }
+        if (tile >= p.n_tiles) break;
+        const int64_t base = tile * BLOCK;
+
+        // ---- phase A: one step per thread ----------------------------------
+        const int64_t i = base + tid;
+        int nb = 0;
+        if (i < p.n) {
+            Yield y;
+            step_yield(p, step_valid<R>(p, i), __ldg(p.z0 + i), __ldg(p.len + i),
+                       __ldg(p.ekin + i), static_cast<double>(load_dir<R>(p.uz, i)), y);
+            nb = y.nb;
+            ++st_steps;
+            st_emit += (nb > 0);
+            st_inval += !y.valid;
+            if constexpr (MODE == MODE_YIELD) {
+                p.y_nb[i] = nb;
+                p.y_w[i] = nb > 0 ? y.N / static_cast<double>(nb) : 0.0;
+            } else {
+                prep_step<R>(p, i, y, seg[tid]);
+            }
+        }
+        if constexpr (MODE == MODE_YIELD) {
+            if (!p.tile_counter) break;
+            continue;
+        }
+        st_bunch += nb;
+
+        // ---- CTA exclusive scan of nb ---------------------------------------
+        int v = nb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane == 31) wsum[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < BLOCK / 32 ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, w, o);
+                if (lane >= o) w += t;
+            }
+            if (lane < BLOCK / 32) wsum[lane] = w;   // inclusive warp totals
+        }
+        __syncthreads();
+        const int excl = v - nb + (warp > 0 ? wsum[warp - 1] : 0);
+        off[tid] = excl;
+        if (tid == BLOCK - 1) off[BLOCK] = excl + nb;
+        __syncthreads();
+        const int total = off[BLOCK];
+
+        // ---- phase B: the tile's bunches -------------------------------------
+        for (int b0 = 0; b0 < total; b0 += BLOCK) {
+            const int bidx = b0 + tid;
+            const bool live = bidx < total;
+            BunchOut<R> o;
+            o.status = -1;
+            int s = 0, j = 0;
+            if (live) {
+                int lo = 0, hi = BLOCK;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (off[mid] <= bidx) lo = mid; else hi = mid;
+                }
+                s = lo;
+                j = bidx - off[s];
+                bunch<R>(p, c, eta_s, seg[s], p.track_base + base + s, j, o);
+                st_up += o.status == ST_UPWARD;
+                st_below += o.status == ST_BELOW;
+                st_above += o.status == ST_ABOVE;
+                st_angle += o.status == ST_ANGLE;
+                st_ground += o.status == ST_GROUND;
+            }
+            int s0 = 0;
+            unsigned hm = live ? sphere_hits<R>(p, o, s0) : 0u;
+            st_hits += __popc(hm);
+            if constexpr (MODE == MODE_TRACE) {
+                if (live) {
+                    const int64_t gb = __ldg(p.bunch_off + base + s) + j;
+                    const R w = seg[s].w;
+                    if (o.status == ST_GROUND) {
+                        store4<R>(p.pos, gb, o.X, o.Y, o.cx, o.cy);
+                        store4<R>(p.tim, gb, o.t, o.he, w, o.lam);
+                    } else {
+                        store4<R>(p.pos, gb, R(0), R(0), R(0), R(0));
+                        store4<R>(p.tim, gb, R(0), o.he, w, o.lam);
+                    }
+                    p.t_status[gb] = o.status;
+                    p.t_nhit[gb] = __popc(hm);
+                    p.t_first[gb] = hm ? __ldg(p.cell_tel + s0 + __ffs(hm) - 1) : -1;
+                }
+            } else {
+                // warp-aggregated compaction into the per-telescope buffers
+                const R w = live ? seg[s].w : R(0);
+                const uint64_t key = (static_cast<uint64_t>(p.track_base + base + s) << 32) |
+                                     static_cast<uint32_t>(j);
+                for (;;) {
+                    if (!__any_sync(kFull, hm != 0u)) break;
+                    int tel = -1;
+                    if (hm) {
+                        const int bit = __ffs(hm) - 1;
+                        hm &= hm - 1u;
+                        tel = __ldg(p.cell_tel + s0 + bit);
+                    }
+                    const unsigned grp = __match_any_sync(kFull, tel);
+                    if (tel >= 0) {
+                        const int leader = __ffs(grp) - 1;
+                        const unsigned rank = __popc(grp & ((1u << lane) - 1u));
+                        unsigned long long slot0 = 0;
+                        if (lane == leader)
+                            slot0 = atomicAdd(p.count + tel, static_cast<unsigned long long>(__popc(grp)));
+                        slot0 = __shfl_sync(grp, slot0, leader);
+                        const unsigned long long slot = slot0 + rank;
+                        if (slot < static_cast<unsigned long long>(p.cap)) {
+                            R tx, ty, tz;
+                            tel_xyz<R>(p, tel, tx, ty, tz);
+                            const R sl = tz / o.cz;       // to the plane through the centre
+                            const int64_t r = static_cast<int64_t>(tel) * p.cap + static_cast<int64_t>(slot);
+                            store4<R>(p.pos, r, o.X + sl * o.cx - tx, o.Y + sl * o.cy - ty, o.cx, o.cy);
+                            store4<R>(p.tim, r, o.t + sl * np1o * R(1.0 / kC), o.he, w, o.lam);
+                            p.key[r] = key;
+                        } else {
+                            ++st_over;
+                        }
+                    }
+                }
+            }
+        }
+        if (!p.tile_counter) break;
+    }
+
+    unsigned long long *S = p.stats;
+    if (S) {
+        flush_stat(S, CHER_STAT_STEPS, st_steps);
+        flush_stat(S, CHER_STAT_EMITTING, st_emit);
+        flush_stat(S, CHER_STAT_INVALID, st_inval);
+        if (MODE != MODE_YIELD) {
+            flush_stat(S, CHER_STAT_BUNCHES, st_bunch);
+            flush_stat(S, CHER_STAT_UPWARD, st_up);
+            flush_stat(S, CHER_STAT_BELOW_OBS, st_below);
+            flush_stat(S, CHER_STAT_ABOVE_MAX, st_above);
+            flush_stat(S, CHER_STAT_ANGLE, st_angle);
+            flush_stat(S, CHER_STAT_GROUND, st_ground);
+            flush_stat(S, CHER_STAT_HITS, st_hits);
+            flush_stat(S, CHER_STAT_OVERFLOW, st_over);
+        }
+    }
+}
+
+template <class R, int BLOCK>
+size_t smem_bytes(const KParams &p) {
+    size_t b = sizeof(Seg<R>) * BLOCK + sizeof(int) * (BLOCK + 1 + 32);
+    b = (b + 15) & ~size_t(15);
+    if (std::is_same<R, float>::value && p.eta_in_smem) b += sizeof(float) * p.n_fine;
+    return b;
+}
+
+template <class R, int BLOCK, int MODE>
+const void *kernel_ptr() {
+    return reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE>);
+}
+
+template <class R, int MODE>
+const void *pick(int block) {
+    switch (block) {
+    case 128: return kernel_ptr<R, 128, MODE>();
+    case 256: return kernel_ptr<R, 256, MODE>();
+    case 512: return kernel_ptr<R, 512, MODE>();
+    }
+    return nullptr;
+}
+
+const void *pick_kernel(bool fp32, int block, int mode) {
+    if (fp32) {
+        switch (mode) {
+        case MODE_HITS: return pick<float, MODE_HITS>(block);
+        case MODE_TRACE: return pick<float, MODE_TRACE>(block);
+        case MODE_YIELD: return pick<float, MODE_YIELD>(block);
+        }
+    } else {
+        switch (mode) {
+        case MODE_HITS: return pick<double, MODE_HITS>(block);
+        case MODE_TRACE: return pick<double, MODE_TRACE>(block);
+        case MODE_YIELD: return pick<double, MODE_YIELD>(block);
+        }
+    }
+    return nullptr;
+}
+
+}  // namespace
+
+size_t kernel_smem_bytes(bool fp32, int block, const KParams &p) {
+    if (fp32) {
+        switch (block) {
+        case 128: return smem_bytes<float, 128>(p);
+        case 256: return smem_bytes<float, 256>(p);
+        case 512: return smem_bytes<float, 512>(p);
+        }
+    } else {
+        switch (block) {
+        case 128: return smem_bytes<double, 128>(p);
+        case 256: return smem_bytes<double, 256>(p);
+        case 512: return smem_bytes<double, 512>(p);
+        }
+    }
+    return 0;
+}
+
+cudaError_t kernel_prepare(bool fp32, int block, int mode, size_t smem) {
+    const void *k = pick_kernel(fp32, block, mode);
+    if (!k) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(smem));
+}
+
+int kernel_max_ctas_per_sm(bool fp32, int block, int mode, size_t smem) {
+    const void *k = pick_kernel(fp32, block, mode);
+    int n = 0;
+    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t kernel_launch(bool fp32, int block, int mode, int grid, size_t smem,
+                          const KParams &p, void *stream) {
+    const void *k = pick_kernel(fp32, block, mode);
+    if (!k) return cudaErrorInvalidValue;
+    void *args[] = {const_cast<KParams *>(&p)};
+    return cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem,
+                            static_cast<cudaStream_t>(stream));
+}
+
+}  // namespace cher

@@ -1,0 +1,310 @@
+// cher_tables.cpp -- step a0: atmosphere tables and the telescope grid,
+// built once per context on the host in double precision.
+//
+// * Fine table of eta = n - 1 at n_fine uniformly spaced heights on
+//   [0, h_max]: the paper's "fast interpolation" (section 3.3.2), which
+//   replaces the per-call binary search over ~55 tabulated altitudes
+//   (section 3.3.1) by an index computed from a uniform step.
+// * Refraction-correction tables (section 3.3.1: "coefficients for air
+//   refraction correction"; section 3.3.2 extends fast interpolation to them)
+//   over uniform heights and uniform squared sines of the observation-level
+//   zenith angle.  For a ray that reaches the observation level at zenith
+//   theta_o, Snell's law in flat layers (n(h) sin theta(h) = n_o sin theta_o)
+//   gives its horizontal offset x(h) and optical path l(h) between h_obs and
+//   h.  The tables store the differences to the straight line at theta_o,
+//   divided by their leading angular factors:
+//       ax = (x - dH tan theta_o) cos^3 theta_o / sin theta_o
+//       al = (l - dH / cos theta_o) cos^3 theta_o
+//   so that bilinear interpolation stays accurate up to the largest angles.
+//   The integrals are split at layer boundaries (the density jumps there)
+//   and done with fixed 12-point Gauss-Legendre rules on each piece, with
+//   the integrands rewritten so that no difference of nearly equal numbers
+//   is formed.
+// * Ground grid: every telescope is listed in each cell its conservative
+//   reach disc touches, so a bunch only tests the spheres of its own cell.
+#include <algorithm>
+#include <cmath>
+#include <thread>
+
+#include "cher_internal.h"
+
+namespace cher {
+namespace {
+
+struct Layered {
+    double hb[6], a[5], b[5], c[5], n0m1, rho0;
+};
+
+int layer_of(const Layered &A, double h) {
+    int i = 0;
+    while (i < 4 && h >= A.hb[i + 1]) ++i;
+    return i;
+}
+
+// rho(h) = (b_i / c_i) exp(-h / c_i); zero above the top of the atmosphere.
+double rho(const Layered &A, double h) {
+    if (h >= A.hb[5]) return 0.0;
+    const int i = layer_of(A, h);
+    const double r = A.b[i] / A.c[i];
+    const double e = std::exp(-(h / A.c[i]));
+    return r * e;
+}
+
+// eta = n0_minus_1 * rho / rho(0), evaluated in this order (the bunch count
+// depends on the exact rounding of the fine-table entries).
+double eta_of(const Layered &A, double h) {
+    const double r = rho(A, h);
+    const double q = r / A.rho0;
+    return A.n0m1 * q;
+}
+
+Layered make_layered(const cher_atmosphere &atm) {
+    Layered A;
+    for (int i = 0; i < 6; ++i) A.hb[i] = atm.h_bound[i];
+    for (int i = 0; i < 5; ++i) { A.a[i] = atm.a[i]; A.b[i] = atm.b[i]; A.c[i] = atm.c[i]; }
+    A.n0m1 = atm.n0_minus_1;
+    A.rho0 = 1.0;
+    A.rho0 = rho(A, 0.0);
+    return A;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_n.
+struct GaussLegendre {
+    static constexpr int N = 12;
+    double x[N], w[N];
+    GaussLegendre() {
+        for (int i = 0; i < N; ++i) {
+            double z = std::cos(kPi * (i + 0.75) / (N + 0.5));
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1.0, p1 = 0.0;
+                for (int k = 1; k <= N; ++k) {
+                    const double p2 = p1;
+                    p1 = p0;
+                    p0 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p2) / k;
+                }
+                const double dp = N * (z * p0 - p1) / (z * z - 1.0);
+                const double dz = p0 / dp;
+                z -= dz;
+                if (std::fabs(dz) < 1e-16) {
+                    x[i] = z;
+                    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+                    break;
+                }
+                x[i] = z;
+                w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+            }
+        }
+    }
+};
+
+// Integrands of ax and al at height h for a ray with observation sine so,
+// cosine co (co = sqrt(1 - so^2)).  With r = n_o / n(h) = (1 + eta_o)/(1 + eta),
+// s = so r and c = sqrt(1 - s^2):
+//   tan(theta) - tan(theta_o) = so (r - 1)(r + 1) / ((r co + c) c co)
+//   1/c - 1/co                = so^2 (r - 1)(r + 1) / ((co + c) c co)
+// so that, after the normalisation,
+//   d(ax)/dh = (r - 1)(r + 1) co^2 / ((r co + c) c)
+//   d(al)/dh = eta co^3 / c + so^2 (r - 1)(r + 1) co^2 / ((co + c) c)
+// with r - 1 = (eta_o - eta) / (1 + eta) formed without cancellation.
+struct RayIntegrand {
+    const Layered *A;
+    double eta_o, so, co;
+    void operator()(double h, double &gx, double &gl) const {
+        const double eta = eta_of(*A, h);
+        const double rm1 = (eta_o - eta) / (1.0 + eta);
+        const double r = 1.0 + rm1;
+        const double s = so * r;
+        const double c = std::sqrt((1.0 - s) * (1.0 + s));
+        const double rr = rm1 * (r + 1.0);
+        const double co2 = co * co;
+        gx = rr * co2 / ((r * co + c) * c);
+        gl = eta * co2 * co / c + so * so * rr * co2 / ((co + c) * c);
+    }
+};
+
+void integrate_piece(const RayIntegrand &f, const GaussLegendre &gl, double lo, double hi,
+                     double &ix, double &il) {
+    const double m = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
+    double sx = 0.0, sl = 0.0;
+    for (int i = 0; i < GaussLegendre::N; ++i) {
+        double gx, gL;
+        f(m + hw * gl.x[i], gx, gL);
+        sx += gl.w[i] * gx;
+        sl += gl.w[i] * gL;
+    }
+    ix = sx * hw;
+    il = sl * hw;
+}
+
+// integral over [lo, hi], split at the layer boundaries inside it
+void integrate(const RayIntegrand &f, const GaussLegendre &gl, double lo, double hi,
+               double &ix, double &il) {
+    ix = il = 0.0;
+    double a = lo;
+    for (int i = 1; i <= 5; ++i) {
+        const double hb = f.A->hb[i];
+        if (hb > a && hb < hi) {
+            double px, pl;
+            integrate_piece(f, gl, a, hb, px, pl);
+            ix += px;
+            il += pl;
+            a = hb;
+        }
+    }
+    double px, pl;
+    integrate_piece(f, gl, a, hi, px, pl);
+    ix += px;
+    il += pl;
+}
+
+bool atm_valid(const cher_atmosphere &atm) {
+    for (int i = 0; i < 5; ++i) {
+        if (!(atm.c[i] > 0.0) || !(atm.b[i] >= 0.0) || !std::isfinite(atm.a[i]) ||
+            !std::isfinite(atm.b[i]) || !std::isfinite(atm.c[i]))
+            return false;
+        if (!(atm.h_bound[i + 1] > atm.h_bound[i])) return false;
+    }
+    if (!std::isfinite(atm.h_bound[0]) || !std::isfinite(atm.h_bound[5])) return false;
+    if (!(atm.n0_minus_1 >= 0.0 && atm.n0_minus_1 < 0.01)) return false;
+    if (!(atm.b[0] > 0.0)) return false;
+    return true;
+}
+
+}  // namespace
+
+double eta_lookup(const HostTables &t, double h) {
+    double hc = h;
+    if (hc < 0.0) hc = 0.0;
+    if (hc > t.h_max) hc = t.h_max;
+    const double x = hc * t.inv_dh;
+    int k = static_cast<int>(x);
+    if (k > t.n_fine - 2) k = t.n_fine - 2;
+    const double f = x - static_cast<double>(k);
+    const double d = t.eta[k + 1] - t.eta[k];
+    const double fd = f * d;
+    return t.eta[k] + fd;
+}
+
+cher_status build_tables(const cher_atmosphere &atm, double h_obs, int32_t n_fine, int32_t H,
+                         int32_t Z, double theta_max, double h_max, HostTables &T) {
+    if (!atm_valid(atm)) return CHER_EINVAL;
+    if (n_fine < 2 || n_fine > (1 << 20)) return CHER_EINVAL;
+    if (H < 2 || H > 65536 || Z < 2 || Z > 4096) return CHER_EINVAL;
+    if (!(theta_max > 0.0) || !(theta_max < 85.0 * kPi / 180.0)) return CHER_EINVAL;
+    if (!std::isfinite(h_obs) || !(h_max > h_obs) || !(h_max <= atm.h_bound[5]) ||
+        !(h_max > 0.0) || h_obs < 0.0)
+        return CHER_EINVAL;
+    const Layered A = make_layered(atm);
+    if (!(A.rho0 > 0.0)) return CHER_EINVAL;
+
+    // fine eta table: h_k = k * dh
+    T.n_fine = n_fine;
+    T.h_max = h_max;
+    T.dh = h_max / static_cast<double>(n_fine - 1);
+    T.inv_dh = 1.0 / T.dh;
+    T.eta.assign(n_fine, 0.0);
+    for (int k = 0; k < n_fine; ++k) {
+        const double h = static_cast<double>(k) * T.dh;
+        T.eta[k] = eta_of(A, h);
+    }
+
+    // refraction tables
+    T.H = H;
+    T.Z = Z;
+    T.theta_max = theta_max;
+    T.dht = (h_max - h_obs) / static_cast<double>(H - 1);
+    T.inv_dht = 1.0 / T.dht;
+    const double smax = std::sin(theta_max);
+    T.q_max = smax * smax;
+    T.dq = T.q_max / static_cast<double>(Z - 1);
+    T.inv_dq = 1.0 / T.dq;
+    T.ax.assign(static_cast<size_t>(H) * Z, 0.0);
+    T.al.assign(static_cast<size_t>(H) * Z, 0.0);
+    const double eta_o = eta_of(A, h_obs);
+    static const GaussLegendre gl;
+
+    auto column = [&](int k) {
+        const double q = static_cast<double>(k) * T.dq;
+        const double so = std::sqrt(q);
+        RayIntegrand f{&A, eta_o, so, std::sqrt((1.0 - so) * (1.0 + so))};
+        double cx = 0.0, cl = 0.0;
+        for (int j = 1; j < H; ++j) {
+            const double lo = h_obs + static_cast<double>(j - 1) * T.dht;
+            const double hi = h_obs + static_cast<double>(j) * T.dht;
+            double ix, il;
+            integrate(f, gl, lo, hi, ix, il);
+            cx += ix;
+            cl += il;
+            T.ax[static_cast<size_t>(j) * Z + k] = cx;
+            T.al[static_cast<size_t>(j) * Z + k] = cl;
+        }
+    };
+    unsigned nthr = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    nthr = std::min<unsigned>(nthr, static_cast<unsigned>(Z));
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < nthr; ++t)
+        pool.emplace_back([&, t] {
+            for (int k = static_cast<int>(t); k < Z; k += static_cast<int>(nthr)) column(k);
+        });
+    for (auto &th : pool) th.join();
+    return CHER_OK;
+}
+
+cher_status build_grid(const cher_telescope *tel, int32_t n_tel, double theta_max,
+                       HostGrid &g) {
+    // A line that crosses sphere k within the zenith range reaches h_obs at
+    // a horizontal distance of at most |z| tan(theta_max) + r / cos(theta_max)
+    // from the centre; a margin covers single-precision ground points.
+    std::vector<double> reach(n_tel);
+    double rmax = 0.0, xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    for (int k = 0; k < n_tel; ++k) {
+        const double mag = std::fabs(tel[k].x) + std::fabs(tel[k].y);
+        reach[k] = std::fabs(tel[k].z) * std::tan(theta_max) + tel[k].r / std::cos(theta_max) +
+                   0.5 + 1e-5 * mag;
+        rmax = std::max(rmax, reach[k]);
+        xmin = std::min(xmin, tel[k].x - reach[k]);
+        xmax = std::max(xmax, tel[k].x + reach[k]);
+        ymin = std::min(ymin, tel[k].y - reach[k]);
+        ymax = std::max(ymax, tel[k].y + reach[k]);
+    }
+    double cs = 2.0 * rmax;
+    for (int attempt = 0; attempt < 24; ++attempt) {
+        const double ex = xmax - xmin, ey = ymax - ymin;
+        const double nxd = std::ceil(ex / cs), nyd = std::ceil(ey / cs);
+        if (nxd * nyd > double(1 << 22)) return CHER_ERANGE;
+        g.nx = std::max(1, static_cast<int>(nxd));
+        g.ny = std::max(1, static_cast<int>(nyd));
+        g.x0 = xmin;
+        g.y0 = ymin;
+        g.cs = cs;
+        g.inv_cs = 1.0 / cs;
+        const size_t nc = static_cast<size_t>(g.nx) * g.ny;
+        std::vector<std::vector<int32_t>> cells(nc);
+        for (int k = 0; k < n_tel; ++k) {
+            const int cx0 = std::max(0, static_cast<int>(std::floor((tel[k].x - reach[k] - g.x0) * g.inv_cs)));
+            const int cx1 = std::min(g.nx - 1, static_cast<int>(std::floor((tel[k].x + reach[k] - g.x0) * g.inv_cs)));
+            const int cy0 = std::max(0, static_cast<int>(std::floor((tel[k].y - reach[k] - g.y0) * g.inv_cs)));
+            const int cy1 = std::min(g.ny - 1, static_cast<int>(std::floor((tel[k].y + reach[k] - g.y0) * g.inv_cs)));
+            for (int cy = cy0; cy <= cy1; ++cy)
+                for (int cx = cx0; cx <= cx1; ++cx) cells[static_cast<size_t>(cy) * g.nx + cx].push_back(k);
+        }
+        size_t worst = 0;
+        for (auto &c : cells) worst = std::max(worst, c.size());
+        if (worst <= static_cast<size_t>(kMaxCandPerCell)) {
+            g.cell_start.assign(nc + 1, 0);
+            g.cell_tel.clear();
+            for (size_t c = 0; c < nc; ++c) {
+                g.cell_start[c] = static_cast<int32_t>(g.cell_tel.size());
+                g.cell_tel.insert(g.cell_tel.end(), cells[c].begin(), cells[c].end());
+            }
+            g.cell_start[nc] = static_cast<int32_t>(g.cell_tel.size());
+            if (g.cell_tel.empty()) g.cell_tel.push_back(0);
+            return CHER_OK;
+        }
+        cs *= 0.5;   // too many spheres share a cell: refine
+        if (cs < 1e-3) break;
+    }
+    return CHER_ERANGE;
+}
+
+}  // namespace cher

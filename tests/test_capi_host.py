@@ -1,0 +1,73 @@
+"""The C-ABI library on a machine without a GPU: it builds, loads, exports
+every symbol include/cher.h declares, rejects bad arguments before touching
+CUDA, and its host table builder agrees with the oracle's tables."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2006_14927_gb300 as P
+import workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    P.build()
+    return P.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    hdr = open(os.path.join(ROOT, "include", "cher.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    declared = set(re.findall(r"\b(cher_[a-z0-9_]+)\s*\(", hdr))
+    assert "cher_generate_propagate" in declared and len(declared) >= 13
+    for name in declared:
+        assert hasattr(L, name), name
+    assert declared == set(P.SIGNATURES)
+
+
+def test_status_strings(L):
+    for code in range(8):
+        assert L.cher_status_string(code)
+    assert L.cher_status_string(99) == b"unknown status"
+
+
+def test_create_rejects_bad_arguments_without_cuda(L):
+    h = ctypes.c_void_p()
+    A = P._binding.atmosphere_struct(workloads.us_standard_atmosphere())
+    T = (P._binding.Telescope * 1)(P._binding.Telescope(0, 0, 0, 12.0))
+    assert L.cher_create(None, 2200.0, T, 1, None, ctypes.byref(h)) == 1
+    assert L.cher_create(ctypes.byref(A), 2200.0, T, 0, None, ctypes.byref(h)) == 1
+    bad = (P._binding.Telescope * 1)(P._binding.Telescope(0, 0, 0, -1.0))
+    assert L.cher_create(ctypes.byref(A), 2200.0, bad, 1, None, ctypes.byref(h)) == 1
+    assert L.cher_build_refraction_tables(None, 10, 10, 70.0, 6e4) == 1
+    assert L.cher_generate_propagate(None, None, 0, 1, None, None) == 1
+    assert L.cher_destroy(None) == 0
+
+
+@pytest.mark.parametrize("H,Z,zen,hmax", [(1000, 64, 70.0, 60000.0), (257, 33, 75.0, 75000.0)])
+def test_host_tables_match_oracle(H, Z, zen, hmax):
+    atm = workloads.us_standard_atmosphere()
+    eta, ax, al = P.build_tables_host(atm, 2200.0, 10000, H, Z, zen, hmax)
+    M = oracle.Model(atm, 2200.0, np.array([[0, 0, 0, 12.0]]), H=H, Z=Z, theta_max_deg=zen,
+                     h_max=hmax)
+    # the fine n table decides bunch counts: it must be bit-identical
+    assert np.array_equal(eta, M.eta_tab)
+    # refraction tables: two independent integrations of the same integrals
+    assert np.max(np.abs(ax - M.ax)) < 1e-9
+    assert np.max(np.abs(al - M.al)) < 1e-9
+
+
+def test_host_tables_reject_bad_ranges():
+    atm = workloads.us_standard_atmosphere()
+    with pytest.raises(P.CherError):
+        P.build_tables_host(atm, 2200.0, 10000, 1, 64, 70.0, 60000.0)
+    with pytest.raises(P.CherError):
+        P.build_tables_host(atm, 2200.0, 10000, 100, 64, 89.0, 60000.0)
+    with pytest.raises(P.CherError):
+        P.build_tables_host(atm, 2200.0, 10000, 100, 64, 70.0, 1000.0)

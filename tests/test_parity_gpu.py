@@ -1,0 +1,202 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Sizes: the small workloads in full, reduced versions of the shower workloads
+that still span many tiles and end in a ragged tile, and the 2e6-step
+vertical 1 TeV shower at full size in the launch configuration the benchmark
+times, where the oracle checks every bunch count and a sample of steps bunch
+by bunch.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2006_14927_gb300 as P
+import workloads
+from parity import (FP32, FP64, compare_hits, compare_trace, compare_yield, context, gpu_hits,
+                    gpu_trace, host_tracks, oracle_model)
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x5EED_1234_ABCD
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    P.build()
+
+
+def _reduced(sc, n, stride=None):
+    """The first n steps of a scenario (or every stride-th one)."""
+    sl = slice(0, n) if stride is None else slice(0, n * stride, stride)
+    sc = dict(sc)
+    sc["tracks"] = {k: np.asarray(v)[sl] for k, v in sc["tracks"].items()}
+    return sc
+
+
+def _full_compare(sc, prec, seed=SEED, cap=200_000):
+    M = oracle_model(sc)
+    ctx = context(sc)
+    tr = host_tracks(sc, prec)
+    o = M.bunches(tr, seed)
+    nb_o, w_o, _, _ = M.segment_yield(tr)
+    g = gpu_trace(ctx, tr, sc["t_ref"], seed, prec)
+    compare_yield(nb_o, g["nb"], w_o, g["w"])
+    rt = compare_trace(M, o, g, prec)
+    code, stats, out = gpu_hits(ctx, tr, sc["t_ref"], seed, prec, cap)
+    assert code == 0
+    rec = out.records()
+    rh = compare_hits(M, o, rec, prec)
+    # the counters add up (conservation of bunches)
+    assert stats[P.STAT_NAMES.index("bunches")] == nb_o.sum()
+    assert stats[3] == stats[4] + stats[5] + stats[6] + stats[7] + stats[8]
+    assert stats[9] == len(rec["tel"])
+    assert stats[0] == len(nb_o)
+    ctx.close()
+    return rt, rh, stats
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_plain_fp64_workload(prec):
+    rt, rh, stats = _full_compare(workloads.plain_fp64(), prec)
+    assert rt["edge_status"] + rt["edge_hit"] < 0.01 * rt["n"]
+    assert rh["n_common"] > 0
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_vertical_shower_reduced(prec):
+    sc = _reduced(workloads.vertical_1tev(n=20_011), 20_011)
+    rt, rh, stats = _full_compare(sc, prec)
+    assert rt["n"] > 100_000
+    assert rh["n_common"] > 100
+    assert rt["edge_status"] + rt["edge_hit"] < 0.01 * rt["n"]
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_inclined_shower_large_tables(prec):
+    sc = workloads.inclined_20tev(n=6_007)
+    rt, rh, stats = _full_compare(sc, prec)
+    assert rt["n"] > 10_000
+
+
+def test_batched_showers_reduced():
+    sc = workloads.batched_256(total=60_000)
+    rt, rh, stats = _full_compare(sc, FP32)
+    assert rt["n"] > 50_000
+
+
+def test_launch_shapes_agree():
+    """Persistent and one-CTA-per-tile launches, every block size: the same
+    records (order inside a telescope aside)."""
+    sc = _reduced(workloads.vertical_1tev(n=5_000), 5_000)
+    ctx = context(sc)
+    tr = host_tracks(sc, FP32)
+    ref = None
+    for launch in [(256, 3), (128, 0), (512, 1), (256, 8), (128, 5)]:
+        code, stats, out = gpu_hits(ctx, tr, sc["t_ref"], SEED, FP32, 50_000, launch=launch)
+        assert code == 0
+        rec = out.records()
+        if ref is None:
+            ref = (rec, stats)
+            continue
+        assert np.array_equal(stats, ref[1])
+        for k in rec:
+            assert np.array_equal(rec[k], ref[0][k]), k
+
+
+def test_track_base_splits_reproduce():
+    """Two calls over halves with track_base give the records of one call."""
+    sc = _reduced(workloads.vertical_1tev(n=3_000), 3_000)
+    ctx = context(sc)
+    tr = host_tracks(sc, FP32)
+    _, st, out = gpu_hits(ctx, tr, sc["t_ref"], SEED, FP32, 50_000)
+    whole = out.records()
+    parts = []
+    for lo, hi in [(0, 1234), (1234, 3000)]:
+        sub = {k: v[lo:hi] for k, v in tr.items()}
+        _, _, o = gpu_hits(ctx, sub, sc["t_ref"], SEED, FP32, 50_000, track_base=lo)
+        parts.append(o.records())
+    cat = {k: np.concatenate([p[k] for p in parts]) for k in whole}
+    order = np.lexsort((cat["key"], cat["tel"]))
+    for k in whole:
+        assert np.array_equal(cat[k][order], whole[k]), k
+
+
+def test_edge_cases():
+    sc = workloads.plain_fp64(n=300)
+    ctx = context(sc)
+    # empty input: nothing launched, counters cleared
+    tr0 = host_tracks(sc, FP32, slice(0, 0))
+    code, stats, out = gpu_hits(ctx, tr0, sc["t_ref"], SEED, FP32, 16)
+    assert code == 0 and stats.sum() == 0 and out.count.sum().item() == 0
+    # a single step, and every step below threshold
+    tr1 = host_tracks(sc, FP32, slice(0, 1))
+    code, stats, _ = gpu_hits(ctx, tr1, sc["t_ref"], SEED, FP32, 16)
+    assert code == 0 and stats[0] == 1
+    low = host_tracks(sc, FP32)
+    low["ekin"] = np.full(len(low["ekin"]), 5.0)
+    code, stats, out = gpu_hits(ctx, low, sc["t_ref"], SEED, FP32, 16)
+    assert code == 0 and stats[1] == 0 and stats[3] == 0
+    # invalid fields are counted, not propagated
+    bad = host_tracks(sc, FP32)
+    bad["len"][::7] = np.nan
+    bad["ekin"][3::11] = -1.0
+    bad["x0"][5::13] = np.inf
+    bad["uy"][2::17] = np.nan
+    code, stats, _ = gpu_hits(ctx, bad, sc["t_ref"], SEED, FP32, 4096)
+    n_bad = np.sum(~np.isfinite(bad["len"]) | (bad["ekin"] <= 0) | ~np.isfinite(bad["x0"])
+                   | ~np.isfinite(bad["uy"]))
+    assert stats[2] == n_bad
+    # capacity overflow: counted, never written past the buffer
+    full = host_tracks(workloads.plain_fp64(n=1000), FP32)
+    code, stats, out = gpu_hits(ctx, full, sc["t_ref"], SEED, FP32, 2)
+    cnt = out.count.cpu().numpy()
+    if cnt.max() > 2:
+        assert code == 6
+        assert stats[10] == np.maximum(cnt - 2, 0).sum()
+    # a NULL track list is rejected before any launch
+    assert P.lib().cher_generate_propagate(ctx._h, None, 0, 1, None, None) == 1
+    ctx.close()
+
+
+def test_full_size_vertical_shower_sampled():
+    """2e6 steps (the benchmark's workload and launch shape): every bunch
+    count against the oracle, and every crossing of 400 sampled steps."""
+    sc = workloads.vertical_1tev()
+    M = oracle_model(sc)
+    ctx = context(sc)
+    tr = host_tracks(sc, FP32)
+    import torch
+    dev = P.device_tracks(tr, FP32, t_ref=sc["t_ref"])
+    nb_g, w_g = ctx.segment_yield(dev, FP32)
+    nb_o, w_o, _, _ = M.segment_yield(tr)
+    compare_yield(nb_o, nb_g.cpu().numpy(), w_o, w_g.cpu().numpy())
+    out = ctx.alloc_hits(2_000_000, FP32)
+    ctx.generate_propagate(dev, SEED, FP32, out)
+    code, stats = ctx.sync_status(out)
+    assert code == 0
+    assert stats[3] == nb_o.sum()
+    rec = out.records()
+    assert stats[9] == len(rec["tel"])
+    rng = np.random.default_rng(17)
+    sample = np.sort(rng.choice(len(nb_o), 400, replace=False))
+    sub = {k: v[sample] for k, v in tr.items()}
+    # the oracle must see the same global step indices: run it per step
+    o_all = []
+    for i in sample:
+        one = {k: v[i:i + 1] for k, v in tr.items()}
+        o_all.append(M.bunches(one, SEED, track_base=int(i)))
+    keys = set()
+    for i, o in zip(sample, o_all):
+        j = o["j"]
+        keys |= set(((np.uint64(i) << np.uint64(32)) | j.astype(np.uint64)).tolist())
+    sel = np.array([k in keys for k in rec["key"].tolist()], bool)
+    grec = {k: v[sel] for k, v in rec.items()}
+    got = 0
+    for i, o in zip(sample, o_all):
+        kk = set(((np.uint64(i) << np.uint64(32)) | o["j"].astype(np.uint64)).tolist())
+        m = np.array([k in kk for k in grec["key"].tolist()], bool)
+        r = compare_hits(M, o, {k: v[m] for k, v in grec.items()}, FP32, track_base=int(i))
+        got += r["n_common"]
+    assert got > 0
+    torch.cuda.synchronize()
+    ctx.close()
