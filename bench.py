@@ -190,14 +190,16 @@ def run_ours(args):
     ctx = P.Context(sc["atm"], sc["h_obs"], sc["telescopes"])
     ctx.build_refraction_tables(sc["H"], sc["Z"], sc["theta_max_deg"], sc["h_max"])
     table_s = time.perf_counter() - t0
-    cap = 600_000
+    cap = args.cap
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def measure(prec, steps, warmup, autotune):
         dtr = P.device_tracks(sc["tracks"], prec, device=dev, t_ref=sc["t_ref"])
         out = ctx.alloc_hits(cap, prec, device=dev)
-        if autotune:
+        if autotune and args.launch is None:
             ctx.autotune(dtr, 11, prec, out)
+        elif args.launch is not None:
+            ctx.set_launch(*(int(v) for v in args.launch.split(",")))
         for _ in range(warmup):
             ctx.generate_propagate(dtr, 11, prec, out, track_base=track_base)
         code, stats = ctx.sync_status(out)
@@ -225,6 +227,25 @@ def run_ours(args):
         r32 = measure(P.CHER_FP32_BULK, steps, warmup, autotune=True)
     clocks = clk.summary()
     launch = ctx.get_launch()
+    if args.sweep and rank == 0:
+        for shape in [(128, 1), (128, 2), (128, 4), (128, 6), (256, 1), (256, 2), (256, 3),
+                      (256, 4), (512, 1), (512, 2), (128, 0), (256, 0)]:
+            args.launch = f"{shape[0]},{shape[1]}"
+            r = measure(P.CHER_FP32_BULK, 5, 2, autotune=False)
+            t = statistics.median(r["ms"])
+            print(json.dumps({"sweep": shape, "ms": t,
+                              "bunches_per_s": float(r["stats"][3]) / (t / 1e3)}), flush=True)
+        args.launch = f"{launch[0]},{launch[1]}"
+        ctx.set_launch(*launch)
+    if args.quick:
+        t = sum(r32["ms"]) / 1e3
+        if rank == 0:
+            print(json.dumps({"quick": True, "value": float(r32["stats"][3]) * len(r32["ms"]) / t,
+                              "unit": UNIT, "ms_per_step": 1e3 * t / len(r32["ms"]),
+                              "launch": launch, "clocks": clocks}), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     r64 = measure(P.CHER_FP64, max(3, steps // 4), max(3, min(warmup, 3)), autotune=False)
 
     def total(r):
@@ -375,6 +396,12 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--quick", action="store_true",
+                    help="FP32 device timing only (no FP64, end-to-end or CPU legs)")
+    ap.add_argument("--launch", default=None,
+                    help="block,ctas_per_sm instead of the autotuner's choice")
+    ap.add_argument("--cap", type=int, default=600_000, help="records per telescope")
+    ap.add_argument("--sweep", action="store_true", help="time a set of launch shapes")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

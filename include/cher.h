@@ -196,6 +196,22 @@ cher_status cher_generate_propagate(cher_ctx *ctx, const cher_tracks *tracks,
                                     uint64_t seed, cher_precision prec,
                                     const cher_output *out, void *stream);
 
+/* A cher_generate_propagate call captured once into an executable CUDA
+ * graph (the counter clears and the persistent kernel), for replaying the
+ * same batch of showers with one launch (the batched, graph-captured launch
+ * of the independent-shower parallelism of section 2).  The graph keeps the
+ * pointers of `tracks` and `out`: the caller keeps those buffers alive and
+ * may change their contents between launches, not their addresses.
+ * Errors as cher_generate_propagate; CHER_ECUDA if capture fails. */
+typedef struct cher_graph cher_graph;
+cher_status cher_graph_create(cher_ctx *ctx, const cher_tracks *tracks, uint64_t seed,
+                              cher_precision prec, const cher_output *out,
+                              cher_graph **graph);
+/* Launch the captured graph on `stream` (asynchronous). */
+cher_status cher_graph_launch(cher_graph *graph, void *stream);
+/* Release the graph (NULL is accepted). */
+cher_status cher_graph_destroy(cher_graph *graph);
+
 /* Synchronise `stream`, read out->stats and report CHER_EOVERFLOW if a
  * telescope buffer overflowed during the last call, else CHER_OK (or
  * CHER_ECUDA if the stream reports an error).  stats_host (optional,

@@ -82,6 +82,10 @@ SIGNATURES = {
     "cher_destroy": (_S, [_P]),
     "cher_generate_propagate": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
                                      ctypes.POINTER(Output), _P]),
+    "cher_graph_create": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
+                               ctypes.POINTER(Output), ctypes.POINTER(_P)]),
+    "cher_graph_launch": (_S, [_P, _P]),
+    "cher_graph_destroy": (_S, [_P]),
     "cher_sync_status": (_S, [_P, ctypes.POINTER(Output), ctypes.POINTER(ctypes.c_ulonglong), _P]),
     "cher_set_launch": (_S, [_P, ctypes.c_int32, ctypes.c_int32]),
     "cher_get_launch": (_S, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
@@ -341,6 +345,17 @@ class Context:
                "cher_trace_bunches")
         return dict(pos=pos, tim=tim, status=status, nhit=nhit, first_hit=first)
 
+    def graph(self, dev_tracks: dict, seed: int, precision: int, out: HitBuffers,
+              track_base: int = 0) -> "Graph":
+        """Capture one generate_propagate call into a CUDA graph."""
+        t = self.tracks_struct(dev_tracks, track_base)
+        o = out.struct()
+        h = ctypes.c_void_p()
+        _check(lib().cher_graph_create(self._h, ctypes.byref(t), ctypes.c_uint64(seed),
+                                       int(precision), ctypes.byref(o), ctypes.byref(h)),
+               "cher_graph_create")
+        return Graph(h, (dev_tracks, out))
+
     def autotune(self, dev_tracks: dict, seed: int, precision: int, out: HitBuffers,
                  cache_path: str | None = None, stream=None):
         t = self.tracks_struct(dev_tracks)
@@ -350,3 +365,26 @@ class Context:
                                    cache_path.encode() if cache_path else None,
                                    ctypes.c_void_p(_stream_ptr(stream))), "cher_autotune")
         return self.get_launch()
+
+
+class Graph:
+    """An executable CUDA graph of one generate_propagate call."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep            # the buffers the graph points into
+
+    def launch(self, stream=None):
+        _check(lib().cher_graph_launch(self._h, ctypes.c_void_p(_stream_ptr(stream))),
+               "cher_graph_launch")
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().cher_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

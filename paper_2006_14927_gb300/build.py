@@ -27,10 +27,15 @@ def nvcc() -> str:
 
 def _flags(src: str):
     f = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo"] + ARCH
-    if src.endswith(".cu"):
-        f += ["-Xptxas", "-v"] if os.environ.get("CHER_PTXAS_VERBOSE") else []
-    else:
-        f += ["-x", "c++"]
+    if not src.endswith(".cu"):
+        return f + ["-x", "c++"]
+    if os.environ.get("CHER_PTXAS_VERBOSE"):
+        f += ["-Xptxas", "-v"]
+    if src == "cher_kernels.cu":
+        # single-precision division and square root by the hardware
+        # approximations (<= 2 ulp); double precision is unaffected and the
+        # FP64 yield uses explicitly rounded intrinsics
+        f += ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
     return f
 
 

@@ -125,6 +125,7 @@ cher::KParams base_params(const cher_ctx *c, const cher_tracks *t, uint64_t seed
     p.inv_gcs = c->G.inv_cs;
     p.cell_start = c->d_cell_start;
     p.cell_tel = c->d_cell_tel;
+    cher::fill_float_constants(p);
     return p;
 }
 
@@ -431,7 +432,7 @@ cher_status cher_autotune(cher_ctx *c, const cher_tracks *t, uint64_t seed, cher
     if (!c->built) return CHER_ESTATE;
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) return CHER_ECUDA;
-    char tag[256];
+    char tag[512];
     const long long tiles_bucket = static_cast<long long>(std::log2(double(t->n) + 1.0));
     std::snprintf(tag, sizeof(tag), "%s|%d|%lld|%d|%d", prop.name, static_cast<int>(prec),
                   tiles_bucket, static_cast<int>(c->tel.size()), c->T.Z);
@@ -501,3 +502,69 @@ cher_status cher_autotune(cher_ctx *c, const cher_tracks *t, uint64_t seed, cher
 }
 
 }  // extern "C"
+
+struct cher_graph {
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" cher_status cher_graph_destroy(cher_graph *g) {
+    if (!g) return CHER_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+    return CHER_OK;
+}
+
+extern "C" cher_status cher_graph_create(cher_ctx *c, const cher_tracks *t, uint64_t seed,
+                                         cher_precision prec, const cher_output *out,
+                                         cher_graph **graph) {
+    if (!graph) return CHER_EINVAL;
+    *graph = nullptr;
+    if (!c || !out || !tracks_ok(t)) return CHER_EINVAL;
+    if (!c->built) return CHER_ESTATE;
+    cher_graph *g = new (std::nothrow) cher_graph;
+    if (!g) return CHER_ENOMEM;
+    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete g;
+        return CHER_ECUDA;
+    }
+    // a first uncaptured call sets the kernel attributes and checks arguments
+    cher_status s = cher_generate_propagate(c, t, seed, prec, out, g->stream);
+    if (s == CHER_OK && cudaStreamSynchronize(g->stream) != cudaSuccess) s = CHER_ECUDA;
+    if (s != CHER_OK) {
+        cher_graph_destroy(g);
+        return s;
+    }
+    if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaGetLastError();
+        cher_graph_destroy(g);
+        return CHER_ECUDA;
+    }
+    s = cher_generate_propagate(c, t, seed, prec, out, g->stream);
+    const cudaError_t e = cudaStreamEndCapture(g->stream, &g->graph);
+    if (s != CHER_OK || e != cudaSuccess || !g->graph) {
+        cudaGetLastError();
+        cher_graph_destroy(g);
+        return s != CHER_OK ? s : CHER_ECUDA;
+    }
+    if (cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cher_graph_destroy(g);
+        return CHER_ECUDA;
+    }
+    *graph = g;
+    return CHER_OK;
+}
+
+extern "C" cher_status cher_graph_launch(cher_graph *g, void *stream) {
+    if (!g || !g->exec) return CHER_EINVAL;
+    if (cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        cudaGetLastError();
+        return CHER_ECUDA;
+    }
+    return CHER_OK;
+}

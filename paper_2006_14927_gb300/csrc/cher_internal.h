@@ -99,7 +99,16 @@ struct KParams {
     // scheduling
     unsigned long long *tile_counter;     // NULL: one CTA per tile
     int64_t n_tiles;
+    // the per-launch constants of the bunch loop, rounded to float on the
+    // host: the FP32 path converts nothing from double on the device
+    struct {
+        float h_obs, dH_max, eta_o, inv_np1o, np1o, q_max, inv_dht, inv_dq, inv_dh;
+        float lam_inv1, lam_dinv, gx0, gy0, inv_gcs;
+    } f;
 };
+
+// Fill KParams::f from the double fields.
+void fill_float_constants(KParams &p);
 
 enum Mode : int { MODE_HITS = 0, MODE_TRACE = 1, MODE_YIELD = 2 };
 

@@ -68,7 +68,14 @@ struct Yield {
     double N, s2, g, gam, eta;
 };
 
-__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
+// finiteness from the exponent bits: integer ops only (GB300's FP64 pipe is
+// about 1/64 of the FP32 rate, so the per-step code keeps off it where it can)
+__device__ __forceinline__ bool finite_d(double v) {
+    return (__double2hiint(v) & 0x7ff00000) != 0x7ff00000;
+}
+__device__ __forceinline__ bool finite_f(float v) {
+    return (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u;
+}
 
 __device__ __forceinline__ double eta_exact_lookup(const KParams &p, double h) {
     double hc = h;
@@ -86,10 +93,16 @@ __device__ __forceinline__ double eta_exact_lookup(const KParams &p, double h) {
 
 // A step emits only if every field is finite, len >= 0 and ekin > 0.
 template <class R>
+__device__ __forceinline__ bool finite_r(R v) {
+    if constexpr (std::is_same<R, float>::value) return finite_f(v);
+    else return finite_d(v);
+}
+
+template <class R>
 __device__ __forceinline__ bool step_valid(const KParams &p, int64_t i) {
     return finite_d(__ldg(p.x0 + i)) && finite_d(__ldg(p.y0 + i)) && finite_d(__ldg(p.t0 + i)) &&
-           finite_d(static_cast<double>(__ldg(static_cast<const R *>(p.ux) + i))) &&
-           finite_d(static_cast<double>(__ldg(static_cast<const R *>(p.uy) + i)));
+           finite_r<R>(__ldg(static_cast<const R *>(p.ux) + i)) &&
+           finite_r<R>(__ldg(static_cast<const R *>(p.uy) + i));
 }
 
 __device__ __forceinline__ void step_yield(const KParams &p, bool others_valid, double z0,
@@ -154,10 +167,9 @@ __device__ __forceinline__ R load_dir(const void *p, int64_t i) {
 
 template <class R>
 __device__ __forceinline__ void prep_step(const KParams &p, int64_t i, const Yield &y, Seg<R> &S) {
-    const double ux = static_cast<double>(load_dir<R>(p.ux, i));
-    const double uy = static_cast<double>(load_dir<R>(p.uy, i));
-    const double uz = static_cast<double>(load_dir<R>(p.uz, i));
-    const double len = __ldg(p.len + i);
+    const R ux = load_dir<R>(p.ux, i);
+    const R uy = load_dir<R>(p.uy, i);
+    const R uz = load_dir<R>(p.uz, i);
     double t_ref = 0.0;
     if (p.t_ref) {
         const uint32_t sh = p.shower ? __ldg(p.shower + i) : 0u;
@@ -165,39 +177,44 @@ __device__ __forceinline__ void prep_step(const KParams &p, int64_t i, const Yie
     }
     S.nb = y.nb;
     S.pad = 0;
-    S.ux = static_cast<R>(ux);
-    S.uy = static_cast<R>(uy);
-    S.uz = static_cast<R>(uz);
-    S.L = static_cast<R>(len);
+    S.ux = ux;
+    S.uy = uy;
+    S.uz = uz;
+    S.L = static_cast<R>(__ldg(p.len + i));
     S.x0 = static_cast<R>(__ldg(p.x0 + i));
     S.y0 = static_cast<R>(__ldg(p.y0 + i));
+    // the two absolute differences stay in FP64 (tens of km, ~1e5 ns)
     S.dz0 = static_cast<R>(__ldg(p.z0 + i) - p.h_obs);
     S.tseg = static_cast<R>(__ldg(p.t0 + i) - t_ref);
     // azimuth basis around the step: e1 horizontal, e2 = d x e1
     R e1x, e1y;
-    const R rho2 = S.ux * S.ux + S.uy * S.uy;
+    const R rho2 = ux * ux + uy * uy;
     if (rho2 > R(1e-20)) {
         const R inv = R(1) / sqrt(rho2);
-        e1x = -S.uy * inv;
-        e1y = S.ux * inv;
+        e1x = -uy * inv;
+        e1y = ux * inv;
     } else {
         e1x = R(1);
         e1y = R(0);
     }
     S.e1x = e1x;
     S.e1y = e1y;
-    S.e2x = -S.uz * e1y;
-    S.e2y = S.uz * e1x;
-    S.e2z = S.ux * e1y - S.uy * e1x;
+    S.e2x = -uz * e1y;
+    S.e2y = uz * e1x;
+    S.e2z = ux * e1y - uy * e1x;
     if (y.nb > 0) {
         // beta = sqrt(g (2 + g)) / gamma ; cos = 1 / (beta n) ; sin = sqrt(s2)
-        const R bg = sqrt(static_cast<R>(y.g * (2.0 + y.g)));
-        const R beta = bg / static_cast<R>(y.gam);
-        S.cosc = R(1) / (beta * static_cast<R>(1.0 + y.eta));
+        const R g = static_cast<R>(y.g);
+        const R beta = sqrt(g * (R(2) + g)) / (R(1) + g);
+        const R inv_nb = R(1) / static_cast<R>(y.nb);
+        S.cosc = R(1) / (beta * (R(1) + static_cast<R>(y.eta)));
         S.sinc = sqrt(static_cast<R>(y.s2));
-        S.inv_nb = R(1) / static_cast<R>(y.nb);
+        S.inv_nb = inv_nb;
         S.inv_bc = R(1) / (beta * R(kC));
-        S.w = static_cast<R>(y.N / static_cast<double>(y.nb));
+        if constexpr (std::is_same<R, float>::value)
+            S.w = static_cast<float>(y.N) * inv_nb;
+        else
+            S.w = y.N / static_cast<double>(y.nb);
     } else {
         S.cosc = S.sinc = S.inv_nb = S.inv_bc = S.w = R(0);
     }
@@ -215,6 +232,7 @@ struct BunchOut {
 template <class R>
 struct Consts {
     R h_obs, dH_max, eta_o, inv_np1o, q_max, inv_dht, inv_dq, inv_dh, lam_inv1, lam_dinv;
+    R gx0, gy0, inv_gcs;
     int H, Z, n_fine;
 };
 
@@ -338,11 +356,12 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
 // Candidate spheres of the bunch's grid cell: bit m of the mask is cell
 // entry s0 + m.
 template <class R>
-__device__ __forceinline__ unsigned sphere_hits(const KParams &p, const BunchOut<R> &o, int &s0) {
+__device__ __forceinline__ unsigned sphere_hits(const KParams &p, const Consts<R> &c,
+                                                const BunchOut<R> &o, int &s0) {
     s0 = 0;
     if (o.status != ST_GROUND) return 0u;
-    const R gx = (o.X - static_cast<R>(p.gx0)) * static_cast<R>(p.inv_gcs);
-    const R gy = (o.Y - static_cast<R>(p.gy0)) * static_cast<R>(p.inv_gcs);
+    const R gx = (o.X - c.gx0) * c.inv_gcs;
+    const R gy = (o.Y - c.gy0) * c.inv_gcs;
     if (!(gx >= R(0)) || !(gy >= R(0)) || !(gx < static_cast<R>(p.gnx)) ||
         !(gy < static_cast<R>(p.gny)))
         return 0u;
@@ -421,20 +440,41 @@ __global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     Consts<R> c;
-    c.h_obs = static_cast<R>(p.h_obs);
-    c.dH_max = static_cast<R>(p.h_max - p.h_obs);
-    c.eta_o = static_cast<R>(p.eta_obs);
-    c.inv_np1o = static_cast<R>(1.0 / (1.0 + p.eta_obs));
-    c.q_max = static_cast<R>(p.q_max);
-    c.inv_dht = static_cast<R>(p.inv_dht);
-    c.inv_dq = static_cast<R>(p.inv_dq);
-    c.inv_dh = static_cast<R>(p.inv_dh);
-    c.lam_inv1 = static_cast<R>(p.lam_inv1);
-    c.lam_dinv = static_cast<R>(p.lam_dinv);
+    R np1o;
+    if constexpr (std::is_same<R, float>::value) {
+        c.h_obs = p.f.h_obs;
+        c.dH_max = p.f.dH_max;
+        c.eta_o = p.f.eta_o;
+        c.inv_np1o = p.f.inv_np1o;
+        c.q_max = p.f.q_max;
+        c.inv_dht = p.f.inv_dht;
+        c.inv_dq = p.f.inv_dq;
+        c.inv_dh = p.f.inv_dh;
+        c.lam_inv1 = p.f.lam_inv1;
+        c.lam_dinv = p.f.lam_dinv;
+        c.gx0 = p.f.gx0;
+        c.gy0 = p.f.gy0;
+        c.inv_gcs = p.f.inv_gcs;
+        np1o = p.f.np1o;
+    } else {
+        c.h_obs = p.h_obs;
+        c.dH_max = p.h_max - p.h_obs;
+        c.eta_o = p.eta_obs;
+        c.inv_np1o = 1.0 / (1.0 + p.eta_obs);
+        c.q_max = p.q_max;
+        c.inv_dht = p.inv_dht;
+        c.inv_dq = p.inv_dq;
+        c.inv_dh = p.inv_dh;
+        c.lam_inv1 = p.lam_inv1;
+        c.lam_dinv = p.lam_dinv;
+        c.gx0 = p.gx0;
+        c.gy0 = p.gy0;
+        c.inv_gcs = p.inv_gcs;
+        np1o = 1.0 + p.eta_obs;
+    }
     c.H = p.H;
     c.Z = p.Z;
     c.n_fine = p.n_fine;
-    const R np1o = static_cast<R>(1.0 + p.eta_obs);
 
     unsigned st_steps = 0, st_emit = 0, st_inval = 0, st_bunch = 0, st_up = 0, st_below = 0,
              st_above = 0, st_angle = 0, st_ground = 0, st_hits = 0, st_over = 0;
@@ -522,7 +562,7 @@ __global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
                 st_ground += o.status == ST_GROUND;
             }
             int s0 = 0;
-            unsigned hm = live ? sphere_hits<R>(p, o, s0) : 0u;
+            unsigned hm = live ? sphere_hits<R>(p, c, o, s0) : 0u;
             st_hits += __popc(hm);
             if constexpr (MODE == MODE_TRACE) {
                 if (live) {
@@ -638,6 +678,23 @@ const void *pick_kernel(bool fp32, int block, int mode) {
 }
 
 }  // namespace
+
+void fill_float_constants(KParams &p) {
+    p.f.h_obs = static_cast<float>(p.h_obs);
+    p.f.dH_max = static_cast<float>(p.h_max - p.h_obs);
+    p.f.eta_o = static_cast<float>(p.eta_obs);
+    p.f.inv_np1o = static_cast<float>(1.0 / (1.0 + p.eta_obs));
+    p.f.np1o = static_cast<float>(1.0 + p.eta_obs);
+    p.f.q_max = static_cast<float>(p.q_max);
+    p.f.inv_dht = static_cast<float>(p.inv_dht);
+    p.f.inv_dq = static_cast<float>(p.inv_dq);
+    p.f.inv_dh = static_cast<float>(p.inv_dh);
+    p.f.lam_inv1 = static_cast<float>(p.lam_inv1);
+    p.f.lam_dinv = static_cast<float>(p.lam_dinv);
+    p.f.gx0 = static_cast<float>(p.gx0);
+    p.f.gy0 = static_cast<float>(p.gy0);
+    p.f.inv_gcs = static_cast<float>(p.inv_gcs);
+}
 
 size_t kernel_smem_bytes(bool fp32, int block, const KParams &p) {
     if (fp32) {

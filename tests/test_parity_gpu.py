@@ -200,3 +200,29 @@ def test_full_size_vertical_shower_sampled():
     assert got > 0
     torch.cuda.synchronize()
     ctx.close()
+
+
+def test_graph_capture_replays_the_call():
+    """A captured graph of the whole call gives the direct call's records,
+    launch after launch."""
+    sc = workloads.batched_256(total=20_000)
+    ctx = context(sc)
+    tr = host_tracks(sc, FP32)
+    _, st_ref, out = gpu_hits(ctx, tr, sc["t_ref"], SEED, FP32, 50_000)
+    ref = out.records()
+    import torch
+    dev = P.device_tracks(tr, FP32, t_ref=sc["t_ref"])
+    out2 = ctx.alloc_hits(50_000, FP32)
+    g = ctx.graph(dev, SEED, FP32, out2)
+    for _ in range(3):
+        out2.count.zero_()
+        g.launch()
+        code, st = ctx.sync_status(out2)
+        assert code == 0
+        assert np.array_equal(st, st_ref)
+        rec = out2.records()
+        for k in ref:
+            assert np.array_equal(rec[k], ref[k]), k
+    g.close()
+    torch.cuda.synchronize()
+    ctx.close()
