@@ -196,6 +196,28 @@ cher_status cher_generate_propagate(cher_ctx *ctx, const cher_tracks *tracks,
                                     uint64_t seed, cher_precision prec,
                                     const cher_output *out, void *stream);
 
+/* The same hot path as cher_generate_propagate (same kernel, same results)
+ * for callers that must not allocate device memory when they run it: code
+ * that runs while a stream of the process is being captured into a CUDA
+ * graph in global mode (where cudaMalloc is refused), pipelines whose device
+ * memory is all held by another allocator (a framework's caching pool), and
+ * real-time loops that forbid allocation after start-up.  The paper has no
+ * counterpart.  The context must have been created and its tables built
+ * beforehand; this call allocates nothing and does not use the context's own
+ * scratch word.  The persistent kernel's only scratch, its 8-byte tile
+ * counter, lives in a fixed 256-byte device array compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ * The first call on each device looks the array's device address up (with
+ * that device current), so make that first call before any stream capture.
+ * Every call shares the array and clears the counter before its launch:
+ * calls that overlap on the GPU (different streams, or several contexts)
+ * race on it and must be serialised by the caller.  A step count above
+ * 2^40, the library-wide limit, is refused with CHER_ERANGE before anything
+ * is launched.  Other errors as cher_generate_propagate. */
+cher_status cher_generate_propagate_noalloc(cher_ctx *ctx, const cher_tracks *tracks,
+                                            uint64_t seed, cher_precision prec,
+                                            const cher_output *out, void *stream);
+
 /* A cher_generate_propagate call captured once into an executable CUDA
  * graph (the counter clears and the persistent kernel), for replaying the
  * same batch of showers with one launch (the batched, graph-captured launch

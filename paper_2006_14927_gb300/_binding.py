@@ -82,6 +82,8 @@ SIGNATURES = {
     "cher_destroy": (_S, [_P]),
     "cher_generate_propagate": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
                                      ctypes.POINTER(Output), _P]),
+    "cher_generate_propagate_noalloc": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
+                                             ctypes.POINTER(Output), _P]),
     "cher_graph_create": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
                                ctypes.POINTER(Output), ctypes.POINTER(_P)]),
     "cher_graph_launch": (_S, [_P, _P]),

@@ -568,3 +568,109 @@ extern "C" cher_status cher_graph_launch(cher_graph *g, void *stream) {
     }
     return CHER_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Entry point that allocates nothing (no counterpart in the paper).
+//
+// The persistent kernel needs one word of scratch: the counter its CTAs
+// take tiles from.  cher_generate_propagate uses a word the context
+// allocated with cudaMalloc; this variant uses a fixed array compiled into
+// the library instead, so the call itself never allocates.  Every GPU that
+// loads the library holds the array until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = 256;
+static __device__ __align__(256) unsigned long long
+    g_static_scratch[kStaticScratchBytes / sizeof(unsigned long long)];
+
+// Clears the words a call uses.  Naming the array in device code also keeps
+// it in the module (an unreferenced file-scope array may be dropped).
+__global__ void k_clear_static_scratch(int words) {
+    if (static_cast<int>(threadIdx.x) < words) g_static_scratch[threadIdx.x] = 0ull;
+}
+
+// Device address of g_static_scratch on each device, looked up once per
+// device with that device current (host code may not use the symbol itself:
+// on the host it names a stand-in, not device memory).
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void *g_static_addr[kMaxDevices] = {};
+
+cher_status static_scratch(int device, unsigned long long **out) {
+    if (device < 0 || device >= kMaxDevices) return CHER_ERANGE;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_addr[device]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return CHER_ECUDA;
+        }
+        g_static_addr[device] = ptr;
+    }
+    *out = static_cast<unsigned long long *>(g_static_addr[device]);
+    return CHER_OK;
+}
+
+}  // namespace
+
+extern "C" cher_status cher_generate_propagate_noalloc(cher_ctx *c, const cher_tracks *t,
+                                                       uint64_t seed, cher_precision prec,
+                                                       const cher_output *out, void *stream) {
+    if (!c || !out || !t) return CHER_EINVAL;
+    // one 8-byte tile counter of the fixed array; tile indices beyond the
+    // library-wide step limit are refused before anything is launched
+    const size_t need = sizeof(unsigned long long);
+    if (need > kStaticScratchBytes) return CHER_ERANGE;
+    if (t->n > (int64_t(1) << 40) || t->track_base > (int64_t(1) << 40)) return CHER_ERANGE;
+    if (!tracks_ok(t)) return CHER_EINVAL;
+    if (prec != CHER_FP64 && prec != CHER_FP32_BULK) return CHER_EINVAL;
+    if (!c->built) return CHER_ESTATE;
+    if (!check_device(c)) return CHER_EINVAL;
+    if (bad_ptr(out->count) || bad_ptr(out->stats) || out->cap_per_tel < 0) return CHER_EINVAL;
+    if (out->cap_per_tel > 0 && (bad_ptr(out->pos) || bad_ptr(out->tim) || bad_ptr(out->key)))
+        return CHER_EINVAL;
+    if (reinterpret_cast<uintptr_t>(out->pos) % 16 || reinterpret_cast<uintptr_t>(out->tim) % 16)
+        return CHER_EINVAL;
+    unsigned long long *scratch = nullptr;
+    cher_status s = static_scratch(c->device, &scratch);
+    if (s != CHER_OK) return s;
+
+    const bool fp32 = prec == CHER_FP32_BULK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(out->count, 0, c->tel.size() * sizeof(unsigned long long), st) !=
+            cudaSuccess ||
+        cudaMemsetAsync(out->stats, 0, CHER_NSTATS * sizeof(unsigned long long), st) !=
+            cudaSuccess)
+        return CHER_ECUDA;
+    cher::KParams p = base_params(c, t, seed, fp32);
+    p.pos = out->pos;
+    p.tim = out->tim;
+    p.key = out->key;
+    p.cap = out->cap_per_tel;
+    p.count = out->count;
+    p.stats = out->stats;
+    const int block = c->block;
+    p.n_tiles = (p.n + block - 1) / block;
+    if (p.n_tiles == 0) return CHER_OK;
+    const size_t smem = cher::kernel_smem_bytes(fp32, block, p);
+    if (cher::kernel_prepare(fp32, block, cher::MODE_HITS, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return CHER_ERANGE;
+    }
+    const int fit = cher::kernel_max_ctas_per_sm(fp32, block, cher::MODE_HITS, smem);
+    const int per_sm = std::max(1, std::min(c->ctas_per_sm > 0 ? c->ctas_per_sm : 1, fit));
+    const int grid =
+        static_cast<int>(std::min<int64_t>(p.n_tiles, int64_t(per_sm) * c->num_sms));
+    // the array keeps the previous call's contents: clear the counter first
+    k_clear_static_scratch<<<1, 32, 0, st>>>(static_cast<int>(need / sizeof(unsigned long long)));
+    if (cudaGetLastError() != cudaSuccess) return CHER_ECUDA;
+    p.tile_counter = scratch;
+    if (cher::kernel_launch(fp32, block, cher::MODE_HITS, grid, smem, p, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return CHER_ECUDA;
+    }
+    return CHER_OK;
+}
