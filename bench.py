@@ -33,6 +33,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Cherenkov bunches generated+propagated/s (FP32 vs FP64 path), % of roofline"
+WORKLOAD_TEXT = {
+    "vertical_1tev": "vertical_1tev: 1 TeV vertical gamma-like shower, 2e6 e+- steps per GPU, "
+                     "19 spheres (R 6-12 m, hex 120 m), tables 1000 x 64 to 70 deg, h_obs 2.2 km",
+    "inclined_20tev": "inclined_20tev: 20 TeV shower at 60 deg zenith, 1e8 steps per GPU, "
+                      "100 spheres over 2 x 2 km, tables 4000 x 256 to 75 deg",
+    "batched_256": "batched_256: 256 showers (10 GeV - 10 TeV, zenith 0-40 deg), 2e8 steps per "
+                   "GPU in one persistent launch, 100 spheres over 2 x 2 km",
+}
 UNIT = "bunches/s"
 WORKLOAD = "vertical_1tev"
 
@@ -42,19 +50,24 @@ WORKLOAD = "vertical_1tev"
 # stage; per emitting step, the FP64 operations of the yield.
 # ---------------------------------------------------------------------------
 OPS_PER_BUNCH_FP32 = {
+    "sub_step_loop": 2,
     "philox4x32_10": 98,        # 10 x (2 mul.lo + 2 mul.hi + 4 xor) + 9 x 2 key adds
     "deviates": 9,              # 3 x (shift, convert, fma)
-    "emission": 33,             # sub-step fraction, sincospi(2u), cone rotation, lambda
-    "drops_and_snell": 26,      # height, checks, n(h) lookup, ratio, sin^2, sqrt
-    "tables": 22,               # two indices, two fractions, 2 x 3 lerps
-    "ground_point_time": 24,    # sec, tan, offsets, X, Y, t, direction cosines
-    "grid_and_spheres": 24,     # cell index + bounds, one sphere test (cross product)
-    "bunch_slot": 20,           # binary search over 256 tile offsets
+    "emission": 36,             # sub-step fraction, sin/cos of the azimuth, cone, lambda, height
+    "rare_conditions": 3,
+    "n_lookup_snell": 17,       # fine-table lookup, Snell ratio, sin^2, cos
+    "tables": 24,               # two indices, two fractions, 2 x bilinear
+    "ground_point_time": 21,    # sec, tan, offsets, X, Y, t, direction cosines
+    "grid_and_sphere": 24,      # grid cell, one line-sphere test
+    "output_counters": 8,       # amortised compaction and counters
 }
-OPS_PER_BUNCH = sum(OPS_PER_BUNCH_FP32.values())
+OPS_PER_BUNCH = sum(OPS_PER_BUNCH_FP32.values())          # 242
+# the floating-point part (everything but Philox), which the FP64 path runs
+# on the FP64 pipe
+FP64_OPS_PER_BUNCH = OPS_PER_BUNCH - OPS_PER_BUNCH_FP32["philox4x32_10"]
 FP64_OPS_PER_STEP = 34          # yield chain: 24 mul/add + 1 division (~10 ops)
 FP32_LANES_PER_SM = 128
-FP64_FMA_PER_SM_CLK = 2         # GB300: about 1/64 of the FP32 rate (1.25 TFLOP/s)
+FP64_FMA_PER_SM_CLK = 2         # GB300: 1/64 of the FP32 rate (ncu: 2 DFMA/cycle/SM)
 
 
 def _peaks():
@@ -183,14 +196,23 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     # ---- workload (each rank its own shower: weak scaling) ----------------
-    sc = workloads.vertical_1tev(seed=2 + rank)
+    wl = args.workload
+    if wl == "vertical_1tev":
+        sc = workloads.vertical_1tev(n=int(2_000_000 * args.scale), seed=2 + rank)
+    elif wl == "inclined_20tev":
+        sc = workloads.inclined_20tev(n=int(100_000_000 * args.scale), seed=5 + 100 * rank)
+    elif wl == "batched_256":
+        sc = workloads.batched_256(total=int(200_000_000 * args.scale), seed=3 + 100 * rank)
+    else:
+        sc = workloads.WORKLOADS[wl]()
     n = len(sc["tracks"]["x0"])
     track_base = rank * n
     t0 = time.perf_counter()
     ctx = P.Context(sc["atm"], sc["h_obs"], sc["telescopes"])
     ctx.build_refraction_tables(sc["H"], sc["Z"], sc["theta_max_deg"], sc["h_max"])
     table_s = time.perf_counter() - t0
-    cap = args.cap
+    cap = args.cap or (600_000 if args.workload == "vertical_1tev" else
+                       max(200_000, int(4_000_000 * args.scale)))
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def measure(prec, steps, warmup, autotune):
@@ -264,54 +286,59 @@ def run_ours(args):
     v32, v64 = b32 / t32, b64 / t64
 
     # ---- end to end: host buffers through the C ABI ---------------------
-    prec = P.CHER_FP32_BULK
-    host = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory()
-            for k, v in sc["tracks"].items() if k != "shower"}
-    host["ux"], host["uy"], host["uz"] = (host[k].to(torch.float32).pin_memory()
-                                          for k in ("ux", "uy", "uz"))
-    dtr = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
-    dtr["t_ref"] = torch.as_tensor(sc["t_ref"], dtype=torch.float64, device=dev)
-    out = r32["out"]
-    n_tel = ctx.n_tel
-    h_cnt = torch.empty(n_tel, dtype=torch.int64).pin_memory()
-    h_st = torch.empty(P.NSTATS, dtype=torch.int64).pin_memory()
-    h_pos = torch.empty((n_tel, cap, 4), dtype=torch.float32).pin_memory()
-    h_tim = torch.empty((n_tel, cap, 4), dtype=torch.float32).pin_memory()
-    h_key = torch.empty((n_tel, cap), dtype=torch.int64).pin_memory()
-    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    e2e = None
+    if not args.no_e2e:
+        prec = P.CHER_FP32_BULK
+        host = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory()
+                for k, v in sc["tracks"].items() if k != "shower"}
+        host["ux"], host["uy"], host["uz"] = (host[k].to(torch.float32).pin_memory()
+                                              for k in ("ux", "uy", "uz"))
+        host["shower"] = torch.as_tensor(
+            np.ascontiguousarray(sc["tracks"]["shower"]).view(np.int32)).pin_memory()
+        dtr = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+        dtr["t_ref"] = torch.as_tensor(sc["t_ref"], dtype=torch.float64, device=dev)
+        out = r32["out"]
+        n_tel = ctx.n_tel
+        h_cnt = torch.empty(n_tel, dtype=torch.int64).pin_memory()
+        h_st = torch.empty(P.NSTATS, dtype=torch.int64).pin_memory()
+        h_pos = torch.empty((n_tel, cap, 4), dtype=torch.float32).pin_memory()
+        h_tim = torch.empty((n_tel, cap, 4), dtype=torch.float32).pin_memory()
+        h_key = torch.empty((n_tel, cap), dtype=torch.int64).pin_memory()
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
 
-    def e2e_step():
-        for k, v in host.items():
-            dtr[k].copy_(v, non_blocking=True)
-        ctx.generate_propagate(dtr, 11, prec, out, track_base=track_base)
-        h_cnt.copy_(out.count, non_blocking=True)
-        h_st.copy_(out.stats, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        d2h = h_cnt.numel() * 8 + h_st.numel() * 8
-        for k_ in range(n_tel):
-            c = min(int(h_cnt[k_]), cap)
-            if c:
-                h_pos[k_, :c].copy_(out.pos[k_, :c], non_blocking=True)
-                h_tim[k_, :c].copy_(out.tim[k_, :c], non_blocking=True)
-                h_key[k_, :c].copy_(out.key[k_, :c], non_blocking=True)
-                d2h += c * 40
-        torch.cuda.current_stream().synchronize()
-        return d2h
+        def e2e_step():
+            for k, v in host.items():
+                dtr[k].copy_(v, non_blocking=True)
+            ctx.generate_propagate(dtr, 11, prec, out, track_base=track_base)
+            h_cnt.copy_(out.count, non_blocking=True)
+            h_st.copy_(out.stats, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            d2h = h_cnt.numel() * 8 + h_st.numel() * 8
+            for k_ in range(n_tel):
+                c = min(int(h_cnt[k_]), cap)
+                if c:
+                    h_pos[k_, :c].copy_(out.pos[k_, :c], non_blocking=True)
+                    h_tim[k_, :c].copy_(out.tim[k_, :c], non_blocking=True)
+                    h_key[k_, :c].copy_(out.key[k_, :c], non_blocking=True)
+                    d2h += c * 40
+            torch.cuda.current_stream().synchronize()
+            return d2h
 
-    for _ in range(max(1, warmup // 2)):
-        e2e_step()
-    barrier()
-    e0 = time.perf_counter()
-    d2h = 0
-    for _ in range(steps):
-        d2h = e2e_step()
-    barrier()
-    te = time.perf_counter() - e0
-    if world > 1:
-        tt = torch.tensor([te], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        te = float(tt.item())
-    e2e_value = b32 / len(r32["ms"]) * steps / te
+        for _ in range(max(1, warmup // 2)):
+            e2e_step()
+        barrier()
+        e0 = time.perf_counter()
+        d2h = 0
+        for _ in range(steps):
+            d2h = e2e_step()
+        barrier()
+        te = time.perf_counter() - e0
+        if world > 1:
+            tt = torch.tensor([te], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": b32 / len(r32["ms"]) * steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     if rank != 0:
         if world > 1:
@@ -332,22 +359,31 @@ def run_ours(args):
     achieved = ops / per_launch_s
     t_alu = ops / alu_peak
     t_fp64 = emitting * FP64_OPS_PER_STEP / fp64_peak
-    cpu = cpu_baseline() if world == 1 else None
+    cpu = cpu_baseline(args.workload) if world == 1 else None
     line = {
         "metric": METRIC, "value": v32, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": warmup, "ms_per_step": 1e3 * t32 / len(r32["ms"]),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "vertical_1tev: 1 TeV vertical gamma-like shower, 2e6 e+- "
-                               "steps per GPU, 19 spheres (R 6-12 m, hex 120 m), tables "
-                               "1000 x 64 to 70 deg, h_obs 2.2 km",
+        "config": {"workload": WORKLOAD_TEXT.get(args.workload, args.workload) +
+                               (f" (scale {args.scale})" if args.scale != 1.0 else ""),
+                   "steps_per_gpu": n, "n_showers": int(len(sc["t_ref"])),
                    "precision": "fp32_bulk (FP64 yield)", "bunches_per_step": int(bunches),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "launch": {"block": launch[0], "ctas_per_sm": launch[1],
                               "persistent": launch[1] > 0},
                    "table_build_s": table_s},
         "fp64": {"value": v64, "unit": UNIT, "ms_per_step": 1e3 * t64 / len(r64["ms"]),
-                 "steps": len(r64["ms"])},
+                 "steps": len(r64["ms"]),
+                 "roofline": {"bound": "fp64", "unit": "Tops/s",
+                              "achieved": float(r64["stats"][3]) * FP64_OPS_PER_BUNCH /
+                              (statistics.mean(r64["ms"]) / 1e3) / 1e12,
+                              "peak": fp64_peak / 1e12,
+                              "frac": float(r64["stats"][3]) * FP64_OPS_PER_BUNCH /
+                              (statistics.mean(r64["ms"]) / 1e3) / fp64_peak,
+                              "ops_per_bunch": FP64_OPS_PER_BUNCH,
+                              "peak_source": f"{sm_count} SMs x {FP64_FMA_PER_SM_CLK} FP64 "
+                                             f"lanes x {mhz:.0f} MHz"}},
         "fp32_over_fp64": v32 / v64,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
                      "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None,
@@ -359,8 +395,7 @@ def run_ours(args):
                      "launch_ms": 1e3 * per_launch_s},
         "gpu_launches": len(r32["ms"]),
         "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+        "e2e": e2e,
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
@@ -369,14 +404,22 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def cpu_baseline():
-    """The oracle as it stands on this host's cores, bounded sample."""
+def cpu_baseline(workload: str = WORKLOAD):
+    """The oracle as it stands on this host's cores, bounded sample: the
+    workload's generator with its first 20 000 steps."""
     import oracle
     import workloads
     oracle.build()
     n = 20_000
-    sc = workloads.vertical_1tev(n=n)
-    M = oracle.Model(sc["atm"], sc["h_obs"], sc["telescopes"], t_ref=sc["t_ref"])
+    if workload == "batched_256":
+        sc = workloads.batched_256(total=n)
+    elif workload in ("plain_fp64", "adjoint_300gev"):
+        sc = workloads.WORKLOADS[workload]()
+        n = len(sc["tracks"]["x0"])
+    else:
+        sc = workloads.WORKLOADS[workload](n=n)
+    M = oracle.Model(sc["atm"], sc["h_obs"], sc["telescopes"], h_max=sc["h_max"], H=sc["H"],
+                     Z=sc["Z"], theta_max_deg=sc["theta_max_deg"], t_ref=sc["t_ref"])
     M.bunches(sc["tracks"], 7)
     t0 = time.perf_counter()
     reps, nb = 0, 0
@@ -386,8 +429,8 @@ def cpu_baseline():
         reps += 1
     dt = time.perf_counter() - t0
     return {"value": nb / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"first {n} of the 2e6 steps ({nb // reps} bunches), repeated "
-                      f"{reps} times, FP64 table variant, OpenMP over steps"}
+            "sample": f"{workload}: {n} steps ({nb // reps} bunches), repeated {reps} times, "
+                      f"FP64 table variant, OpenMP over steps"}
 
 
 def main():
@@ -400,8 +443,13 @@ def main():
                     help="FP32 device timing only (no FP64, end-to-end or CPU legs)")
     ap.add_argument("--launch", default=None,
                     help="block,ctas_per_sm instead of the autotuner's choice")
-    ap.add_argument("--cap", type=int, default=600_000, help="records per telescope")
+    ap.add_argument("--cap", type=int, default=None, help="records per telescope")
     ap.add_argument("--sweep", action="store_true", help="time a set of launch shapes")
+    ap.add_argument("--workload", default="vertical_1tev",
+                    choices=["vertical_1tev", "inclined_20tev", "batched_256", "plain_fp64",
+                             "adjoint_300gev"])
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of the workload's steps")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

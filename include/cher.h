@@ -250,6 +250,55 @@ cher_status cher_set_launch(cher_ctx *ctx, int32_t block_threads,
 cher_status cher_get_launch(const cher_ctx *ctx, int32_t *block_threads,
                             int32_t *ctas_per_sm);
 
+/* ---- differentiable read-out and its adjoint ---------------------------
+ * No counterpart in the paper (its path is a forward simulation); these
+ * make the path differentiable.  For telescope k and smoothing length sigma
+ *   S_k = sum_b w_b G(r_bk),  U_k = sum_b w_b G(r_bk) t_b,
+ *   G(r) = exp(-r^2 / (2 sigma^2)) / (2 pi sigma^2) for r < 6 sigma, else 0,
+ * over the bunches b that reach the ground, r_bk the distance in the
+ * observation plane from the bunch's ground point to the centre (x_k, y_k),
+ * w_b its photons, t_b its arrival time (relative to t_ref):
+ *   D_k = S_k (photons per m^2),  Tbar_k = U_k / S_k (0 where S_k = 0).
+ * nb_frozen (device, n int32, optional) fixes the bunch counts so that the
+ * read-out is smooth in the parameters; NULL takes this call's yield.  The
+ * bunches within 6 sigma of a centre are listed in an FP32 pass over all
+ * bunches, then recomputed one thread each (precision as `prec`) from
+ * their Philox counters; sums and gradients accumulate in FP64.  Both calls
+ * synchronise `stream` and use scratch the context allocates on first use.
+ * n must be below 2^31.  Errors: CHER_EINVAL, CHER_ESTATE, CHER_ERANGE,
+ * CHER_ENOMEM, CHER_ECUDA.
+ *
+ * cher_density: D and Tbar (device, n_tel doubles each). */
+cher_status cher_density(cher_ctx *ctx, const cher_tracks *tracks, uint64_t seed,
+                         cher_precision prec, double sigma, const int32_t *nb_frozen,
+                         double *D, double *Tbar, void *stream);
+
+/* cher_adjoint: for L = sum_k dL_dD[k] D_k + dL_dT[k] Tbar_k (device inputs,
+ * n_tel doubles each) the gradients
+ *   grad_atm[15]    dL/d(a_0..a_4, b_0..b_4, c_0..c_4) of cher_atmosphere
+ *                   (n depends on b and c only: the a entries are 0),
+ *   grad_tracks[6n] dL/dx0, dL/dy0, dL/dz0, dL/dux, dL/duy, dL/duz per step,
+ *                   stored as six consecutive arrays of n,
+ * both device, overwritten.  The direction components are differentiated as
+ * independent inputs (no renormalisation). */
+cher_status cher_adjoint(cher_ctx *ctx, const cher_tracks *tracks, uint64_t seed,
+                         cher_precision prec, double sigma, const int32_t *nb_frozen,
+                         const double *dL_dD, const double *dL_dT, double *grad_atm,
+                         double *grad_tracks, void *stream);
+
+/* Replace the atmosphere and, if tables were built, rebuild them with the
+ * same sizes (blocking).  Errors as cher_build_refraction_tables. */
+cher_status cher_set_atmosphere(cher_ctx *ctx, const cher_atmosphere *atm);
+
+/* The host sensitivity tables of the adjoint on their own (no CUDA call):
+ * dax[p][j][k] = d ax[j][k] / d p and dal likewise, for the ten parameters
+ * p = b_0..b_4, c_0..c_4, each [10][n_heights][n_zenith].  Errors:
+ * CHER_EINVAL. */
+cher_status cher_build_sensitivity_host(const cher_atmosphere *atm, double h_obs,
+                                        int32_t n_fine, int32_t n_heights, int32_t n_zenith,
+                                        double zenith_max_deg, double h_max, double *dax,
+                                        double *dal);
+
 /* ---- inspection entry points (same device code, for validation) ------- */
 
 /* a1 only: per-step bunch count nb[i] (int32) and photons per bunch w[i]

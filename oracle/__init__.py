@@ -62,7 +62,8 @@ class _Cfg(ctypes.Structure):
                 ("bunch_size", ctypes.c_double), ("lambda1_nm", ctypes.c_double),
                 ("lambda2_nm", ctypes.c_double),
                 ("n_tel", ctypes.c_int), ("tel", _dp),
-                ("t_ref", _dp), ("n_showers", ctypes.c_int), ("bf_tol", ctypes.c_double)]
+                ("t_ref", _dp), ("n_showers", ctypes.c_int), ("bf_tol", ctypes.c_double),
+                ("philox_key", ctypes.c_uint32 * 2)]
 
 
 class _Tracks(ctypes.Structure):
@@ -112,6 +113,8 @@ def lib():
                                   ctypes.c_uint64, _i64p, ctypes.c_int,
                                   ctypes.POINTER(_Out)]
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_density.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Tracks), ctypes.c_uint64,
+                                  _i32p, ctypes.c_double, _dp, _dp]
         L.orc_philox_fill.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                       ctypes.c_int64, _u32p]
         _lib = L
@@ -336,6 +339,22 @@ class Model:
         out["nb"] = nb
         out["off"] = off
         return out
+
+    # ---- differentiable read-out: smoothed density and mean time ----------
+    def density_sums(self, tracks: dict, seed: int, nb_frozen, sigma: float = 1.0,
+                     track_base: int = 0):
+        """S_k = sum w G, U_k = sum w G t over the telescopes (frozen nb)."""
+        T, keep = self._tracks(tracks, track_base)
+        nb = np.ascontiguousarray(nb_frozen, dtype=np.int32)
+        S = np.zeros(self.telescopes.shape[0])
+        U = np.zeros(self.telescopes.shape[0])
+        C = self._cfg()
+        rc = lib().orc_density(ctypes.byref(C), ctypes.byref(T), ctypes.c_uint64(seed),
+                               _ptr(nb, ctypes.c_int32), float(sigma), _ptr(S), _ptr(U))
+        if rc != 0:
+            raise ValueError("orc_density failed")
+        del keep
+        return S, U
 
     def propagate_photon(self, xe, ye, he, te, px, py, pz, variant=0):
         r = np.zeros(6)

@@ -101,6 +101,7 @@ typedef struct {
     const double *t_ref;
     int n_showers;
     double bf_tol;           /* absolute tolerance of the (B) integrals    */
+    uint32_t philox_key[2];  /* set from the seed by the entry points      */
 } orc_cfg;
 
 typedef struct {
@@ -590,6 +591,66 @@ static int orc_telescopes(const orc_cfg *C, double X, double Y, double t,
 }
 
 /* ======================================================================= */
+/* One bunch: emission (a2) and propagation (a3) of bunch j of step i,      */
+/* given the step's yield and the bunch count in use.                       */
+/* ======================================================================= */
+typedef struct {
+    int status;
+    double xe, ye, he, te, px, py, pz, lam;
+    double r[6];                      /* X, Y, t (before t_ref), cx, cy, cz */
+} orc_bunch1;
+
+static void orc_one_bunch(const orc_cfg *C, const orc_tracks *Tk, int64_t i, int64_t j,
+                          int64_t nb, const orc_yield *Y, int variant, orc_bunch1 *B)
+{
+    double ux = Tk->ux[i], uy = Tk->uy[i], uz = Tk->uz[i];
+    double cos_c = 1.0 / (Y->beta * (1.0 + Y->eta));
+    double sin_c = sqrt(Y->s2);
+    /* azimuth basis around the step direction */
+    double e1x, e1y, e1z = 0.0;
+    double rho2 = ux * ux + uy * uy;
+    if (rho2 > 1e-20) {
+        double r = sqrt(rho2);
+        e1x = -uy / r; e1y = ux / r;
+    } else {
+        e1x = 1.0; e1y = 0.0;
+    }
+    double e2x = uy * e1z - uz * e1y;
+    double e2y = uz * e1x - ux * e1z;
+    double e2z = ux * e1y - uy * e1x;
+    int64_t gi = Tk->track_base + i;
+    uint32_t ctr[4] = { (uint32_t)((uint64_t)gi & 0xffffffffu),
+                        (uint32_t)((uint64_t)gi >> 32), (uint32_t)j, 0u };
+    uint32_t x[4];
+    orc_philox4x32_10(ctr, C->philox_key, x);
+    double u0 = orc_u01(x[0]), u1 = orc_u01(x[1]), u2 = orc_u01(x[2]);
+    /* sub-step j, emission point uniform inside it */
+    double f = ((double)j + u0) / (double)nb;
+    double phi = 2.0 * ORC_PI * u1;
+    /* 1/lambda^2 spectrum on [lambda1, lambda2] by inversion */
+    double inv1 = 1.0 / C->lambda1_nm, inv2 = 1.0 / C->lambda2_nm;
+    B->lam = 1.0 / (inv1 - u2 * (inv1 - inv2));
+    double cp = cos(phi), sp = sin(phi);
+    B->px = cos_c * ux + sin_c * (cp * e1x + sp * e2x);
+    B->py = cos_c * uy + sin_c * (cp * e1y + sp * e2y);
+    B->pz = cos_c * uz + sin_c * (cp * e1z + sp * e2z);
+    double fl = f * Tk->len[i];
+    double inv_bc = 1.0 / (Y->beta * ORC_C_M_PER_NS);
+    B->xe = Tk->x0[i] + fl * ux;
+    B->ye = Tk->y0[i] + fl * uy;
+    B->he = Tk->z0[i] + fl * uz;
+    B->te = Tk->t0[i] + fl * inv_bc;
+    B->status = orc_propagate_photon(C, variant, B->xe, B->ye, B->he, B->te, B->px, B->py,
+                                     B->pz, B->r);
+}
+
+static double orc_t_ref(const orc_cfg *C, const orc_tracks *Tk, int64_t i)
+{
+    uint32_t sh = Tk->shower ? Tk->shower[i] : 0u;
+    return (C->t_ref && (int)sh < C->n_showers) ? C->t_ref[sh] : 0.0;
+}
+
+/* ======================================================================= */
 /* Whole path for a set of steps: every bunch of every step.               */
 /* bunch_off[i] is the index of the first bunch of step i (a prefix sum of */
 /* nb from orc_segment_yield).  variant 0 = (T), 1 = (B).                  */
@@ -599,8 +660,9 @@ int orc_bunches(const orc_cfg *C, const orc_tracks *Tk, uint64_t seed,
                 const int64_t *bunch_off, int variant, orc_bunch_out *O)
 {
     if (!C || !Tk || !bunch_off || !O) return -1;
-    uint32_t key[2] = { (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) };
-    double inv1 = 1.0 / C->lambda1_nm, inv2 = 1.0 / C->lambda2_nm;
+    orc_cfg Cs = *C;
+    Cs.philox_key[0] = (uint32_t)(seed & 0xffffffffu);
+    Cs.philox_key[1] = (uint32_t)(seed >> 32);
     double np1_obs_T = 1.0 + orc_eta_lookup(C->eta_tab, C->n_fine, C->h_max, C->h_obs);
     double np1_obs_B = 1.0 + orc_eta_exact(&C->atm, C->h_obs);
     double np1_obs = (variant == 0) ? np1_obs_T : np1_obs_B;
@@ -608,69 +670,82 @@ int orc_bunches(const orc_cfg *C, const orc_tracks *Tk, uint64_t seed,
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < Tk->n; ++i) {
         orc_yield Y;
-        if (orc_step_yield(C, Tk, i, &Y) != 0)
+        if (orc_step_yield(&Cs, Tk, i, &Y) != 0)
             continue;
         if (Y.nb == 0) continue;
-        double ux = Tk->ux[i], uy = Tk->uy[i], uz = Tk->uz[i];
-        double cos_c = 1.0 / (Y.beta * (1.0 + Y.eta));
-        double sin_c = sqrt(Y.s2);
-        /* azimuth basis around the step direction */
-        double e1x, e1y, e1z = 0.0;
-        double rho2 = ux * ux + uy * uy;
-        if (rho2 > 1e-20) {
-            double r = sqrt(rho2);
-            e1x = -uy / r; e1y = ux / r;
-        } else {
-            e1x = 1.0; e1y = 0.0;
-        }
-        double e2x = uy * e1z - uz * e1y;
-        double e2y = uz * e1x - ux * e1z;
-        double e2z = ux * e1y - uy * e1x;
-        uint32_t sh = Tk->shower ? Tk->shower[i] : 0u;
-        double t_ref = (C->t_ref && (int)sh < C->n_showers) ? C->t_ref[sh] : 0.0;
-        int64_t gi = Tk->track_base + i;
-        double inv_bc = 1.0 / (Y.beta * ORC_C_M_PER_NS);
+        double t_ref = orc_t_ref(&Cs, Tk, i);
         for (int64_t j = 0; j < Y.nb; ++j) {
             int64_t bidx = bunch_off[i] + j;
-            uint32_t ctr[4] = { (uint32_t)((uint64_t)gi & 0xffffffffu),
-                                (uint32_t)((uint64_t)gi >> 32), (uint32_t)j, 0u };
-            uint32_t x[4];
-            orc_philox4x32_10(ctr, key, x);
-            double u0 = orc_u01(x[0]), u1 = orc_u01(x[1]), u2 = orc_u01(x[2]);
-            /* sub-step j, emission point uniform inside it */
-            double f = ((double)j + u0) / (double)Y.nb;
-            double phi = 2.0 * ORC_PI * u1;
-            /* 1/lambda^2 spectrum on [lambda1, lambda2] by inversion */
-            double lam = 1.0 / (inv1 - u2 * (inv1 - inv2));
-            double cp = cos(phi), sp = sin(phi);
-            double px = cos_c * ux + sin_c * (cp * e1x + sp * e2x);
-            double py = cos_c * uy + sin_c * (cp * e1y + sp * e2y);
-            double pz = cos_c * uz + sin_c * (cp * e1z + sp * e2z);
-            double fl = f * Tk->len[i];
-            double xe = Tk->x0[i] + fl * ux;
-            double ye = Tk->y0[i] + fl * uy;
-            double he = Tk->z0[i] + fl * uz;
-            double te = Tk->t0[i] + fl * inv_bc;
-            O->xe[bidx] = xe; O->ye[bidx] = ye; O->he[bidx] = he; O->te[bidx] = te;
-            O->px[bidx] = px; O->py[bidx] = py; O->pz[bidx] = pz;
-            O->lam[bidx] = lam; O->w[bidx] = Y.w;
-            double r[6];
-            int st = orc_propagate_photon(C, variant, xe, ye, he, te, px, py, pz, r);
-            O->status[bidx] = st;
+            orc_bunch1 B;
+            orc_one_bunch(&Cs, Tk, i, j, Y.nb, &Y, variant, &B);
+            O->xe[bidx] = B.xe; O->ye[bidx] = B.ye; O->he[bidx] = B.he; O->te[bidx] = B.te;
+            O->px[bidx] = B.px; O->py[bidx] = B.py; O->pz[bidx] = B.pz;
+            O->lam[bidx] = B.lam; O->w[bidx] = Y.w;
+            O->status[bidx] = B.status;
             O->nhit[bidx] = 0;
-            if (st != ORC_ST_GROUND) {
+            if (B.status != ORC_ST_GROUND) {
                 O->X[bidx] = O->Y[bidx] = O->t[bidx] = 0.0;
                 O->cx[bidx] = O->cy[bidx] = O->cz[bidx] = 0.0;
                 continue;
             }
-            double t = r[2] - t_ref;
-            O->X[bidx] = r[0]; O->Y[bidx] = r[1]; O->t[bidx] = t;
-            O->cx[bidx] = r[3]; O->cy[bidx] = r[4]; O->cz[bidx] = r[5];
-            O->nhit[bidx] = orc_telescopes(C, r[0], r[1], t, r[3], r[4], r[5], np1_obs,
+            double t = B.r[2] - t_ref;
+            O->X[bidx] = B.r[0]; O->Y[bidx] = B.r[1]; O->t[bidx] = t;
+            O->cx[bidx] = B.r[3]; O->cy[bidx] = B.r[4]; O->cz[bidx] = B.r[5];
+            O->nhit[bidx] = orc_telescopes(&Cs, B.r[0], B.r[1], t, B.r[3], B.r[4], B.r[5],
+                                           np1_obs,
                                            O->hit_tel + ORC_MAX_HITS * bidx,
                                            O->hit_x + ORC_MAX_HITS * bidx,
                                            O->hit_y + ORC_MAX_HITS * bidx,
                                            O->hit_t + ORC_MAX_HITS * bidx);
+        }
+    }
+    return 0;
+}
+
+/* ======================================================================= */
+/* Gaussian-smoothed photon density and mean arrival time at the telescope  */
+/* centres, the quantities whose gradient the adjoint computes (the paper   */
+/* has no counterpart: this is the differentiable read-out of the path):    */
+/*   S_k = sum_b w_b G(r_bk),   U_k = sum_b w_b G(r_bk) t_b,                */
+/*   G(r) = exp(-r^2 / (2 sigma^2)) / (2 pi sigma^2) for r < 6 sigma, else 0, */
+/* r_bk the distance in the observation plane between the ground point of   */
+/* bunch b and the centre (x_k, y_k) of telescope k; only bunches reaching  */
+/* the ground count.  The density is D_k = S_k and the mean arrival time    */
+/* Tbar_k = U_k / S_k.  nb_frozen fixes the bunch counts (the sub-step      */
+/* structure) so that the sums are smooth in the parameters: w = N / nb.    */
+/* Table variant (T).  S, U: n_tel entries each, overwritten.               */
+/* ======================================================================= */
+int orc_density(const orc_cfg *C, const orc_tracks *Tk, uint64_t seed, const int32_t *nb_frozen,
+                double sigma, double *S, double *U)
+{
+    if (!C || !Tk || !nb_frozen || !S || !U || !(sigma > 0.0)) return -1;
+    orc_cfg Cs = *C;
+    Cs.philox_key[0] = (uint32_t)(seed & 0xffffffffu);
+    Cs.philox_key[1] = (uint32_t)(seed >> 32);
+    double norm = 1.0 / (2.0 * ORC_PI * sigma * sigma);
+    double rcut2 = 36.0 * sigma * sigma;
+    for (int k = 0; k < C->n_tel; ++k) { S[k] = 0.0; U[k] = 0.0; }
+    for (int64_t i = 0; i < Tk->n; ++i) {
+        orc_yield Y;
+        if (orc_step_yield(&Cs, Tk, i, &Y) != 0) continue;
+        int64_t nb = nb_frozen[i];
+        if (nb <= 0 || !(Y.s2 > 0.0)) continue;
+        double w = Y.N / (double)nb;
+        double t_ref = orc_t_ref(&Cs, Tk, i);
+        for (int64_t j = 0; j < nb; ++j) {
+            orc_bunch1 B;
+            orc_one_bunch(&Cs, Tk, i, j, nb, &Y, 0, &B);
+            if (B.status != ORC_ST_GROUND) continue;
+            double t = B.r[2] - t_ref;
+            for (int k = 0; k < C->n_tel; ++k) {
+                double dx = B.r[0] - C->tel[4 * k + 0];
+                double dy = B.r[1] - C->tel[4 * k + 1];
+                double r2 = dx * dx + dy * dy;
+                if (!(r2 < rcut2)) continue;
+                double G = norm * exp(-r2 / (2.0 * sigma * sigma));
+                S[k] += w * G;
+                U[k] += w * G * t;
+            }
         }
     }
     return 0;

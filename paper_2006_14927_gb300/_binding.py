@@ -100,6 +100,14 @@ SIGNATURES = {
                                     ctypes.c_double, _P, _P, _P]),
     "cher_autotune": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
                            ctypes.POINTER(Output), ctypes.c_char_p, _P]),
+    "cher_density": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S, ctypes.c_double, _P,
+                          _P, _P, _P]),
+    "cher_adjoint": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S, ctypes.c_double, _P,
+                          _P, _P, _P, _P, _P]),
+    "cher_set_atmosphere": (_S, [_P, ctypes.POINTER(Atmosphere)]),
+    "cher_build_sensitivity_host": (_S, [ctypes.POINTER(Atmosphere), ctypes.c_double,
+                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_double, ctypes.c_double, _P, _P]),
 }
 
 
@@ -146,6 +154,21 @@ def build_tables_host(atm: dict, h_obs: float, n_fine: int, n_heights: int, n_ze
                                         float(h_max), eta.ctypes.data, ax.ctypes.data,
                                         al.ctypes.data), "cher_build_tables_host")
     return eta, ax, al
+
+
+def build_sensitivity_host(atm: dict, h_obs: float, n_fine: int, n_heights: int,
+                           n_zenith: int, zenith_max_deg: float, h_max: float):
+    """The adjoint's refraction-table sensitivities (host, no CUDA call):
+    d ax / d p and d al / d p for p = b_0..b_4, c_0..c_4, each (10, H, Z)."""
+    dax = np.zeros((10, n_heights, n_zenith))
+    dal = np.zeros((10, n_heights, n_zenith))
+    A = atmosphere_struct(atm)
+    _check(lib().cher_build_sensitivity_host(ctypes.byref(A), float(h_obs), int(n_fine),
+                                             int(n_heights), int(n_zenith),
+                                             float(zenith_max_deg), float(h_max),
+                                             dax.ctypes.data, dal.ctypes.data),
+           "cher_build_sensitivity_host")
+    return dax, dal
 
 
 def _torch():
@@ -357,6 +380,43 @@ class Context:
                                        int(precision), ctypes.byref(o), ctypes.byref(h)),
                "cher_graph_create")
         return Graph(h, (dev_tracks, out))
+
+    def set_atmosphere(self, atm: dict):
+        A = atmosphere_struct(atm)
+        _check(lib().cher_set_atmosphere(self._h, ctypes.byref(A)), "cher_set_atmosphere")
+
+    def density(self, dev_tracks: dict, seed: int, precision: int, sigma: float = 1.0,
+                nb_frozen=None, stream=None, track_base: int = 0):
+        """Smoothed photon density D_k and mean arrival time Tbar_k (device f64)."""
+        torch = _torch()
+        dev = dev_tracks["x0"].device
+        D = torch.zeros(self.n_tel, dtype=torch.float64, device=dev)
+        T = torch.zeros(self.n_tel, dtype=torch.float64, device=dev)
+        t = self.tracks_struct(dev_tracks, track_base)
+        _check(lib().cher_density(self._h, ctypes.byref(t), ctypes.c_uint64(seed), int(precision),
+                                  float(sigma),
+                                  nb_frozen.data_ptr() if nb_frozen is not None else None,
+                                  D.data_ptr(), T.data_ptr(),
+                                  ctypes.c_void_p(_stream_ptr(stream))), "cher_density")
+        return D, T
+
+    def adjoint(self, dev_tracks: dict, seed: int, precision: int, dL_dD, dL_dT,
+                sigma: float = 1.0, nb_frozen=None, stream=None, track_base: int = 0):
+        """Gradients of sum dL_dD D + dL_dT Tbar: (15,) atmosphere, (6, n) steps."""
+        torch = _torch()
+        dev = dev_tracks["x0"].device
+        n = int(dev_tracks["x0"].numel())
+        ga = torch.zeros(15, dtype=torch.float64, device=dev)
+        gt = torch.zeros((6, n), dtype=torch.float64, device=dev)
+        gD = torch.as_tensor(dL_dD, dtype=torch.float64, device=dev).contiguous()
+        gT = torch.as_tensor(dL_dT, dtype=torch.float64, device=dev).contiguous()
+        t = self.tracks_struct(dev_tracks, track_base)
+        _check(lib().cher_adjoint(self._h, ctypes.byref(t), ctypes.c_uint64(seed), int(precision),
+                                  float(sigma),
+                                  nb_frozen.data_ptr() if nb_frozen is not None else None,
+                                  gD.data_ptr(), gT.data_ptr(), ga.data_ptr(), gt.data_ptr(),
+                                  ctypes.c_void_p(_stream_ptr(stream))), "cher_adjoint")
+        return ga, gt
 
     def autotune(self, dev_tracks: dict, seed: int, precision: int, out: HitBuffers,
                  cache_path: str | None = None, stream=None):

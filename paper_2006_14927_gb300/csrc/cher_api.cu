@@ -26,18 +26,33 @@ struct cher_ctx {
     // tables
     bool built = false;
     cher::HostTables T;
-    cher::HostGrid G;
+    cher::HostGrid G[2];                  // zenith bands: steep, all
+    double q_band = 0;
     double eta_obs = 0;
     double *d_eta64 = nullptr;
     float *d_eta32 = nullptr;
     void *d_tab64 = nullptr, *d_tab32 = nullptr;
     void *d_tel64 = nullptr, *d_tel32 = nullptr;
-    int32_t *d_cell_start = nullptr, *d_cell_tel = nullptr;
+    int32_t *d_cell_start[2] = {nullptr, nullptr}, *d_cell_tel[2] = {nullptr, nullptr};
+    float *d_cand32[2] = {nullptr, nullptr};
+    double *d_cand64[2] = {nullptr, nullptr};
     // scratch: the persistent kernel's tile counter
     unsigned long long *d_scratch = nullptr;
     // launch shape
     int block = 256;
     int ctas_per_sm = 3;
+    // table sizes of the last build (cher_set_atmosphere rebuilds with them)
+    int32_t tab_H = 0, tab_Z = 0;
+    double tab_zen = 0, tab_hmax = 0;
+    // adjoint: sensitivity tables and scratch, allocated on first use
+    double *d_sens = nullptr;
+    int32_t *d_nb = nullptr;
+    double *d_w = nullptr;
+    int64_t nb_cap = 0;
+    uint64_t *d_list = nullptr;
+    int64_t list_cap = 0;
+    unsigned long long *d_list_count = nullptr;
+    double *d_SU = nullptr;
 };
 
 namespace {
@@ -51,14 +66,36 @@ void free_tables(cher_ctx *c) {
     cudaFree(c->d_tab32);
     cudaFree(c->d_tel64);
     cudaFree(c->d_tel32);
-    cudaFree(c->d_cell_start);
-    cudaFree(c->d_cell_tel);
+    for (int g = 0; g < 2; ++g) {
+        cudaFree(c->d_cell_start[g]);
+        cudaFree(c->d_cell_tel[g]);
+        cudaFree(c->d_cand32[g]);
+        cudaFree(c->d_cand64[g]);
+        c->d_cell_start[g] = c->d_cell_tel[g] = nullptr;
+        c->d_cand32[g] = nullptr;
+        c->d_cand64[g] = nullptr;
+    }
     c->d_eta64 = nullptr;
     c->d_eta32 = nullptr;
     c->d_tab64 = c->d_tab32 = nullptr;
     c->d_tel64 = c->d_tel32 = nullptr;
-    c->d_cell_start = c->d_cell_tel = nullptr;
+    cudaFree(c->d_sens);
+    c->d_sens = nullptr;
     c->built = false;
+}
+
+void free_adjoint_scratch(cher_ctx *c) {
+    cudaFree(c->d_nb);
+    cudaFree(c->d_w);
+    cudaFree(c->d_list);
+    cudaFree(c->d_list_count);
+    cudaFree(c->d_SU);
+    c->d_nb = nullptr;
+    c->d_w = nullptr;
+    c->d_list = nullptr;
+    c->d_list_count = nullptr;
+    c->d_SU = nullptr;
+    c->nb_cap = c->list_cap = 0;
 }
 
 template <class T>
@@ -69,6 +106,29 @@ cher_status upload(T **dst, const T *src, size_t n) {
     }
     if (cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
         return CHER_ECUDA;
+    return CHER_OK;
+}
+
+// device copies of grid g: cell starts, candidate telescopes and their
+// centres and squared radii in both precisions
+cher_status upload_grid(cher_ctx *c, int g) {
+    const cher::HostGrid &G = c->G[g];
+    std::vector<float> c32(G.cell_tel.size() * 4);
+    std::vector<double> c64(G.cell_tel.size() * 4);
+    for (size_t m = 0; m < G.cell_tel.size(); ++m) {
+        const cher_telescope &q = c->tel[G.cell_tel[m]];
+        const double v[4] = {q.x, q.y, q.z, q.r * q.r};
+        for (int e = 0; e < 4; ++e) {
+            c64[4 * m + e] = v[e];
+            c32[4 * m + e] = static_cast<float>(v[e]);
+        }
+    }
+    cher_status r;
+    if ((r = upload(&c->d_cell_start[g], G.cell_start.data(), G.cell_start.size())) != CHER_OK ||
+        (r = upload(&c->d_cell_tel[g], G.cell_tel.data(), G.cell_tel.size())) != CHER_OK ||
+        (r = upload(&c->d_cand32[g], c32.data(), c32.size())) != CHER_OK ||
+        (r = upload(&c->d_cand64[g], c64.data(), c64.size())) != CHER_OK)
+        return r;
     return CHER_OK;
 }
 
@@ -118,13 +178,20 @@ cher::KParams base_params(const cher_ctx *c, const cher_tracks *t, uint64_t seed
     p.lam_dinv = c->lam_dinv;
     p.n_tel = static_cast<int32_t>(c->tel.size());
     p.tel = fp32 ? c->d_tel32 : c->d_tel64;
-    p.gnx = c->G.nx;
-    p.gny = c->G.ny;
-    p.gx0 = c->G.x0;
-    p.gy0 = c->G.y0;
-    p.inv_gcs = c->G.inv_cs;
-    p.cell_start = c->d_cell_start;
-    p.cell_tel = c->d_cell_tel;
+    for (int g = 0; g < 2; ++g) {
+        p.grid[g].nx = c->G[g].nx;
+        p.grid[g].ny = c->G[g].ny;
+        p.grid[g].n_cand = static_cast<int32_t>(c->G[g].cell_tel.size());
+        p.grid[g].x0 = c->G[g].x0;
+        p.grid[g].y0 = c->G[g].y0;
+        p.grid[g].inv_cs = c->G[g].inv_cs;
+        p.grid[g].cell_start = c->d_cell_start[g];
+        p.grid[g].cand_tel = c->d_cell_tel[g];
+        p.grid[g].cand32 = c->d_cand32[g];
+        p.grid[g].cand64 = c->d_cand64[g];
+    }
+    p.q_band = c->q_band;
+    p.grid_in_smem = 0;
     cher::fill_float_constants(p);
     return p;
 }
@@ -243,13 +310,20 @@ cher_status cher_build_refraction_tables(cher_ctx *c, int32_t n_heights, int32_t
     cher_status s = cher::build_tables(c->atm, c->h_obs, c->opt.n_fine, n_heights, n_zenith, th,
                                        h_max, T);
     if (s != CHER_OK) return s;
-    cher::HostGrid G;
-    s = cher::build_grid(c->tel.data(), static_cast<int32_t>(c->tel.size()), th, G);
+    // candidate grids for two zenith bands: photons steeper than 25 degrees
+    // (the bulk of a near-vertical shower) see a much smaller reach
+    cher::HostGrid G[2];
+    const double th_band = std::min(th, 25.0 * cher::kPi / 180.0);
+    s = cher::build_grid(c->tel.data(), static_cast<int32_t>(c->tel.size()), th_band, G[0]);
+    if (s != CHER_OK) return s;
+    s = cher::build_grid(c->tel.data(), static_cast<int32_t>(c->tel.size()), th, G[1]);
     if (s != CHER_OK) return s;
     if (static_cast<double>(n_heights) * n_zenith * 32.0 > 4.0e9) return CHER_ERANGE;
     free_tables(c);
     c->T = std::move(T);
-    c->G = std::move(G);
+    c->G[0] = std::move(G[0]);
+    c->G[1] = std::move(G[1]);
+    c->q_band = std::sin(th_band) * std::sin(th_band);
     c->eta_obs = cher::eta_lookup(c->T, c->h_obs);
 
     const int H = c->T.H, Z = c->T.Z;
@@ -287,8 +361,7 @@ cher_status cher_build_refraction_tables(cher_ctx *c, int32_t n_heights, int32_t
         (r = upload(&d_tab32, t32.data(), t32.size())) != CHER_OK ||
         (r = upload(&d_tel64, tel64.data(), tel64.size())) != CHER_OK ||
         (r = upload(&d_tel32, tel32.data(), tel32.size())) != CHER_OK ||
-        (r = upload(&c->d_cell_start, c->G.cell_start.data(), c->G.cell_start.size())) != CHER_OK ||
-        (r = upload(&c->d_cell_tel, c->G.cell_tel.data(), c->G.cell_tel.size())) != CHER_OK) {
+        (r = upload_grid(c, 0)) != CHER_OK || (r = upload_grid(c, 1)) != CHER_OK) {
         c->d_tab64 = d_tab64;
         c->d_tab32 = d_tab32;
         c->d_tel64 = d_tel64;
@@ -301,12 +374,28 @@ cher_status cher_build_refraction_tables(cher_ctx *c, int32_t n_heights, int32_t
     c->d_tel64 = d_tel64;
     c->d_tel32 = d_tel32;
     c->built = true;
+    c->tab_H = n_heights;
+    c->tab_Z = n_zenith;
+    c->tab_zen = zenith_max_deg;
+    c->tab_hmax = h_max;
     return CHER_OK;
+}
+
+cher_status cher_set_atmosphere(cher_ctx *c, const cher_atmosphere *atm) {
+    if (!c || !atm) return CHER_EINVAL;
+    const cher_atmosphere old = c->atm;
+    c->atm = *atm;
+    if (!c->built) return CHER_OK;
+    const cher_status s = cher_build_refraction_tables(c, c->tab_H, c->tab_Z, c->tab_zen,
+                                                       c->tab_hmax);
+    if (s != CHER_OK) c->atm = old;
+    return s;
 }
 
 cher_status cher_destroy(cher_ctx *c) {
     if (!c) return CHER_OK;
     free_tables(c);
+    free_adjoint_scratch(c);
     cudaFree(c->d_scratch);
     delete c;
     return CHER_OK;
@@ -502,6 +591,193 @@ cher_status cher_autotune(cher_ctx *c, const cher_tracks *t, uint64_t seed, cher
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Differentiable read-out and its adjoint (no counterpart in the paper).
+// ---------------------------------------------------------------------------
+namespace {
+
+template <class T>
+cher_status grow(T **ptr, int64_t &cap, int64_t need) {
+    if (need <= cap && *ptr) return CHER_OK;
+    cudaFree(*ptr);
+    *ptr = nullptr;
+    cap = 0;
+    if (cudaMalloc(reinterpret_cast<void **>(ptr), std::max<int64_t>(need, 1) * sizeof(T)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return CHER_ENOMEM;
+    }
+    cap = need;
+    return CHER_OK;
+}
+
+cher_status readout(cher_ctx *c, const cher_tracks *t, uint64_t seed, cher_precision prec,
+                    double sigma, const int32_t *nb_frozen, double *D, double *Tbar,
+                    const double *gD, const double *gT, double *grad_atm, double *grad_tracks,
+                    void *stream) {
+    if (!c || !tracks_ok(t)) return CHER_EINVAL;
+    if (prec != CHER_FP64 && prec != CHER_FP32_BULK) return CHER_EINVAL;
+    if (!(sigma > 0.0) || !std::isfinite(sigma)) return CHER_EINVAL;
+    if (!c->built) return CHER_ESTATE;
+    if (!check_device(c)) return CHER_EINVAL;
+    if (t->n > 0x7fffffffLL) return CHER_ERANGE;
+    const bool fp32 = prec == CHER_FP32_BULK;
+    const int n_tel = static_cast<int>(c->tel.size());
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cher_status r;
+    // sensitivity tables of the refraction corrections
+    if (grad_atm && !c->d_sens) {
+        std::vector<double> sv;
+        if ((r = cher::build_sensitivity(c->atm, c->h_obs, c->T, sv)) != CHER_OK) return r;
+        if ((r = upload(&c->d_sens, sv.data(), sv.size())) != CHER_OK) return r;
+    }
+    int64_t cap_tmp = c->nb_cap;
+    if ((r = grow(&c->d_nb, cap_tmp, t->n)) != CHER_OK) return r;
+    int64_t cap_w = c->nb_cap;
+    if ((r = grow(&c->d_w, cap_w, t->n)) != CHER_OK) return r;
+    c->nb_cap = std::max(cap_tmp, cap_w);
+    int64_t one = c->d_list_count ? 1 : 0;
+    if ((r = grow(&c->d_list_count, one, 1)) != CHER_OK) return r;
+    int64_t su = c->d_SU ? 2 * n_tel : 0;
+    if ((r = grow(&c->d_SU, su, 2 * n_tel)) != CHER_OK) return r;
+    if (!c->d_list && (r = grow(&c->d_list, c->list_cap, std::max<int64_t>(1 << 16, t->n / 8))) != CHER_OK)
+        return r;
+    // frozen bunch counts: the caller's, or this call's yield
+    const int32_t *nb = nb_frozen;
+    if (!nb) {
+        cher::KParams p = base_params(c, t, seed, fp32);
+        p.y_nb = c->d_nb;
+        p.y_w = c->d_w;
+        if ((r = launch(c, p, fp32, cher::MODE_YIELD, false, stream)) != CHER_OK) return r;
+        nb = c->d_nb;
+    }
+    // screen: list the bunches within 6 sigma (plus a margin) of a centre
+    const double rscreen = 6.0 * sigma + 0.05;
+    unsigned long long count = 0;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        if (cudaMemsetAsync(c->d_list_count, 0, sizeof(unsigned long long), st) != cudaSuccess)
+            return CHER_ECUDA;
+        cher::KParams p = base_params(c, t, seed, fp32);
+        p.nb_frozen = nb;
+        p.list = c->d_list;
+        p.list_count = c->d_list_count;
+        p.list_cap = c->list_cap;
+        p.rcut2 = rscreen * rscreen;
+        cher::fill_float_constants(p);
+        if ((r = launch(c, p, fp32, cher::MODE_SCREEN, false, stream)) != CHER_OK) return r;
+        if (cudaMemcpyAsync(&count, c->d_list_count, sizeof(count), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return CHER_ECUDA;
+        if (static_cast<int64_t>(count) <= c->list_cap) break;
+        if ((r = grow(&c->d_list, c->list_cap, static_cast<int64_t>(count) + count / 4 + 1024)) !=
+            CHER_OK)
+            return r;
+    }
+    if (static_cast<int64_t>(count) > c->list_cap) return CHER_ERANGE;
+    // the pass over the listed bunches: sums, then gradients
+    cher::AdjParams A;
+    std::memset(&A, 0, sizeof(A));
+    A.k = base_params(c, t, seed, fp32);
+    A.list = c->d_list;
+    A.n_list = static_cast<int64_t>(count);
+    A.nb = nb;
+    A.sigma = sigma;
+    A.inv_2s2 = 1.0 / (2.0 * sigma * sigma);
+    A.norm = 1.0 / (2.0 * cher::kPi * sigma * sigma);
+    A.rcut2 = 36.0 * sigma * sigma;
+    A.S = c->d_SU;
+    A.U = c->d_SU + n_tel;
+    A.sens = c->d_sens;
+    for (int i = 0; i < 6; ++i) A.hb[i] = c->atm.h_bound[i];
+    for (int i = 0; i < 5; ++i) {
+        A.b[i] = c->atm.b[i];
+        A.c[i] = c->atm.c[i];
+    }
+    A.layer0 = 0;
+    while (A.layer0 < 4 && 0.0 >= A.hb[A.layer0 + 1]) ++A.layer0;
+    A.dh_fine = c->T.dh;
+    {
+        double hc = std::min(std::max(c->h_obs, 0.0), c->T.h_max);
+        const double x = hc * c->T.inv_dh;
+        int k = static_cast<int>(x);
+        if (k > c->T.n_fine - 2) k = c->T.n_fine - 2;
+        A.ko = k;
+        A.fo = x - k;
+    }
+    if (cudaMemsetAsync(c->d_SU, 0, 2 * n_tel * sizeof(double), st) != cudaSuccess)
+        return CHER_ECUDA;
+    if (cher::adjoint_pairs(fp32, 0, A, stream) != cudaSuccess) return CHER_ECUDA;
+    if (D || Tbar) {
+        std::vector<double> su(2 * n_tel), d(n_tel), tb(n_tel);
+        if (cudaMemcpyAsync(su.data(), c->d_SU, su.size() * sizeof(double),
+                            cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return CHER_ECUDA;
+        for (int k = 0; k < n_tel; ++k) {
+            d[k] = su[k];
+            tb[k] = su[k] > 0.0 ? su[n_tel + k] / su[k] : 0.0;
+        }
+        if ((D && cudaMemcpyAsync(D, d.data(), n_tel * sizeof(double), cudaMemcpyHostToDevice,
+                                  st) != cudaSuccess) ||
+            (Tbar && cudaMemcpyAsync(Tbar, tb.data(), n_tel * sizeof(double),
+                                     cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return CHER_ECUDA;
+    }
+    if (grad_atm) {
+        if (cudaMemsetAsync(grad_atm, 0, 15 * sizeof(double), st) != cudaSuccess ||
+            cudaMemsetAsync(grad_tracks, 0, 6 * static_cast<size_t>(t->n) * sizeof(double), st) !=
+                cudaSuccess)
+            return CHER_ECUDA;
+        A.gD = gD;
+        A.gT = gT;
+        A.grad_atm = grad_atm;
+        A.grad_tracks = grad_tracks;
+        if (cher::adjoint_pairs(fp32, 1, A, stream) != cudaSuccess) return CHER_ECUDA;
+    }
+    return CHER_OK;
+}
+
+}  // namespace
+
+extern "C" cher_status cher_density(cher_ctx *c, const cher_tracks *t, uint64_t seed,
+                                    cher_precision prec, double sigma, const int32_t *nb_frozen,
+                                    double *D, double *Tbar, void *stream) {
+    if (!D || !Tbar) return CHER_EINVAL;
+    return readout(c, t, seed, prec, sigma, nb_frozen, D, Tbar, nullptr, nullptr, nullptr,
+                   nullptr, stream);
+}
+
+extern "C" cher_status cher_adjoint(cher_ctx *c, const cher_tracks *t, uint64_t seed,
+                                    cher_precision prec, double sigma, const int32_t *nb_frozen,
+                                    const double *dL_dD, const double *dL_dT, double *grad_atm,
+                                    double *grad_tracks, void *stream) {
+    if (!dL_dD || !dL_dT || !grad_atm || (!grad_tracks && t && t->n > 0)) return CHER_EINVAL;
+    return readout(c, t, seed, prec, sigma, nb_frozen, nullptr, nullptr, dL_dD, dL_dT, grad_atm,
+                   grad_tracks, stream);
+}
+
+extern "C" cher_status cher_build_sensitivity_host(const cher_atmosphere *atm, double h_obs,
+                                                   int32_t n_fine, int32_t n_heights,
+                                                   int32_t n_zenith, double zenith_max_deg,
+                                                   double h_max, double *dax, double *dal) {
+    if (!atm || !dax || !dal) return CHER_EINVAL;
+    cher::HostTables T;
+    cher_status s = cher::build_tables(*atm, h_obs, n_fine, n_heights, n_zenith,
+                                       zenith_max_deg * cher::kPi / 180.0, h_max, T);
+    if (s != CHER_OK) return s;
+    std::vector<double> sv;
+    if ((s = cher::build_sensitivity(*atm, h_obs, T, sv)) != CHER_OK) return s;
+    const size_t HZ = static_cast<size_t>(n_heights) * n_zenith;
+    for (size_t e = 0; e < HZ; ++e)
+        for (int q = 0; q < 10; ++q) {
+            dax[q * HZ + e] = sv[e * 20 + q];
+            dal[q * HZ + e] = sv[e * 20 + 10 + q];
+        }
+    return CHER_OK;
+}
 
 struct cher_graph {
     cudaStream_t stream = nullptr;

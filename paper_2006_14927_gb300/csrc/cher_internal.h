@@ -51,6 +51,11 @@ cher_status build_tables(const cher_atmosphere &atm, double h_obs, int32_t n_fin
 double eta_lookup(const HostTables &t, double h);
 cher_status build_grid(const cher_telescope *tel, int32_t n_tel, double theta_max,
                        HostGrid &g);
+// Adjoint support: d eta(h) / d p and the refraction-table sensitivities
+// [H][Z][20] = {d ax / d p (10), d al / d p (10)}, p = b_0..b_4, c_0..c_4.
+void eta_sensitivity(const cher_atmosphere &atm, double h, double *d);
+cher_status build_sensitivity(const cher_atmosphere &atm, double h_obs, const HostTables &T,
+                              std::vector<double> &out);
 
 // Everything a kernel launch needs, passed by value.
 struct KParams {
@@ -79,12 +84,21 @@ struct KParams {
     const void *tab;                      // float4 or double4 [H][Z-1]
     // wavelength band in 1/nm
     double lam_inv1, lam_dinv;
-    // telescopes and grid
+    // telescopes and two ground grids of candidate spheres: grid 0 serves
+    // photons arriving with sin^2(zenith) <= q_band (small reach), grid 1
+    // the rest (reach of the largest zenith)
     int32_t n_tel;
     const void *tel;                      // float4 / double4: x, y, z, r^2
-    int32_t gnx, gny;
-    double gx0, gy0, inv_gcs;
-    const int32_t *cell_start, *cell_tel;
+    struct Grid {
+        int32_t nx, ny, n_cand;
+        double x0, y0, inv_cs;
+        const int32_t *cell_start;        // [nx * ny + 1]
+        const int32_t *cand_tel;          // telescope of each entry
+        const void *cand32;               // float4 per entry: x, y, z, r^2
+        const void *cand64;               // double4 per entry
+    } grid[2];
+    double q_band;
+    int32_t grid_in_smem;                 // FP32: both grids staged in smem
     // outputs
     void *pos, *tim;
     uint64_t *key;
@@ -99,18 +113,48 @@ struct KParams {
     // scheduling
     unsigned long long *tile_counter;     // NULL: one CTA per tile
     int64_t n_tiles;
+    // adjoint screening: frozen bunch counts, list of (step, bunch) pairs
+    // that land within the read-out radius of a telescope centre
+    const int32_t *nb_frozen;
+    uint64_t *list;
+    unsigned long long *list_count;
+    int64_t list_cap;
+    double rcut2;
     // the per-launch constants of the bunch loop, rounded to float on the
     // host: the FP32 path converts nothing from double on the device
     struct {
         float h_obs, dH_max, eta_o, inv_np1o, np1o, q_max, inv_dht, inv_dq, inv_dh;
-        float lam_inv1, lam_dinv, gx0, gy0, inv_gcs;
+        float lam_inv1, lam_dinv, rcut2, q_band;
+        float gx0[2], gy0[2], inv_gcs[2];
     } f;
 };
 
+// Adjoint pass over the listed bunches (cher_adjoint.cu).
+struct AdjParams {
+    KParams k;
+    const uint64_t *list;
+    int64_t n_list;
+    const int32_t *nb;
+    double sigma, inv_2s2, norm, rcut2;
+    double *S, *U;                 // [n_tel] read-out sums
+    const double *gD, *gT;         // [n_tel] upstream gradients
+    double *grad_atm;              // [15]: a_0..a_4, b_0..b_4, c_0..c_4
+    double *grad_tracks;           // [6][n]: x0, y0, z0, ux, uy, uz
+    const double *sens;            // [H][Z][20] table sensitivities
+    double hb[6], b[5], c[5];
+    int layer0;                    // layer of h = 0 (rho(0))
+    double dh_fine;
+    int ko;                        // fine-table position of h_obs
+    double fo;
+};
+cudaError_t adjoint_pairs(bool fp32, int mode, const AdjParams &A, void *stream);
+
 // Fill KParams::f from the double fields.
 void fill_float_constants(KParams &p);
+// Shared-memory bytes of the two candidate grids (FP32 staging).
+size_t grid_smem_bytes(const KParams &p);
 
-enum Mode : int { MODE_HITS = 0, MODE_TRACE = 1, MODE_YIELD = 2 };
+enum Mode : int { MODE_HITS = 0, MODE_TRACE = 1, MODE_YIELD = 2, MODE_SCREEN = 3 };
 
 // Launchers (cher_kernels.cu).  fp32 selects CHER_FP32_BULK.
 size_t kernel_smem_bytes(bool fp32, int block, const KParams &p);

@@ -24,128 +24,13 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "cher_device.cuh"
 #include "cher_internal.h"
 
 namespace cher {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-// ------------------------------------------------------------------------
-// Philox4x32-10 (Salmon et al., SC'11).  Counter (lo(i), hi(i), j, 0), key
-// (lo(seed), hi(seed)).
-// ------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r > 0) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-    }
-    return c;
-}
-
-// uniform deviates in (0, 1)
-__device__ __forceinline__ double u01d(uint32_t x) {
-    return (static_cast<double>(x) + 0.5) * (1.0 / 4294967296.0);
-}
-__device__ __forceinline__ float u01f(uint32_t x) {
-    // top 24 bits, centred: exactly representable, never 0 or 1
-    return __uint2float_rz(x >> 8) * (1.0f / 16777216.0f) + (1.0f / 33554432.0f);
-}
-
-// ------------------------------------------------------------------------
-// a1: per-step yield, FP64, one IEEE operation per statement in a fixed
-// order (the bunch count must not depend on the precision of the rest).
-// ------------------------------------------------------------------------
-struct Yield {
-    int nb;
-    bool valid;
-    double N, s2, g, gam, eta;
-};
-
-// finiteness from the exponent bits: integer ops only (GB300's FP64 pipe is
-// about 1/64 of the FP32 rate, so the per-step code keeps off it where it can)
-__device__ __forceinline__ bool finite_d(double v) {
-    return (__double2hiint(v) & 0x7ff00000) != 0x7ff00000;
-}
-__device__ __forceinline__ bool finite_f(float v) {
-    return (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u;
-}
-
-__device__ __forceinline__ double eta_exact_lookup(const KParams &p, double h) {
-    double hc = h;
-    if (hc < 0.0) hc = 0.0;
-    if (hc > p.h_max) hc = p.h_max;
-    const double x = __dmul_rn(hc, p.inv_dh);
-    int k = static_cast<int>(x);
-    if (k > p.n_fine - 2) k = p.n_fine - 2;
-    const double f = __dsub_rn(x, static_cast<double>(k));
-    const double t0 = __ldg(p.eta64 + k), t1 = __ldg(p.eta64 + k + 1);
-    const double d = __dsub_rn(t1, t0);
-    const double fd = __dmul_rn(f, d);
-    return __dadd_rn(t0, fd);
-}
-
-// A step emits only if every field is finite, len >= 0 and ekin > 0.
-template <class R>
-__device__ __forceinline__ bool finite_r(R v) {
-    if constexpr (std::is_same<R, float>::value) return finite_f(v);
-    else return finite_d(v);
-}
-
-template <class R>
-__device__ __forceinline__ bool step_valid(const KParams &p, int64_t i) {
-    return finite_d(__ldg(p.x0 + i)) && finite_d(__ldg(p.y0 + i)) && finite_d(__ldg(p.t0 + i)) &&
-           finite_r<R>(__ldg(static_cast<const R *>(p.ux) + i)) &&
-           finite_r<R>(__ldg(static_cast<const R *>(p.uy) + i));
-}
-
-__device__ __forceinline__ void step_yield(const KParams &p, bool others_valid, double z0,
-                                           double len, double ekin, double uz, Yield &y) {
-    y.nb = 0;
-    y.valid = false;
-    y.N = y.s2 = y.g = y.gam = y.eta = 0.0;
-    if (!others_valid || !finite_d(z0) || !finite_d(len) || !finite_d(ekin) || !finite_d(uz) ||
-        len < 0.0 || ekin <= 0.0)
-        return;
-    const double g = __dmul_rn(ekin, p.inv_me);
-    const double gam = __dadd_rn(1.0, g);
-    const double gam2 = __dmul_rn(gam, gam);
-    const double half_len = __dmul_rn(0.5, len);
-    const double dz = __dmul_rn(half_len, uz);
-    const double hm = __dadd_rn(z0, dz);
-    const double eta = eta_exact_lookup(p, hm);
-    const double np1 = __dadd_rn(1.0, eta);
-    const double np1sq = __dmul_rn(np1, np1);
-    const double two_eta = __dadd_rn(2.0, eta);
-    const double a = __dmul_rn(eta, two_eta);
-    const double b = __dmul_rn(a, gam2);
-    const double num = __dsub_rn(b, np1sq);
-    const double two_g = __dadd_rn(2.0, g);
-    const double bg2 = __dmul_rn(g, two_g);
-    const double den = __dmul_rn(bg2, np1sq);
-    const double s2 = __ddiv_rn(num, den);
-    y.g = g;
-    y.gam = gam;
-    y.eta = eta;
-    y.valid = true;
-    if (!(s2 > 0.0)) return;
-    const double Ks2 = __dmul_rn(p.K, s2);
-    const double N = __dmul_rn(len, Ks2);
-    const double q = __dmul_rn(N, p.inv_B);
-    if (!(q < 2147483647.0)) {
-        y.valid = false;
-        return;
-    }
-    y.nb = static_cast<int>(ceil(q));
-    y.N = N;
-    y.s2 = s2;
-}
+using namespace dev;
 
 // ------------------------------------------------------------------------
 // Per-step constants staged in shared memory for the bunch loop.
@@ -232,8 +117,16 @@ struct BunchOut {
 template <class R>
 struct Consts {
     R h_obs, dH_max, eta_o, inv_np1o, q_max, inv_dht, inv_dq, inv_dh, lam_inv1, lam_dinv;
-    R gx0, gy0, inv_gcs;
+    R gx0[2], gy0[2], inv_gcs[2], q_band;
     int H, Z, n_fine;
+};
+
+// the candidate grids as the kernel reads them (shared or global memory)
+struct GridView {
+    const int32_t *cell_start;
+    const int32_t *cand_tel;
+    const float4 *cand;
+    int nx, ny;
 };
 
 template <class R>
@@ -280,10 +173,16 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
     const R f = (static_cast<R>(j) + u0) * S.inv_nb;
     const R fl = f * S.L;
     R sp, cp;
-    if constexpr (std::is_same<R, float>::value)
-        sincospif(2.0f * u1, &sp, &cp);
-    else
+    if constexpr (std::is_same<R, float>::value) {
+        // phi = 2 pi u1 = a + pi with a in (-pi, pi), where the hardware
+        // sine and cosine are accurate to 2^-21 (direction error < 1e-8)
+        float sa, ca;
+        __sincosf((u1 - 0.5f) * 6.28318530717958647692f, &sa, &ca);
+        sp = -sa;
+        cp = -ca;
+    } else {
         sincospi(2.0 * u1, &sp, &cp);
+    }
     const R px = S.cosc * S.ux + S.sinc * (cp * S.e1x + sp * S.e2x);
     const R py = S.cosc * S.uy + S.sinc * (cp * S.e1y + sp * S.e2y);
     const R pz = S.cosc * S.uz + S.sinc * (sp * S.e2z);
@@ -354,40 +253,69 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
 }
 
 // Candidate spheres of the bunch's grid cell: bit m of the mask is cell
-// entry s0 + m.
+// entry s0 + m of grid g (chosen by the arrival zenith).
 template <class R>
 __device__ __forceinline__ unsigned sphere_hits(const KParams &p, const Consts<R> &c,
-                                                const BunchOut<R> &o, int &s0) {
+                                                const GridView *gv, const BunchOut<R> &o, int &s0,
+                                                int &g) {
     s0 = 0;
+    g = 0;
     if (o.status != ST_GROUND) return 0u;
-    const R gx = (o.X - c.gx0) * c.inv_gcs;
-    const R gy = (o.Y - c.gy0) * c.inv_gcs;
-    if (!(gx >= R(0)) || !(gy >= R(0)) || !(gx < static_cast<R>(p.gnx)) ||
-        !(gy < static_cast<R>(p.gny)))
+    g = (o.cx * o.cx + o.cy * o.cy <= c.q_band) ? 0 : 1;
+    // (selects, not indexing: the small arrays stay in registers)
+    const R gx = (o.X - (g ? c.gx0[1] : c.gx0[0])) * (g ? c.inv_gcs[1] : c.inv_gcs[0]);
+    const R gy = (o.Y - (g ? c.gy0[1] : c.gy0[0])) * (g ? c.inv_gcs[1] : c.inv_gcs[0]);
+    const int nx = g ? gv[1].nx : gv[0].nx;
+    const int ny = g ? gv[1].ny : gv[0].ny;
+    if (!(gx >= R(0)) || !(gy >= R(0)) || !(gx < static_cast<R>(nx)) ||
+        !(gy < static_cast<R>(ny)))
         return 0u;
-    const int cell = static_cast<int>(gy) * p.gnx + static_cast<int>(gx);
-    s0 = __ldg(p.cell_start + cell);
-    const int s1 = __ldg(p.cell_start + cell + 1);
+    const int cell = static_cast<int>(gy) * nx + static_cast<int>(gx);
     unsigned mask = 0u;
-    for (int m = s0; m < s1; ++m) {
-        const int k = __ldg(p.cell_tel + m);
-        R tx, ty, tz, r2;
-        if constexpr (std::is_same<R, float>::value) {
-            const float4 T = __ldg(static_cast<const float4 *>(p.tel) + k);
-            tx = T.x; ty = T.y; tz = T.z; r2 = T.w;
-        } else {
-            const double2 *T = static_cast<const double2 *>(p.tel);
-            const double2 A = __ldg(T + 2 * k), B = __ldg(T + 2 * k + 1);
-            tx = A.x; ty = A.y; tz = B.x; r2 = B.y;
+    if constexpr (std::is_same<R, float>::value) {
+        const int32_t *cs = g ? gv[1].cell_start : gv[0].cell_start;
+        const float4 *cd = g ? gv[1].cand : gv[0].cand;
+        s0 = __ldg(cs + cell);
+        const int s1 = __ldg(cs + cell + 1);
+        for (int m = s0; m < s1; ++m) {
+            const float4 T = __ldg(cd + m);
+            const float dx = T.x - o.X, dy = T.y - o.Y, dz = T.z;
+            const float q0 = dy * o.cz - dz * o.cy;
+            const float q1 = dz * o.cx - dx * o.cz;
+            const float q2 = dx * o.cy - dy * o.cx;
+            if (q0 * q0 + q1 * q1 + q2 * q2 <= T.w) mask |= 1u << (m - s0);
         }
-        const R dx = tx - o.X, dy = ty - o.Y, dz = tz;
-        const R q0 = dy * o.cz - dz * o.cy;
-        const R q1 = dz * o.cx - dx * o.cz;
-        const R q2 = dx * o.cy - dy * o.cx;
-        const R d2 = q0 * q0 + q1 * q1 + q2 * q2;
-        if (d2 <= r2) mask |= 1u << (m - s0);
+    } else {
+        const int32_t *cs = g ? p.grid[1].cell_start : p.grid[0].cell_start;
+        s0 = __ldg(cs + cell);
+        const int s1 = __ldg(cs + cell + 1);
+        const double2 *T = static_cast<const double2 *>(g ? p.grid[1].cand64 : p.grid[0].cand64);
+        for (int m = s0; m < s1; ++m) {
+            const double2 A = __ldg(T + 2 * m), B = __ldg(T + 2 * m + 1);
+            const double dx = A.x - o.X, dy = A.y - o.Y, dz = B.x;
+            const double q0 = dy * o.cz - dz * o.cy;
+            const double q1 = dz * o.cx - dx * o.cz;
+            const double q2 = dx * o.cy - dy * o.cx;
+            if (q0 * q0 + q1 * q1 + q2 * q2 <= B.y) mask |= 1u << (m - s0);
+        }
     }
     return mask;
+}
+
+// telescope index and centre of entry m of grid g
+template <class R>
+__device__ __forceinline__ int cand_info(const KParams &p, const GridView *gv, int g, int m, R &tx,
+                                         R &ty, R &tz) {
+    if constexpr (std::is_same<R, float>::value) {
+        const float4 T = __ldg((g ? gv[1].cand : gv[0].cand) + m);
+        tx = T.x; ty = T.y; tz = T.z;
+        return __ldg((g ? gv[1].cand_tel : gv[0].cand_tel) + m);
+    } else {
+        const double2 *T = static_cast<const double2 *>(g ? p.grid[1].cand64 : p.grid[0].cand64);
+        const double2 A = __ldg(T + 2 * m), B = __ldg(T + 2 * m + 1);
+        tx = A.x; ty = A.y; tz = B.x;
+        return __ldg((g ? p.grid[1].cand_tel : p.grid[0].cand_tel) + m);
+    }
 }
 
 template <class R>
@@ -420,6 +348,14 @@ __device__ __forceinline__ void flush_stat(unsigned long long *stats, int idx, u
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(stats + idx, static_cast<unsigned long long>(v));
 }
 
+// the same for a counter whose per-thread part may be negative
+__device__ __forceinline__ void flush_stat_signed(unsigned long long *stats, int idx, int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0 && v)
+        atomicAdd(stats + idx, static_cast<unsigned long long>(static_cast<long long>(v)));
+}
+
 // ------------------------------------------------------------------------
 // The fused kernel.
 // ------------------------------------------------------------------------
@@ -438,6 +374,16 @@ __global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
         }
     }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // candidate grids, read through L1 (a few KB)
+    GridView gv[2];
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+        gv[g].cell_start = p.grid[g].cell_start;
+        gv[g].cand_tel = p.grid[g].cand_tel;
+        gv[g].cand = static_cast<const float4 *>(p.grid[g].cand32);
+        gv[g].nx = p.grid[g].nx;
+        gv[g].ny = p.grid[g].ny;
+    }
 
     Consts<R> c;
     R np1o;
@@ -452,9 +398,13 @@ __global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
         c.inv_dh = p.f.inv_dh;
         c.lam_inv1 = p.f.lam_inv1;
         c.lam_dinv = p.f.lam_dinv;
-        c.gx0 = p.f.gx0;
-        c.gy0 = p.f.gy0;
-        c.inv_gcs = p.f.inv_gcs;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            c.gx0[g] = p.f.gx0[g];
+            c.gy0[g] = p.f.gy0[g];
+            c.inv_gcs[g] = p.f.inv_gcs[g];
+        }
+        c.q_band = p.f.q_band;
         np1o = p.f.np1o;
     } else {
         c.h_obs = p.h_obs;
@@ -467,9 +417,13 @@ __global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
         c.inv_dh = p.inv_dh;
         c.lam_inv1 = p.lam_inv1;
         c.lam_dinv = p.lam_dinv;
-        c.gx0 = p.gx0;
-        c.gy0 = p.gy0;
-        c.inv_gcs = p.inv_gcs;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            c.gx0[g] = p.grid[g].x0;
+            c.gy0[g] = p.grid[g].y0;
+            c.inv_gcs[g] = p.grid[g].inv_cs;
+        }
+        c.q_band = p.q_band;
         np1o = 1.0 + p.eta_obs;
     }
     c.H = p.H;
@@ -477,7 +431,7 @@ __global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
     c.n_fine = p.n_fine;
 
     unsigned st_steps = 0, st_emit = 0, st_inval = 0, st_bunch = 0, st_up = 0, st_below = 0,
-             st_above = 0, st_angle = 0, st_ground = 0, st_hits = 0, st_over = 0;
+             st_above = 0, st_angle = 0, st_hits = 0, st_over = 0;
 
     int64_t tile = blockIdx.x;
     for (;;) {
@@ -497,6 +451,11 @@ __global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
             Yield y;
             step_yield(p, step_valid<R>(p, i), __ldg(p.z0 + i), __ldg(p.len + i),
                        __ldg(p.ekin + i), static_cast<double>(load_dir<R>(p.uz, i)), y);
+            if constexpr (MODE == MODE_SCREEN) {
+                // the adjoint freezes the sub-step structure
+                const int nf = __ldg(p.nb_frozen + i);
+                y.nb = (y.s2 > 0.0 && nf > 0) ? nf : 0;
+            }
             nb = y.nb;
             ++st_steps;
             st_emit += (nb > 0);
@@ -540,31 +499,74 @@ __global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
         const int total = off[BLOCK];
 
         // ---- phase B: the tile's bunches -------------------------------------
-        for (int b0 = 0; b0 < total; b0 += BLOCK) {
-            const int bidx = b0 + tid;
+        // Each warp takes a contiguous run of 32-bunch windows.  The step of
+        // a window's first bunch comes from the previous window (one search
+        // per warp and tile); inside a window a lane's step is the last
+        // step whose first bunch is <= its own, counted from the at most 32
+        // step starts that follow with one ballot and a few shuffles.
+        const int nwin = (total + 31) >> 5;
+        const int per_warp = (nwin + BLOCK / 32 - 1) / (BLOCK / 32);
+        const int w_lo = warp * per_warp;
+        const int w_hi = min(w_lo + per_warp, nwin);
+        int s_cur = 0;
+        if (w_lo < w_hi) {
+            int lo = 0, hi = BLOCK;
+            const int b_first = w_lo * 32;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (off[mid] <= b_first) lo = mid; else hi = mid;
+            }
+            s_cur = lo;
+        }
+        for (int win = w_lo; win < w_hi; ++win) {
+            const int bidx = win * 32 + lane;
             const bool live = bidx < total;
+            int s = s_cur;
+            for (int batch = s_cur;; batch += 32) {
+                const int idx = batch + 1 + lane;
+                const int v = (idx <= BLOCK ? off[idx] : 0x7fffffff) - win * 32;
+                const int k = __popc(__ballot_sync(kFull, v <= 31));
+                for (int q = 0; q < k; ++q) s += (__shfl_sync(kFull, v, q) <= lane);
+                if (k < 32) break;
+            }
+            s_cur = __shfl_sync(kFull, s, 31);
             BunchOut<R> o;
             o.status = -1;
-            int s = 0, j = 0;
+            int j = 0;
             if (live) {
-                int lo = 0, hi = BLOCK;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (off[mid] <= bidx) lo = mid; else hi = mid;
-                }
-                s = lo;
                 j = bidx - off[s];
                 bunch<R>(p, c, eta_s, seg[s], p.track_base + base + s, j, o);
-                st_up += o.status == ST_UPWARD;
-                st_below += o.status == ST_BELOW;
-                st_above += o.status == ST_ABOVE;
-                st_angle += o.status == ST_ANGLE;
-                st_ground += o.status == ST_GROUND;
+                if (o.status != ST_GROUND) {       // rare: the drops
+                    st_up += o.status == ST_UPWARD;
+                    st_below += o.status == ST_BELOW;
+                    st_above += o.status == ST_ABOVE;
+                    st_angle += o.status == ST_ANGLE;
+                }
             }
-            int s0 = 0;
-            unsigned hm = live ? sphere_hits<R>(p, c, o, s0) : 0u;
-            st_hits += __popc(hm);
+            if constexpr (MODE == MODE_SCREEN) {
+                // list the bunch if it lands near a telescope centre
+                if (live && o.status == ST_GROUND) {
+                    const R rc2 = std::is_same<R, float>::value ? static_cast<R>(p.f.rcut2)
+                                                                : static_cast<R>(p.rcut2);
+                    for (int k = 0; k < p.n_tel; ++k) {
+                        R tx, ty, tz;
+                        tel_xyz<R>(p, k, tx, ty, tz);
+                        const R dx = o.X - tx, dy = o.Y - ty;
+                        if (dx * dx + dy * dy < rc2) {
+                            const unsigned long long at = atomicAdd(p.list_count, 1ull);
+                            if (at < static_cast<unsigned long long>(p.list_cap))
+                                p.list[at] = (static_cast<uint64_t>(base + s) << 32) |
+                                             static_cast<uint32_t>(j);
+                            break;
+                        }
+                    }
+                }
+                continue;
+            }
+            int s0 = 0, gsel = 0;
+            unsigned hm = live ? sphere_hits<R>(p, c, gv, o, s0, gsel) : 0u;
             if constexpr (MODE == MODE_TRACE) {
+                st_hits += __popc(hm);
                 if (live) {
                     const int64_t gb = __ldg(p.bunch_off + base + s) + j;
                     const R w = seg[s].w;
@@ -577,7 +579,13 @@ __global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
                     }
                     p.t_status[gb] = o.status;
                     p.t_nhit[gb] = __popc(hm);
-                    p.t_first[gb] = hm ? __ldg(p.cell_tel + s0 + __ffs(hm) - 1) : -1;
+                    int first = -1;
+                    for (unsigned mm = hm; mm; mm &= mm - 1u) {      // lowest telescope index
+                        R tx, ty, tz;
+                        const int k = cand_info<R>(p, gv, gsel, s0 + __ffs(mm) - 1, tx, ty, tz);
+                        first = (first < 0 || k < first) ? k : first;
+                    }
+                    p.t_first[gb] = first;
                 }
             } else {
                 // warp-aggregated compaction into the per-telescope buffers
@@ -587,10 +595,12 @@ __global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
                 for (;;) {
                     if (!__any_sync(kFull, hm != 0u)) break;
                     int tel = -1;
+                    R tx = R(0), ty = R(0), tz = R(0);
                     if (hm) {
                         const int bit = __ffs(hm) - 1;
                         hm &= hm - 1u;
-                        tel = __ldg(p.cell_tel + s0 + bit);
+                        tel = cand_info<R>(p, gv, gsel, s0 + bit, tx, ty, tz);
+                        ++st_hits;
                     }
                     const unsigned grp = __match_any_sync(kFull, tel);
                     if (tel >= 0) {
@@ -602,8 +612,6 @@ __global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
                         slot0 = __shfl_sync(grp, slot0, leader);
                         const unsigned long long slot = slot0 + rank;
                         if (slot < static_cast<unsigned long long>(p.cap)) {
-                            R tx, ty, tz;
-                            tel_xyz<R>(p, tel, tx, ty, tz);
                             const R sl = tz / o.cz;       // to the plane through the centre
                             const int64_t r = static_cast<int64_t>(tel) * p.cap + static_cast<int64_t>(slot);
                             store4<R>(p.pos, r, o.X + sl * o.cx - tx, o.Y + sl * o.cy - ty, o.cx, o.cy);
@@ -630,7 +638,10 @@ __global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
             flush_stat(S, CHER_STAT_BELOW_OBS, st_below);
             flush_stat(S, CHER_STAT_ABOVE_MAX, st_above);
             flush_stat(S, CHER_STAT_ANGLE, st_angle);
-            flush_stat(S, CHER_STAT_GROUND, st_ground);
+            // reached the ground = generated - dropped (a per-thread partial
+            // may be negative; the sum modulo 2^64 is exact)
+            flush_stat_signed(S, CHER_STAT_GROUND, static_cast<int>(st_bunch) -
+                                                       static_cast<int>(st_up + st_below + st_above + st_angle));
             flush_stat(S, CHER_STAT_HITS, st_hits);
             flush_stat(S, CHER_STAT_OVERFLOW, st_over);
         }
@@ -666,18 +677,30 @@ const void *pick_kernel(bool fp32, int block, int mode) {
         case MODE_HITS: return pick<float, MODE_HITS>(block);
         case MODE_TRACE: return pick<float, MODE_TRACE>(block);
         case MODE_YIELD: return pick<float, MODE_YIELD>(block);
+        case MODE_SCREEN: return pick<float, MODE_SCREEN>(block);
         }
     } else {
         switch (mode) {
         case MODE_HITS: return pick<double, MODE_HITS>(block);
         case MODE_TRACE: return pick<double, MODE_TRACE>(block);
         case MODE_YIELD: return pick<double, MODE_YIELD>(block);
+        case MODE_SCREEN: return pick<double, MODE_SCREEN>(block);
         }
     }
     return nullptr;
 }
 
 }  // namespace
+
+size_t grid_smem_bytes(const KParams &p) {
+    size_t b = 0;
+    for (int g = 0; g < 2; ++g) {
+        b += 16 * static_cast<size_t>(p.grid[g].n_cand);
+        b += 4 * (static_cast<size_t>(p.grid[g].nx) * p.grid[g].ny + 1 + p.grid[g].n_cand);
+        b = (b + 15) & ~size_t(15);
+    }
+    return b;
+}
 
 void fill_float_constants(KParams &p) {
     p.f.h_obs = static_cast<float>(p.h_obs);
@@ -691,9 +714,13 @@ void fill_float_constants(KParams &p) {
     p.f.inv_dh = static_cast<float>(p.inv_dh);
     p.f.lam_inv1 = static_cast<float>(p.lam_inv1);
     p.f.lam_dinv = static_cast<float>(p.lam_dinv);
-    p.f.gx0 = static_cast<float>(p.gx0);
-    p.f.gy0 = static_cast<float>(p.gy0);
-    p.f.inv_gcs = static_cast<float>(p.inv_gcs);
+    for (int g = 0; g < 2; ++g) {
+        p.f.gx0[g] = static_cast<float>(p.grid[g].x0);
+        p.f.gy0[g] = static_cast<float>(p.grid[g].y0);
+        p.f.inv_gcs[g] = static_cast<float>(p.grid[g].inv_cs);
+    }
+    p.f.q_band = static_cast<float>(p.q_band);
+    p.f.rcut2 = static_cast<float>(p.rcut2);
 }
 
 size_t kernel_smem_bytes(bool fp32, int block, const KParams &p) {

@@ -250,11 +250,130 @@ cher_status build_tables(const cher_atmosphere &atm, double h_obs, int32_t n_fin
     return CHER_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Sensitivities for the adjoint (no counterpart in the paper).  eta depends
+// on the atmosphere only through rho(h)/rho(0) = (b_i/c_i) e^{-h/c_i} /
+// (b_0/c_0): d ln eta / d b_i = [layer(h) = i] / b_i - [layer(0) = i] / b_i,
+// d ln eta / d c_i = [layer(h) = i] (h - c_i) / c_i^2 + [layer(0) = i] / c_i,
+// and not on a_i at all.  Parameter index p: b_0..b_4 then c_0..c_4.
+// ---------------------------------------------------------------------------
+namespace {
+
+void dlneta_dp(const Layered &A, double h, double *d /*[10]*/) {
+    for (int q = 0; q < 10; ++q) d[q] = 0.0;
+    if (h >= A.hb[5]) return;
+    const int i = layer_of(A, h), i0 = layer_of(A, 0.0);
+    d[i] += 1.0 / A.b[i];
+    d[i0] -= 1.0 / A.b[i0];
+    d[5 + i] += (h - A.c[i]) / (A.c[i] * A.c[i]);
+    d[5 + i0] += 1.0 / A.c[i0];
+}
+
+// d(integrand)/d(eta at h) and d(integrand)/d(eta_o) of ax and al.
+struct RaySensitivity {
+    const Layered *A;
+    double eta_o, so, co;
+    void operator()(double h, double &gx_e, double &gx_o, double &gl_e, double &gl_o,
+                    double &eta) const {
+        eta = eta_of(*A, h);
+        const double np1 = 1.0 + eta;
+        const double rm1 = (eta_o - eta) / np1;
+        const double r = 1.0 + rm1;
+        const double s = so * r;
+        const double c = std::sqrt((1.0 - s) * (1.0 + s));
+        const double dc = -so * so * r / c;                 // dc/dr
+        const double Aq = rm1 * (r + 1.0);                  // r^2 - 1
+        const double co2 = co * co;
+        const double E = (r * co + c) * c;
+        const double dE = (co + dc) * c + (r * co + c) * dc;
+        const double dgx = co2 * (2.0 * r * E - Aq * dE) / (E * E);
+        const double F = (co + c) * c;
+        const double dF = dc * (2.0 * c + co);
+        const double dgl = -eta * co2 * co * dc / (c * c) + so * so * co2 * (2.0 * r * F - Aq * dF) / (F * F);
+        const double dr_de = -r / np1, dr_do = 1.0 / np1;
+        gx_e = dgx * dr_de;
+        gx_o = dgx * dr_do;
+        gl_e = co2 * co / c + dgl * dr_de;
+        gl_o = dgl * dr_do;
+    }
+};
+
+}  // namespace
+
+void eta_sensitivity(const cher_atmosphere &atm, double h, double *d /*[10]*/) {
+    const Layered A = make_layered(atm);
+    dlneta_dp(A, h, d);
+    const double e = eta_of(A, h);
+    for (int q = 0; q < 10; ++q) d[q] *= e;
+}
+
+cher_status build_sensitivity(const cher_atmosphere &atm, double h_obs, const HostTables &T,
+                              std::vector<double> &out) {
+    const Layered A = make_layered(atm);
+    const int H = T.H, Z = T.Z;
+    out.assign(static_cast<size_t>(H) * Z * 20, 0.0);
+    const double eta_o = eta_of(A, h_obs);
+    double deo[10];
+    dlneta_dp(A, h_obs, deo);
+    for (int q = 0; q < 10; ++q) deo[q] *= eta_o;
+    static const GaussLegendre gl;
+    auto column = [&](int k) {
+        const double q2 = static_cast<double>(k) * T.dq;
+        const double so = std::sqrt(q2);
+        RaySensitivity f{&A, eta_o, so, std::sqrt((1.0 - so) * (1.0 + so))};
+        double acc[20] = {0};
+        for (int j = 1; j < H; ++j) {
+            const double lo = h_obs + static_cast<double>(j - 1) * T.dht;
+            const double hi = h_obs + static_cast<double>(j) * T.dht;
+            // pieces split at the layer boundaries, 12-point Gauss-Legendre
+            double a = lo;
+            for (int pi = 1; pi <= 6; ++pi) {
+                double b = hi;
+                if (pi <= 5) {
+                    const double hb = A.hb[pi];
+                    if (!(hb > a && hb < hi)) continue;
+                    b = hb;
+                }
+                const double m = 0.5 * (a + b), hw = 0.5 * (b - a);
+                for (int g = 0; g < GaussLegendre::N; ++g) {
+                    const double h = m + hw * gl.x[g];
+                    double gxe, gxo, gle, glo, eta;
+                    f(h, gxe, gxo, gle, glo, eta);
+                    double de[10];
+                    dlneta_dp(A, h, de);
+                    const double wgt = gl.w[g] * hw;
+                    for (int q = 0; q < 10; ++q) {
+                        const double dep = de[q] * eta;
+                        acc[q] += wgt * (gxe * dep + gxo * deo[q]);
+                        acc[10 + q] += wgt * (gle * dep + glo * deo[q]);
+                    }
+                }
+                a = b;
+                if (pi > 5) break;
+            }
+            double *dst = &out[(static_cast<size_t>(j) * Z + k) * 20];
+            for (int q = 0; q < 20; ++q) dst[q] = acc[q];
+        }
+    };
+    unsigned nthr = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    nthr = std::min<unsigned>(nthr, static_cast<unsigned>(Z));
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < nthr; ++t)
+        pool.emplace_back([&, t] {
+            for (int k = static_cast<int>(t); k < Z; k += static_cast<int>(nthr)) column(k);
+        });
+    for (auto &th : pool) th.join();
+    return CHER_OK;
+}
+
 cher_status build_grid(const cher_telescope *tel, int32_t n_tel, double theta_max,
                        HostGrid &g) {
-    // A line that crosses sphere k within the zenith range reaches h_obs at
-    // a horizontal distance of at most |z| tan(theta_max) + r / cos(theta_max)
-    // from the centre; a margin covers single-precision ground points.
+    // A line that crosses sphere k with zenith at most theta_max reaches h_obs
+    // at a horizontal distance of at most |z| tan(theta_max) + r / cos(theta_max)
+    // from the centre (the distance from the centre to the line is at least
+    // cos(theta) times the horizontal distance in the plane of the centre); a
+    // margin covers single-precision ground points.  Cells of the size of the
+    // largest reach; a sphere is listed in every cell its reach disc touches.
     std::vector<double> reach(n_tel);
     double rmax = 0.0, xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
     for (int k = 0; k < n_tel; ++k) {
@@ -267,7 +386,7 @@ cher_status build_grid(const cher_telescope *tel, int32_t n_tel, double theta_ma
         ymin = std::min(ymin, tel[k].y - reach[k]);
         ymax = std::max(ymax, tel[k].y + reach[k]);
     }
-    double cs = 2.0 * rmax;
+    double cs = rmax;
     for (int attempt = 0; attempt < 24; ++attempt) {
         const double ex = xmax - xmin, ey = ymax - ymin;
         const double nxd = std::ceil(ex / cs), nyd = std::ceil(ey / cs);
@@ -286,7 +405,15 @@ cher_status build_grid(const cher_telescope *tel, int32_t n_tel, double theta_ma
             const int cy0 = std::max(0, static_cast<int>(std::floor((tel[k].y - reach[k] - g.y0) * g.inv_cs)));
             const int cy1 = std::min(g.ny - 1, static_cast<int>(std::floor((tel[k].y + reach[k] - g.y0) * g.inv_cs)));
             for (int cy = cy0; cy <= cy1; ++cy)
-                for (int cx = cx0; cx <= cx1; ++cx) cells[static_cast<size_t>(cy) * g.nx + cx].push_back(k);
+                for (int cx = cx0; cx <= cx1; ++cx) {
+                    // distance from the centre to the cell rectangle
+                    const double rx0 = g.x0 + cx * cs, rx1 = rx0 + cs;
+                    const double ry0 = g.y0 + cy * cs, ry1 = ry0 + cs;
+                    const double dx = std::max({rx0 - tel[k].x, 0.0, tel[k].x - rx1});
+                    const double dy = std::max({ry0 - tel[k].y, 0.0, tel[k].y - ry1});
+                    if (dx * dx + dy * dy <= reach[k] * reach[k])
+                        cells[static_cast<size_t>(cy) * g.nx + cx].push_back(k);
+                }
         }
         size_t worst = 0;
         for (auto &c : cells) worst = std::max(worst, c.size());

@@ -71,3 +71,25 @@ def test_host_tables_reject_bad_ranges():
         P.build_tables_host(atm, 2200.0, 10000, 100, 64, 89.0, 60000.0)
     with pytest.raises(P.CherError):
         P.build_tables_host(atm, 2200.0, 10000, 100, 64, 70.0, 1000.0)
+
+
+def test_adjoint_sensitivity_tables_match_finite_differences():
+    """d(ax, al)/d(b_i, c_i) of the host builder against central differences
+    of the table builder itself (the tables are smooth in the parameters)."""
+    atm = workloads.us_standard_atmosphere()
+    args = (2200.0, 10000, 120, 12, 70.0, 60000.0)
+    dax, dal = P.build_sensitivity_host(atm, *args)
+    for q, (key, i) in enumerate([("b", k) for k in range(5)] + [("c", k) for k in range(5)]):
+        eps = 1e-6
+        a1 = {k: (list(v) if isinstance(v, list) else v) for k, v in atm.items()}
+        a2 = {k: (list(v) if isinstance(v, list) else v) for k, v in atm.items()}
+        a1[key][i] *= 1 + eps
+        a2[key][i] *= 1 - eps
+        _, x1, l1 = P.build_tables_host(a1, *args)
+        _, x2, l2 = P.build_tables_host(a2, *args)
+        h = atm[key][i] * eps
+        fx, fl = (x1 - x2) / (2 * h), (l1 - l2) / (2 * h)
+        sx = max(np.abs(fx).max(), 1e-30)
+        sl = max(np.abs(fl).max(), 1e-30)
+        assert np.abs(fx - dax[q]).max() <= 1e-5 * sx + 1e-14, (key, i)
+        assert np.abs(fl - dal[q]).max() <= 1e-5 * sl + 1e-14, (key, i)

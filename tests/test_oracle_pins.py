@@ -420,3 +420,25 @@ def test_sphere_hits_are_geometric():
         D = np.stack([out["cx"][miss], out["cy"][miss], out["cz"][miss]], 1)
         dist = np.linalg.norm(np.cross(d, D), axis=1)
         assert np.all(dist > tr)
+
+
+# --------------------------------------------------------------------------
+# The differentiable read-out (smoothed density, mean arrival time)
+# --------------------------------------------------------------------------
+def test_density_read_out_is_the_gaussian_sum():
+    """S_k = sum_b w_b G(r_bk) with the normalised 2-D Gaussian of width sigma
+    cut at 6 sigma, U_k = sum w G t, over the bunches that reach the ground."""
+    sc = workloads.vertical_1tev(n=3000)
+    tel = np.array([[0.0, 0.0, 0.0, 12.0], [120.0, 0.0, 0.0, 8.0], [60.0, 103.9, 0.0, 6.0]])
+    M = oracle.Model(sc["atm"], sc["h_obs"], tel, H=300, Z=32, t_ref=sc["t_ref"])
+    out = M.bunches(sc["tracks"], seed=5)
+    for sigma in (1.0, 4.0):
+        S, U = M.density_sums(sc["tracks"], 5, out["nb"], sigma)
+        g = out["status"] == oracle.ST_GROUND
+        for k, (x, y, _, _) in enumerate(tel):
+            r2 = (out["X"][g] - x) ** 2 + (out["Y"][g] - y) ** 2
+            G = np.exp(-r2 / (2 * sigma ** 2)) / (2 * math.pi * sigma ** 2) * (r2 < 36 * sigma ** 2)
+            assert S[k] == pytest.approx(np.sum(out["w"][g] * G), rel=1e-12, abs=1e-300)
+            assert U[k] == pytest.approx(np.sum(out["w"][g] * G * out["t"][g]), rel=1e-12,
+                                         abs=1e-300)
+        assert S.sum() > 0
