@@ -29,6 +29,7 @@ struct cher_ctx {
     cher::HostGrid G[2];                  // zenith bands: steep, all
     double q_band = 0;
     double eta_obs = 0;
+    double eta_slope = 0;                 // max |eta[k+1] - eta[k]| / dh
     double *d_eta64 = nullptr;
     float *d_eta32 = nullptr;
     void *d_tab64 = nullptr, *d_tab32 = nullptr;
@@ -166,6 +167,7 @@ cher::KParams base_params(const cher_ctx *c, const cher_tracks *t, uint64_t seed
     p.eta64 = c->d_eta64;
     p.eta32 = c->d_eta32;
     p.eta_in_smem = (fp32 && c->T.n_fine <= 16384) ? 1 : 0;
+    p.eta_slope = c->eta_slope;
     p.h_obs = c->h_obs;
     p.eta_obs = c->eta_obs;
     p.H = c->T.H;
@@ -325,6 +327,9 @@ cher_status cher_build_refraction_tables(cher_ctx *c, int32_t n_heights, int32_t
     c->G[1] = std::move(G[1]);
     c->q_band = std::sin(th_band) * std::sin(th_band);
     c->eta_obs = cher::eta_lookup(c->T, c->h_obs);
+    c->eta_slope = 0.0;
+    for (int k = 0; k + 1 < c->T.n_fine; ++k)
+        c->eta_slope = std::max(c->eta_slope, std::fabs(c->T.eta[k + 1] - c->T.eta[k]) * c->T.inv_dh);
 
     const int H = c->T.H, Z = c->T.Z;
     std::vector<double> t64(static_cast<size_t>(H) * (Z - 1) * 4);

@@ -75,6 +75,7 @@ struct KParams {
     const double *eta64;
     const float *eta32;
     int32_t eta_in_smem;
+    double eta_slope;                     // max |eta[k+1] - eta[k]| / dh
     // observation level
     double h_obs, eta_obs;
     // refraction tables, pair-interleaved: entry (j, k), k < Z-1, holds
@@ -125,6 +126,8 @@ struct KParams {
     struct {
         float h_obs, dH_max, eta_o, inv_np1o, np1o, q_max, inv_dht, inv_dq, inv_dh;
         float lam_inv1, lam_dinv, rcut2, q_band;
+        // FP32 screen of the yield: constants and the table's largest slope
+        float inv_me, K, inv_B, h_max, dh, eta_slope;
         float gx0[2], gy0[2], inv_gcs[2];
     } f;
 };

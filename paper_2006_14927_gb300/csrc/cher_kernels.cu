@@ -45,13 +45,98 @@ struct alignas(16) Seg {
     int nb, pad;
 };
 
+// ------------------------------------------------------------------------
+// a1 in the FP32 path: the yield evaluated in single precision with a bound
+// E on the rounding error of q = N / B.  When no integer lies within
+// [q - E, q + E] the bunch count ceil(q) is certain and equals the FP64
+// result; when the Cherenkov-threshold cancellation in the numerator is
+// strong, or an integer is within reach, the exact FP64 chain decides.
+// ------------------------------------------------------------------------
+struct YieldF {
+    int nb;
+    bool valid;
+    float g, eta, s2, N;
+};
+
+// sign and zero tests on the bit pattern (no FP64 instruction)
+__device__ __forceinline__ bool d_negative(double v) {
+    const long long b = __double_as_longlong(v);
+    return b < 0 && (b & 0x7fffffffffffffffLL) != 0;
+}
+__device__ __forceinline__ bool d_not_positive(double v) {
+    const long long b = __double_as_longlong(v);
+    return b < 0 || b == 0;
+}
+
+__device__ __forceinline__ void step_yield_screened(const KParams &p, bool others_valid,
+                                                    double z0, double len, double ekin, float uz,
+                                                    const float *eta_s, YieldF &y) {
+    y.nb = 0;
+    y.valid = false;
+    y.g = y.eta = y.s2 = y.N = 0.0f;
+    if (!others_valid || !finite_d(z0) || !finite_d(len) || !finite_d(ekin) || !finite_f(uz) ||
+        d_negative(len) || d_not_positive(ekin))
+        return;
+    y.valid = true;
+    const float u = 5.9604645e-8f;                       // 2^-24
+    const float e = static_cast<float>(ekin), L = static_cast<float>(len);
+    const float z = static_cast<float>(z0);
+    const float g = e * p.f.inv_me;
+    const float gam = 1.0f + g, gam2 = gam * gam;
+    const float hm = z + (0.5f * L) * uz;
+    float hc = fminf(fmaxf(hm, 0.0f), p.f.h_max);
+    const float x = hc * p.f.inv_dh;
+    int k = static_cast<int>(x);
+    k = k > p.n_fine - 2 ? p.n_fine - 2 : k;
+    const float f = x - static_cast<float>(k);
+    const float t0 = eta_s ? eta_s[k] : __ldg(p.eta32 + k);
+    const float t1 = eta_s ? eta_s[k + 1] : __ldg(p.eta32 + k + 1);
+    const float eta = t0 + f * (t1 - t0);
+    const float np1 = 1.0f + eta, np1sq = np1 * np1;
+    const float a = eta * (2.0f + eta);
+    const float A = a * gam2;
+    const float num = A - np1sq;
+    const float bg2 = g * (2.0f + g);
+    const float den = bg2 * np1sq;
+    const float s2 = num / den;
+    const float KL = p.f.K * L;
+    const float q = KL * s2 * p.f.inv_B;
+    // rounding-error bound (first order, each term padded)
+    const float d_eta = 6.0f * u * p.f.eta_slope * (fabsf(z) + L + p.f.dh) + 5.0f * u * eta;
+    const float d_a = (2.0f + 2.0f * eta) * d_eta + 3.0f * u * a;
+    const float d_A = gam2 * (d_a + 10.0f * u * a);
+    const float d_B = 2.0f * np1 * d_eta + 3.0f * u * np1sq;
+    const float d_num = d_A + d_B + u * (A + np1sq);
+    const float d_s2 = d_num / den + fabsf(s2) * (12.0f * u + 2.0f * d_eta);
+    const float E = 4.0f * (KL * p.f.inv_B * d_s2 + fabsf(q) * 8.0f * u) + 1e-30f;
+    const float lo = q - E, hi = q + E;
+    if (hi <= 0.0f) return;                              // below threshold for sure
+    if (lo > 0.0f && ceilf(lo) == ceilf(hi) && num >= 0.01f * (A + np1sq) && hi < 1.0e9f) {
+        y.nb = static_cast<int>(ceilf(hi));
+        y.g = g;
+        y.eta = eta;
+        y.s2 = s2;
+        y.N = KL * s2;
+        return;
+    }
+    // exact FP64 chain (rare)
+    Yield yd;
+    step_yield(p, true, z0, len, ekin, static_cast<double>(uz), yd);
+    y.valid = yd.valid;
+    y.nb = yd.nb;
+    y.g = static_cast<float>(yd.g);
+    y.eta = static_cast<float>(yd.eta);
+    y.s2 = static_cast<float>(yd.s2);
+    y.N = static_cast<float>(yd.N);
+}
+
 template <class R>
 __device__ __forceinline__ R load_dir(const void *p, int64_t i) {
     return __ldg(static_cast<const R *>(p) + i);
 }
 
-template <class R>
-__device__ __forceinline__ void prep_step(const KParams &p, int64_t i, const Yield &y, Seg<R> &S) {
+template <class R, class Y>
+__device__ __forceinline__ void prep_step(const KParams &p, int64_t i, const Y &y, Seg<R> &S) {
     const R ux = load_dir<R>(p.ux, i);
     const R uy = load_dir<R>(p.uy, i);
     const R uz = load_dir<R>(p.uz, i);
@@ -360,7 +445,7 @@ __device__ __forceinline__ void flush_stat_signed(unsigned long long *stats, int
 // The fused kernel.
 // ------------------------------------------------------------------------
 template <class R, int BLOCK, int MODE>
-__global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_gen_prop(const KParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     Seg<R> *seg = reinterpret_cast<Seg<R> *>(smem);
     int *off = reinterpret_cast<int *>(seg + BLOCK);          // BLOCK + 1
@@ -373,6 +458,7 @@ __global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
             for (int k = threadIdx.x; k < p.n_fine; k += BLOCK) eta_s[k] = __ldg(p.eta32 + k);
         }
     }
+    __syncthreads();          // the staged table is read from phase A on
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // candidate grids, read through L1 (a few KB)
     GridView gv[2];
@@ -448,9 +534,16 @@ __global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
         const int64_t i = base + tid;
         int nb = 0;
         if (i < p.n) {
-            Yield y;
-            step_yield(p, step_valid<R>(p, i), __ldg(p.z0 + i), __ldg(p.len + i),
-                       __ldg(p.ekin + i), static_cast<double>(load_dir<R>(p.uz, i)), y);
+            // the FP32 path screens the yield in FP32 (same bunch counts as FP64)
+            using YT = typename std::conditional<std::is_same<R, float>::value, YieldF,
+                                                 Yield>::type;
+            YT y;
+            if constexpr (std::is_same<YT, YieldF>::value)
+                step_yield_screened(p, step_valid<R>(p, i), __ldg(p.z0 + i), __ldg(p.len + i),
+                                    __ldg(p.ekin + i), load_dir<float>(p.uz, i), eta_s, y);
+            else
+                step_yield(p, step_valid<R>(p, i), __ldg(p.z0 + i), __ldg(p.len + i),
+                           __ldg(p.ekin + i), static_cast<double>(load_dir<R>(p.uz, i)), y);
             if constexpr (MODE == MODE_SCREEN) {
                 // the adjoint freezes the sub-step structure
                 const int nf = __ldg(p.nb_frozen + i);
@@ -462,7 +555,7 @@ __global__ void __launch_bounds__(BLOCK) k_gen_prop(const KParams p) {
             st_inval += !y.valid;
             if constexpr (MODE == MODE_YIELD) {
                 p.y_nb[i] = nb;
-                p.y_w[i] = nb > 0 ? y.N / static_cast<double>(nb) : 0.0;
+                p.y_w[i] = nb > 0 ? static_cast<double>(y.N) / static_cast<double>(nb) : 0.0;
             } else {
                 prep_step<R>(p, i, y, seg[tid]);
             }
@@ -720,6 +813,12 @@ void fill_float_constants(KParams &p) {
         p.f.inv_gcs[g] = static_cast<float>(p.grid[g].inv_cs);
     }
     p.f.q_band = static_cast<float>(p.q_band);
+    p.f.inv_me = static_cast<float>(p.inv_me);
+    p.f.K = static_cast<float>(p.K);
+    p.f.inv_B = static_cast<float>(p.inv_B);
+    p.f.h_max = static_cast<float>(p.h_max);
+    p.f.dh = static_cast<float>(1.0 / p.inv_dh);
+    p.f.eta_slope = static_cast<float>(p.eta_slope * 1.01);
     p.f.rcut2 = static_cast<float>(p.rcut2);
 }
 

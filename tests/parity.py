@@ -4,13 +4,16 @@ the oracle on the same seeded inputs, compare element by element.
 Tolerances (the FP64 path against the FP64 oracle; the FP32-bulk path with
 the stated accuracy targets):
 
-* bunch counts nb: bit-exact on both paths (the yield is FP64 on both
-  sides, in the same operation order);
+* bunch counts nb: bit-exact on both paths (the FP64 path evaluates the
+  yield in FP64 in the oracle's operation order; the FP32 path screens it in
+  FP32 with a rounding-error bound and falls back to that FP64 chain
+  whenever the count is not certain);
 * FP64 path: relative 1e-9 of max(|value|, scale), scale 1 km for ground
   coordinates and 1 us for times (the sizes of the terms they are formed
   from), 1e-9 for direction cosines;
 * FP32 path: 5 cm in ground position, 0.1 ns in arrival time, 1e-5 in
-  direction cosines, 1e-6 relative in photons and wavelength;
+  direction cosines, 1e-4 relative in photons (the yield is screened in
+  FP32), 1e-7 relative in wavelength;
 * statuses and telescope crossings: exact, after leaving out the bunches
   whose oracle value lies within the path's precision of a decision
   boundary (5 cm of a sphere surface or of h_obs / h_max, 1e-5 of the
@@ -32,7 +35,7 @@ FP64 = P.CHER_FP64
 TOL = {
     FP64: dict(pos_rel=1e-9, pos_scale=1e3, t_rel=1e-9, t_scale=1e3, dir=1e-9, rel=1e-12,
                edge_m=1e-6, edge_q=1e-12, edge_pz=1e-12),
-    FP32: dict(pos_abs=0.05, t_abs=0.1, dir=1e-5, rel=1e-6, edge_m=0.05, edge_q=1e-5,
+    FP32: dict(pos_abs=0.05, t_abs=0.1, dir=1e-5, rel=1e-4, edge_m=0.05, edge_q=1e-5,
                edge_pz=1e-6),
 }
 
@@ -123,9 +126,15 @@ def sphere_distance(M: oracle.Model, o: dict) -> np.ndarray:
     return out
 
 
-def compare_yield(o_nb, g_nb, o_w, g_w):
+def compare_yield(o_nb, g_nb, o_w, g_w, precision=FP64):
+    """Bunch counts bit-exact; photons per bunch to 1e-15 (FP64) or 1e-4
+    relative plus 1e-6 photons (FP32: the yield is screened in FP32 and its
+    photon count keeps FP32 rounding, amplified near the threshold)."""
     assert np.array_equal(o_nb, g_nb), f"{np.sum(o_nb != g_nb)} bunch counts differ"
-    np.testing.assert_allclose(g_w, o_w, rtol=1e-15, atol=0)
+    if precision == FP64:
+        np.testing.assert_allclose(g_w, o_w, rtol=1e-15, atol=0)
+    else:
+        np.testing.assert_allclose(g_w, o_w, rtol=1e-4, atol=1e-6)
 
 
 def compare_trace(M: oracle.Model, o: dict, g: dict, precision: int) -> dict:
@@ -162,8 +171,8 @@ def compare_trace(M: oracle.Model, o: dict, g: dict, precision: int) -> dict:
         assert np.all(dt <= t["t_abs"]), dt.max()
         assert np.all(dz <= t["pos_abs"]), dz.max()
     assert np.all(dcx <= t["dir"]) and np.all(dcy <= t["dir"]), (dcx.max(), dcy.max())
-    assert np.all(dw <= t["rel"]), dw.max()
-    assert np.all(dl <= max(t["rel"], 1e-7 if precision == FP32 else 1e-14)), dl.max()
+    assert np.all(dw <= t["rel"] + 1e-6 / o["w"]), dw.max()
+    assert np.all(dl <= (1e-6 if precision == FP32 else 1e-14)), dl.max()
     # crossings per bunch
     dist = sphere_distance(M, o)
     hit_edge = np.any(np.abs(dist) < t["edge_m"], axis=1)

@@ -40,7 +40,7 @@ def _full_compare(sc, prec, seed=SEED, cap=200_000):
     o = M.bunches(tr, seed)
     nb_o, w_o, _, _ = M.segment_yield(tr)
     g = gpu_trace(ctx, tr, sc["t_ref"], seed, prec)
-    compare_yield(nb_o, g["nb"], w_o, g["w"])
+    compare_yield(nb_o, g["nb"], w_o, g["w"], prec)
     rt = compare_trace(M, o, g, prec)
     code, stats, out = gpu_hits(ctx, tr, sc["t_ref"], seed, prec, cap)
     assert code == 0
@@ -169,7 +169,7 @@ def test_full_size_vertical_shower_sampled():
     dev = P.device_tracks(tr, FP32, t_ref=sc["t_ref"])
     nb_g, w_g = ctx.segment_yield(dev, FP32)
     nb_o, w_o, _, _ = M.segment_yield(tr)
-    compare_yield(nb_o, nb_g.cpu().numpy(), w_o, w_g.cpu().numpy())
+    compare_yield(nb_o, nb_g.cpu().numpy(), w_o, w_g.cpu().numpy(), FP32)
     out = ctx.alloc_hits(2_000_000, FP32)
     ctx.generate_propagate(dev, SEED, FP32, out)
     code, stats = ctx.sync_status(out)
@@ -225,4 +225,51 @@ def test_graph_capture_replays_the_call():
             assert np.array_equal(rec[k], ref[k]), k
     g.close()
     torch.cuda.synchronize()
+    ctx.close()
+
+
+def test_fp32_yield_screen_exact_at_integer_and_threshold_edges():
+    """The FP32 path screens the yield in single precision and falls back to
+    the FP64 chain when the bunch count is not certain.  Horizontal steps (the
+    midpoint height then does not depend on the length) whose N/B lies within
+    1e-12 .. 1e-6 of an integer, and steps at the Cherenkov threshold to
+    1e-7, must give the oracle's bunch counts."""
+    import math
+    sc = workloads.plain_fp64(n=10)
+    M = oracle_model(sc)
+    ctx = context(sc)
+    rng = np.random.default_rng(23)
+    K = 2 * math.pi * 7.2973525693e-3 * (1e9 / 300.0 - 1e9 / 600.0)
+    rows = []
+    for _ in range(400):
+        z = float(rng.uniform(0.0, 59000.0))
+        e = float(np.exp(rng.uniform(math.log(25.0), math.log(5e4))))
+        probe = dict(x0=[0.0], y0=[0.0], z0=[z], t0=[0.0], len=[1.0], ekin=[e],
+                     ux=[1.0], uy=[0.0], uz=[0.0])
+        _, _, s2, _ = M.segment_yield({k: np.array(v) for k, v in probe.items()})
+        if not s2[0] > 0:
+            continue
+        for m in (1, 2, 7, 40, 173):
+            for d in (-1e-6, -1e-9, -1e-12, 0.0, 1e-12, 1e-9, 1e-6):
+                L = m * 5.0 / (K * s2[0]) * (1.0 + d)
+                rows.append((z, e, L))
+    # threshold: n at the height from the table, E_t from beta n = 1
+    for z in np.linspace(0.0, 50000.0, 60):
+        eta = oracle.eta_lookup(M.eta_tab, M.h_max, z)[0]
+        n = 1.0 + eta
+        e_t = 0.51099895 * (n / math.sqrt(n * n - 1.0) - 1.0)
+        for d in (-1e-7, -1e-9, 0.0, 1e-9, 1e-7, 1e-5):
+            rows.append((float(z), e_t * (1.0 + d), 7.5))
+    rows = np.array(rows)
+    n = len(rows)
+    tr = dict(x0=np.zeros(n), y0=np.zeros(n), z0=rows[:, 0], t0=np.zeros(n), len=rows[:, 2],
+              ekin=rows[:, 1], ux=np.ones(n), uy=np.zeros(n), uz=np.zeros(n),
+              shower=np.zeros(n, np.uint32))
+    nb_o, w_o, _, _ = M.segment_yield(tr)
+    dev = P.device_tracks(tr, FP32, t_ref=sc["t_ref"])
+    nb_g, w_g = ctx.segment_yield(dev, FP32)
+    compare_yield(nb_o, nb_g.cpu().numpy(), w_o, w_g.cpu().numpy(), FP32)
+    # and the fused kernel generates exactly that many bunches
+    code, stats, _ = gpu_hits(ctx, tr, sc["t_ref"], SEED, FP32, 16)
+    assert int(stats[3]) == int(nb_o.sum())
     ctx.close()
