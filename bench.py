@@ -137,6 +137,27 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def shard(rank: int, n_per_rank: int, base_seed: int):
+    """Weak scaling: rank r simulates its own shower (seed base + r) and
+    numbers its steps from r * n_per_rank, so no two ranks share a Philox
+    counter and no collective is needed on the data path."""
+    return base_seed + rank, rank * n_per_rank
+
+
+def reduce_over_ranks(t_local: float, bunches_local: float, world: int, device):
+    """Whole-job figures: the slowest rank's time and the bunches of all
+    ranks (the only collectives of the benchmark, outside the timed work)."""
+    if world <= 1:
+        return t_local, bunches_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    b = torch.tensor([bunches_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(b.item())
+
+
 def run_reference(args):
     """The FP64 CPU oracle on a bounded sample of the same workload."""
     rank, world, _ = _env_rank()
@@ -198,21 +219,27 @@ def run_ours(args):
     # ---- workload (each rank its own shower: weak scaling) ----------------
     wl = args.workload
     if wl == "vertical_1tev":
-        sc = workloads.vertical_1tev(n=int(2_000_000 * args.scale), seed=2 + rank)
+        n_req = int(2_000_000 * args.scale)
+        seed, track_base = shard(rank, n_req, 2)
+        sc = workloads.vertical_1tev(n=n_req, seed=seed)
     elif wl == "inclined_20tev":
-        sc = workloads.inclined_20tev(n=int(100_000_000 * args.scale), seed=5 + 100 * rank)
+        n_req = int(100_000_000 * args.scale)
+        seed, track_base = shard(rank, n_req, 5)
+        sc = workloads.inclined_20tev(n=n_req, seed=seed)
     elif wl == "batched_256":
-        sc = workloads.batched_256(total=int(200_000_000 * args.scale), seed=3 + 100 * rank)
+        n_req = int(200_000_000 * args.scale)
+        seed, track_base = shard(rank, n_req, 3)
+        sc = workloads.batched_256(total=n_req, seed=seed)
     else:
         sc = workloads.WORKLOADS[wl]()
+        track_base = rank * len(sc["tracks"]["x0"])
     n = len(sc["tracks"]["x0"])
-    track_base = rank * n
     t0 = time.perf_counter()
     ctx = P.Context(sc["atm"], sc["h_obs"], sc["telescopes"])
     ctx.build_refraction_tables(sc["H"], sc["Z"], sc["theta_max_deg"], sc["h_max"])
     table_s = time.perf_counter() - t0
     cap = args.cap or (600_000 if args.workload == "vertical_1tev" else
-                       max(200_000, int(4_000_000 * args.scale)))
+                       max(200_000, int(8_000_000 * args.scale)))
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def measure(prec, steps, warmup, autotune):
@@ -225,7 +252,7 @@ def run_ours(args):
         for _ in range(warmup):
             ctx.generate_propagate(dtr, 11, prec, out, track_base=track_base)
         code, stats = ctx.sync_status(out)
-        if code != 0:
+        if code not in (0, 6):                      # 6: a buffer overflowed (counted)
             raise RuntimeError(f"status {code} in warm-up")
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
@@ -271,15 +298,8 @@ def run_ours(args):
     r64 = measure(P.CHER_FP64, max(3, steps // 4), max(3, min(warmup, 3)), autotune=False)
 
     def total(r):
-        t = sum(r["ms"]) / 1e3
-        b = float(r["stats"][3]) * len(r["ms"])
-        if world > 1:
-            tt = torch.tensor([t, b], dtype=torch.float64, device=dev)
-            tmax = tt[:1].clone()
-            torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-            torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
-            return float(tmax.item()), float(tt[1].item())
-        return t, b
+        return reduce_over_ranks(sum(r["ms"]) / 1e3, float(r["stats"][3]) * len(r["ms"]),
+                                 world, dev)
 
     t32, b32 = total(r32)
     t64, b64 = total(r64)
@@ -333,10 +353,7 @@ def run_ours(args):
             d2h = e2e_step()
         barrier()
         te = time.perf_counter() - e0
-        if world > 1:
-            tt = torch.tensor([te], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = float(tt.item())
+        te, _ = reduce_over_ranks(te, 0.0, world, dev)
         e2e = {"value": b32 / len(r32["ms"]) * steps / te, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
@@ -393,6 +410,7 @@ def run_ours(args):
                      "roofline_ms": 1e3 * max(t_alu, t_fp64),
                      "fp64_yield_ms_at_peak": 1e3 * t_fp64,
                      "launch_ms": 1e3 * per_launch_s},
+        "overflowed_records": int(r32["stats"][10]),
         "gpu_launches": len(r32["ms"]),
         "clocks": clocks,
         "e2e": e2e,

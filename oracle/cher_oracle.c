@@ -296,7 +296,7 @@ static int orc_step_yield_valid(const orc_cfg *C, double z0, double len, double 
     double Ks2 = K * s2;
     double N = len * Ks2;
     double q = N * inv_B;
-    if (!(q < 2147483647.0)) return -1;
+    if (!(q < 4194304.0)) return -1;           /* more than 2^22 bunches */
     double nbd = ceil(q);
     Y->s2 = s2;
     Y->N = N;

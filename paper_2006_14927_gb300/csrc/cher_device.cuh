@@ -122,7 +122,7 @@ __device__ __forceinline__ void step_yield(const KParams &p, bool others_valid, 
     const double Ks2 = __dmul_rn(p.K, s2);
     const double N = __dmul_rn(len, Ks2);
     const double q = __dmul_rn(N, p.inv_B);
-    if (!(q < 2147483647.0)) {
+    if (!(q < 4194304.0)) {                    // more than 2^22 bunches: invalid
         y.valid = false;
         return;
     }
