@@ -34,11 +34,9 @@ struct cher_ctx {
     float *d_eta32 = nullptr;
     void *d_tab64 = nullptr, *d_tab32 = nullptr;
     void *d_tel64 = nullptr, *d_tel32 = nullptr;
-    uint32_t *d_cellw = nullptr;          // both grids, one word per cell
-    float *d_cand32 = nullptr;
-    double *d_cand64 = nullptr;
-    int32_t *d_cand_tel = nullptr;
-    int32_t n_cellw = 0, n_cand = 0, cell_base[2] = {0, 0};
+    int32_t *d_cell_start[2] = {nullptr, nullptr}, *d_cell_tel[2] = {nullptr, nullptr};
+    float *d_cand32[2] = {nullptr, nullptr};
+    double *d_cand64[2] = {nullptr, nullptr};
     // scratch: the persistent kernel's tile counter
     unsigned long long *d_scratch = nullptr;
     // launch shape
@@ -69,14 +67,15 @@ void free_tables(cher_ctx *c) {
     cudaFree(c->d_tab32);
     cudaFree(c->d_tel64);
     cudaFree(c->d_tel32);
-    cudaFree(c->d_cellw);
-    cudaFree(c->d_cand32);
-    cudaFree(c->d_cand64);
-    cudaFree(c->d_cand_tel);
-    c->d_cellw = nullptr;
-    c->d_cand32 = nullptr;
-    c->d_cand64 = nullptr;
-    c->d_cand_tel = nullptr;
+    for (int g = 0; g < 2; ++g) {
+        cudaFree(c->d_cell_start[g]);
+        cudaFree(c->d_cell_tel[g]);
+        cudaFree(c->d_cand32[g]);
+        cudaFree(c->d_cand64[g]);
+        c->d_cell_start[g] = c->d_cell_tel[g] = nullptr;
+        c->d_cand32[g] = nullptr;
+        c->d_cand64[g] = nullptr;
+    }
     c->d_eta64 = nullptr;
     c->d_eta32 = nullptr;
     c->d_tab64 = c->d_tab32 = nullptr;
@@ -111,42 +110,25 @@ cher_status upload(T **dst, const T *src, size_t n) {
     return CHER_OK;
 }
 
-// Device copies of both grids, packed: one word per cell (index of its
-// first candidate | count << 24) and per candidate the telescope centre and
-// squared radius in both precisions and the telescope index.
-cher_status upload_grids(cher_ctx *c) {
-    std::vector<uint32_t> cellw;
-    std::vector<float> c32;
-    std::vector<double> c64;
-    std::vector<int32_t> ctel;
-    for (int g = 0; g < 2; ++g) {
-        const cher::HostGrid &G = c->G[g];
-        c->cell_base[g] = static_cast<int32_t>(cellw.size());
-        const size_t cand_base = ctel.size();
-        const size_t nc = static_cast<size_t>(G.nx) * G.ny;
-        for (size_t cell = 0; cell < nc; ++cell) {
-            const size_t start = cand_base + G.cell_start[cell];
-            const size_t count = G.cell_start[cell + 1] - G.cell_start[cell];
-            if (start >= (size_t(1) << 24) || count > 255) return CHER_ERANGE;
-            cellw.push_back(static_cast<uint32_t>(start | (count << 24)));
-        }
-        for (const int32_t k : G.cell_tel) {
-            const cher_telescope &q = c->tel[k];
-            const double v[4] = {q.x, q.y, q.z, q.r * q.r};
-            for (int e = 0; e < 4; ++e) {
-                c64.push_back(v[e]);
-                c32.push_back(static_cast<float>(v[e]));
-            }
-            ctel.push_back(k);
+// device copies of grid g: cell starts, candidate telescopes and their
+// centres and squared radii in both precisions
+cher_status upload_grid(cher_ctx *c, int g) {
+    const cher::HostGrid &G = c->G[g];
+    std::vector<float> c32(G.cell_tel.size() * 4);
+    std::vector<double> c64(G.cell_tel.size() * 4);
+    for (size_t m = 0; m < G.cell_tel.size(); ++m) {
+        const cher_telescope &q = c->tel[G.cell_tel[m]];
+        const double v[4] = {q.x, q.y, q.z, q.r * q.r};
+        for (int e = 0; e < 4; ++e) {
+            c64[4 * m + e] = v[e];
+            c32[4 * m + e] = static_cast<float>(v[e]);
         }
     }
-    c->n_cellw = static_cast<int32_t>(cellw.size());
-    c->n_cand = static_cast<int32_t>(ctel.size());
     cher_status r;
-    if ((r = upload(&c->d_cellw, cellw.data(), cellw.size())) != CHER_OK ||
-        (r = upload(&c->d_cand32, c32.data(), c32.size())) != CHER_OK ||
-        (r = upload(&c->d_cand64, c64.data(), c64.size())) != CHER_OK ||
-        (r = upload(&c->d_cand_tel, ctel.data(), ctel.size())) != CHER_OK)
+    if ((r = upload(&c->d_cell_start[g], G.cell_start.data(), G.cell_start.size())) != CHER_OK ||
+        (r = upload(&c->d_cell_tel[g], G.cell_tel.data(), G.cell_tel.size())) != CHER_OK ||
+        (r = upload(&c->d_cand32[g], c32.data(), c32.size())) != CHER_OK ||
+        (r = upload(&c->d_cand64[g], c64.data(), c64.size())) != CHER_OK)
         return r;
     return CHER_OK;
 }
@@ -201,22 +183,16 @@ cher::KParams base_params(const cher_ctx *c, const cher_tracks *t, uint64_t seed
     for (int g = 0; g < 2; ++g) {
         p.grid[g].nx = c->G[g].nx;
         p.grid[g].ny = c->G[g].ny;
-        p.grid[g].cell_base = c->cell_base[g];
+        p.grid[g].n_cand = static_cast<int32_t>(c->G[g].cell_tel.size());
         p.grid[g].x0 = c->G[g].x0;
         p.grid[g].y0 = c->G[g].y0;
         p.grid[g].inv_cs = c->G[g].inv_cs;
+        p.grid[g].cell_start = c->d_cell_start[g];
+        p.grid[g].cand_tel = c->d_cell_tel[g];
+        p.grid[g].cand32 = c->d_cand32[g];
+        p.grid[g].cand64 = c->d_cand64[g];
     }
-    p.cellw = c->d_cellw;
-    p.cand32 = c->d_cand32;
-    p.cand64 = c->d_cand64;
-    p.cand_tel = c->d_cand_tel;
-    p.n_cellw = c->n_cellw;
-    p.n_cand = c->n_cand;
     p.q_band = c->q_band;
-    // small grids live in shared memory in the FP32 kernel
-    p.grid_smem_off = (fp32 && cher::grid_smem_bytes(p) <= 24 * 1024)
-                          ? static_cast<int32_t>(cher::grid_smem_offset(c->block, p))
-                          : -1;
     cher::fill_float_constants(p);
     return p;
 }
@@ -389,7 +365,7 @@ cher_status cher_build_refraction_tables(cher_ctx *c, int32_t n_heights, int32_t
         (r = upload(&d_tab32, t32.data(), t32.size())) != CHER_OK ||
         (r = upload(&d_tel64, tel64.data(), tel64.size())) != CHER_OK ||
         (r = upload(&d_tel32, tel32.data(), tel32.size())) != CHER_OK ||
-        (r = upload_grids(c)) != CHER_OK) {
+        (r = upload_grid(c, 0)) != CHER_OK || (r = upload_grid(c, 1)) != CHER_OK) {
         c->d_tab64 = d_tab64;
         c->d_tab32 = d_tab32;
         c->d_tel64 = d_tel64;

@@ -91,16 +91,13 @@ struct KParams {
     int32_t n_tel;
     const void *tel;                      // float4 / double4: x, y, z, r^2
     struct Grid {
-        int32_t nx, ny, cell_base;        // cells of grid g: cellw[cell_base ..]
+        int32_t nx, ny, n_cand;
         double x0, y0, inv_cs;
+        const int32_t *cell_start;        // [nx * ny + 1]
+        const int32_t *cand_tel;          // telescope of each entry
+        const void *cand32;               // float4 per entry: x, y, z, r^2
+        const void *cand64;               // double4 per entry
     } grid[2];
-    // both grids packed: one word per cell, start | count << 24, indexing the
-    // candidate arrays (x, y, z, r^2 per entry, and the telescope index)
-    const uint32_t *cellw;
-    const void *cand32, *cand64;
-    const int32_t *cand_tel;
-    int32_t n_cellw, n_cand;
-    int32_t grid_smem_off;                // FP32: byte offset of the staged grid
     double q_band;
     // outputs
     void *pos, *tim;
@@ -156,10 +153,6 @@ cudaError_t adjoint_pairs(bool fp32, int mode, const AdjParams &A, void *stream)
 
 // Fill KParams::f from the double fields.
 void fill_float_constants(KParams &p);
-// Shared-memory bytes of the two candidate grids (FP32 staging) and their
-// offset in the FP32 kernel's dynamic shared memory for a block size.
-size_t grid_smem_bytes(const KParams &p);
-size_t grid_smem_offset(int block, const KParams &p);
 
 enum Mode : int { MODE_HITS = 0, MODE_TRACE = 1, MODE_YIELD = 2, MODE_SCREEN = 3 };
 

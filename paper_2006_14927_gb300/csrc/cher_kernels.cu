@@ -206,8 +206,13 @@ struct Consts {
     int H, Z, n_fine;
 };
 
-// the dynamic shared memory of the fused kernel
-extern __shared__ __align__(16) unsigned char g_smem[];
+// the candidate grids as the kernel reads them (shared or global memory)
+struct GridView {
+    const int32_t *cell_start;
+    const int32_t *cand_tel;
+    const float4 *cand;
+    int nx, ny;
+};
 
 template <class R>
 __device__ __forceinline__ R eta_at(const KParams &p, const Consts<R> &c, const R *eta_s, R h) {
@@ -235,23 +240,6 @@ __device__ __forceinline__ R eta_at(const KParams &p, const Consts<R> &c, const 
 template <class R>
 __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, const R *eta_s,
                                       const Seg<R> &S, int64_t gi, int j, BunchOut<R> &o) {
-    // the step's constants, four 16-byte shared-memory loads (FP32)
-    R ux, uy, uz, L, e1x, e1y, e2x, e2y, e2z, cosc, sinc, inv_nb, x0, y0, dz0, tseg, inv_bc;
-    if constexpr (std::is_same<R, float>::value) {
-        const float4 *q = reinterpret_cast<const float4 *>(&S);
-        const float4 A = q[0], B = q[1], C = q[2], D = q[3];
-        ux = A.x; uy = A.y; uz = A.z; L = A.w;
-        e1x = B.x; e1y = B.y; e2x = B.z; e2y = B.w;
-        e2z = C.x; cosc = C.y; sinc = C.z; inv_nb = C.w;
-        x0 = D.x; y0 = D.y; dz0 = D.z; tseg = D.w;
-        inv_bc = S.inv_bc;
-    } else {
-        ux = S.ux; uy = S.uy; uz = S.uz; L = S.L;
-        e1x = S.e1x; e1y = S.e1y; e2x = S.e2x; e2y = S.e2y;
-        e2z = S.e2z; cosc = S.cosc; sinc = S.sinc; inv_nb = S.inv_nb;
-        x0 = S.x0; y0 = S.y0; dz0 = S.dz0; tseg = S.tseg;
-        inv_bc = S.inv_bc;
-    }
     const uint4 x = philox4x32_10(
         make_uint4(static_cast<uint32_t>(gi), static_cast<uint32_t>(static_cast<uint64_t>(gi) >> 32),
                    static_cast<uint32_t>(j), 0u),
@@ -267,8 +255,8 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
         u2 = u01d(x.z);
     }
     // sub-step j, emission point uniform inside it
-    const R f = (static_cast<R>(j) + u0) * inv_nb;
-    const R fl = f * L;
+    const R f = (static_cast<R>(j) + u0) * S.inv_nb;
+    const R fl = f * S.L;
     R sp, cp;
     if constexpr (std::is_same<R, float>::value) {
         // phi = 2 pi u1 = a + pi with a in (-pi, pi), where the hardware
@@ -280,12 +268,12 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
     } else {
         sincospi(2.0 * u1, &sp, &cp);
     }
-    const R px = cosc * ux + sinc * (cp * e1x + sp * e2x);
-    const R py = cosc * uy + sinc * (cp * e1y + sp * e2y);
-    const R pz = cosc * uz + sinc * (sp * e2z);
+    const R px = S.cosc * S.ux + S.sinc * (cp * S.e1x + sp * S.e2x);
+    const R py = S.cosc * S.uy + S.sinc * (cp * S.e1y + sp * S.e2y);
+    const R pz = S.cosc * S.uz + S.sinc * (sp * S.e2z);
     // 1/lambda^2 spectrum by inversion
     o.lam = R(1) / (c.lam_inv1 - u2 * c.lam_dinv);
-    const R dH = dz0 + fl * uz;                 // h_e - h_obs
+    const R dH = S.dz0 + fl * S.uz;                 // h_e - h_obs
     o.he = c.h_obs + dH;
     // rare conditions first (paper Alg. 2)
     if (!(pz < R(0))) { o.status = ST_UPWARD; return; }
@@ -340,43 +328,42 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
     const R tn = so * sec;
     const R D = tn * (dH + Ax * sec2);              // horizontal offset
     const R Lp = sec * (dH + Al * sec2);            // optical path
-    o.X = x0 + fl * ux + D * hx;
-    o.Y = y0 + fl * uy + D * hy;
-    o.t = tseg + fl * inv_bc + Lp * R(1.0 / kC);
+    o.X = S.x0 + fl * S.ux + D * hx;
+    o.Y = S.y0 + fl * S.uy + D * hy;
+    o.t = S.tseg + fl * S.inv_bc + Lp * R(1.0 / kC);
     o.cx = so * hx;
     o.cy = so * hy;
     o.cz = -co;
     o.status = ST_GROUND;
 }
 
-// Candidate spheres of the bunch's grid cell: bit m of the mask is
-// candidate entry s0 + m (the grid is chosen by the arrival zenith).
+// Candidate spheres of the bunch's grid cell: bit m of the mask is cell
+// entry s0 + m of grid g (chosen by the arrival zenith).
 template <class R>
 __device__ __forceinline__ unsigned sphere_hits(const KParams &p, const Consts<R> &c,
-                                                const BunchOut<R> &o, int &s0) {
+                                                const GridView *gv, const BunchOut<R> &o, int &s0,
+                                                int &g) {
     s0 = 0;
+    g = 0;
     if (o.status != ST_GROUND) return 0u;
+    g = (o.cx * o.cx + o.cy * o.cy <= c.q_band) ? 0 : 1;
     // (selects, not indexing: the small arrays stay in registers)
-    const bool g = !(o.cx * o.cx + o.cy * o.cy <= c.q_band);
     const R gx = (o.X - (g ? c.gx0[1] : c.gx0[0])) * (g ? c.inv_gcs[1] : c.inv_gcs[0]);
     const R gy = (o.Y - (g ? c.gy0[1] : c.gy0[0])) * (g ? c.inv_gcs[1] : c.inv_gcs[0]);
-    if (!(gx >= R(0)) || !(gy >= R(0))) return 0u;
-    const int ix = static_cast<int>(gx), iy = static_cast<int>(gy);   // saturating
-    const int nx = g ? p.grid[1].nx : p.grid[0].nx;
-    const int ny = g ? p.grid[1].ny : p.grid[0].ny;
-    if (ix >= nx || iy >= ny) return 0u;
-    const int cell = (g ? p.grid[1].cell_base : p.grid[0].cell_base) + iy * nx + ix;
+    const int nx = g ? gv[1].nx : gv[0].nx;
+    const int ny = g ? gv[1].ny : gv[0].ny;
+    if (!(gx >= R(0)) || !(gy >= R(0)) || !(gx < static_cast<R>(nx)) ||
+        !(gy < static_cast<R>(ny)))
+        return 0u;
+    const int cell = static_cast<int>(gy) * nx + static_cast<int>(gx);
     unsigned mask = 0u;
     if constexpr (std::is_same<R, float>::value) {
-        const bool sm = p.grid_smem_off >= 0;
-        const uint32_t *cw = reinterpret_cast<const uint32_t *>(g_smem + p.grid_smem_off);
-        const uint32_t w = sm ? cw[cell] : __ldg(p.cellw + cell);
-        s0 = static_cast<int>(w & 0xffffffu);
-        const int s1 = s0 + static_cast<int>(w >> 24);
-        const float4 *cd = reinterpret_cast<const float4 *>(
-            g_smem + p.grid_smem_off + ((4 * p.n_cellw + 15) & ~15));
+        const int32_t *cs = g ? gv[1].cell_start : gv[0].cell_start;
+        const float4 *cd = g ? gv[1].cand : gv[0].cand;
+        s0 = __ldg(cs + cell);
+        const int s1 = __ldg(cs + cell + 1);
         for (int m = s0; m < s1; ++m) {
-            const float4 T = sm ? cd[m] : __ldg(static_cast<const float4 *>(p.cand32) + m);
+            const float4 T = __ldg(cd + m);
             const float dx = T.x - o.X, dy = T.y - o.Y, dz = T.z;
             const float q0 = dy * o.cz - dz * o.cy;
             const float q1 = dz * o.cx - dx * o.cz;
@@ -384,10 +371,10 @@ __device__ __forceinline__ unsigned sphere_hits(const KParams &p, const Consts<R
             if (q0 * q0 + q1 * q1 + q2 * q2 <= T.w) mask |= 1u << (m - s0);
         }
     } else {
-        const uint32_t w = __ldg(p.cellw + cell);
-        s0 = static_cast<int>(w & 0xffffffu);
-        const int s1 = s0 + static_cast<int>(w >> 24);
-        const double2 *T = static_cast<const double2 *>(p.cand64);
+        const int32_t *cs = g ? p.grid[1].cell_start : p.grid[0].cell_start;
+        s0 = __ldg(cs + cell);
+        const int s1 = __ldg(cs + cell + 1);
+        const double2 *T = static_cast<const double2 *>(g ? p.grid[1].cand64 : p.grid[0].cand64);
         for (int m = s0; m < s1; ++m) {
             const double2 A = __ldg(T + 2 * m), B = __ldg(T + 2 * m + 1);
             const double dx = A.x - o.X, dy = A.y - o.Y, dz = B.x;
@@ -400,18 +387,20 @@ __device__ __forceinline__ unsigned sphere_hits(const KParams &p, const Consts<R
     return mask;
 }
 
-// telescope index and centre of candidate entry m
+// telescope index and centre of entry m of grid g
 template <class R>
-__device__ __forceinline__ int cand_info(const KParams &p, int m, R &tx, R &ty, R &tz) {
+__device__ __forceinline__ int cand_info(const KParams &p, const GridView *gv, int g, int m, R &tx,
+                                         R &ty, R &tz) {
     if constexpr (std::is_same<R, float>::value) {
-        const float4 T = __ldg(static_cast<const float4 *>(p.cand32) + m);
+        const float4 T = __ldg((g ? gv[1].cand : gv[0].cand) + m);
         tx = T.x; ty = T.y; tz = T.z;
+        return __ldg((g ? gv[1].cand_tel : gv[0].cand_tel) + m);
     } else {
-        const double2 *T = static_cast<const double2 *>(p.cand64);
+        const double2 *T = static_cast<const double2 *>(g ? p.grid[1].cand64 : p.grid[0].cand64);
         const double2 A = __ldg(T + 2 * m), B = __ldg(T + 2 * m + 1);
         tx = A.x; ty = A.y; tz = B.x;
+        return __ldg((g ? p.grid[1].cand_tel : p.grid[0].cand_tel) + m);
     }
-    return __ldg(p.cand_tel + m);
 }
 
 template <class R>
@@ -458,32 +447,31 @@ __device__ __forceinline__ void flush_stat_signed(unsigned long long *stats, int
 template <class R, int BLOCK, int MODE>
 __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / BLOCK : 1)
     k_gen_prop(const KParams p) {
-    Seg<R> *seg = reinterpret_cast<Seg<R> *>(g_smem);
+    extern __shared__ __align__(16) unsigned char smem[];
+    Seg<R> *seg = reinterpret_cast<Seg<R> *>(smem);
     int *off = reinterpret_cast<int *>(seg + BLOCK);          // BLOCK + 1
     int *wsum = off + BLOCK + 1;                                // BLOCK / 32
     __shared__ unsigned long long s_tile;
     R *eta_s = nullptr;
     if constexpr (std::is_same<R, float>::value) {
         if (p.eta_in_smem) {
-            eta_s = reinterpret_cast<R *>(
-                g_smem + ((sizeof(Seg<R>) * BLOCK + sizeof(int) * (BLOCK + 33) + 15) & ~size_t(15)));
+            eta_s = reinterpret_cast<R *>(wsum + 32);
             for (int k = threadIdx.x; k < p.n_fine; k += BLOCK) eta_s[k] = __ldg(p.eta32 + k);
         }
     }
     __syncthreads();          // the staged table is read from phase A on
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // candidate grids: staged into shared memory when they fit (FP32)
-    if constexpr (std::is_same<R, float>::value) {
-        if (p.grid_smem_off >= 0) {
-            uint32_t *cw = reinterpret_cast<uint32_t *>(g_smem + p.grid_smem_off);
-            float4 *cd = reinterpret_cast<float4 *>(g_smem + p.grid_smem_off +
-                                                    ((4 * p.n_cellw + 15) & ~15));
-            for (int k = tid; k < p.n_cellw; k += BLOCK) cw[k] = __ldg(p.cellw + k);
-            for (int k = tid; k < p.n_cand; k += BLOCK)
-                cd[k] = __ldg(static_cast<const float4 *>(p.cand32) + k);
-        }
+    // candidate grids, read through L1 (a few KB)
+    GridView gv[2];
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+        gv[g].cell_start = p.grid[g].cell_start;
+        gv[g].cand_tel = p.grid[g].cand_tel;
+        gv[g].cand = static_cast<const float4 *>(p.grid[g].cand32);
+        gv[g].nx = p.grid[g].nx;
+        gv[g].ny = p.grid[g].ny;
     }
-    __syncthreads();
+
     Consts<R> c;
     R np1o;
     if constexpr (std::is_same<R, float>::value) {
@@ -605,11 +593,6 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
         const int total = off[BLOCK];
 
         // ---- phase B: the tile's bunches -------------------------------------
-        // Each warp takes a contiguous run of 32-bunch windows.  The step of
-        // a window's first bunch comes from the previous window (one search
-        // per warp and tile); inside a window a lane's step is the last
-        // step whose first bunch is <= its own, counted from the at most 32
-        // step starts that follow with one ballot and a few shuffles.
         // Each warp takes an even share of contiguous 32-bunch windows (shares
         // differ by at most one window).  The step of a window's first bunch
         // comes from the previous window (one search per warp and tile);
@@ -674,8 +657,8 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                 }
                 continue;
             }
-            int s0 = 0;
-            unsigned hm = live ? sphere_hits<R>(p, c, o, s0) : 0u;
+            int s0 = 0, gsel = 0;
+            unsigned hm = live ? sphere_hits<R>(p, c, gv, o, s0, gsel) : 0u;
             if constexpr (MODE == MODE_TRACE) {
                 st_hits += __popc(hm);
                 if (live) {
@@ -693,7 +676,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                     int first = -1;
                     for (unsigned mm = hm; mm; mm &= mm - 1u) {      // lowest telescope index
                         R tx, ty, tz;
-                        const int k = cand_info<R>(p, s0 + __ffs(mm) - 1, tx, ty, tz);
+                        const int k = cand_info<R>(p, gv, gsel, s0 + __ffs(mm) - 1, tx, ty, tz);
                         first = (first < 0 || k < first) ? k : first;
                     }
                     p.t_first[gb] = first;
@@ -710,7 +693,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                     if (hm) {
                         const int bit = __ffs(hm) - 1;
                         hm &= hm - 1u;
-                        tel = cand_info<R>(p, s0 + bit, tx, ty, tz);
+                        tel = cand_info<R>(p, gv, gsel, s0 + bit, tx, ty, tz);
                         ++st_hits;
                     }
                     const unsigned grp = __match_any_sync(kFull, tel);
@@ -764,8 +747,6 @@ size_t smem_bytes(const KParams &p) {
     size_t b = sizeof(Seg<R>) * BLOCK + sizeof(int) * (BLOCK + 1 + 32);
     b = (b + 15) & ~size_t(15);
     if (std::is_same<R, float>::value && p.eta_in_smem) b += sizeof(float) * p.n_fine;
-    b = (b + 15) & ~size_t(15);
-    if (std::is_same<R, float>::value && p.grid_smem_off >= 0) b += grid_smem_bytes(p);
     return b;
 }
 
@@ -804,19 +785,6 @@ const void *pick_kernel(bool fp32, int block, int mode) {
 }
 
 }  // namespace
-
-size_t grid_smem_bytes(const KParams &p) {
-    return ((4 * static_cast<size_t>(p.n_cellw) + 15) & ~size_t(15)) +
-           16 * static_cast<size_t>(p.n_cand);
-}
-
-// where the staged grid starts in the FP32 kernel's shared memory
-size_t grid_smem_offset(int block, const KParams &p) {
-    size_t b = sizeof(Seg<float>) * block + sizeof(int) * (block + 1 + 32);
-    b = (b + 15) & ~size_t(15);
-    if (p.eta_in_smem) b += sizeof(float) * p.n_fine;
-    return (b + 15) & ~size_t(15);
-}
 
 void fill_float_constants(KParams &p) {
     p.f.h_obs = static_cast<float>(p.h_obs);

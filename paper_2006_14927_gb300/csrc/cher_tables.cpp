@@ -386,9 +386,7 @@ cher_status build_grid(const cher_telescope *tel, int32_t n_tel, double theta_ma
         ymin = std::min(ymin, tel[k].y - reach[k]);
         ymax = std::max(ymax, tel[k].y + reach[k]);
     }
-    // at most 64 x 64 cells (the FP32 kernel stages small grids in shared
-    // memory)
-    double cs = std::max(rmax, std::max(xmax - xmin, ymax - ymin) / 64.0);
+    double cs = rmax;
     for (int attempt = 0; attempt < 24; ++attempt) {
         const double ex = xmax - xmin, ey = ymax - ymin;
         const double nxd = std::ceil(ex / cs), nyd = std::ceil(ey / cs);
