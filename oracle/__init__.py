@@ -115,6 +115,8 @@ def lib():
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_density.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Tracks), ctypes.c_uint64,
                                   _i32p, ctypes.c_double, _dp, _dp]
+        L.orc_profile.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Tracks), _dp,
+                                  ctypes.c_double, ctypes.c_int, _dp]
         L.orc_philox_fill.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                       ctypes.c_int64, _u32p]
         _lib = L
@@ -355,6 +357,26 @@ class Model:
             raise ValueError("orc_density failed")
         del keep
         return S, U
+
+    # ---- longitudinal production profile (CERLDE) --------------------------
+    def profile(self, tracks: dict, bin_gcm2: float, n_bins: int, axis_cos=None):
+        """Photons produced per depth bin and shower: (n_showers, n_bins)."""
+        T, keep = self._tracks(tracks)
+        C = self._cfg()
+        ns = max(C.n_showers, 1)
+        prof = np.zeros((ns, int(n_bins)))
+        ac = None
+        if axis_cos is not None:
+            ac = _f64(np.atleast_1d(axis_cos))
+            if ac.shape[0] < ns:
+                raise ValueError("axis_cos needs one entry per shower")
+        rc = lib().orc_profile(ctypes.byref(C), ctypes.byref(T),
+                               _ptr(ac) if ac is not None else None, float(bin_gcm2),
+                               int(n_bins), _ptr(prof))
+        if rc != 0:
+            raise ValueError("orc_profile failed")
+        del keep
+        return prof
 
     def propagate_photon(self, xe, ye, he, te, px, py, pz, variant=0):
         r = np.zeros(6)

@@ -157,7 +157,8 @@ def _scenario(name, tracks, telescopes, t_ref, seed, h_obs=2200.0, H=1000, Z=64,
     n = len(tracks["x0"])
     if "shower" not in tracks:
         tracks["shower"] = np.zeros(n, np.uint32)
-    return dict(name=name, tracks=tracks, telescopes=np.asarray(telescopes, float),
+    n_sh = len(np.atleast_1d(t_ref))
+    return dict(name=name, axis_zenith_rad=np.zeros(n_sh), tracks=tracks, telescopes=np.asarray(telescopes, float),
                 t_ref=np.atleast_1d(np.asarray(t_ref, float)),
                 atm=us_standard_atmosphere(), h_obs=h_obs, h_max=h_max, n_fine=10000,
                 H=H, Z=Z, theta_max_deg=theta_max_deg, bunch_size=5.0,
@@ -232,6 +233,7 @@ def batched_256(total: int = 200_000_000, n_showers: int = 256, seed: int = 3) -
     sc = _scenario("batched_256", tracks, tel, t_ref, seed)
     sc["shower_counts"] = cnt
     sc["primary_energy_mev"] = e0
+    sc["axis_zenith_rad"] = zen
     return sc
 
 
@@ -239,8 +241,10 @@ def inclined_20tev(n: int = 100_000_000, seed: int = 5) -> dict:
     rng = np.random.Generator(np.random.PCG64(seed))
     tel = scattered_telescopes(np.random.Generator(np.random.PCG64(3)))
     tracks, t_ref = shower_segments(rng, n, 2.0e7, math.radians(60.0), 0.0, 0.0, 0.0, 2200.0)
-    return _scenario("inclined_20tev", tracks, tel, t_ref, seed, H=4000, Z=256,
-                     theta_max_deg=75.0)
+    sc = _scenario("inclined_20tev", tracks, tel, t_ref, seed, H=4000, Z=256,
+                   theta_max_deg=75.0)
+    sc["axis_zenith_rad"] = np.array([math.radians(60.0)])
+    return sc
 
 
 WORKLOADS = {
