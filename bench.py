@@ -69,6 +69,29 @@ FP64_OPS_PER_STEP = 34          # yield chain: 24 mul/add + 1 division (~10 ops)
 FP32_LANES_PER_SM = 128
 FP64_FMA_PER_SM_CLK = 2         # GB300: 1/64 of the FP32 rate (ncu: 2 DFMA/cycle/SM)
 
+# DRAM bytes (read + write) of one FP32 launch, from one ncu capture (the
+# summary in profiles/k_gen_prop_vertical_1tev.md: 128.20 MB read, 24.43 MB
+# written, 512 threads x 2 CTAs per SM).  Reported only for that workload at
+# full size and only while the kernel sources hash to what was profiled.
+TRAFFIC = {"vertical_1tev": (152_637_440, "292352464eb63963")}
+KERNEL_SOURCES = ("cher_kernels.cu", "cher_device.cuh", "cher_internal.h")
+
+
+def _kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2006_14927_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(workload: str, scale: float):
+    t = TRAFFIC.get(workload)
+    if t is None or scale != 1.0 or _kernel_hash() != t[1]:
+        return None
+    return t[0]
+
 
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -238,8 +261,12 @@ def run_ours(args):
     ctx = P.Context(sc["atm"], sc["h_obs"], sc["telescopes"])
     ctx.build_refraction_tables(sc["H"], sc["Z"], sc["theta_max_deg"], sc["h_max"])
     table_s = time.perf_counter() - t0
-    cap = args.cap or (600_000 if args.workload == "vertical_1tev" else
-                       max(200_000, int(8_000_000 * args.scale)))
+    # records per telescope: the densest telescope of each workload fits
+    # (batched: 12e6 x 100 telescopes x 40 B = 48 GB of the 288 GB)
+    cap_full = {"vertical_1tev": 600_000, "batched_256": 12_000_000}.get(args.workload,
+                                                                         8_000_000)
+    cap = args.cap or (cap_full if args.workload == "vertical_1tev" else
+                       max(200_000, int(cap_full * args.scale)))
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def measure(prec, steps, warmup, autotune):
@@ -403,7 +430,8 @@ def run_ours(args):
                                              f"lanes x {mhz:.0f} MHz"}},
         "fp32_over_fp64": v32 / v64,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
-                     "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None,
+                     "unit": "Tops/s", "frac": achieved / alu_peak,
+                     "traffic": _traffic(args.workload, args.scale),
                      "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32/INT32 lanes x "
                                     f"{mhz:.0f} MHz ({src} max clock)",
                      "ops_per_bunch": OPS_PER_BUNCH,
