@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cher_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
-ST_GROUND, ST_UPWARD, ST_BELOW_OBS, ST_ABOVE_MAX, ST_ANGLE = 0, 1, 2, 3, 4
+ST_GROUND, ST_UPWARD, ST_BELOW_OBS, ST_ABOVE_MAX, ST_ANGLE, ST_ABSORBED = 0, 1, 2, 3, 4, 5
 MAX_HITS = 4
 
 
@@ -63,7 +63,11 @@ class _Cfg(ctypes.Structure):
                 ("lambda2_nm", ctypes.c_double),
                 ("n_tel", ctypes.c_int), ("tel", _dp),
                 ("t_ref", _dp), ("n_showers", ctypes.c_int), ("bf_tol", ctypes.c_double),
-                ("philox_key", ctypes.c_uint32 * 2)]
+                ("philox_key", ctypes.c_uint32 * 2),
+                ("trans_nl", ctypes.c_int), ("trans_nh", ctypes.c_int),
+                ("trans_l0", ctypes.c_double), ("trans_l1", ctypes.c_double),
+                ("trans_h0", ctypes.c_double), ("trans_h1", ctypes.c_double),
+                ("trans_tau", _dp)]
 
 
 class _Tracks(ctypes.Structure):
@@ -237,6 +241,9 @@ class Model:
     lambda1_nm: float = 300.0
     lambda2_nm: float = 600.0
     t_ref: np.ndarray | None = None
+    # atmospheric transmission: dict(tau=(n_lambda, n_height) vertical optical
+    # depths, lambda_nm=(first, last node), height_m=(first, last node)) or None
+    transmission: dict | None = None
     table_tol: float = 1e-13
     bf_tol: float = 1e-12
     eta_tab: np.ndarray = field(init=False, repr=False)
@@ -276,6 +283,17 @@ class Model:
             C.t_ref = None
             C.n_showers = 0
         C.bf_tol = self.bf_tol
+        if self.transmission is not None:
+            tr = self.transmission
+            self._tau = _f64(np.asarray(tr["tau"], float))
+            if self._tau.ndim != 2 or min(self._tau.shape) < 2:
+                raise ValueError("transmission table needs at least 2 x 2 nodes")
+            C.trans_nl, C.trans_nh = self._tau.shape
+            C.trans_l0, C.trans_l1 = (float(v) for v in tr["lambda_nm"])
+            C.trans_h0, C.trans_h1 = (float(v) for v in tr["height_m"])
+            C.trans_tau = _ptr(self._tau)
+        else:
+            C.trans_tau = None
         return C
 
     # ---- a1: per-step yield ------------------------------------------------

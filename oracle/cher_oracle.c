@@ -67,6 +67,8 @@
 #define ORC_ST_BELOW_OBS 2   /* emitted below the observation level         */
 #define ORC_ST_ABOVE_MAX 3   /* emitted above the top of the tables         */
 #define ORC_ST_ANGLE 4       /* zenith at the observation level > table max */
+#define ORC_ST_ABSORBED 5    /* reached the ground level, then lost to the  */
+                             /* atmospheric transmission draw              */
 
 #define ORC_MAX_HITS 4       /* telescopes recorded per bunch               */
 
@@ -102,6 +104,13 @@ typedef struct {
     int n_showers;
     double bf_tol;           /* absolute tolerance of the (B) integrals    */
     uint32_t philox_key[2];  /* set from the seed by the entry points      */
+    /* atmospheric transmission (NULL tau: off): vertical optical depth     */
+    /* between height h and h_obs at wavelength lambda, on the uniform      */
+    /* nodes lambda_a = l0 + a (l1 - l0)/(nl - 1), h_b = h0 + b (h1 - h0)/(nh - 1), */
+    /* tau[a * nh + b]                                                      */
+    int trans_nl, trans_nh;
+    double trans_l0, trans_l1, trans_h0, trans_h1;
+    const double *trans_tau;
 } orc_cfg;
 
 typedef struct {
@@ -600,6 +609,36 @@ typedef struct {
     double r[6];                      /* X, Y, t (before t_ref), cx, cy, cz */
 } orc_bunch1;
 
+/* ======================================================================= */
+/* Atmospheric transmission (an extension: the paper's RAYBND only bends   */
+/* and times the photons; CORSIKA's IACT option can also drop photons that */
+/* the atmosphere absorbs or scatters, using external transmission         */
+/* profiles).  Reading: a bunch that reaches the observation level survives */
+/* with probability P = exp(-tau_v(lambda, h_e) / cos(theta_obs))          */
+/* (Beer-Lambert along a straight line at the observation-level zenith     */
+/* through a flat atmosphere), tau_v from a table interpolated bilinearly  */
+/* in (lambda, h) and clamped to its range; the draw is the fourth Philox  */
+/* word of the bunch: it survives when u3 < P.                            */
+/* ======================================================================= */
+static double orc_trans_tau(const orc_cfg *C, double lam, double h)
+{
+    double xl = (lam - C->trans_l0) / (C->trans_l1 - C->trans_l0) * (double)(C->trans_nl - 1);
+    double xh = (h - C->trans_h0) / (C->trans_h1 - C->trans_h0) * (double)(C->trans_nh - 1);
+    if (xl < 0.0) xl = 0.0;
+    if (xl > (double)(C->trans_nl - 1)) xl = (double)(C->trans_nl - 1);
+    if (xh < 0.0) xh = 0.0;
+    if (xh > (double)(C->trans_nh - 1)) xh = (double)(C->trans_nh - 1);
+    int a = (int)xl, b = (int)xh;
+    if (a > C->trans_nl - 2) a = C->trans_nl - 2;
+    if (b > C->trans_nh - 2) b = C->trans_nh - 2;
+    double s = xl - (double)a, t = xh - (double)b;
+    const double *T = C->trans_tau;
+    int nh = C->trans_nh;
+    double t00 = T[a * nh + b], t01 = T[a * nh + b + 1];
+    double t10 = T[(a + 1) * nh + b], t11 = T[(a + 1) * nh + b + 1];
+    return (1.0 - s) * ((1.0 - t) * t00 + t * t01) + s * ((1.0 - t) * t10 + t * t11);
+}
+
 static void orc_one_bunch(const orc_cfg *C, const orc_tracks *Tk, int64_t i, int64_t j,
                           int64_t nb, const orc_yield *Y, int variant, orc_bunch1 *B)
 {
@@ -642,6 +681,13 @@ static void orc_one_bunch(const orc_cfg *C, const orc_tracks *Tk, int64_t i, int
     B->te = Tk->t0[i] + fl * inv_bc;
     B->status = orc_propagate_photon(C, variant, B->xe, B->ye, B->he, B->te, B->px, B->py,
                                      B->pz, B->r);
+    if (B->status == ORC_ST_GROUND && C->trans_tau) {
+        double tau = orc_trans_tau(C, B->lam, B->he);
+        double cos_obs = -B->r[5];
+        double P = exp(-(tau / cos_obs));
+        double u3 = orc_u01(x[3]);
+        if (!(u3 < P)) B->status = ORC_ST_ABSORBED;
+    }
 }
 
 static double orc_t_ref(const orc_cfg *C, const orc_tracks *Tk, int64_t i)
@@ -769,7 +815,8 @@ int orc_density(const orc_cfg *C, const orc_tracks *Tk, uint64_t seed, const int
 /* fraction is the overlap of the bin's height interval with the step's     */
 /* height interval, divided by the latter; the heights of the bin edges     */
 /* come from bisection on T.  A horizontal step puts all its photons in     */
-/* the bin of its depth.  Steps emitting no bunch add nothing.              */
+/* the bin of its depth.  Steps emitting no bunch, and steps whose shower  */
+/* index has no row, add nothing.                                          */
 /* prof: n_showers (at least 1) x n_bins, overwritten.                      */
 /* ======================================================================= */
 static double orc_height_of_thickness(const orc_atm *A, double target, double lo, double hi)
@@ -793,8 +840,8 @@ int orc_profile(const orc_cfg *C, const orc_tracks *Tk, const double *axis_cos,
     for (int64_t i = 0; i < Tk->n; ++i) {
         orc_yield Y;
         if (orc_step_yield(C, Tk, i, &Y) != 0 || Y.nb <= 0) continue;
-        int s = Tk->shower ? (int)Tk->shower[i] : 0;
-        if (s < 0 || s >= ns) return -1;
+        int64_t s = Tk->shower ? (int64_t)Tk->shower[i] : 0;
+        if (s >= ns) continue;                               /* no row: not counted */
         double cz = axis_cos ? axis_cos[s] : 1.0;
         double za = Tk->z0[i];
         double zb = za + Tk->len[i] * Tk->uz[i];

@@ -165,6 +165,25 @@ def _scenario(name, tracks, telescopes, t_ref, seed, h_obs=2200.0, H=1000, Z=64,
                 lambda1_nm=300.0, lambda2_nm=600.0, seed=seed)
 
 
+def synthetic_transmission(h_obs: float = 2200.0, h_max: float = 60000.0, n_lambda: int = 16,
+                           n_height: int = 121, tau_rayleigh: float = 0.36,
+                           tau_aerosol: float = 0.10) -> dict:
+    """A stand-in for an external transmission profile: vertical optical
+    depth between height h and h_obs, Rayleigh scattering (lambda^-4, scale
+    height 8.4 km, tau_rayleigh at 400 nm from sea level) plus aerosols
+    (lambda^-1.3, scale height 1.2 km, tau_aerosol at 400 nm from sea
+    level), on a uniform (lambda, h) grid over 250-700 nm and [h_obs, h_max]."""
+    lam = np.linspace(250.0, 700.0, n_lambda)
+    h = np.linspace(h_obs, h_max, n_height)
+    ray = tau_rayleigh * (lam / 400.0) ** -4.0
+    aer = tau_aerosol * (lam / 400.0) ** -1.3
+    col_r = np.exp(-h_obs / 8400.0) - np.exp(-h / 8400.0)
+    col_a = np.exp(-h_obs / 1200.0) - np.exp(-h / 1200.0)
+    tau = ray[:, None] * col_r[None, :] + aer[:, None] * col_a[None, :]
+    return dict(tau=tau, lambda_nm=(float(lam[0]), float(lam[-1])),
+                height_m=(float(h[0]), float(h[-1])))
+
+
 def plain_fp64(n: int = 1000, seed: int = 1) -> dict:
     rng = np.random.Generator(np.random.PCG64(seed))
     z0 = rng.uniform(5000.0, 25000.0, n)
