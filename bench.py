@@ -269,15 +269,19 @@ def run_ours(args):
                        max(200_000, int(cap_full * args.scale)))
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
-    def measure(prec, steps, warmup, autotune):
-        dtr = P.device_tracks(sc["tracks"], prec, device=dev, t_ref=sc["t_ref"])
-        out = ctx.alloc_hits(cap, prec, device=dev)
+    def measure(prec, steps, warmup, autotune, prof=None, reuse=None):
+        if reuse is not None:
+            dtr, out = reuse["dtr"], reuse["out"]
+        else:
+            dtr = P.device_tracks(sc["tracks"], prec, device=dev, t_ref=sc["t_ref"])
+            out = ctx.alloc_hits(cap, prec, device=dev)
+        pkw = {} if prof is None else dict(profile=prof[0], bin_gcm2=prof[1], axis_cos=prof[2])
         if autotune and args.launch is None:
             ctx.autotune(dtr, 11, prec, out)
         elif args.launch is not None:
             ctx.set_launch(*(int(v) for v in args.launch.split(",")))
         for _ in range(warmup):
-            ctx.generate_propagate(dtr, 11, prec, out, track_base=track_base)
+            ctx.generate_propagate(dtr, 11, prec, out, track_base=track_base, **pkw)
         code, stats = ctx.sync_status(out)
         if code not in (0, 6):                      # 6: a buffer overflowed (counted)
             raise RuntimeError(f"status {code} in warm-up")
@@ -288,7 +292,7 @@ def run_ours(args):
         for k in range(steps):
             flush.fill_(k & 0xff)                   # evict L2 between timed steps
             ev[k][0].record(stream)
-            ctx.generate_propagate(dtr, 11, prec, out, track_base=track_base)
+            ctx.generate_propagate(dtr, 11, prec, out, track_base=track_base, **pkw)
             ev[k][1].record(stream)
         barrier()
         wall = time.perf_counter() - w0
@@ -323,6 +327,13 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
     r64 = measure(P.CHER_FP64, max(3, steps // 4), max(3, min(warmup, 3)), autotune=False)
+    # the longitudinal production profile (CERLDE) in the same launch:
+    # 10 g/cm^2 bins to 2000 g/cm^2 of slant depth, one row per shower
+    n_rows = max(len(sc["t_ref"]), 1)
+    prof_t = torch.zeros((n_rows, 200), dtype=torch.float64, device=dev)
+    axis_cos = np.cos(np.asarray(sc.get("axis_zenith_rad", np.zeros(n_rows)), float))
+    r32p = measure(P.CHER_FP32_BULK, steps, max(3, min(warmup, 3)), autotune=False,
+                   prof=(prof_t, 10.0, axis_cos), reuse=r32)
 
     def total(r):
         return reduce_over_ranks(sum(r["ms"]) / 1e3, float(r["stats"][3]) * len(r["ms"]),
@@ -429,6 +440,10 @@ def run_ours(args):
                               "peak_source": f"{sm_count} SMs x {FP64_FMA_PER_SM_CLK} FP64 "
                                              f"lanes x {mhz:.0f} MHz"}},
         "fp32_over_fp64": v32 / v64,
+        "profile": {"ms_per_step": statistics.mean(r32p["ms"]),
+                    "overhead": statistics.mean(r32p["ms"]) / statistics.mean(r32["ms"]) - 1.0,
+                    "bins": int(prof_t.shape[1]), "bin_gcm2": 10.0, "rows": n_rows,
+                    "depth": "slant" if np.any(axis_cos < 1.0) else "vertical"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
                      "unit": "Tops/s", "frac": achieved / alu_peak,
                      "traffic": _traffic(args.workload, args.scale),
@@ -445,9 +460,95 @@ def run_ours(args):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if args.workload == "vertical_1tev" and args.scale == 1.0 and world == 1:
+        line["graph"] = graph_leg(ctx, r32, steps, flush, stream)
+        line["adjoint"] = adjoint_leg(dev, steps)
+        line["adjoint"]["cpu_baseline"] = cpu_baseline_readout()
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def graph_leg(ctx, r32, steps, flush, stream):
+    """The same FP32 launch replayed from a captured CUDA graph (counter
+    clears and the persistent kernel in one graph launch)."""
+    import torch
+
+    import paper_2006_14927_gb300 as P
+    g = ctx.graph(r32["dtr"], 11, P.CHER_FP32_BULK, r32["out"])
+    for _ in range(3):
+        g.launch()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xff)
+        ev[k][0].record(stream)
+        g.launch()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    g.close()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return {"ms_per_step": statistics.mean(ms),
+            "value": float(r32["stats"][3]) / (statistics.mean(ms) / 1e3), "unit": UNIT}
+
+
+def adjoint_leg(dev, steps):
+    """The adjoint of the telescope read-out on the 300 GeV shower (1e5
+    steps, 19 telescopes, sigma 1 m): screening launch, listed bunch pairs
+    recomputed in dual numbers, FP64 gradient atomics.  Unit: bunches of the
+    input handled per second of the whole call."""
+    import torch
+
+    import paper_2006_14927_gb300 as P
+    import workloads
+    sc = workloads.adjoint_300gev()
+    ctx = P.Context(sc["atm"], sc["h_obs"], sc["telescopes"])
+    ctx.build_refraction_tables(sc["H"], sc["Z"], sc["theta_max_deg"], sc["h_max"])
+    rng = np.random.default_rng(99)
+    n_tel = len(sc["telescopes"])
+    gD, gT = rng.normal(0.0, 1.0, n_tel), rng.normal(0.0, 0.05, n_tel)
+    res = {}
+    for name, prec in (("fp32", P.CHER_FP32_BULK), ("fp64", P.CHER_FP64)):
+        dtr = P.device_tracks(sc["tracks"], prec, device=dev, t_ref=sc["t_ref"])
+        nb, _ = ctx.segment_yield(dtr, prec)
+        bunches = float(nb.to(torch.float64).sum())
+        for _ in range(3):
+            ctx.adjoint(dtr, 4, prec, gD, gT, 1.0, nb)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(max(3, steps // 2)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.adjoint(dtr, 4, prec, gD, gT, 1.0, nb)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = statistics.mean(ms)
+        res[name] = {"ms_per_call": t, "value": bunches / (t / 1e3), "unit": UNIT}
+    res["bunches"] = int(bunches)
+    res["steps"] = int(len(sc["tracks"]["x0"]))
+    ctx.close()
+    return res
+
+
+def cpu_baseline_readout(n: int = 20000):
+    """Beside the adjoint: the oracle's read-out S_k, U_k (the function
+    whose gradient the adjoint computes) as it stands, on the first n steps
+    of the 300 GeV shower."""
+    import oracle
+    import workloads
+    oracle.build()
+    sc = workloads.adjoint_300gev()
+    sub = {k: v[:n] for k, v in sc["tracks"].items()}
+    M = oracle.Model(sc["atm"], sc["h_obs"], sc["telescopes"], h_max=sc["h_max"], H=sc["H"],
+                     Z=sc["Z"], theta_max_deg=sc["theta_max_deg"], t_ref=sc["t_ref"])
+    nb_o, _, _, _ = M.segment_yield(sub)
+    t0 = time.perf_counter()
+    M.density_sums(sub, 4, nb_o, 1.0)
+    dt = time.perf_counter() - t0
+    return {"value": float(nb_o.sum()) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"read-out S, U of the first {n} steps ({int(nb_o.sum())} bunches), "
+                      f"single-threaded"}
 
 
 def cpu_baseline(workload: str = WORKLOAD):

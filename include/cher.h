@@ -196,6 +196,54 @@ cher_status cher_generate_propagate(cher_ctx *ctx, const cher_tracks *tracks,
                                     uint64_t seed, cher_precision prec,
                                     const cher_output *out, void *stream);
 
+/* Longitudinal profile of Cherenkov production (CERLDE; paper section 4:
+ * the simulation optionally keeps the number of photons produced versus
+ * atmospheric depth, which follows the density profile, and the paper
+ * vectorised it with the generation).  The paper gives no formula.  Here a
+ * step spreads its photons N uniformly along its straight path, and a
+ * photon counts at the atmospheric depth of its emission point,
+ * X = T(h) / axis_cos[shower] in g/cm^2 (T the thickness of the layered
+ * atmosphere; axis_cos = NULL gives the vertical depth T(h)).  Bin k of a
+ * shower's row holds the depths [k bin_gcm2, (k + 1) bin_gcm2); a step adds
+ * N times the fraction of its path whose depth falls in bin k.  Photons
+ * deeper than the last bin, and steps whose shower index has no row, are
+ * not counted.
+ *   profile  : device, double [max(n_showers, 1)][n_bins], ADDED to (clear
+ *              it before the first call of a batch), 8-byte aligned;
+ *   n_bins   : 1 .. 65536, and max(n_showers, 1) * n_bins < 2^31;
+ *   bin_gcm2 : finite and > 0;
+ *   axis_cos : device, double [max(n_showers, 1)] with values in (0, 1],
+ *              or NULL.
+ * The sums are FP64 atomic additions, so their rounding order varies from
+ * call to call. */
+typedef struct cher_profile {
+    double *profile;
+    int32_t n_bins;
+    double bin_gcm2;
+    const double *axis_cos;
+} cher_profile;
+
+/* cher_generate_propagate plus, when `profile` is not NULL, the
+ * longitudinal production profile of the same steps, accumulated in the
+ * same launch (per step, from the yield the launch computes).  Errors as
+ * cher_generate_propagate; CHER_EINVAL for a profile whose fields are out
+ * of range. */
+cher_status cher_generate_propagate_ex(cher_ctx *ctx, const cher_tracks *tracks,
+                                       uint64_t seed, cher_precision prec,
+                                       const cher_output *out, const cher_profile *profile,
+                                       void *stream);
+
+/* The double -> float rounding that the FP32 path applies to its FP64
+ * inputs (positions, lengths, energies, the differences to h_obs and
+ * t_ref): round to nearest even, done on the integer pipes because GB300
+ * converts on its slow FP64 pipe; results below the smallest normal float
+ * flush to zero, beyond the largest float they become infinities.  The
+ * paper has no counterpart; it is exposed so that the rounding can be
+ * checked against the IEEE conversion.  in, out: device arrays of n
+ * elements (n >= 0), 8- and 4-byte aligned; asynchronous on `stream`.
+ * Errors: CHER_EINVAL (NULL array with n > 0, n < 0), CHER_ECUDA. */
+cher_status cher_round_to_float(const double *in, float *out, int64_t n, void *stream);
+
 /* The same hot path as cher_generate_propagate (same kernel, same results)
  * for callers that must not allocate device memory when they run it: code
  * that runs while a stream of the process is being captured into a CUDA

@@ -62,6 +62,11 @@ class Output(ctypes.Structure):
                 ("stats", ctypes.c_void_p)]
 
 
+class Profile(ctypes.Structure):
+    _fields_ = [("profile", ctypes.c_void_p), ("n_bins", ctypes.c_int32),
+                ("bin_gcm2", ctypes.c_double), ("axis_cos", ctypes.c_void_p)]
+
+
 class Trace(ctypes.Structure):
     _fields_ = [("pos", ctypes.c_void_p), ("tim", ctypes.c_void_p), ("status", ctypes.c_void_p),
                 ("nhit", ctypes.c_void_p), ("first_hit", ctypes.c_void_p),
@@ -82,6 +87,9 @@ SIGNATURES = {
     "cher_destroy": (_S, [_P]),
     "cher_generate_propagate": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
                                      ctypes.POINTER(Output), _P]),
+    "cher_generate_propagate_ex": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
+                                        ctypes.POINTER(Output), ctypes.POINTER(Profile), _P]),
+    "cher_round_to_float": (_S, [_P, _P, ctypes.c_int64, _P]),
     "cher_generate_propagate_noalloc": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
                                              ctypes.POINTER(Output), _P]),
     "cher_graph_create": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
@@ -321,13 +329,37 @@ class Context:
                           cap=int(cap_per_tel), precision=precision)
 
     def generate_propagate(self, dev_tracks: dict, seed: int, precision: int,
-                           out: HitBuffers, stream=None, track_base: int = 0):
+                           out: HitBuffers, stream=None, track_base: int = 0,
+                           profile=None, bin_gcm2: float = 10.0, axis_cos=None):
+        """The hot path; with `profile` (a device float64 tensor of shape
+        (max(n_showers, 1), n_bins), added to) also the longitudinal
+        production profile in the same launch."""
         t = self.tracks_struct(dev_tracks, track_base)
         o = out.struct()
-        _check(lib().cher_generate_propagate(self._h, ctypes.byref(t), ctypes.c_uint64(seed),
-                                             int(precision), ctypes.byref(o),
-                                             ctypes.c_void_p(_stream_ptr(stream))),
-               "cher_generate_propagate")
+        if profile is None:
+            _check(lib().cher_generate_propagate(self._h, ctypes.byref(t), ctypes.c_uint64(seed),
+                                                 int(precision), ctypes.byref(o),
+                                                 ctypes.c_void_p(_stream_ptr(stream))),
+                   "cher_generate_propagate")
+            return
+        torch = _torch()
+        if profile.dtype != torch.float64 or not profile.is_contiguous() or profile.dim() != 2:
+            raise ValueError("profile must be a contiguous 2-D float64 device tensor")
+        rows = max(int(dev_tracks["t_ref"].numel()) if dev_tracks.get("t_ref") is not None
+                   else 0, 1)
+        if profile.shape[0] < rows:
+            raise ValueError("profile needs one row per shower")
+        if axis_cos is not None:
+            axis_cos = torch.as_tensor(axis_cos, dtype=torch.float64,
+                                       device=profile.device).contiguous()
+            if axis_cos.numel() < rows:
+                raise ValueError("axis_cos needs one entry per shower")
+        pr = Profile(profile.data_ptr(), int(profile.shape[1]), float(bin_gcm2),
+                     axis_cos.data_ptr() if axis_cos is not None else None)
+        _check(lib().cher_generate_propagate_ex(self._h, ctypes.byref(t), ctypes.c_uint64(seed),
+                                                int(precision), ctypes.byref(o), ctypes.byref(pr),
+                                                ctypes.c_void_p(_stream_ptr(stream))),
+               "cher_generate_propagate_ex")
 
     def sync_status(self, out: HitBuffers, stream=None):
         st = (ctypes.c_ulonglong * NSTATS)()
@@ -427,6 +459,19 @@ class Context:
                                    cache_path.encode() if cache_path else None,
                                    ctypes.c_void_p(_stream_ptr(stream))), "cher_autotune")
         return self.get_launch()
+
+
+def round_to_float(x):
+    """The FP32 path's double -> float rounding applied to a device float64
+    tensor (cher_round_to_float)."""
+    torch = _torch()
+    x = x.contiguous()
+    if x.dtype != torch.float64 or not x.is_cuda:
+        raise ValueError("a CUDA float64 tensor is needed")
+    y = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    _check(lib().cher_round_to_float(x.data_ptr(), y.data_ptr(), x.numel(),
+                                     ctypes.c_void_p(_stream_ptr(None))), "cher_round_to_float")
+    return y
 
 
 class Graph:

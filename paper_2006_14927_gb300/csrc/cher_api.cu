@@ -193,6 +193,15 @@ cher::KParams base_params(const cher_ctx *c, const cher_tracks *t, uint64_t seed
         p.grid[g].cand64 = c->d_cand64[g];
     }
     p.q_band = c->q_band;
+    // the layered thickness, for the production profile
+    for (int l = 0; l < 6; ++l) p.atm.hb[l] = c->atm.h_bound[l];
+    for (int l = 0; l < 5; ++l) {
+        p.atm.a[l] = c->atm.a[l];
+        p.atm.b[l] = c->atm.b[l];
+        p.atm.c[l] = c->atm.c[l];
+        p.atm.inv_c[l] = 1.0 / c->atm.c[l];
+        p.atm.t_top[l] = c->atm.a[l] + c->atm.b[l] * std::exp(-(c->atm.h_bound[l + 1] / c->atm.c[l]));
+    }
     cher::fill_float_constants(p);
     return p;
 }
@@ -423,7 +432,19 @@ cher_status cher_get_launch(const cher_ctx *c, int32_t *block_threads, int32_t *
 
 cher_status cher_generate_propagate(cher_ctx *c, const cher_tracks *t, uint64_t seed,
                                     cher_precision prec, const cher_output *out, void *stream) {
+    return cher_generate_propagate_ex(c, t, seed, prec, out, nullptr, stream);
+}
+
+cher_status cher_generate_propagate_ex(cher_ctx *c, const cher_tracks *t, uint64_t seed,
+                                       cher_precision prec, const cher_output *out,
+                                       const cher_profile *prof, void *stream) {
     if (!c || !out || !tracks_ok(t)) return CHER_EINVAL;
+    if (prof && (bad_ptr(prof->profile) || prof->n_bins < 1 || prof->n_bins > 65536 ||
+                 !(prof->bin_gcm2 > 0.0) || !std::isfinite(prof->bin_gcm2) ||
+                 reinterpret_cast<uintptr_t>(prof->profile) % alignof(double) ||
+                 reinterpret_cast<uintptr_t>(prof->axis_cos) % alignof(double) ||
+                 int64_t(std::max(t->n_showers, 1)) * prof->n_bins > 0x7fffffffLL))
+        return CHER_EINVAL;
     if (prec != CHER_FP64 && prec != CHER_FP32_BULK) return CHER_EINVAL;
     if (!c->built) return CHER_ESTATE;
     if (!check_device(c)) return CHER_EINVAL;
@@ -431,7 +452,7 @@ cher_status cher_generate_propagate(cher_ctx *c, const cher_tracks *t, uint64_t 
     if (out->cap_per_tel < 0) return CHER_EINVAL;
     if (out->cap_per_tel > 0 && (bad_ptr(out->pos) || bad_ptr(out->tim) || bad_ptr(out->key)))
         return CHER_EINVAL;
-    const size_t al = prec == CHER_FP32_BULK ? 16 : 16;
+    constexpr size_t al = 16;
     if (reinterpret_cast<uintptr_t>(out->pos) % al || reinterpret_cast<uintptr_t>(out->tim) % al)
         return CHER_EINVAL;
     const bool fp32 = prec == CHER_FP32_BULK;
@@ -447,7 +468,29 @@ cher_status cher_generate_propagate(cher_ctx *c, const cher_tracks *t, uint64_t 
     p.cap = out->cap_per_tel;
     p.count = out->count;
     p.stats = out->stats;
+    if (prof) {
+        p.prof = prof->profile;
+        p.prof_cos = prof->axis_cos;
+        p.prof_bins = prof->n_bins;
+        p.prof_rows = std::max(t->n_showers, 1);
+        p.prof_dx = prof->bin_gcm2;
+        p.prof_inv_dx = 1.0 / prof->bin_gcm2;
+        cher::fill_float_constants(p);
+    }
     return launch(c, p, fp32, cher::MODE_HITS, true, stream);
+}
+
+cher_status cher_round_to_float(const double *in, float *out, int64_t n, void *stream) {
+    if (n < 0 || (n > 0 && (bad_ptr(in) || bad_ptr(out)))) return CHER_EINVAL;
+    if (n == 0) return CHER_OK;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return CHER_ECUDA;
+    }
+    if (cher::round_to_float(in, out, n, sms, stream) != cudaSuccess) return CHER_ECUDA;
+    return CHER_OK;
 }
 
 cher_status cher_sync_status(cher_ctx *c, const cher_output *out, unsigned long long *stats_host,

@@ -61,6 +61,26 @@ __device__ __forceinline__ bool finite_f(float v) {
     return (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u;
 }
 
+// double -> float with round-to-nearest-even (IEEE 754), on the integer
+// pipes: keep the top 23 fraction bits, round on the 29 dropped ones, let a
+// carry run into the exponent.  Results below the smallest normal float
+// flush to zero (the FP32 path runs with flush-to-zero), results beyond the
+// largest float become infinities, NaN stays NaN.
+__device__ __forceinline__ float d2f_rn(double d) {
+    const unsigned hi = static_cast<unsigned>(__double2hiint(d));
+    const unsigned lo = static_cast<unsigned>(__double2loint(d));
+    const unsigned sign = hi & 0x80000000u;
+    const unsigned ex = (hi >> 20) & 0x7ffu;
+    const int e = static_cast<int>(ex) - 1023 + 127;
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;
+    const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    unsigned r = (static_cast<unsigned>(e) << 23) + m + up;
+    r = e <= 0 ? 0u : (e >= 255 ? 0x7f800000u : r);
+    if (ex == 0x7ffu && ((hi & 0xfffffu) | lo)) r = 0x7fc00000u;
+    return __uint_as_float(r | sign);
+}
+
 __device__ __forceinline__ double eta_exact_lookup(const KParams &p, double h) {
     double hc = h;
     if (hc < 0.0) hc = 0.0;

@@ -120,6 +120,17 @@ struct KParams {
     unsigned long long *list_count;
     int64_t list_cap;
     double rcut2;
+    // longitudinal production profile: rows of n_bins per shower (NULL:
+    // off); the layered thickness T(h) = a + b exp(-h / c) per layer, with
+    // the thickness at each layer's top from its own formula (the inverse
+    // picks the layer by it)
+    double *prof;
+    const double *prof_cos;
+    int32_t prof_bins, prof_rows;
+    double prof_dx, prof_inv_dx;
+    struct Layers {
+        double hb[6], a[5], b[5], c[5], inv_c[5], t_top[5];
+    } atm;
     // the per-launch constants of the bunch loop, rounded to float on the
     // host: the FP32 path converts nothing from double on the device
     struct {
@@ -128,6 +139,8 @@ struct KParams {
         // FP32 screen of the yield: constants and the table's largest slope
         float inv_me, K, inv_B, h_max, dh, eta_slope;
         float gx0[2], gy0[2], inv_gcs[2];
+        float prof_dx, prof_inv_dx;
+        float hb[6], a[5], b[5], c[5], inv_c[5], t_top[5];
     } f;
 };
 
@@ -158,6 +171,8 @@ enum Mode : int { MODE_HITS = 0, MODE_TRACE = 1, MODE_YIELD = 2, MODE_SCREEN = 3
 
 // Launchers (cher_kernels.cu).  fp32 selects CHER_FP32_BULK.
 size_t kernel_smem_bytes(bool fp32, int block, const KParams &p);
+// The FP32 path's double -> float rounding over an array (grid-stride).
+cudaError_t round_to_float(const double *in, float *out, int64_t n, int num_sms, void *stream);
 cudaError_t kernel_prepare(bool fp32, int block, int mode, size_t smem);
 cudaError_t kernel_launch(bool fp32, int block, int mode, int grid, size_t smem,
                           const KParams &p, void *stream);

@@ -93,3 +93,9 @@ def test_adjoint_sensitivity_tables_match_finite_differences():
         sl = max(np.abs(fl).max(), 1e-30)
         assert np.abs(fx - dax[q]).max() <= 1e-5 * sx + 1e-14, (key, i)
         assert np.abs(fl - dal[q]).max() <= 1e-5 * sl + 1e-14, (key, i)
+
+
+def test_round_to_float_rejects_bad_arguments(L):
+    assert L.cher_round_to_float(None, None, 5, None) == 1
+    assert L.cher_round_to_float(None, None, -1, None) == 1
+    assert L.cher_round_to_float(None, None, 0, None) == 0
