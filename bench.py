@@ -334,6 +334,10 @@ def run_ours(args):
     axis_cos = np.cos(np.asarray(sc.get("axis_zenith_rad", np.zeros(n_rows)), float))
     r32p = measure(P.CHER_FP32_BULK, steps, max(3, min(warmup, 3)), autotune=False,
                    prof=(prof_t, 10.0, axis_cos), reuse=r32)
+    # the atmospheric transmission draw (synthetic Rayleigh + aerosol table)
+    ctx.set_transmission(workloads.synthetic_transmission(h_obs=sc["h_obs"], h_max=sc["h_max"]))
+    r32t = measure(P.CHER_FP32_BULK, steps, max(3, min(warmup, 3)), autotune=False, reuse=r32)
+    ctx.set_transmission(None)
 
     def total(r):
         return reduce_over_ranks(sum(r["ms"]) / 1e3, float(r["stats"][3]) * len(r["ms"]),
@@ -440,6 +444,10 @@ def run_ours(args):
                               "peak_source": f"{sm_count} SMs x {FP64_FMA_PER_SM_CLK} FP64 "
                                              f"lanes x {mhz:.0f} MHz"}},
         "fp32_over_fp64": v32 / v64,
+        "transmission": {"ms_per_step": statistics.mean(r32t["ms"]),
+                         "overhead": statistics.mean(r32t["ms"]) / statistics.mean(r32["ms"]) - 1,
+                         "absorbed_frac": float(r32t["stats"][11]) / float(r32t["stats"][3]),
+                         "table": "synthetic Rayleigh + aerosol, 16 x 121"},
         "profile": {"ms_per_step": statistics.mean(r32p["ms"]),
                     "overhead": statistics.mean(r32p["ms"]) / statistics.mean(r32["ms"]) - 1.0,
                     "bins": int(prof_t.shape[1]), "bin_gcm2": 10.0, "rows": n_rows,

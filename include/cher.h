@@ -160,7 +160,8 @@ enum {
     CHER_STAT_ANGLE = 7,        /* dropped: zenith beyond the tables        */
     CHER_STAT_GROUND = 8,       /* reached the observation level            */
     CHER_STAT_HITS = 9,         /* (bunch, telescope) crossings found       */
-    CHER_STAT_OVERFLOW = 10     /* crossings not stored (buffer full)       */
+    CHER_STAT_OVERFLOW = 10,    /* crossings not stored (buffer full)       */
+    CHER_STAT_ABSORBED = 11     /* reached h_obs, lost to the transmission  */
 };
 
 /* Per-telescope output buffers (device).  Telescope k owns records
@@ -334,6 +335,32 @@ cher_status cher_adjoint(cher_ctx *ctx, const cher_tracks *tracks, uint64_t seed
                          const double *dL_dD, const double *dL_dT, double *grad_atm,
                          double *grad_tracks, void *stream);
 
+/* Atmospheric transmission (an extension of the propagation: the paper
+ * notes that CORSIKA works with external atmospheric profiles).  With a
+ * table set, a bunch that reaches the observation level survives with
+ * probability P = exp(-tau / cos(theta_obs)) -- Beer-Lambert along the
+ * arrival direction through a flat atmosphere -- and is otherwise counted
+ * in stats[CHER_STAT_ABSORBED] and not recorded (trace status 5).  tau is
+ * the vertical optical depth between the emission height and h_obs at the
+ * bunch's wavelength, interpolated bilinearly in the table and clamped to
+ * its range.  The draw is the bunch's fourth Philox deviate u3: it survives
+ * when u3 < P, so the same seed gives the same survivors in every code
+ * version.
+ *   tau       : host, [n_lambda][n_height], finite and >= 0, copied;
+ *   node a, b : lambda_a = lambda_min + a (lambda_max - lambda_min) / (n_lambda - 1),
+ *               h_b = h_min + b (h_max - h_min) / (n_height - 1);
+ *   n_lambda, n_height: 2 .. 4096.
+ * NULL removes the table.  Blocking.  Errors: CHER_EINVAL, CHER_ENOMEM,
+ * CHER_ECUDA. */
+typedef struct cher_transmission {
+    int32_t n_lambda, n_height;
+    double lambda_min_nm, lambda_max_nm;
+    double h_min, h_max;
+    const double *tau;
+} cher_transmission;
+
+cher_status cher_set_transmission(cher_ctx *ctx, const cher_transmission *table);
+
 /* Replace the atmosphere and, if tables were built, rebuild them with the
  * same sizes (blocking).  Errors as cher_build_refraction_tables. */
 cher_status cher_set_atmosphere(cher_ctx *ctx, const cher_atmosphere *atm);
@@ -361,7 +388,8 @@ cher_status cher_segment_yield(cher_ctx *ctx, const cher_tracks *tracks,
  *   pos[4 b ..] = X, Y, cx, cy   (ground point at h_obs, direction)
  *   tim[4 b ..] = t, z_emit, photons, lambda_nm
  *   status[b]   = 0 ground, 1 upward, 2 below h_obs, 3 above h_max,
- *                 4 beyond the zenith range
+ *                 4 beyond the zenith range, 5 reached h_obs but lost to
+ *                 the atmospheric transmission (no ground point then)
  *   nhit[b], first_hit[b] = number of spheres crossed, lowest index or -1.
  * pos/tim are float (CHER_FP32_BULK) or double (CHER_FP64). */
 typedef struct cher_trace {

@@ -81,7 +81,7 @@ class _Out(ctypes.Structure):
                 ("px", _dp), ("py", _dp), ("pz", _dp), ("X", _dp), ("Y", _dp), ("t", _dp),
                 ("cx", _dp), ("cy", _dp), ("cz", _dp), ("lam", _dp), ("w", _dp),
                 ("nhit", _i32p), ("hit_tel", _i32p), ("hit_x", _dp), ("hit_y", _dp),
-                ("hit_t", _dp)]
+                ("hit_t", _dp), ("tr_margin", _dp)]
 
 
 _lib = None
@@ -345,6 +345,7 @@ class Model:
         out["hit_tel"] = np.full((nbt, MAX_HITS), -1, np.int32)
         for k in ("hit_x", "hit_y", "hit_t"):
             out[k] = np.zeros((nbt, MAX_HITS))
+        out["tr_margin"] = np.full(nbt, np.nan)
         O = _Out()
         for k, v in out.items():
             setattr(O, k, _ptr(v, ctypes.c_int32 if v.dtype == np.int32 else ctypes.c_double))

@@ -132,6 +132,8 @@ typedef struct {
     int32_t *nhit;                    /* telescopes crossed                */
     int32_t *hit_tel;                 /* [ORC_MAX_HITS] per bunch          */
     double *hit_x, *hit_y, *hit_t;    /* record in the telescope frame     */
+    double *tr_margin;                /* u3 - P of the transmission draw (NaN */
+                                      /* where none), optional              */
 } orc_bunch_out;
 
 /* ======================================================================= */
@@ -607,6 +609,7 @@ typedef struct {
     int status;
     double xe, ye, he, te, px, py, pz, lam;
     double r[6];                      /* X, Y, t (before t_ref), cx, cy, cz */
+    double tr_margin;                 /* u3 - P of the transmission draw, or NaN */
 } orc_bunch1;
 
 /* ======================================================================= */
@@ -681,11 +684,13 @@ static void orc_one_bunch(const orc_cfg *C, const orc_tracks *Tk, int64_t i, int
     B->te = Tk->t0[i] + fl * inv_bc;
     B->status = orc_propagate_photon(C, variant, B->xe, B->ye, B->he, B->te, B->px, B->py,
                                      B->pz, B->r);
+    B->tr_margin = NAN;
     if (B->status == ORC_ST_GROUND && C->trans_tau) {
         double tau = orc_trans_tau(C, B->lam, B->he);
         double cos_obs = -B->r[5];
         double P = exp(-(tau / cos_obs));
         double u3 = orc_u01(x[3]);
+        B->tr_margin = u3 - P;
         if (!(u3 < P)) B->status = ORC_ST_ABSORBED;
     }
 }
@@ -729,6 +734,7 @@ int orc_bunches(const orc_cfg *C, const orc_tracks *Tk, uint64_t seed,
             O->lam[bidx] = B.lam; O->w[bidx] = Y.w;
             O->status[bidx] = B.status;
             O->nhit[bidx] = 0;
+            if (O->tr_margin) O->tr_margin[bidx] = B.tr_margin;
             if (B.status != ORC_ST_GROUND) {
                 O->X[bidx] = O->Y[bidx] = O->t[bidx] = 0.0;
                 O->cx[bidx] = O->cy[bidx] = O->cz[bidx] = 0.0;

@@ -20,7 +20,7 @@ CHER_FP64 = 0
 CHER_FP32_BULK = 1
 NSTATS = 16
 STAT_NAMES = ["steps", "emitting", "invalid", "bunches", "upward", "below_obs", "above_max",
-              "angle", "ground", "hits", "overflow"]
+              "angle", "ground", "hits", "overflow", "absorbed"]
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
                 4: "tables not built", 5: "out of range", 6: "overflow", 7: "timeout"}
 
@@ -67,6 +67,13 @@ class Profile(ctypes.Structure):
                 ("bin_gcm2", ctypes.c_double), ("axis_cos", ctypes.c_void_p)]
 
 
+class Transmission(ctypes.Structure):
+    _fields_ = [("n_lambda", ctypes.c_int32), ("n_height", ctypes.c_int32),
+                ("lambda_min_nm", ctypes.c_double), ("lambda_max_nm", ctypes.c_double),
+                ("h_min", ctypes.c_double), ("h_max", ctypes.c_double),
+                ("tau", ctypes.POINTER(ctypes.c_double))]
+
+
 class Trace(ctypes.Structure):
     _fields_ = [("pos", ctypes.c_void_p), ("tim", ctypes.c_void_p), ("status", ctypes.c_void_p),
                 ("nhit", ctypes.c_void_p), ("first_hit", ctypes.c_void_p),
@@ -90,6 +97,7 @@ SIGNATURES = {
     "cher_generate_propagate_ex": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
                                         ctypes.POINTER(Output), ctypes.POINTER(Profile), _P]),
     "cher_round_to_float": (_S, [_P, _P, ctypes.c_int64, _P]),
+    "cher_set_transmission": (_S, [_P, ctypes.POINTER(Transmission)]),
     "cher_generate_propagate_noalloc": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
                                              ctypes.POINTER(Output), _P]),
     "cher_graph_create": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
@@ -412,6 +420,22 @@ class Context:
                                        int(precision), ctypes.byref(o), ctypes.byref(h)),
                "cher_graph_create")
         return Graph(h, (dev_tracks, out))
+
+    def set_transmission(self, table: dict | None):
+        """Atmospheric transmission: dict(tau=(n_lambda, n_height) vertical
+        optical depths, lambda_nm=(first, last node), height_m=(first, last
+        node)), or None to remove it."""
+        if table is None:
+            _check(lib().cher_set_transmission(self._h, None), "cher_set_transmission")
+            return
+        tau = np.ascontiguousarray(np.asarray(table["tau"], dtype=np.float64))
+        if tau.ndim != 2:
+            raise ValueError("tau must be 2-D")
+        T = Transmission(int(tau.shape[0]), int(tau.shape[1]), float(table["lambda_nm"][0]),
+                         float(table["lambda_nm"][1]), float(table["height_m"][0]),
+                         float(table["height_m"][1]),
+                         tau.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        _check(lib().cher_set_transmission(self._h, ctypes.byref(T)), "cher_set_transmission")
 
     def set_atmosphere(self, atm: dict):
         A = atmosphere_struct(atm)

@@ -54,6 +54,11 @@ struct cher_ctx {
     int64_t list_cap = 0;
     unsigned long long *d_list_count = nullptr;
     double *d_SU = nullptr;
+    // atmospheric transmission table (both precisions), NULL when off
+    double *d_trans64 = nullptr;
+    float *d_trans32 = nullptr;
+    int32_t trans_nl = 0, trans_nh = 0;
+    double trans_l0 = 0, trans_l1 = 0, trans_h0 = 0, trans_h1 = 0;
 };
 
 namespace {
@@ -201,6 +206,15 @@ cher::KParams base_params(const cher_ctx *c, const cher_tracks *t, uint64_t seed
         p.atm.c[l] = c->atm.c[l];
         p.atm.inv_c[l] = 1.0 / c->atm.c[l];
         p.atm.t_top[l] = c->atm.a[l] + c->atm.b[l] * std::exp(-(c->atm.h_bound[l + 1] / c->atm.c[l]));
+    }
+    if (c->d_trans64) {
+        p.trans = fp32 ? static_cast<const void *>(c->d_trans32) : c->d_trans64;
+        p.trans_nl = c->trans_nl;
+        p.trans_nh = c->trans_nh;
+        p.trans_l0 = c->trans_l0;
+        p.trans_lscale = (c->trans_nl - 1) / (c->trans_l1 - c->trans_l0);
+        p.trans_h0 = c->trans_h0;
+        p.trans_hscale = (c->trans_nh - 1) / (c->trans_h1 - c->trans_h0);
     }
     cher::fill_float_constants(p);
     return p;
@@ -405,10 +419,54 @@ cher_status cher_set_atmosphere(cher_ctx *c, const cher_atmosphere *atm) {
     return s;
 }
 
+static void free_transmission(cher_ctx *c) {
+    cudaFree(c->d_trans64);
+    cudaFree(c->d_trans32);
+    c->d_trans64 = nullptr;
+    c->d_trans32 = nullptr;
+}
+
+cher_status cher_set_transmission(cher_ctx *c, const cher_transmission *tb) {
+    if (!c) return CHER_EINVAL;
+    if (!check_device(c)) return CHER_EINVAL;
+    if (!tb) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return CHER_ECUDA;
+        free_transmission(c);
+        return CHER_OK;
+    }
+    if (!tb->tau || tb->n_lambda < 2 || tb->n_lambda > 4096 || tb->n_height < 2 ||
+        tb->n_height > 4096 || !std::isfinite(tb->lambda_min_nm) ||
+        !std::isfinite(tb->lambda_max_nm) || !(tb->lambda_max_nm > tb->lambda_min_nm) ||
+        !std::isfinite(tb->h_min) || !std::isfinite(tb->h_max) || !(tb->h_max > tb->h_min))
+        return CHER_EINVAL;
+    const size_t n = static_cast<size_t>(tb->n_lambda) * tb->n_height;
+    std::vector<float> t32(n);
+    for (size_t k = 0; k < n; ++k) {
+        if (!std::isfinite(tb->tau[k]) || tb->tau[k] < 0.0) return CHER_EINVAL;
+        t32[k] = static_cast<float>(tb->tau[k]);
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return CHER_ECUDA;
+    free_transmission(c);
+    cher_status r;
+    if ((r = upload(&c->d_trans64, tb->tau, n)) != CHER_OK ||
+        (r = upload(&c->d_trans32, t32.data(), n)) != CHER_OK) {
+        free_transmission(c);
+        return r;
+    }
+    c->trans_nl = tb->n_lambda;
+    c->trans_nh = tb->n_height;
+    c->trans_l0 = tb->lambda_min_nm;
+    c->trans_l1 = tb->lambda_max_nm;
+    c->trans_h0 = tb->h_min;
+    c->trans_h1 = tb->h_max;
+    return CHER_OK;
+}
+
 cher_status cher_destroy(cher_ctx *c) {
     if (!c) return CHER_OK;
     free_tables(c);
     free_adjoint_scratch(c);
+    free_transmission(c);
     cudaFree(c->d_scratch);
     delete c;
     return CHER_OK;

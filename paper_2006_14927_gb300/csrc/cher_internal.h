@@ -20,7 +20,9 @@ constexpr double kAlpha = 7.2973525693e-3;  // fine-structure constant
 constexpr double kPi = 3.14159265358979323846;
 
 // Bunch status codes (the rare branches of the paper's Algorithm 1).
-enum : int32_t { ST_GROUND = 0, ST_UPWARD = 1, ST_BELOW = 2, ST_ABOVE = 3, ST_ANGLE = 4 };
+enum : int32_t {
+    ST_GROUND = 0, ST_UPWARD = 1, ST_BELOW = 2, ST_ABOVE = 3, ST_ANGLE = 4, ST_ABSORBED = 5
+};
 
 constexpr int kMaxCandPerCell = 32;   // telescope candidates in one grid cell
 
@@ -131,6 +133,12 @@ struct KParams {
     struct Layers {
         double hb[6], a[5], b[5], c[5], inv_c[5], t_top[5];
     } atm;
+    // atmospheric transmission (NULL: off): vertical optical depth on a
+    // uniform (lambda, h) grid, [nl][nh], float (FP32) or double (FP64);
+    // index = (value - first node) * scale
+    const void *trans;
+    int32_t trans_nl, trans_nh;
+    double trans_l0, trans_lscale, trans_h0, trans_hscale;
     // the per-launch constants of the bunch loop, rounded to float on the
     // host: the FP32 path converts nothing from double on the device
     struct {
@@ -140,6 +148,7 @@ struct KParams {
         float inv_me, K, inv_B, h_max, dh, eta_slope;
         float gx0[2], gy0[2], inv_gcs[2];
         float prof_dx, prof_inv_dx;
+        float trans_l0, trans_lscale, trans_h0, trans_hscale;
         float hb[6], a[5], b[5], c[5], inv_c[5], t_top[5];
     } f;
 };

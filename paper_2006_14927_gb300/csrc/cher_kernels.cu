@@ -302,6 +302,30 @@ __device__ __forceinline__ void profile_step(const KParams &p, int64_t i, R N) {
 }
 
 // ------------------------------------------------------------------------
+// Atmospheric transmission: the vertical optical depth tau(lambda, h)
+// interpolated bilinearly in its table (clamped to the nodes).
+// ------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ R trans_tau(const KParams &p, R lam, R h) {
+    R xl, xh;
+    if constexpr (std::is_same<R, float>::value) {
+        xl = (lam - p.f.trans_l0) * p.f.trans_lscale;
+        xh = (h - p.f.trans_h0) * p.f.trans_hscale;
+    } else {
+        xl = (lam - p.trans_l0) * p.trans_lscale;
+        xh = (h - p.trans_h0) * p.trans_hscale;
+    }
+    const int nl = p.trans_nl, nh = p.trans_nh;
+    xl = fmin(fmax(xl, R(0)), static_cast<R>(nl - 1));
+    xh = fmin(fmax(xh, R(0)), static_cast<R>(nh - 1));
+    const int a = min(static_cast<int>(xl), nl - 2), b = min(static_cast<int>(xh), nh - 2);
+    const R s = xl - static_cast<R>(a), t = xh - static_cast<R>(b);
+    const R *T = static_cast<const R *>(p.trans) + a * nh + b;
+    const R t00 = __ldg(T), t01 = __ldg(T + 1), t10 = __ldg(T + nh), t11 = __ldg(T + nh + 1);
+    return (R(1) - s) * ((R(1) - t) * t00 + t * t01) + s * ((R(1) - t) * t10 + t * t11);
+}
+
+// ------------------------------------------------------------------------
 // a2 + a3: one bunch, from the Philox block to the ground.
 // ------------------------------------------------------------------------
 template <class R>
@@ -445,6 +469,22 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
     o.cx = so * hx;
     o.cy = so * hy;
     o.cz = -co;
+    if (p.trans) {
+        // survive the atmosphere when u3 < exp(-tau / cos(theta_obs))
+        const R tau = trans_tau<R>(p, o.lam, o.he);
+        R P, u3;
+        if constexpr (std::is_same<R, float>::value) {
+            P = __expf(-(tau * sec));
+            u3 = u01f(x.w);
+        } else {
+            P = exp(-(tau / co));
+            u3 = u01d(x.w);
+        }
+        if (!(u3 < P)) {
+            o.status = ST_ABSORBED;
+            return;
+        }
+    }
     o.status = ST_GROUND;
 }
 
@@ -629,7 +669,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
     c.n_fine = p.n_fine;
 
     unsigned st_steps = 0, st_emit = 0, st_inval = 0, st_bunch = 0, st_up = 0, st_below = 0,
-             st_above = 0, st_angle = 0, st_hits = 0, st_over = 0;
+             st_above = 0, st_angle = 0, st_absorb = 0, st_hits = 0, st_over = 0;
 
     int64_t tile = blockIdx.x;
     for (;;) {
@@ -749,6 +789,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                     st_below += o.status == ST_BELOW;
                     st_above += o.status == ST_ABOVE;
                     st_angle += o.status == ST_ANGLE;
+                    st_absorb += o.status == ST_ABSORBED;
                 }
             }
             if constexpr (MODE == MODE_SCREEN) {
@@ -846,10 +887,12 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             flush_stat(S, CHER_STAT_BELOW_OBS, st_below);
             flush_stat(S, CHER_STAT_ABOVE_MAX, st_above);
             flush_stat(S, CHER_STAT_ANGLE, st_angle);
+            flush_stat(S, CHER_STAT_ABSORBED, st_absorb);
             // reached the ground = generated - dropped (a per-thread partial
             // may be negative; the sum modulo 2^64 is exact)
-            flush_stat_signed(S, CHER_STAT_GROUND, static_cast<int>(st_bunch) -
-                                                       static_cast<int>(st_up + st_below + st_above + st_angle));
+            flush_stat_signed(S, CHER_STAT_GROUND,
+                              static_cast<int>(st_bunch) -
+                                  static_cast<int>(st_up + st_below + st_above + st_angle + st_absorb));
             flush_stat(S, CHER_STAT_HITS, st_hits);
             flush_stat(S, CHER_STAT_OVERFLOW, st_over);
         }
@@ -925,6 +968,10 @@ void fill_float_constants(KParams &p) {
     p.f.dh = static_cast<float>(1.0 / p.inv_dh);
     p.f.eta_slope = static_cast<float>(p.eta_slope * 1.01);
     p.f.rcut2 = static_cast<float>(p.rcut2);
+    p.f.trans_l0 = static_cast<float>(p.trans_l0);
+    p.f.trans_lscale = static_cast<float>(p.trans_lscale);
+    p.f.trans_h0 = static_cast<float>(p.trans_h0);
+    p.f.trans_hscale = static_cast<float>(p.trans_hscale);
     p.f.prof_dx = static_cast<float>(p.prof_dx);
     p.f.prof_inv_dx = static_cast<float>(p.prof_inv_dx);
     for (int l = 0; l < 6; ++l) p.f.hb[l] = static_cast<float>(p.atm.hb[l]);

@@ -17,8 +17,11 @@ the stated accuracy targets):
 * statuses and telescope crossings: exact, after leaving out the bunches
   whose oracle value lies within the path's precision of a decision
   boundary (5 cm of a sphere surface or of h_obs / h_max, 1e-5 of the
-  largest sin^2 zenith, 1e-6 of horizontal travel for FP32; 1e-6 m / 1e-12
-  for FP64).  The number left out is reported and must stay far below 1 %.
+  largest sin^2 zenith, 1e-6 of horizontal travel, 2e-5 between the
+  transmission draw u3 and its survival probability for FP32 -- the FP32
+  probability is an FP32 exponential of an FP32-interpolated depth; 1e-6 m /
+  1e-12 for FP64).  The number left out is reported and must stay far below
+  1 %.
 """
 from __future__ import annotations
 
@@ -34,9 +37,9 @@ FP64 = P.CHER_FP64
 
 TOL = {
     FP64: dict(pos_rel=1e-9, pos_scale=1e3, t_rel=1e-9, t_scale=1e3, dir=1e-9, rel=1e-12,
-               edge_m=1e-6, edge_q=1e-12, edge_pz=1e-12),
+               edge_m=1e-6, edge_q=1e-12, edge_pz=1e-12, edge_tr=1e-12),
     FP32: dict(pos_abs=0.05, t_abs=0.1, dir=1e-5, rel=1e-4, edge_m=0.05, edge_q=1e-5,
-               edge_pz=1e-6),
+               edge_pz=1e-6, edge_tr=2e-5),
 }
 
 
@@ -107,6 +110,8 @@ def borderline_status(M: oracle.Model, o: dict, precision: int) -> np.ndarray:
     q = (o["px"] ** 2 + o["py"] ** 2) * ratio ** 2
     q_max = math.sin(M.theta_max_rad) ** 2
     near |= np.abs(q - q_max) < t["edge_q"]
+    if "tr_margin" in o:       # the transmission draw u3 < P
+        near |= np.abs(np.nan_to_num(o["tr_margin"], nan=1.0)) < t["edge_tr"]
     return near
 
 
