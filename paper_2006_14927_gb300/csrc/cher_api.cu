@@ -226,13 +226,14 @@ cher_status launch(cher_ctx *c, cher::KParams &p, bool fp32, int mode, bool pers
     p.n_tiles = (p.n + block - 1) / block;
     if (p.n_tiles == 0) return CHER_OK;
     const size_t smem = cher::kernel_smem_bytes(fp32, block, p);
-    if (cher::kernel_prepare(fp32, block, mode, smem) != cudaSuccess) {
+    const int kmode = cher::kernel_mode(mode, p);
+    if (cher::kernel_prepare(fp32, block, kmode, smem) != cudaSuccess) {
         cudaGetLastError();
         return CHER_ERANGE;
     }
     int grid;
     if (persistent && c->ctas_per_sm > 0) {
-        const int fit = cher::kernel_max_ctas_per_sm(fp32, block, mode, smem);
+        const int fit = cher::kernel_max_ctas_per_sm(fp32, block, kmode, smem);
         const int per_sm = std::max(1, std::min(c->ctas_per_sm, fit));
         grid = static_cast<int>(std::min<int64_t>(p.n_tiles, int64_t(per_sm) * c->num_sms));
         p.tile_counter = c->d_scratch;
@@ -244,7 +245,7 @@ cher_status launch(cher_ctx *c, cher::KParams &p, bool fp32, int mode, bool pers
         grid = static_cast<int>(p.n_tiles);
         p.tile_counter = nullptr;
     }
-    if (cher::kernel_launch(fp32, block, mode, grid, smem, p, stream) != cudaSuccess) {
+    if (cher::kernel_launch(fp32, block, kmode, grid, smem, p, stream) != cudaSuccess) {
         cudaGetLastError();
         return CHER_ECUDA;
     }
@@ -1037,11 +1038,12 @@ extern "C" cher_status cher_generate_propagate_noalloc(cher_ctx *c, const cher_t
     p.n_tiles = (p.n + block - 1) / block;
     if (p.n_tiles == 0) return CHER_OK;
     const size_t smem = cher::kernel_smem_bytes(fp32, block, p);
-    if (cher::kernel_prepare(fp32, block, cher::MODE_HITS, smem) != cudaSuccess) {
+    const int kmode = cher::kernel_mode(cher::MODE_HITS, p);
+    if (cher::kernel_prepare(fp32, block, kmode, smem) != cudaSuccess) {
         cudaGetLastError();
         return CHER_ERANGE;
     }
-    const int fit = cher::kernel_max_ctas_per_sm(fp32, block, cher::MODE_HITS, smem);
+    const int fit = cher::kernel_max_ctas_per_sm(fp32, block, kmode, smem);
     const int per_sm = std::max(1, std::min(c->ctas_per_sm > 0 ? c->ctas_per_sm : 1, fit));
     const int grid =
         static_cast<int>(std::min<int64_t>(p.n_tiles, int64_t(per_sm) * c->num_sms));
@@ -1049,7 +1051,7 @@ extern "C" cher_status cher_generate_propagate_noalloc(cher_ctx *c, const cher_t
     k_clear_static_scratch<<<1, 32, 0, st>>>(static_cast<int>(need / sizeof(unsigned long long)));
     if (cudaGetLastError() != cudaSuccess) return CHER_ECUDA;
     p.tile_counter = scratch;
-    if (cher::kernel_launch(fp32, block, cher::MODE_HITS, grid, smem, p, stream) != cudaSuccess) {
+    if (cher::kernel_launch(fp32, block, kmode, grid, smem, p, stream) != cudaSuccess) {
         cudaGetLastError();
         return CHER_ECUDA;
     }

@@ -177,6 +177,11 @@ cudaError_t adjoint_pairs(bool fp32, int mode, const AdjParams &A, void *stream)
 void fill_float_constants(KParams &p);
 
 enum Mode : int { MODE_HITS = 0, MODE_TRACE = 1, MODE_YIELD = 2, MODE_SCREEN = 3 };
+// added to a Mode when the launch applies the transmission draw
+constexpr int kTransBit = 4;
+inline int kernel_mode(int mode, const KParams &p) {
+    return (p.trans && mode != MODE_YIELD) ? (mode | kTransBit) : mode;
+}
 
 // Launchers (cher_kernels.cu).  fp32 selects CHER_FP32_BULK.
 size_t kernel_smem_bytes(bool fp32, int block, const KParams &p);

@@ -372,7 +372,7 @@ __device__ __forceinline__ R eta_at(const KParams &p, const Consts<R> &c, const 
     return t0 + f * (t1 - t0);
 }
 
-template <class R>
+template <class R, bool TR>
 __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, const R *eta_s,
                                       const Seg<R> &S, int64_t gi, int j, BunchOut<R> &o) {
     const uint4 x = philox4x32_10(
@@ -469,7 +469,7 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
     o.cx = so * hx;
     o.cy = so * hy;
     o.cz = -co;
-    if (p.trans) {
+    if constexpr (TR) {
         // survive the atmosphere when u3 < exp(-tau / cos(theta_obs))
         const R tau = trans_tau<R>(p, o.lam, o.he);
         R P, u3;
@@ -577,6 +577,11 @@ __device__ __forceinline__ void store4(void *base, int64_t r, R a, R b, R c, R d
     }
 }
 
+// ask L2 for a line this CTA reads soon (no result, nothing waits on it)
+__device__ __forceinline__ void prefetch_l2(const void *ptr) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
+
 // warp-wide sum of a counter, one atomic per warp
 __device__ __forceinline__ void flush_stat(unsigned long long *stats, int idx, unsigned v) {
 #pragma unroll
@@ -595,7 +600,9 @@ __device__ __forceinline__ void flush_stat_signed(unsigned long long *stats, int
 // ------------------------------------------------------------------------
 // The fused kernel.
 // ------------------------------------------------------------------------
-template <class R, int BLOCK, int MODE>
+// TR: the atmospheric transmission draw is compiled in (a separate
+// instantiation: present but switched off it cost 2 % of the launch)
+template <class R, int BLOCK, int MODE, bool TR>
 __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / BLOCK : 1)
     k_gen_prop(const KParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -671,14 +678,17 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
     unsigned st_steps = 0, st_emit = 0, st_inval = 0, st_bunch = 0, st_up = 0, st_below = 0,
              st_above = 0, st_angle = 0, st_absorb = 0, st_hits = 0, st_over = 0;
 
+    // Persistent CTAs claim their next tile one tile ahead, during the scan
+    // (its barriers publish the claim), and prefetch that tile's step
+    // arrays into L2 while they work through the current tile's bunches.
     int64_t tile = blockIdx.x;
+    if (p.tile_counter) {
+        __syncthreads();
+        if (tid == 0) s_tile = atomicAdd(p.tile_counter, 1ull);
+        __syncthreads();
+        tile = static_cast<int64_t>(s_tile);
+    }
     for (;;) {
-        if (p.tile_counter) {
-            __syncthreads();
-            if (tid == 0) s_tile = atomicAdd(p.tile_counter, 1ull);
-            __syncthreads();
-            tile = static_cast<int64_t>(s_tile);
-        }
         if (tile >= p.n_tiles) break;
         const int64_t base = tile * BLOCK;
 
@@ -717,6 +727,10 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
         }
         if constexpr (MODE == MODE_YIELD) {
             if (!p.tile_counter) break;
+            __syncthreads();
+            if (tid == 0) s_tile = atomicAdd(p.tile_counter, 1ull);
+            __syncthreads();
+            tile = static_cast<int64_t>(s_tile);
             continue;
         }
         st_bunch += nb;
@@ -729,7 +743,9 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             if (lane >= o) v += t;
         }
         if (lane == 31) wsum[warp] = v;
+        if (tid == 0 && p.tile_counter) s_tile = atomicAdd(p.tile_counter, 1ull);
         __syncthreads();
+        const int64_t next = p.tile_counter ? static_cast<int64_t>(s_tile) : p.n_tiles;
         if (warp == 0) {
             int w = lane < BLOCK / 32 ? wsum[lane] : 0;
 #pragma unroll
@@ -745,6 +761,21 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
         if (tid == BLOCK - 1) off[BLOCK] = excl + nb;
         __syncthreads();
         const int total = off[BLOCK];
+        if (next < p.n_tiles) {
+            const int64_t ni = next * BLOCK + tid;
+            if (ni < p.n) {
+                prefetch_l2(p.x0 + ni);
+                prefetch_l2(p.y0 + ni);
+                prefetch_l2(p.z0 + ni);
+                prefetch_l2(p.t0 + ni);
+                prefetch_l2(p.len + ni);
+                prefetch_l2(p.ekin + ni);
+                prefetch_l2(static_cast<const R *>(p.ux) + ni);
+                prefetch_l2(static_cast<const R *>(p.uy) + ni);
+                prefetch_l2(static_cast<const R *>(p.uz) + ni);
+                if (p.shower) prefetch_l2(p.shower + ni);
+            }
+        }
 
         // ---- phase B: the tile's bunches -------------------------------------
         // Each warp takes an even share of contiguous 32-bunch windows (shares
@@ -783,7 +814,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             int j = 0;
             if (live) {
                 j = bidx - off[s];
-                bunch<R>(p, c, eta_s, seg[s], p.track_base + base + s, j, o);
+                bunch<R, TR>(p, c, eta_s, seg[s], p.track_base + base + s, j, o);
                 if (o.status != ST_GROUND) {       // rare: the drops
                     st_up += o.status == ST_UPWARD;
                     st_below += o.status == ST_BELOW;
@@ -874,6 +905,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             }
         }
         if (!p.tile_counter) break;
+        tile = next;
     }
 
     unsigned long long *S = p.stats;
@@ -908,34 +940,41 @@ size_t smem_bytes(const KParams &p) {
 }
 
 template <class R, int BLOCK, int MODE>
-const void *kernel_ptr() {
-    return reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE>);
+const void *kernel_ptr(bool tr) {
+    if constexpr (MODE == MODE_YIELD)
+        return reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false>);
+    else
+        return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true>)
+                  : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false>);
 }
 
 template <class R, int MODE>
-const void *pick(int block) {
+const void *pick(int block, bool tr) {
     switch (block) {
-    case 128: return kernel_ptr<R, 128, MODE>();
-    case 256: return kernel_ptr<R, 256, MODE>();
-    case 512: return kernel_ptr<R, 512, MODE>();
+    case 128: return kernel_ptr<R, 128, MODE>(tr);
+    case 256: return kernel_ptr<R, 256, MODE>(tr);
+    case 512: return kernel_ptr<R, 512, MODE>(tr);
     }
     return nullptr;
 }
 
+// mode: a Mode, plus kTransBit for the instantiation with the transmission
 const void *pick_kernel(bool fp32, int block, int mode) {
+    const bool tr = (mode & kTransBit) != 0;
+    mode &= ~kTransBit;
     if (fp32) {
         switch (mode) {
-        case MODE_HITS: return pick<float, MODE_HITS>(block);
-        case MODE_TRACE: return pick<float, MODE_TRACE>(block);
-        case MODE_YIELD: return pick<float, MODE_YIELD>(block);
-        case MODE_SCREEN: return pick<float, MODE_SCREEN>(block);
+        case MODE_HITS: return pick<float, MODE_HITS>(block, tr);
+        case MODE_TRACE: return pick<float, MODE_TRACE>(block, tr);
+        case MODE_YIELD: return pick<float, MODE_YIELD>(block, tr);
+        case MODE_SCREEN: return pick<float, MODE_SCREEN>(block, tr);
         }
     } else {
         switch (mode) {
-        case MODE_HITS: return pick<double, MODE_HITS>(block);
-        case MODE_TRACE: return pick<double, MODE_TRACE>(block);
-        case MODE_YIELD: return pick<double, MODE_YIELD>(block);
-        case MODE_SCREEN: return pick<double, MODE_SCREEN>(block);
+        case MODE_HITS: return pick<double, MODE_HITS>(block, tr);
+        case MODE_TRACE: return pick<double, MODE_TRACE>(block, tr);
+        case MODE_YIELD: return pick<double, MODE_YIELD>(block, tr);
+        case MODE_SCREEN: return pick<double, MODE_SCREEN>(block, tr);
         }
     }
     return nullptr;
