@@ -87,6 +87,37 @@ class _Out(ctypes.Structure):
 _lib = None
 
 
+class _Shower(ctypes.Structure):
+    _fields_ = [("e0_mev", ctypes.c_double), ("zenith", ctypes.c_double),
+                ("azimuth", ctypes.c_double), ("core_x", ctypes.c_double),
+                ("core_y", ctypes.c_double), ("first", ctypes.c_int64), ("n", ctypes.c_int64)]
+
+
+def generate_steps(showers, h_obs: float, seed: int, n_cdf: int = 1024) -> dict:
+    """Steps of parameterised showers (orc_generate_steps).  `showers`: a
+    sequence of dicts with e0_mev, zenith, azimuth, core_x, core_y, n; the
+    steps of shower s follow those of shower s - 1.  Returns the step arrays
+    (float64, shower uint32) and t_ref per shower."""
+    arr = (_Shower * len(showers))()
+    first = 0
+    for k, s in enumerate(showers):
+        arr[k] = _Shower(float(s["e0_mev"]), float(s["zenith"]), float(s["azimuth"]),
+                         float(s["core_x"]), float(s["core_y"]), first, int(s["n"]))
+        first += int(s["n"])
+    out = {k: np.zeros(first) for k in ("x0", "y0", "z0", "t0", "len", "ekin", "ux", "uy", "uz")}
+    out["shower"] = np.zeros(first, np.uint32)
+    t_ref = np.zeros(len(showers))
+    rc = lib().orc_generate_steps(arr, len(showers), float(h_obs), ctypes.c_uint64(seed),
+                                  int(n_cdf), *[_ptr(out[k]) for k in ("x0", "y0", "z0", "t0",
+                                                                     "len", "ekin", "ux", "uy",
+                                                                     "uz")],
+                                  _ptr(out["shower"], ctypes.c_uint32), _ptr(t_ref))
+    if rc != 0:
+        raise ValueError("orc_generate_steps failed")
+    out["t_ref"] = t_ref
+    return out
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -121,6 +152,9 @@ def lib():
                                   _i32p, ctypes.c_double, _dp, _dp]
         L.orc_profile.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Tracks), _dp,
                                   ctypes.c_double, ctypes.c_int, _dp]
+        L.orc_generate_steps.argtypes = [ctypes.POINTER(_Shower), ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_uint64, ctypes.c_int] + [_dp] * 9 + \
+            [_u32p, _dp]
         L.orc_philox_fill.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                       ctypes.c_int64, _u32p]
         _lib = L

@@ -874,6 +874,144 @@ int orc_profile(const orc_cfg *C, const orc_tracks *Tk, const double *axis_cos,
     return 0;
 }
 
+/* ======================================================================= */
+/* Shower steps from a parameterised electromagnetic shower (an extension: */
+/* the paper's input are the EGS4 electron/positron steps that CORSIKA      */
+/* hands to CERENK; this generator stands in for them on the device).      */
+/* Per shower: primary energy E0 (MeV), axis zenith and azimuth, core      */
+/* (x, y) at h_obs, n steps at global indices first .. first + n - 1.       */
+/* Per step g, eight deviates u0..u7 from Philox4x32-10 keyed by the seed, */
+/* counters (g_lo, g_hi, 0, 1) and (g_lo, g_hi, 1, 1):                     */
+/*   depth  t (radiation lengths) from the Greisen profile                  */
+/*          N(t) ~ exp(t (1 - 1.5 ln s)) / sqrt(y), s = 3t/(t + 2y),        */
+/*          y = ln(E0/E_c), E_c = 85 MeV, on (0, t_g], t_g the slant depth  */
+/*          of h_obs (isothermal air, X(h) = 1030 exp(-h/8000 m) g/cm^2,    */
+/*          X0 = 36.7 g/cm^2), by inverting the CDF tabulated on n_cdf      */
+/*          uniform nodes (linear between them) at u0;                      */
+/*   height h = 8000 ln(1030 / (t X0 cos(zenith))), at most 29999 m, and    */
+/*          s = (h - h_obs)/cos(zenith) up the axis from the core;          */
+/*   lateral offset r = -50 ln(u1) m (exponential, mean 50 m) at azimuth    */
+/*          2 pi u2 in the plane normal to the axis (basis b1, b2);         */
+/*   kinetic energy E = 20 MeV (5000/20)^u3 (log-uniform 20 MeV - 5 GeV);   */
+/*   direction: axis + sigma (n1 b1 + n2 b2), normalised, with             */
+/*          sigma = 3 deg * 50 MeV / E and (n1, n2) standard normals by     */
+/*          Box-Muller from (u4, u5);                                       */
+/*   start time (s_ref - s)/c with s_ref = (30000 m - h_obs)/cos(zenith);   */
+/*   length 1 + 19 u6 m.                                                    */
+/* The reference time of the shower is s_ref / c.                          */
+/* ======================================================================= */
+typedef struct {
+    double e0_mev, zenith, azimuth, core_x, core_y;
+    int64_t first, n;
+} orc_shower;
+
+static double orc_greisen(double t, double y)
+{
+    if (t <= 0.0) return 1.0 / sqrt(y);
+    double s = 3.0 * t / (t + 2.0 * y);
+    return exp(t * (1.0 - 1.5 * log(s))) / sqrt(y);
+}
+
+static double orc_simpson_greisen(double a, double b, double y, double fa, double fm, double fb,
+                                  double whole, double tol, int depth)
+{
+    double m = 0.5 * (a + b);
+    double lm = orc_greisen(0.5 * (a + m), y), rm = orc_greisen(0.5 * (m + b), y);
+    double left = (m - a) / 6.0 * (fa + 4.0 * lm + fm);
+    double right = (b - m) / 6.0 * (fm + 4.0 * rm + fb);
+    if (depth <= 0 || fabs(left + right - whole) <= 15.0 * tol)
+        return left + right + (left + right - whole) / 15.0;
+    return orc_simpson_greisen(a, m, y, fa, lm, fm, left, 0.5 * tol, depth - 1) +
+           orc_simpson_greisen(m, b, y, fm, rm, fb, right, 0.5 * tol, depth - 1);
+}
+
+/* cdf[0 .. n_cdf-1] on t_k = k t_g / (n_cdf - 1), normalised to 1 */
+static void orc_greisen_cdf(double y, double t_g, int n_cdf, double *cdf)
+{
+    double dt = t_g / (double)(n_cdf - 1);
+    cdf[0] = 0.0;
+    for (int k = 1; k < n_cdf; ++k) {
+        double a = (double)(k - 1) * dt, b = (double)k * dt;
+        double fa = orc_greisen(a, y), fb = orc_greisen(b, y), fm = orc_greisen(0.5 * (a + b), y);
+        double whole = (b - a) / 6.0 * (fa + 4.0 * fm + fb);
+        cdf[k] = cdf[k - 1] + orc_simpson_greisen(a, b, y, fa, fm, fb, whole, 1e-15 * fabs(whole) + 1e-300, 40);
+    }
+    double tot = cdf[n_cdf - 1];
+    for (int k = 0; k < n_cdf; ++k) cdf[k] /= tot;
+}
+
+int orc_generate_steps(const orc_shower *S, int n_showers, double h_obs, uint64_t seed,
+                       int n_cdf, double *x0, double *y0, double *z0, double *t0, double *len,
+                       double *ekin, double *ux, double *uy, double *uz, uint32_t *shower,
+                       double *t_ref)
+{
+    const double c_light = ORC_C_M_PER_NS, X0 = 36.7, E_c = 85.0, X_sea = 1030.0, H = 8000.0;
+    const double h_start = 30000.0;
+    if (!S || n_showers < 1 || n_cdf < 2) return -1;
+    double *cdf = (double *)malloc(sizeof(double) * (size_t)n_cdf);
+    if (!cdf) return -1;
+    uint32_t key[2] = { (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) };
+    for (int sh = 0; sh < n_showers; ++sh) {
+        const orc_shower *P = S + sh;
+        double cz = cos(P->zenith);
+        if (!(P->e0_mev > E_c) || !(cz > 0.0)) { free(cdf); return -1; }
+        double y = log(P->e0_mev / E_c);
+        double t_g = X_sea * exp(-(h_obs / H)) / cz / X0;
+        orc_greisen_cdf(y, t_g, n_cdf, cdf);
+        double dt = t_g / (double)(n_cdf - 1);
+        double sz = sin(P->zenith);
+        double ax = sz * cos(P->azimuth), ay = sz * sin(P->azimuth), az = -cz;
+        /* b1 = axis x z (normalised), b2 = axis x b1 */
+        double b1x = ay, b1y = -ax, b1z = 0.0;
+        double nb = sqrt(b1x * b1x + b1y * b1y);
+        if (nb > 1e-12) { b1x /= nb; b1y /= nb; } else { b1x = 1.0; b1y = 0.0; }
+        double b2x = ay * b1z - az * b1y, b2y = az * b1x - ax * b1z, b2z = ax * b1y - ay * b1x;
+        double s_ref = (h_start - h_obs) / cz;
+        t_ref[sh] = s_ref / c_light;
+        for (int64_t k = 0; k < P->n; ++k) {
+            int64_t g = P->first + k;
+            uint32_t c0[4] = { (uint32_t)((uint64_t)g & 0xffffffffu), (uint32_t)((uint64_t)g >> 32), 0u, 1u };
+            uint32_t c1[4] = { c0[0], c0[1], 1u, 1u };
+            uint32_t w0[4], w1[4];
+            orc_philox4x32_10(c0, key, w0);
+            orc_philox4x32_10(c1, key, w1);
+            double u[8];
+            for (int q = 0; q < 4; ++q) { u[q] = orc_u01(w0[q]); u[4 + q] = orc_u01(w1[q]); }
+            /* depth: the node interval holding u0, then linear inside it */
+            int lo = 0, hi = n_cdf - 1;
+            while (hi - lo > 1) {
+                int mid = (lo + hi) / 2;
+                if (cdf[mid] <= u[0]) lo = mid; else hi = mid;
+            }
+            double t = (double)lo * dt + (u[0] - cdf[lo]) / (cdf[lo + 1] - cdf[lo]) * dt;
+            double h = H * log(X_sea / (t * X0 * cz));
+            if (h > h_start - 1.0) h = h_start - 1.0;
+            double sa = (h - h_obs) / cz;
+            double r = -50.0 * log(u[1]);
+            double psi = 2.0 * ORC_PI * u[2];
+            double lx = r * cos(psi), ly = r * sin(psi);
+            x0[g] = P->core_x - sa * ax + lx * b1x + ly * b2x;
+            y0[g] = P->core_y - sa * ay + lx * b1y + ly * b2y;
+            z0[g] = h_obs - sa * az + lx * b1z + ly * b2z;
+            double e = 20.0 * exp(u[3] * log(5000.0 / 20.0));
+            ekin[g] = e;
+            double sig = (3.0 * ORC_PI / 180.0) * (50.0 / e);
+            double rho = sqrt(-2.0 * log(u[4]));
+            double n1 = rho * cos(2.0 * ORC_PI * u[5]), n2 = rho * sin(2.0 * ORC_PI * u[5]);
+            double dx = ax + sig * (n1 * b1x + n2 * b2x);
+            double dy = ay + sig * (n1 * b1y + n2 * b2y);
+            double dz = az + sig * (n1 * b1z + n2 * b2z);
+            double dn = sqrt(dx * dx + dy * dy + dz * dz);
+            ux[g] = dx / dn; uy[g] = dy / dn; uz[g] = dz / dn;
+            t0[g] = (s_ref - sa) / c_light;
+            len[g] = 1.0 + 19.0 * u[6];
+            shower[g] = (uint32_t)sh;
+        }
+    }
+    free(cdf);
+    return 0;
+}
+
 int orc_max_hits(void) { return ORC_MAX_HITS; }
 
 int orc_num_threads(void)
