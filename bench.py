@@ -349,6 +349,7 @@ def run_ours(args):
 
     # ---- end to end: host buffers through the C ABI ---------------------
     e2e = None
+    e2e_gen = None
     if not args.no_e2e:
         prec = P.CHER_FP32_BULK
         host = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory()
@@ -398,6 +399,45 @@ def run_ours(args):
         te, _ = reduce_over_ranks(te, 0.0, world, dev)
         e2e = {"value": b32 / len(r32["ms"]) * steps / te, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+        # end to end from shower parameters: the steps come from the device
+        # generator (same shower, same step count), only the parameters and
+        # its depth table go to the device
+        if args.workload == "vertical_1tev" and world == 1:
+            showers = [dict(e0_mev=1.0e6, zenith=0.0, azimuth=0.0, core_x=0.0, core_y=0.0,
+                            n=int(len(sc["tracks"]["x0"])))]
+
+            def gen_step():
+                dg = ctx.generate_steps(showers, 11, prec)
+                ctx.generate_propagate(dg, 11, prec, out)
+                h_cnt.copy_(out.count, non_blocking=True)
+                h_st.copy_(out.stats, non_blocking=True)
+                torch.cuda.current_stream().synchronize()
+                nbytes = h_cnt.numel() * 8 + h_st.numel() * 8
+                for k_ in range(n_tel):
+                    c = min(int(h_cnt[k_]), cap)
+                    if c:
+                        h_pos[k_, :c].copy_(out.pos[k_, :c], non_blocking=True)
+                        h_tim[k_, :c].copy_(out.tim[k_, :c], non_blocking=True)
+                        h_key[k_, :c].copy_(out.key[k_, :c], non_blocking=True)
+                        nbytes += c * 40
+                torch.cuda.current_stream().synchronize()
+                return nbytes, int(h_st[3])
+
+            for _ in range(max(1, warmup // 2)):
+                gen_step()
+            g0 = time.perf_counter()
+            gb = 0
+            for _ in range(steps):
+                gd2h, gbunch = gen_step()
+                gb += gbunch
+            tg = time.perf_counter() - g0
+            e2e_gen = {"value": gb / tg, "unit": UNIT,
+                       "h2d_bytes_per_step": 64 + 16 + 4 * 1024 + 8,
+                       "d2h_bytes_per_step": int(gd2h), "steps_generated": showers[0]["n"],
+                       "bunches_per_step": gb // steps,
+                       "note": "steps from cher_generate_steps (Philox draws, not the "
+                               "host workload's)"}
 
     if rank != 0:
         if world > 1:
@@ -466,6 +506,8 @@ def run_ours(args):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if e2e_gen is not None:
+        line["e2e_generated"] = e2e_gen
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if args.workload == "vertical_1tev" and args.scale == 1.0 and world == 1:

@@ -234,6 +234,50 @@ cher_status cher_generate_propagate_ex(cher_ctx *ctx, const cher_tracks *tracks,
                                        const cher_output *out, const cher_profile *profile,
                                        void *stream);
 
+/* Shower steps from a parameterised electromagnetic shower, generated on
+ * the device (an extension, no counterpart in the paper: its input are the
+ * EGS4 electron/positron steps CORSIKA hands to CERENK; this stands in for
+ * them so that a batch of showers needs no step arrays from the host).  Per
+ * shower: primary energy, axis, core at h_obs and a step count; the steps
+ * of shower s follow those of shower s - 1.  Per step g, eight deviates of
+ * Philox4x32-10 keyed by `seed`, counters (g, 0, 1) and (g, 1, 1): the
+ * depth from the Greisen longitudinal profile (y = ln(E0 / 85 MeV), in
+ * isothermal air X = 1030 exp(-h / 8000 m) g/cm^2, X0 = 36.7 g/cm^2, by
+ * inverting its CDF tabulated on 1024 uniform depth nodes), the height on
+ * the axis (at most 29999 m), an exponential lateral offset of mean 50 m at
+ * a uniform azimuth, a log-uniform kinetic energy over 20 MeV - 5 GeV, a
+ * direction spread around the axis by Box-Muller normals of width
+ * 3 deg x 50 MeV / E, a start time (s_ref - s)/c along the axis (s_ref the
+ * distance from 30 km to h_obs) and a length uniform in [1, 20] m.  Per-step
+ * arithmetic in FP32 (outputs widened).
+ *   showers     : host, n_showers entries, e0_mev > 85, zenith in [0, pi/2),
+ *                 finite azimuth and core, n_steps >= 0 (total <= 2^40);
+ *   out         : device arrays of the total step count (x0 .. ekin double,
+ *                 ux, uy, uz float for CHER_FP32_BULK or double for
+ *                 CHER_FP64, shower uint32) and t_ref[n_showers] double (the
+ *                 time the axis reaches h_obs), 8-byte aligned.
+ * The context holds the per-call tables in its scratch: calls on one
+ * context must not overlap on different streams.  Asynchronous on
+ * `stream` after a blocking upload.  Errors: CHER_EINVAL, CHER_ERANGE,
+ * CHER_ENOMEM, CHER_ECUDA. */
+typedef struct cher_shower {
+    double e0_mev;
+    double zenith, azimuth;
+    double core_x, core_y;
+    int64_t n_steps;
+} cher_shower;
+
+typedef struct cher_step_buffers {
+    double *x0, *y0, *z0, *t0, *len, *ekin;
+    void *ux, *uy, *uz;
+    uint32_t *shower;
+    double *t_ref;
+} cher_step_buffers;
+
+cher_status cher_generate_steps(cher_ctx *ctx, const cher_shower *showers, int32_t n_showers,
+                                uint64_t seed, cher_precision prec,
+                                const cher_step_buffers *out, void *stream);
+
 /* The double -> float rounding that the FP32 path applies to its FP64
  * inputs (positions, lengths, energies, the differences to h_obs and
  * t_ref): round to nearest even, done on the integer pipes because GB300

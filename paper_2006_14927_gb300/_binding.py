@@ -67,6 +67,17 @@ class Profile(ctypes.Structure):
                 ("bin_gcm2", ctypes.c_double), ("axis_cos", ctypes.c_void_p)]
 
 
+class Shower(ctypes.Structure):
+    _fields_ = [("e0_mev", ctypes.c_double), ("zenith", ctypes.c_double),
+                ("azimuth", ctypes.c_double), ("core_x", ctypes.c_double),
+                ("core_y", ctypes.c_double), ("n_steps", ctypes.c_int64)]
+
+
+class StepBuffers(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("x0", "y0", "z0", "t0", "len", "ekin", "ux", "uy",
+                                               "uz", "shower", "t_ref")]
+
+
 class Transmission(ctypes.Structure):
     _fields_ = [("n_lambda", ctypes.c_int32), ("n_height", ctypes.c_int32),
                 ("lambda_min_nm", ctypes.c_double), ("lambda_max_nm", ctypes.c_double),
@@ -98,6 +109,8 @@ SIGNATURES = {
                                         ctypes.POINTER(Output), ctypes.POINTER(Profile), _P]),
     "cher_round_to_float": (_S, [_P, _P, ctypes.c_int64, _P]),
     "cher_set_transmission": (_S, [_P, ctypes.POINTER(Transmission)]),
+    "cher_generate_steps": (_S, [_P, ctypes.POINTER(Shower), ctypes.c_int32, ctypes.c_uint64, _S,
+                                 ctypes.POINTER(StepBuffers), _P]),
     "cher_generate_propagate_noalloc": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
                                              ctypes.POINTER(Output), _P]),
     "cher_graph_create": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
@@ -420,6 +433,31 @@ class Context:
                                        int(precision), ctypes.byref(o), ctypes.byref(h)),
                "cher_graph_create")
         return Graph(h, (dev_tracks, out))
+
+    def generate_steps(self, showers, seed: int, precision: int, device="cuda", stream=None):
+        """Device step arrays of parameterised showers (cher_generate_steps):
+        `showers` is a sequence of dicts with e0_mev, zenith, azimuth,
+        core_x, core_y, n.  Returns the dict generate_propagate takes."""
+        torch = _torch()
+        arr = (Shower * len(showers))()
+        for k, s in enumerate(showers):
+            arr[k] = Shower(float(s["e0_mev"]), float(s["zenith"]), float(s["azimuth"]),
+                            float(s["core_x"]), float(s["core_y"]), int(s["n"]))
+        n = sum(max(int(s["n"]), 0) for s in showers)    # (a negative count: EINVAL below)
+        ddt = torch.float32 if precision == CHER_FP32_BULK else torch.float64
+        out = {k: torch.empty(n, dtype=torch.float64, device=device)
+               for k in ("x0", "y0", "z0", "t0", "len", "ekin")}
+        for k in ("ux", "uy", "uz"):
+            out[k] = torch.empty(n, dtype=ddt, device=device)
+        out["shower"] = torch.empty(n, dtype=torch.int32, device=device)
+        out["t_ref"] = torch.empty(len(showers), dtype=torch.float64, device=device)
+        B = StepBuffers(*[out[k].data_ptr() for k in ("x0", "y0", "z0", "t0", "len", "ekin", "ux",
+                                                     "uy", "uz", "shower", "t_ref")])
+        _check(lib().cher_generate_steps(self._h, arr, len(showers), ctypes.c_uint64(seed),
+                                         int(precision), ctypes.byref(B),
+                                         ctypes.c_void_p(_stream_ptr(stream))),
+               "cher_generate_steps")
+        return out
 
     def set_transmission(self, table: dict | None):
         """Atmospheric transmission: dict(tau=(n_lambda, n_height) vertical

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -59,6 +60,11 @@ struct cher_ctx {
     float *d_trans32 = nullptr;
     int32_t trans_nl = 0, trans_nh = 0;
     double trans_l0 = 0, trans_l1 = 0, trans_h0 = 0, trans_h1 = 0;
+    // step generator: per-call shower constants, offsets and CDF tables;
+    // host CDF rows cached by (E0, zenith) (cleared past 4096 entries)
+    unsigned char *d_gen = nullptr;
+    int64_t gen_cap = 0;
+    std::map<std::pair<double, double>, std::vector<float>> cdf_cache;
 };
 
 namespace {
@@ -112,6 +118,21 @@ cher_status upload(T **dst, const T *src, size_t n) {
     }
     if (cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
         return CHER_ECUDA;
+    return CHER_OK;
+}
+
+template <class T>
+cher_status grow(T **ptr, int64_t &cap, int64_t need) {
+    if (need <= cap && *ptr) return CHER_OK;
+    cudaFree(*ptr);
+    *ptr = nullptr;
+    cap = 0;
+    if (cudaMalloc(reinterpret_cast<void **>(ptr), std::max<int64_t>(need, 1) * sizeof(T)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return CHER_ENOMEM;
+    }
+    cap = need;
     return CHER_OK;
 }
 
@@ -463,11 +484,117 @@ cher_status cher_set_transmission(cher_ctx *c, const cher_transmission *tb) {
     return CHER_OK;
 }
 
+cher_status cher_generate_steps(cher_ctx *c, const cher_shower *sh, int32_t n_showers,
+                                uint64_t seed, cher_precision prec, const cher_step_buffers *out,
+                                void *stream) {
+    if (!c || !sh || n_showers < 1 || !out) return CHER_EINVAL;
+    if (prec != CHER_FP64 && prec != CHER_FP32_BULK) return CHER_EINVAL;
+    if (!check_device(c)) return CHER_EINVAL;
+    constexpr int kCdf = 1024;
+    constexpr double kX0 = 36.7, kEc = 85.0, kXsea = 1030.0, kH = 8000.0, kStart = 30000.0;
+    const double pi = 3.14159265358979323846;
+    int64_t total = 0;
+    for (int s = 0; s < n_showers; ++s) {
+        const cher_shower &S = sh[s];
+        if (!(S.e0_mev > kEc) || !std::isfinite(S.e0_mev) || !(S.zenith >= 0.0) ||
+            !(S.zenith < 0.5 * pi) || !std::isfinite(S.azimuth) || !std::isfinite(S.core_x) ||
+            !std::isfinite(S.core_y) || S.n_steps < 0)
+            return CHER_EINVAL;
+        total += S.n_steps;
+        if (total > (int64_t(1) << 40)) return CHER_ERANGE;
+    }
+    if (bad_ptr(out->t_ref)) return CHER_EINVAL;
+    if (total > 0 && (bad_ptr(out->x0) || bad_ptr(out->y0) || bad_ptr(out->z0) ||
+                      bad_ptr(out->t0) || bad_ptr(out->len) || bad_ptr(out->ekin) ||
+                      bad_ptr(out->ux) || bad_ptr(out->uy) || bad_ptr(out->uz) ||
+                      bad_ptr(out->shower)))
+        return CHER_EINVAL;
+    std::vector<cher::GenShower> G(n_showers);
+    std::vector<int64_t> first(n_showers + 1, 0);
+    std::vector<float> cdf(static_cast<size_t>(n_showers) * kCdf);
+    std::vector<double> t_ref(n_showers), row;
+    for (int s = 0; s < n_showers; ++s) {
+        const cher_shower &S = sh[s];
+        const double cz = std::cos(S.zenith), sz = std::sin(S.zenith);
+        const double ax = sz * std::cos(S.azimuth), ay = sz * std::sin(S.azimuth), az = -cz;
+        double b1x = ay, b1y = -ax;
+        const double nb = std::sqrt(b1x * b1x + b1y * b1y);
+        if (nb > 1e-12) {
+            b1x /= nb;
+            b1y /= nb;
+        } else {
+            b1x = 1.0;
+            b1y = 0.0;
+        }
+        const double b1z = 0.0;
+        const double b2x = ay * b1z - az * b1y, b2y = az * b1x - ax * b1z, b2z = ax * b1y - ay * b1x;
+        const double t_g = kXsea * std::exp(-(c->h_obs / kH)) / cz / kX0;
+        const double s_ref = (kStart - c->h_obs) / cz;
+        cher::GenShower &g = G[s];
+        g.ax = static_cast<float>(ax); g.ay = static_cast<float>(ay); g.az = static_cast<float>(az);
+        g.b1x = static_cast<float>(b1x); g.b1y = static_cast<float>(b1y); g.b1z = 0.0f;
+        g.b2x = static_cast<float>(b2x); g.b2y = static_cast<float>(b2y);
+        g.b2z = static_cast<float>(b2z);
+        g.cz = static_cast<float>(cz);
+        g.x0cz = static_cast<float>(kX0 * cz);
+        g.core_x = static_cast<float>(S.core_x);
+        g.core_y = static_cast<float>(S.core_y);
+        g.s_ref = static_cast<float>(s_ref);
+        g.dt = static_cast<float>(t_g / (kCdf - 1));
+        t_ref[s] = s_ref / cher::kC;
+        first[s + 1] = first[s] + S.n_steps;
+        const auto key = std::make_pair(S.e0_mev, S.zenith);
+        auto it = c->cdf_cache.find(key);
+        if (it == c->cdf_cache.end()) {
+            if (c->cdf_cache.size() >= 4096) c->cdf_cache.clear();
+            cher::greisen_cdf_host(std::log(S.e0_mev / kEc), t_g, kCdf, row);
+            std::vector<float> rf(row.begin(), row.end());
+            it = c->cdf_cache.emplace(key, std::move(rf)).first;
+        }
+        std::copy(it->second.begin(), it->second.end(), cdf.begin() + static_cast<size_t>(s) * kCdf);
+    }
+    // one scratch block: shower constants | offsets | tables
+    const size_t o_first = (sizeof(cher::GenShower) * n_showers + 15) & ~size_t(15);
+    const size_t o_cdf = (o_first + sizeof(int64_t) * (n_showers + 1) + 15) & ~size_t(15);
+    const size_t bytes = o_cdf + sizeof(float) * cdf.size();
+    cher_status r;
+    if ((r = grow(&c->d_gen, c->gen_cap, static_cast<int64_t>(bytes))) != CHER_OK) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(c->d_gen, G.data(), sizeof(cher::GenShower) * n_showers,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(c->d_gen + o_first, first.data(), sizeof(int64_t) * (n_showers + 1),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(c->d_gen + o_cdf, cdf.data(), sizeof(float) * cdf.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(out->t_ref, t_ref.data(), sizeof(double) * n_showers,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return CHER_ECUDA;
+    cher::GenParams g;
+    g.showers = reinterpret_cast<const cher::GenShower *>(c->d_gen);
+    g.first = reinterpret_cast<const int64_t *>(c->d_gen + o_first);
+    g.n_showers = n_showers;
+    g.n_cdf = kCdf;
+    g.cdf = reinterpret_cast<const float *>(c->d_gen + o_cdf);
+    g.key0 = static_cast<uint32_t>(seed & 0xffffffffu);
+    g.key1 = static_cast<uint32_t>(seed >> 32);
+    g.h_obs = static_cast<float>(c->h_obs);
+    g.n = total;
+    g.x0 = out->x0; g.y0 = out->y0; g.z0 = out->z0; g.t0 = out->t0;
+    g.len = out->len; g.ekin = out->ekin;
+    g.ux = out->ux; g.uy = out->uy; g.uz = out->uz;
+    g.dirs_fp32 = prec == CHER_FP32_BULK;
+    g.shower = out->shower;
+    if (cher::generate_steps(g, c->num_sms, stream) != cudaSuccess) return CHER_ECUDA;
+    return CHER_OK;
+}
+
 cher_status cher_destroy(cher_ctx *c) {
     if (!c) return CHER_OK;
     free_tables(c);
     free_adjoint_scratch(c);
     free_transmission(c);
+    cudaFree(c->d_gen);
     cudaFree(c->d_scratch);
     delete c;
     return CHER_OK;
@@ -703,20 +830,6 @@ cher_status cher_autotune(cher_ctx *c, const cher_tracks *t, uint64_t seed, cher
 // ---------------------------------------------------------------------------
 namespace {
 
-template <class T>
-cher_status grow(T **ptr, int64_t &cap, int64_t need) {
-    if (need <= cap && *ptr) return CHER_OK;
-    cudaFree(*ptr);
-    *ptr = nullptr;
-    cap = 0;
-    if (cudaMalloc(reinterpret_cast<void **>(ptr), std::max<int64_t>(need, 1) * sizeof(T)) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return CHER_ENOMEM;
-    }
-    cap = need;
-    return CHER_OK;
-}
 
 cher_status readout(cher_ctx *c, const cher_tracks *t, uint64_t seed, cher_precision prec,
                     double sigma, const int32_t *nb_frozen, double *D, double *Tbar,

@@ -185,6 +185,30 @@ inline int kernel_mode(int mode, const KParams &p) {
 
 // Launchers (cher_kernels.cu).  fp32 selects CHER_FP32_BULK.
 size_t kernel_smem_bytes(bool fp32, int block, const KParams &p);
+// Device step generator (cher_generator.cu): per-shower constants in float.
+struct GenShower {
+    float ax, ay, az;            // axis (downward)
+    float b1x, b1y, b1z, b2x, b2y, b2z;   // transverse basis
+    float cz, x0cz;              // cos zenith, X0 cos zenith (g/cm^2)
+    float core_x, core_y, s_ref, dt;      // s_ref: m; dt: CDF node spacing
+};
+struct GenParams {
+    const GenShower *showers;
+    const int64_t *first;        // [n_showers + 1] first global step of each shower
+    int32_t n_showers, n_cdf;
+    const float *cdf;            // [n_showers][n_cdf]
+    uint32_t key0, key1;
+    float h_obs;
+    int64_t n;
+    double *x0, *y0, *z0, *t0, *len, *ekin;
+    void *ux, *uy, *uz;
+    bool dirs_fp32;
+    uint32_t *shower;
+};
+cudaError_t generate_steps(const GenParams &g, int num_sms, void *stream);
+// The Greisen profile's CDF on n_cdf uniform nodes of [0, t_g] (host, FP64).
+void greisen_cdf_host(double y, double t_g, int n_cdf, std::vector<double> &cdf);
+
 // The FP32 path's double -> float rounding over an array (grid-stride).
 cudaError_t round_to_float(const double *in, float *out, int64_t n, int num_sms, void *stream);
 cudaError_t kernel_prepare(bool fp32, int block, int mode, size_t smem);

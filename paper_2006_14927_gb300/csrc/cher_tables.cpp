@@ -434,4 +434,29 @@ cher_status build_grid(const cher_telescope *tel, int32_t n_tel, double theta_ma
     return CHER_ERANGE;
 }
 
+// Greisen profile of a shower of y = ln(E0 / E_c), up to a constant factor,
+// and its CDF on n_cdf uniform nodes of [0, t_g], normalised to 1 (the
+// device step generator inverts it); Gauss-Legendre on each node interval.
+namespace {
+double greisen(double t, double y) {
+    if (t <= 0.0) return 1.0;
+    const double s = 3.0 * t / (t + 2.0 * y);
+    return std::exp(t * (1.0 - 1.5 * std::log(s)));
+}
+}  // namespace
+
+void greisen_cdf_host(double y, double t_g, int n_cdf, std::vector<double> &cdf) {
+    static const GaussLegendre gl;
+    cdf.assign(n_cdf, 0.0);
+    const double dt = t_g / (n_cdf - 1);
+    for (int k = 1; k < n_cdf; ++k) {
+        const double half = 0.5 * dt, mid = (k - 1) * dt + half;
+        double sum = 0.0;
+        for (int q = 0; q < GaussLegendre::N; ++q) sum += gl.w[q] * greisen(mid + half * gl.x[q], y);
+        cdf[k] = cdf[k - 1] + half * sum;
+    }
+    const double tot = cdf[n_cdf - 1];
+    for (double &v : cdf) v /= tot;
+}
+
 }  // namespace cher
