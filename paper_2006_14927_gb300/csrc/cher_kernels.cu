@@ -420,7 +420,9 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
     const R se2 = px * px + py * py;
     const R q = se2 * rat * rat;                    // sin^2(theta_obs)
     if (!(q <= c.q_max)) { o.status = ST_ANGLE; return; }
-    const R co = sqrt(R(1) - q);
+    const R omq = R(1) - q;
+    const R sec = rsqrt(omq);              // 1 / cos(theta_obs)
+    const R co = omq * sec;
     // one cell of the (height, sin^2) tables serves both corrections
     const R fj = dH * c.inv_dht;
     int jj = static_cast<int>(fj);
@@ -451,15 +453,11 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
             Al = l0 + b * (l1 - l0);
         }
     }
-    const R sec = R(1) / co;
     const R sec2 = sec * sec;
-    R hx = R(0), hy = R(0), so = R(0);
-    if (se2 > R(0)) {
-        const R rse = R(1) / sqrt(se2);
-        hx = px * rse;
-        hy = py * rse;
-        so = se2 * rse * rat;
-    }
+    // horizontal unit vector and sin(theta_obs); a vertical photon (se2 = 0)
+    // gets hx = hy = so = 0 through the clamp
+    const R rse = rsqrt(se2 > R(1e-30) ? se2 : R(1e-30));
+    const R hx = px * rse, hy = py * rse, so = se2 * rse * rat;
     const R tn = so * sec;
     const R D = tn * (dH + Ax * sec2);              // horizontal offset
     const R Lp = sec * (dH + Al * sec2);            // optical path
@@ -680,7 +678,8 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
 
     // Persistent CTAs claim their next tile one tile ahead, during the scan
     // (its barriers publish the claim), and prefetch that tile's step
-    // arrays into L2 while they work through the current tile's bunches.
+    // arrays into L2 while they work through the current tile's bunches; one
+    // barrier per tile separates its bunch loop from the next phase A.
     int64_t tile = blockIdx.x;
     if (p.tile_counter) {
         __syncthreads();
@@ -905,6 +904,9 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             }
         }
         if (!p.tile_counter) break;
+        // every warp is done with this tile's step constants and offsets
+        // before the next tile's phase A and scan overwrite them
+        __syncthreads();
         tile = next;
     }
 
