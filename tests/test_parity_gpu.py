@@ -103,6 +103,26 @@ def test_launch_shapes_agree():
             assert np.array_equal(rec[k], ref[0][k]), k
 
 
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_many_tiles_per_persistent_cta(prec):
+    """A persistent launch where every CTA works through ~10 tiles (shared
+    memory reused tile after tile) gives exactly the records of one CTA per
+    tile, where nothing is reused."""
+    sc = _reduced(workloads.vertical_1tev(n=200_003), 200_003)
+    ctx = context(sc)
+    tr = host_tracks(sc, prec)
+    recs = []
+    for launch in [(128, 0), (128, 1), (256, 1)]:
+        code, stats, out = gpu_hits(ctx, tr, sc["t_ref"], SEED, prec, 400_000, launch=launch)
+        assert code == 0
+        recs.append((out.records(), stats))
+    for rec, stats in recs[1:]:
+        assert np.array_equal(stats, recs[0][1])
+        for k in rec:
+            assert np.array_equal(rec[k], recs[0][0][k]), k
+    ctx.close()
+
+
 def test_track_base_splits_reproduce():
     """Two calls over halves with track_base give the records of one call."""
     sc = _reduced(workloads.vertical_1tev(n=3_000), 3_000)
