@@ -70,10 +70,10 @@ FP32_LANES_PER_SM = 128
 FP64_FMA_PER_SM_CLK = 2         # GB300: 1/64 of the FP32 rate (ncu: 2 DFMA/cycle/SM)
 
 # DRAM bytes (read + write) of one FP32 launch, from one ncu capture (the
-# summary in profiles/k_gen_prop_vertical_1tev.md: 128.20 MB read, 24.43 MB
+# summary in profiles/k_gen_prop_vertical_1tev.md: 128.25 MB read, 24.35 MB
 # written, 512 threads x 2 CTAs per SM).  Reported only for that workload at
 # full size and only while the kernel sources hash to what was profiled.
-TRAFFIC = {"vertical_1tev": (152_637_440, "292352464eb63963")}
+TRAFFIC = {"vertical_1tev": (152_606_464, "a3cf0da2448c21c8")}
 KERNEL_SOURCES = ("cher_kernels.cu", "cher_device.cuh", "cher_internal.h")
 
 
@@ -350,6 +350,7 @@ def run_ours(args):
     # ---- end to end: host buffers through the C ABI ---------------------
     e2e = None
     e2e_gen = None
+    gen_leg = None
     if not args.no_e2e:
         prec = P.CHER_FP32_BULK
         host = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory()
@@ -432,6 +433,24 @@ def run_ours(args):
                 gd2h, gbunch = gen_step()
                 gb += gbunch
             tg = time.perf_counter() - g0
+            # the generator alone (CUDA events around the whole call, whose
+            # table upload blocks): 64 B of steps written per step
+            gms = []
+            for _ in range(steps):
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record()
+                ctx.generate_steps(showers, 11, prec)
+                b_.record()
+                torch.cuda.synchronize()
+                gms.append(a_.elapsed_time(b_))
+            g_ms = statistics.median(gms)
+            peaks_, _src = _peaks()
+            g_gbs = showers[0]["n"] * 64 / (g_ms / 1e3) / 1e9
+            gen_leg = {"ms_per_call": g_ms, "steps_per_s": showers[0]["n"] / (g_ms / 1e3),
+                       "roofline": {"bound": "hbm", "achieved": g_gbs,
+                                    "peak": float(peaks_.get("hbm_gbs", 6800.0)), "unit": "GB/s",
+                                    "frac": g_gbs / float(peaks_.get("hbm_gbs", 6800.0)),
+                                    "bytes_per_step": 64}}
             e2e_gen = {"value": gb / tg, "unit": UNIT,
                        "h2d_bytes_per_step": 64 + 16 + 4 * 1024 + 8,
                        "d2h_bytes_per_step": int(gd2h), "steps_generated": showers[0]["n"],
@@ -508,6 +527,7 @@ def run_ours(args):
     }
     if e2e_gen is not None:
         line["e2e_generated"] = e2e_gen
+        line["generator"] = gen_leg
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if args.workload == "vertical_1tev" and args.scale == 1.0 and world == 1:
@@ -517,6 +537,37 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_leg(args):
+    """One secondary leg alone: the step generator (2e6 steps of the 1 TeV
+    vertical shower) or the adjoint (300 GeV shower, both precisions)."""
+    import torch
+
+    import paper_2006_14927_gb300 as P
+    import workloads
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    if args.leg == "adjoint":
+        print(json.dumps({"leg": "adjoint", **adjoint_leg(dev, args.steps)}), flush=True)
+        return
+    sc = workloads.vertical_1tev(n=10)
+    ctx = P.Context(sc["atm"], sc["h_obs"], sc["telescopes"])
+    showers = [dict(e0_mev=1.0e6, zenith=0.0, azimuth=0.0, core_x=0.0, core_y=0.0, n=2_000_000)]
+    for _ in range(args.warmup):
+        ctx.generate_steps(showers, 11, P.CHER_FP32_BULK)
+    ms = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.generate_steps(showers, 11, P.CHER_FP32_BULK)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = statistics.median(ms)
+    print(json.dumps({"leg": "generator", "ms_per_call": t, "steps": showers[0]["n"],
+                      "GBps_written": showers[0]["n"] * 64 / (t / 1e3) / 1e9}), flush=True)
+    ctx.close()
 
 
 def graph_leg(ctx, r32, steps, flush, stream):
@@ -647,10 +698,14 @@ def main():
                              "adjoint_300gev"])
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the workload's steps")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--leg", choices=["all", "generator", "adjoint"], default="all",
+                    help="run one secondary leg alone (for profiling captures)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         run_reference(args)
+    elif args.leg != "all":
+        run_leg(args)
     else:
         run_ours(args)
 
