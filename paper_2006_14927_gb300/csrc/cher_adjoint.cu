@@ -328,8 +328,20 @@ __device__ bool bunch_dual(const AdjParams &A, int64_t i, int j, BunchDual<T> &o
     return true;
 }
 
+// Sums that many pairs add to the same few addresses (S_k, U_k per
+// telescope; the ten atmosphere gradients) are combined per CTA in shared
+// memory first, then added to global memory once per CTA: the pairs of a
+// shower crowd around a handful of telescopes.
+constexpr int kSmemTel = 512;     // telescopes whose S, U are combined in smem
+
 template <class T, int MODE>
 __global__ void __launch_bounds__(128) k_adj_pairs(const AdjParams A) {
+    __shared__ double s_sum[MODE == 0 ? 2 * kSmemTel : 10];
+    const int n_tel = A.k.n_tel;
+    const bool smem_su = MODE == 0 && n_tel <= kSmemTel;
+    const int n_red = MODE == 0 ? (smem_su ? 2 * n_tel : 0) : 10;
+    for (int q = threadIdx.x; q < n_red; q += blockDim.x) s_sum[q] = 0.0;
+    __syncthreads();
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < A.n_list;
          e += stride) {
@@ -357,8 +369,13 @@ __global__ void __launch_bounds__(128) k_adj_pairs(const AdjParams A) {
             if (!(r2 < A.rcut2)) continue;
             const double G = A.norm * exp(-r2 * A.inv_2s2);
             if constexpr (MODE == 0) {
-                atomicAdd(A.S + k, w * G);
-                atomicAdd(A.U + k, w * G * t);
+                if (smem_su) {
+                    atomicAdd(s_sum + k, w * G);
+                    atomicAdd(s_sum + n_tel + k, w * G * t);
+                } else {
+                    atomicAdd(A.S + k, w * G);
+                    atomicAdd(A.U + k, w * G * t);
+                }
             } else {
                 const double S = __ldg(A.S + k), U = __ldg(A.U + k);
                 double dLdS = __ldg(A.gD + k), dLdU = 0.0;
@@ -404,9 +421,18 @@ __global__ void __launch_bounds__(128) k_adj_pairs(const AdjParams A) {
                 }
                 const double gp = gl[C_ETA_M] * dm[q] + gl[C_ETA_E] * de[q] +
                                   gl[C_ETA_O] * dob[q] + gl[C_AX] * tab[0] + gl[C_AL] * tab[1];
-                atomicAdd(A.grad_atm + 5 + q, gp);   // b_i at 5 + i, c_i at 10 + i
+                atomicAdd(s_sum + q, gp);            // b_i at 5 + i, c_i at 10 + i
             }
         }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < n_red; q += blockDim.x) {
+        const double v = s_sum[q];
+        if (v == 0.0) continue;
+        if constexpr (MODE == 0)
+            atomicAdd(q < n_tel ? A.S + q : A.U + (q - n_tel), v);
+        else
+            atomicAdd(A.grad_atm + 5 + q, v);
     }
 }
 

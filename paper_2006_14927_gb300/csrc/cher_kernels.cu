@@ -341,14 +341,6 @@ struct Consts {
     int H, Z, n_fine;
 };
 
-// the candidate grids as the kernel reads them (shared or global memory)
-struct GridView {
-    const int32_t *cell_start;
-    const int32_t *cand_tel;
-    const float4 *cand;
-    int nx, ny;
-};
-
 template <class R>
 __device__ __forceinline__ R eta_at(const KParams &p, const Consts<R> &c, const R *eta_s, R h) {
     R x = h * c.inv_dh;
@@ -490,7 +482,7 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
 // entry s0 + m of grid g (chosen by the arrival zenith).
 template <class R>
 __device__ __forceinline__ unsigned sphere_hits(const KParams &p, const Consts<R> &c,
-                                                const GridView *gv, const BunchOut<R> &o, int &s0,
+                                                const BunchOut<R> &o, int &s0,
                                                 int &g) {
     s0 = 0;
     g = 0;
@@ -499,16 +491,16 @@ __device__ __forceinline__ unsigned sphere_hits(const KParams &p, const Consts<R
     // (selects, not indexing: the small arrays stay in registers)
     const R gx = (o.X - (g ? c.gx0[1] : c.gx0[0])) * (g ? c.inv_gcs[1] : c.inv_gcs[0]);
     const R gy = (o.Y - (g ? c.gy0[1] : c.gy0[0])) * (g ? c.inv_gcs[1] : c.inv_gcs[0]);
-    const int nx = g ? gv[1].nx : gv[0].nx;
-    const int ny = g ? gv[1].ny : gv[0].ny;
+    const int nx = g ? p.grid[1].nx : p.grid[0].nx;
+    const int ny = g ? p.grid[1].ny : p.grid[0].ny;
     if (!(gx >= R(0)) || !(gy >= R(0)) || !(gx < static_cast<R>(nx)) ||
         !(gy < static_cast<R>(ny)))
         return 0u;
     const int cell = static_cast<int>(gy) * nx + static_cast<int>(gx);
     unsigned mask = 0u;
     if constexpr (std::is_same<R, float>::value) {
-        const int32_t *cs = g ? gv[1].cell_start : gv[0].cell_start;
-        const float4 *cd = g ? gv[1].cand : gv[0].cand;
+        const int32_t *cs = g ? p.grid[1].cell_start : p.grid[0].cell_start;
+        const float4 *cd = static_cast<const float4 *>(g ? p.grid[1].cand32 : p.grid[0].cand32);
         s0 = __ldg(cs + cell);
         const int s1 = __ldg(cs + cell + 1);
         for (int m = s0; m < s1; ++m) {
@@ -538,12 +530,11 @@ __device__ __forceinline__ unsigned sphere_hits(const KParams &p, const Consts<R
 
 // telescope index and centre of entry m of grid g
 template <class R>
-__device__ __forceinline__ int cand_info(const KParams &p, const GridView *gv, int g, int m, R &tx,
-                                         R &ty, R &tz) {
+__device__ __forceinline__ int cand_info(const KParams &p, int g, int m, R &tx, R &ty, R &tz) {
     if constexpr (std::is_same<R, float>::value) {
-        const float4 T = __ldg((g ? gv[1].cand : gv[0].cand) + m);
+        const float4 T = __ldg(static_cast<const float4 *>(g ? p.grid[1].cand32 : p.grid[0].cand32) + m);
         tx = T.x; ty = T.y; tz = T.z;
-        return __ldg((g ? gv[1].cand_tel : gv[0].cand_tel) + m);
+        return __ldg((g ? p.grid[1].cand_tel : p.grid[0].cand_tel) + m);
     } else {
         const double2 *T = static_cast<const double2 *>(g ? p.grid[1].cand64 : p.grid[0].cand64);
         const double2 A = __ldg(T + 2 * m), B = __ldg(T + 2 * m + 1);
@@ -617,16 +608,9 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
     }
     __syncthreads();          // the staged table is read from phase A on
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // candidate grids, read through L1 (a few KB)
-    GridView gv[2];
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-        gv[g].cell_start = p.grid[g].cell_start;
-        gv[g].cand_tel = p.grid[g].cand_tel;
-        gv[g].cand = static_cast<const float4 *>(p.grid[g].cand32);
-        gv[g].nx = p.grid[g].nx;
-        gv[g].ny = p.grid[g].ny;
-    }
+    // the candidate grids (a few KB) are read through L1; their sizes and
+    // pointers come straight from the kernel parameters (selects, nothing
+    // held in registers across the bunch loop)
 
     Consts<R> c;
     R np1o;
@@ -843,7 +827,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                 continue;
             }
             int s0 = 0, gsel = 0;
-            unsigned hm = live ? sphere_hits<R>(p, c, gv, o, s0, gsel) : 0u;
+            unsigned hm = live ? sphere_hits<R>(p, c, o, s0, gsel) : 0u;
             if constexpr (MODE == MODE_TRACE) {
                 st_hits += __popc(hm);
                 if (live) {
@@ -861,7 +845,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                     int first = -1;
                     for (unsigned mm = hm; mm; mm &= mm - 1u) {      // lowest telescope index
                         R tx, ty, tz;
-                        const int k = cand_info<R>(p, gv, gsel, s0 + __ffs(mm) - 1, tx, ty, tz);
+                        const int k = cand_info<R>(p, gsel, s0 + __ffs(mm) - 1, tx, ty, tz);
                         first = (first < 0 || k < first) ? k : first;
                     }
                     p.t_first[gb] = first;
@@ -878,7 +862,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                     if (hm) {
                         const int bit = __ffs(hm) - 1;
                         hm &= hm - 1u;
-                        tel = cand_info<R>(p, gv, gsel, s0 + bit, tx, ty, tz);
+                        tel = cand_info<R>(p, gsel, s0 + bit, tx, ty, tz);
                         ++st_hits;
                     }
                     const unsigned grp = __match_any_sync(kFull, tel);
