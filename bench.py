@@ -370,10 +370,32 @@ def run_ours(args):
         h_key = torch.empty((n_tel, cap), dtype=torch.int64).pin_memory()
         h2d = sum(v.numel() * v.element_size() for v in host.values())
 
+        # two device input sets: the next step's inputs upload on a copy
+        # stream while this step's kernel runs (every step still copies its
+        # whole input up and its records back inside the timed region)
+        sets = [dtr, {k: torch.empty_like(v) for k, v in dtr.items()}]
+        sets[1]["t_ref"].copy_(dtr["t_ref"])
+        copy_stream = torch.cuda.Stream(device=dev)
+        comp = torch.cuda.current_stream()
+        ev_copied = [torch.cuda.Event(), torch.cuda.Event()]
+        ev_read = [torch.cuda.Event(), torch.cuda.Event()]
+
+        def upload(b):
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(ev_read[b])     # the last kernel on set b is done
+                for k, v in host.items():
+                    sets[b][k].copy_(v, non_blocking=True)
+                ev_copied[b].record(copy_stream)
+
+        step_no = [0]
+
         def e2e_step():
-            for k, v in host.items():
-                dtr[k].copy_(v, non_blocking=True)
-            ctx.generate_propagate(dtr, 11, prec, out, track_base=track_base)
+            b = step_no[0] % 2
+            step_no[0] += 1
+            upload(1 - b)                               # the next step's inputs
+            comp.wait_event(ev_copied[b])
+            ctx.generate_propagate(sets[b], 11, prec, out, track_base=track_base)
+            ev_read[b].record(comp)
             h_cnt.copy_(out.count, non_blocking=True)
             h_st.copy_(out.stats, non_blocking=True)
             torch.cuda.current_stream().synchronize()
@@ -388,18 +410,22 @@ def run_ours(args):
             torch.cuda.current_stream().synchronize()
             return d2h
 
+        upload(0)
         for _ in range(max(1, warmup // 2)):
             e2e_step()
+        copy_stream.synchronize()
         barrier()
         e0 = time.perf_counter()
         d2h = 0
         for _ in range(steps):
             d2h = e2e_step()
+        copy_stream.synchronize()           # the prefetch of the step after the last
         barrier()
         te = time.perf_counter() - e0
         te, _ = reduce_over_ranks(te, 0.0, world, dev)
         e2e = {"value": b32 / len(r32["ms"]) * steps / te, "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "pipelined": "next step's inputs copied up during this step's kernel"}
 
         # end to end from shower parameters: the steps come from the device
         # generator (same shower, same step count), only the parameters and
