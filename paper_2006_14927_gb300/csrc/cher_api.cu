@@ -192,7 +192,6 @@ cher::KParams base_params(const cher_ctx *c, const cher_tracks *t, uint64_t seed
     p.inv_dh = c->T.inv_dh;
     p.eta64 = c->d_eta64;
     p.eta32 = c->d_eta32;
-    p.eta_in_smem = (fp32 && c->T.n_fine <= 16384) ? 1 : 0;
     p.eta_slope = c->eta_slope;
     p.h_obs = c->h_obs;
     p.eta_obs = c->eta_obs;

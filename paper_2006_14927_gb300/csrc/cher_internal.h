@@ -76,7 +76,6 @@ struct KParams {
     double h_max, inv_dh;
     const double *eta64;
     const float *eta32;
-    int32_t eta_in_smem;
     double eta_slope;                     // max |eta[k+1] - eta[k]| / dh
     // observation level
     double h_obs, eta_obs;

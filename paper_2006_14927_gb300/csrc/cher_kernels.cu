@@ -71,7 +71,7 @@ __device__ __forceinline__ bool d_not_positive(double v) {
 
 __device__ __forceinline__ void step_yield_screened(const KParams &p, bool others_valid,
                                                     double z0, double len, double ekin, float uz,
-                                                    const float *eta_s, YieldF &y) {
+                                                    YieldF &y) {
     y.nb = 0;
     y.valid = false;
     y.g = y.eta = y.s2 = y.N = 0.0f;
@@ -90,8 +90,7 @@ __device__ __forceinline__ void step_yield_screened(const KParams &p, bool other
     int k = static_cast<int>(x);
     k = k > p.n_fine - 2 ? p.n_fine - 2 : k;
     const float f = x - static_cast<float>(k);
-    const float t0 = eta_s ? eta_s[k] : __ldg(p.eta32 + k);
-    const float t1 = eta_s ? eta_s[k + 1] : __ldg(p.eta32 + k + 1);
+    const float t0 = __ldg(p.eta32 + k), t1 = __ldg(p.eta32 + k + 1);
     const float eta = t0 + f * (t1 - t0);
     const float np1 = 1.0f + eta, np1sq = np1 * np1;
     const float a = eta * (2.0f + eta);
@@ -342,7 +341,7 @@ struct Consts {
 };
 
 template <class R>
-__device__ __forceinline__ R eta_at(const KParams &p, const Consts<R> &c, const R *eta_s, R h) {
+__device__ __forceinline__ R eta_at(const KParams &p, const Consts<R> &c, R h) {
     R x = h * c.inv_dh;
     x = x < R(0) ? R(0) : x;
     int k = static_cast<int>(x);
@@ -350,13 +349,8 @@ __device__ __forceinline__ R eta_at(const KParams &p, const Consts<R> &c, const 
     const R f = x - static_cast<R>(k);
     R t0, t1;
     if constexpr (std::is_same<R, float>::value) {
-        if (eta_s) {
-            t0 = eta_s[k];
-            t1 = eta_s[k + 1];
-        } else {
-            t0 = __ldg(p.eta32 + k);
-            t1 = __ldg(p.eta32 + k + 1);
-        }
+        t0 = __ldg(p.eta32 + k);
+        t1 = __ldg(p.eta32 + k + 1);
     } else {
         t0 = __ldg(p.eta64 + k);
         t1 = __ldg(p.eta64 + k + 1);
@@ -365,7 +359,7 @@ __device__ __forceinline__ R eta_at(const KParams &p, const Consts<R> &c, const 
 }
 
 template <class R, bool TR>
-__device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, const R *eta_s,
+__device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c,
                                       const Seg<R> &S, int64_t gi, int j, BunchOut<R> &o) {
     const uint4 x = philox4x32_10(
         make_uint4(static_cast<uint32_t>(gi), static_cast<uint32_t>(static_cast<uint64_t>(gi) >> 32),
@@ -407,7 +401,7 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
     if (!(dH >= R(0))) { o.status = ST_BELOW; return; }
     if (!(dH <= c.dH_max)) { o.status = ST_ABOVE; return; }
     // Snell: sin_obs = sin_em (1 + eta_e) / (1 + eta_o)
-    const R eta_e = eta_at<R>(p, c, eta_s, o.he);
+    const R eta_e = eta_at<R>(p, c, o.he);
     const R rat = R(1) + (eta_e - c.eta_o) * c.inv_np1o;
     const R se2 = px * px + py * py;
     const R q = se2 * rat * rat;                    // sin^2(theta_obs)
@@ -599,14 +593,6 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
     int *off = reinterpret_cast<int *>(seg + BLOCK);          // BLOCK + 1
     int *wsum = off + BLOCK + 1;                                // BLOCK / 32
     __shared__ unsigned long long s_tile;
-    R *eta_s = nullptr;
-    if constexpr (std::is_same<R, float>::value) {
-        if (p.eta_in_smem) {
-            eta_s = reinterpret_cast<R *>(wsum + 32);
-            for (int k = threadIdx.x; k < p.n_fine; k += BLOCK) eta_s[k] = __ldg(p.eta32 + k);
-        }
-    }
-    __syncthreads();          // the staged table is read from phase A on
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // the candidate grids (a few KB) are read through L1; their sizes and
     // pointers come straight from the kernel parameters (selects, nothing
@@ -685,7 +671,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             YT y;
             if constexpr (std::is_same<YT, YieldF>::value)
                 step_yield_screened(p, step_valid<R>(p, i), __ldg(p.z0 + i), __ldg(p.len + i),
-                                    __ldg(p.ekin + i), load_dir<float>(p.uz, i), eta_s, y);
+                                    __ldg(p.ekin + i), load_dir<float>(p.uz, i), y);
             else
                 step_yield(p, step_valid<R>(p, i), __ldg(p.z0 + i), __ldg(p.len + i),
                            __ldg(p.ekin + i), static_cast<double>(load_dir<R>(p.uz, i)), y);
@@ -797,7 +783,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             int j = 0;
             if (live) {
                 j = bidx - off[s];
-                bunch<R, TR>(p, c, eta_s, seg[s], p.track_base + base + s, j, o);
+                bunch<R, TR>(p, c, seg[s], p.track_base + base + s, j, o);
                 if (o.status != ST_GROUND) {       // rare: the drops
                     st_up += o.status == ST_UPWARD;
                     st_below += o.status == ST_BELOW;
@@ -921,7 +907,6 @@ template <class R, int BLOCK>
 size_t smem_bytes(const KParams &p) {
     size_t b = sizeof(Seg<R>) * BLOCK + sizeof(int) * (BLOCK + 1 + 32);
     b = (b + 15) & ~size_t(15);
-    if (std::is_same<R, float>::value && p.eta_in_smem) b += sizeof(float) * p.n_fine;
     return b;
 }
 
