@@ -41,8 +41,8 @@ struct cher_ctx {
     // scratch: the persistent kernel's tile counter
     unsigned long long *d_scratch = nullptr;
     // launch shape
-    int block = 256;
-    int ctas_per_sm = 3;
+    int block = 128;                      // the autotuner's choice on GB300 for the
+    int ctas_per_sm = 8;                  // FP32 path (32 resident warps per SM)
     // table sizes of the last build (cher_set_atmosphere rebuilds with them)
     int32_t tab_H = 0, tab_Z = 0;
     double tab_zen = 0, tab_hmax = 0;
