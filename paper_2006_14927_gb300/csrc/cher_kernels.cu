@@ -487,10 +487,14 @@ __device__ __forceinline__ unsigned sphere_hits(const KParams &p, const Consts<R
     const R gy = (o.Y - (g ? c.gy0[1] : c.gy0[0])) * (g ? c.inv_gcs[1] : c.inv_gcs[0]);
     const int nx = g ? p.grid[1].nx : p.grid[0].nx;
     const int ny = g ? p.grid[1].ny : p.grid[0].ny;
-    if (!(gx >= R(0)) || !(gy >= R(0)) || !(gx < static_cast<R>(nx)) ||
-        !(gy < static_cast<R>(ny)))
+    // range check on the truncated indices (unsigned: negatives fail); a
+    // point just below a grid edge truncates into the first row or column,
+    // whose candidates it cannot hit: the grid covers every telescope's reach
+    const int ix = static_cast<int>(gx), iy = static_cast<int>(gy);
+    if (static_cast<unsigned>(ix) >= static_cast<unsigned>(nx) ||
+        static_cast<unsigned>(iy) >= static_cast<unsigned>(ny))
         return 0u;
-    const int cell = static_cast<int>(gy) * nx + static_cast<int>(gx);
+    const int cell = iy * nx + ix;
     unsigned mask = 0u;
     if constexpr (std::is_same<R, float>::value) {
         const int32_t *cs = g ? p.grid[1].cell_start : p.grid[0].cell_start;
