@@ -12,6 +12,7 @@ source.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from dataclasses import dataclass, field
@@ -67,7 +68,7 @@ class _Cfg(ctypes.Structure):
                 ("trans_nl", ctypes.c_int), ("trans_nh", ctypes.c_int),
                 ("trans_l0", ctypes.c_double), ("trans_l1", ctypes.c_double),
                 ("trans_h0", ctypes.c_double), ("trans_h1", ctypes.c_double),
-                ("trans_tau", _dp)]
+                ("trans_tau", _dp), ("fb_sin2_max", ctypes.c_double)]
 
 
 class _Tracks(ctypes.Structure):
@@ -278,6 +279,9 @@ class Model:
     # atmospheric transmission: dict(tau=(n_lambda, n_height) vertical optical
     # depths, lambda_nm=(first, last node), height_m=(first, last node)) or None
     transmission: dict | None = None
+    # beyond-table fallback: bunches up to this observation-level zenith
+    # (deg) past the tables' range take the ray integrals (0: off)
+    fallback_deg: float = 0.0
     table_tol: float = 1e-13
     bf_tol: float = 1e-12
     eta_tab: np.ndarray = field(init=False, repr=False)
@@ -317,6 +321,9 @@ class Model:
             C.t_ref = None
             C.n_showers = 0
         C.bf_tol = self.bf_tol
+        if self.fallback_deg > 0.0:
+            sf = math.sin(self.fallback_deg * 3.14159265358979323846 / 180.0)
+            C.fb_sin2_max = sf * sf
         if self.transmission is not None:
             tr = self.transmission
             self._tau = _f64(np.asarray(tr["tau"], float))

@@ -111,6 +111,10 @@ typedef struct {
     int trans_nl, trans_nh;
     double trans_l0, trans_l1, trans_h0, trans_h1;
     const double *trans_tau;
+    /* beyond-table fallback (0: off): bunches whose observation-level      */
+    /* sin^2(zenith) exceeds the tables' range but not fb_sin2_max are      */
+    /* propagated by the ray integrals themselves (variant (B))            */
+    double fb_sin2_max;
 } orc_cfg;
 
 typedef struct {
@@ -527,7 +531,14 @@ int orc_propagate_photon(const orc_cfg *C, int variant, double xe, double ye,
     double q = sin_obs * sin_obs;
     double smax = sin(C->theta_max);
     double q_max = smax * smax;
-    if (q > q_max) return ORC_ST_ANGLE;
+    /* the paper's rare-case fallback (section 3.3.1: the few photons that do
+     * not fit the vectorised path take the scalar code): beyond the tables'
+     * zenith range, up to fb_sin2_max, the ray integrals themselves */
+    int fallback = 0;
+    if (q > q_max) {
+        if (!(C->fb_sin2_max > 0.0) || !(q <= C->fb_sin2_max)) return ORC_ST_ANGLE;
+        fallback = 1;
+    }
     double cos_obs = sqrt(1.0 - q);
     double dH = he - C->h_obs;
 
@@ -535,7 +546,7 @@ int orc_propagate_photon(const orc_cfg *C, int variant, double xe, double ye,
     if (sin_em > 0.0) { hx = px / sin_em; hy = py / sin_em; }
 
     double D, L;                      /* horizontal offset, optical path  */
-    if (variant == 0) {
+    if (variant == 0 && !fallback) {
         double dht = (C->h_max - C->h_obs) / (double)(C->H - 1);
         double dq = q_max / (double)(C->Z - 1);
         double fj = dH / dht;
