@@ -577,6 +577,9 @@ def run_leg(args):
     if args.leg == "adjoint":
         print(json.dumps({"leg": "adjoint", **adjoint_leg(dev, args.steps)}), flush=True)
         return
+    if args.leg == "fallback":
+        print(json.dumps({"leg": "fallback", **fallback_leg(dev, args)}), flush=True)
+        return
     sc = workloads.vertical_1tev(n=10)
     ctx = P.Context(sc["atm"], sc["h_obs"], sc["telescopes"])
     showers = [dict(e0_mev=1.0e6, zenith=0.0, azimuth=0.0, core_x=0.0, core_y=0.0, n=2_000_000)]
@@ -594,6 +597,43 @@ def run_leg(args):
     print(json.dumps({"leg": "generator", "ms_per_call": t, "steps": showers[0]["n"],
                       "GBps_written": showers[0]["n"] * 64 / (t / 1e3) / 1e9}), flush=True)
     ctx.close()
+
+
+def fallback_leg(dev, args):
+    """The beyond-table fallback on the 60-degree shower (2e6 steps, FP32):
+    refraction tables to 61 deg with the fallback up to 80 deg (about 9 % of
+    the bunches arrive past the tables and take the ray integrals), against
+    tables to 75 deg that cover every bunch."""
+    import torch
+
+    import paper_2006_14927_gb300 as P
+    import workloads
+    sc = workloads.inclined_20tev(n=2_000_000)
+    dtr = P.device_tracks(sc["tracks"], P.CHER_FP32_BULK, device=dev, t_ref=sc["t_ref"])
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    res = {}
+    for name, theta, fb in (("tables_75deg", 75.0, 0.0), ("tables_61deg_fallback_80deg", 61.0, 80.0)):
+        ctx = P.Context(sc["atm"], sc["h_obs"], sc["telescopes"])
+        ctx.build_refraction_tables(1000, 64, theta, sc["h_max"])
+        ctx.set_fallback(fb)
+        out = ctx.alloc_hits(2_000_000, P.CHER_FP32_BULK, device=dev)
+        for _ in range(args.warmup):
+            ctx.generate_propagate(dtr, 11, P.CHER_FP32_BULK, out)
+        ms = []
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.generate_propagate(dtr, 11, P.CHER_FP32_BULK, out)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        code, st = ctx.sync_status(out)
+        res[name] = {"ms_per_step": statistics.median(ms), "bunches": int(st[3]),
+                     "fallback_bunches": int(st[12]), "angle_drops": int(st[7]),
+                     "hits": int(st[9])}
+        ctx.close()
+    return res
 
 
 def graph_leg(ctx, r32, steps, flush, stream):
@@ -724,7 +764,7 @@ def main():
                              "adjoint_300gev"])
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the workload's steps")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
-    ap.add_argument("--leg", choices=["all", "generator", "adjoint"], default="all",
+    ap.add_argument("--leg", choices=["all", "generator", "adjoint", "fallback"], default="all",
                     help="run one secondary leg alone (for profiling captures)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

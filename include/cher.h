@@ -161,7 +161,10 @@ enum {
     CHER_STAT_GROUND = 8,       /* reached the observation level            */
     CHER_STAT_HITS = 9,         /* (bunch, telescope) crossings found       */
     CHER_STAT_OVERFLOW = 10,    /* crossings not stored (buffer full)       */
-    CHER_STAT_ABSORBED = 11     /* reached h_obs, lost to the transmission  */
+    CHER_STAT_ABSORBED = 11,    /* reached h_obs, lost to the transmission  */
+    CHER_STAT_FALLBACK = 12,    /* propagated by the beyond-table fallback  */
+    CHER_STAT_FB_LOST = 13      /* past the tables' range, the fallback     */
+                                /* queue full: not propagated              */
 };
 
 /* Per-telescope output buffers (device).  Telescope k owns records
@@ -404,6 +407,23 @@ typedef struct cher_transmission {
 } cher_transmission;
 
 cher_status cher_set_transmission(cher_ctx *ctx, const cher_transmission *table);
+
+/* Beyond-table fallback (the paper's rare-case scalar path, section 3.3.1:
+ * the few photons that do not fit the vectorised code take the scalar
+ * one).  Bunches whose observation-level zenith lies past the refraction
+ * tables' range but within `zenith_max_deg` are propagated by the ray
+ * integrals themselves -- n(h) sin(theta(h)) = n_obs sin(theta_obs) in the
+ * layered atmosphere, D = int tan(theta) dh, L = int n / cos(theta) dh,
+ * FP64, 12-point Gauss-Legendre on each layer's part -- instead of being
+ * dropped (stats[CHER_STAT_ANGLE]).  The generation launch queues them and
+ * a second kernel on the same stream propagates them (stats
+ * [CHER_STAT_FALLBACK]); the queue holds max(2^20, n steps) bunches per
+ * call, the rest counted in stats[CHER_STAT_FB_LOST].  Trace launches
+ * integrate them in place.  The adjoint and the allocation-free launch do
+ * not use it (those bunches stay dropped there).
+ *   zenith_max_deg: 0 (off) or in (the tables' zenith range, 85].
+ * Errors: CHER_EINVAL. */
+cher_status cher_set_fallback(cher_ctx *ctx, double zenith_max_deg);
 
 /* Replace the atmosphere and, if tables were built, rebuild them with the
  * same sizes (blocking).  Errors as cher_build_refraction_tables. */

@@ -20,7 +20,7 @@ CHER_FP64 = 0
 CHER_FP32_BULK = 1
 NSTATS = 16
 STAT_NAMES = ["steps", "emitting", "invalid", "bunches", "upward", "below_obs", "above_max",
-              "angle", "ground", "hits", "overflow", "absorbed"]
+              "angle", "ground", "hits", "overflow", "absorbed", "fallback", "fb_lost"]
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
                 4: "tables not built", 5: "out of range", 6: "overflow", 7: "timeout"}
 
@@ -109,6 +109,7 @@ SIGNATURES = {
                                         ctypes.POINTER(Output), ctypes.POINTER(Profile), _P]),
     "cher_round_to_float": (_S, [_P, _P, ctypes.c_int64, _P]),
     "cher_set_transmission": (_S, [_P, ctypes.POINTER(Transmission)]),
+    "cher_set_fallback": (_S, [_P, ctypes.c_double]),
     "cher_generate_steps": (_S, [_P, ctypes.POINTER(Shower), ctypes.c_int32, ctypes.c_uint64, _S,
                                  ctypes.POINTER(StepBuffers), _P]),
     "cher_generate_propagate_noalloc": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
@@ -458,6 +459,11 @@ class Context:
                                          ctypes.c_void_p(_stream_ptr(stream))),
                "cher_generate_steps")
         return out
+
+    def set_fallback(self, zenith_max_deg: float):
+        """Propagate bunches past the tables' zenith range, up to this
+        zenith, by the ray integrals (0: off)."""
+        _check(lib().cher_set_fallback(self._h, float(zenith_max_deg)), "cher_set_fallback")
 
     def set_transmission(self, table: dict | None):
         """Atmospheric transmission: dict(tau=(n_lambda, n_height) vertical

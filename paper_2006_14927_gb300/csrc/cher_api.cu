@@ -60,6 +60,11 @@ struct cher_ctx {
     float *d_trans32 = nullptr;
     int32_t trans_nl = 0, trans_nh = 0;
     double trans_l0 = 0, trans_l1 = 0, trans_h0 = 0, trans_h1 = 0;
+    // beyond-table fallback: zenith limit (deg, 0 off) and its queue
+    double fb_deg = 0.0;
+    void *d_fb = nullptr;
+    int64_t fb_cap = 0;                   // bytes
+    unsigned long long *d_fb_count = nullptr;
     // step generator: per-call shower constants, offsets and CDF tables;
     // host CDF rows cached by (E0, zenith) (cleared past 4096 entries)
     unsigned char *d_gen = nullptr;
@@ -226,6 +231,14 @@ cher::KParams base_params(const cher_ctx *c, const cher_tracks *t, uint64_t seed
         p.atm.c[l] = c->atm.c[l];
         p.atm.inv_c[l] = 1.0 / c->atm.c[l];
         p.atm.t_top[l] = c->atm.a[l] + c->atm.b[l] * std::exp(-(c->atm.h_bound[l + 1] / c->atm.c[l]));
+        // n - 1 = (n0 - 1) rho(h) / rho(0), rho = (b / c) exp(-h / c) in the layer
+        p.atm.eta_coef[l] = c->atm.n0_minus_1 * (c->atm.b[l] / c->atm.c[l]) /
+                            (c->atm.b[0] / c->atm.c[0]);
+    }
+    cher::gauss_legendre12(p.gl_x, p.gl_w);
+    if (c->fb_deg > c->tab_zen && c->built) {
+        const double sf = std::sin(c->fb_deg * 3.14159265358979323846 / 180.0);
+        p.fb_q = sf * sf;
     }
     if (c->d_trans64) {
         p.trans = fp32 ? static_cast<const void *>(c->d_trans32) : c->d_trans64;
@@ -594,6 +607,8 @@ cher_status cher_destroy(cher_ctx *c) {
     free_adjoint_scratch(c);
     free_transmission(c);
     cudaFree(c->d_gen);
+    cudaFree(c->d_fb);
+    cudaFree(c->d_fb_count);
     cudaFree(c->d_scratch);
     delete c;
     return CHER_OK;
@@ -653,6 +668,30 @@ cher_status cher_generate_propagate_ex(cher_ctx *c, const cher_tracks *t, uint64
     p.cap = out->cap_per_tel;
     p.count = out->count;
     p.stats = out->stats;
+    const bool fb = p.fb_q > 0.0;
+    if (fb) {
+        // the fallback queue: max(2^20, n) records, grown as needed
+        const size_t rec = cher::fallback_record_bytes(fp32);
+        const int64_t want = std::max<int64_t>(int64_t(1) << 20, t->n);
+        int64_t bytes_cap = c->fb_cap;
+        if (static_cast<int64_t>(want * rec) > bytes_cap) {
+            unsigned char *buf = static_cast<unsigned char *>(c->d_fb);
+            cher_status r = grow(&buf, bytes_cap, static_cast<int64_t>(want * rec));
+            c->d_fb = buf;
+            c->fb_cap = bytes_cap;
+            if (r != CHER_OK) return r;
+        }
+        if (!c->d_fb_count) {
+            int64_t one = 0;
+            cher_status r = grow(&c->d_fb_count, one, 1);
+            if (r != CHER_OK) return r;
+        }
+        if (cudaMemsetAsync(c->d_fb_count, 0, sizeof(unsigned long long), s) != cudaSuccess)
+            return CHER_ECUDA;
+        p.fb_list = c->d_fb;
+        p.fb_count = c->d_fb_count;
+        p.fb_cap = c->fb_cap / static_cast<int64_t>(rec);
+    }
     if (prof) {
         p.prof = prof->profile;
         p.prof_cos = prof->axis_cos;
@@ -662,7 +701,25 @@ cher_status cher_generate_propagate_ex(cher_ctx *c, const cher_tracks *t, uint64
         p.prof_inv_dx = 1.0 / prof->bin_gcm2;
         cher::fill_float_constants(p);
     }
-    return launch(c, p, fp32, cher::MODE_HITS, true, stream);
+    cher_status r = launch(c, p, fp32, cher::MODE_HITS, true, stream);
+    if (r != CHER_OK || !fb || p.n == 0) return r;
+    if (cher::launch_fallback(fp32, p.trans != nullptr, p, c->num_sms, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return CHER_ECUDA;
+    }
+    return CHER_OK;
+}
+
+cher_status cher_set_fallback(cher_ctx *c, double zenith_max_deg) {
+    if (!c || !std::isfinite(zenith_max_deg)) return CHER_EINVAL;
+    if (zenith_max_deg == 0.0) {
+        c->fb_deg = 0.0;
+        return CHER_OK;
+    }
+    if (!(zenith_max_deg > 0.0) || zenith_max_deg > 85.0) return CHER_EINVAL;
+    if (c->built && !(zenith_max_deg > c->tab_zen)) return CHER_EINVAL;
+    c->fb_deg = zenith_max_deg;
+    return CHER_OK;
 }
 
 cher_status cher_round_to_float(const double *in, float *out, int64_t n, void *stream) {
@@ -1140,6 +1197,8 @@ extern "C" cher_status cher_generate_propagate_noalloc(cher_ctx *c, const cher_t
             cudaSuccess)
         return CHER_ECUDA;
     cher::KParams p = base_params(c, t, seed, fp32);
+    p.fb_q = 0.0;                         // no fallback queue here (it needs scratch)
+    cher::fill_float_constants(p);
     p.pos = out->pos;
     p.tim = out->tim;
     p.key = out->key;

@@ -21,7 +21,8 @@ constexpr double kPi = 3.14159265358979323846;
 
 // Bunch status codes (the rare branches of the paper's Algorithm 1).
 enum : int32_t {
-    ST_GROUND = 0, ST_UPWARD = 1, ST_BELOW = 2, ST_ABOVE = 3, ST_ANGLE = 4, ST_ABSORBED = 5
+    ST_GROUND = 0, ST_UPWARD = 1, ST_BELOW = 2, ST_ABOVE = 3, ST_ANGLE = 4, ST_ABSORBED = 5,
+    ST_DEFER = 6    // internal: past the tables' zenith range, queued for the fallback pass
 };
 
 constexpr int kMaxCandPerCell = 32;   // telescope candidates in one grid cell
@@ -131,7 +132,17 @@ struct KParams {
     double prof_dx, prof_inv_dx;
     struct Layers {
         double hb[6], a[5], b[5], c[5], inv_c[5], t_top[5];
+        double eta_coef[5];      // n - 1 = eta_coef * exp(-h / c) in each layer
     } atm;
+    // beyond-table fallback (fb_q = 0: off): bunches with the tables'
+    // q_max < sin^2(zenith) <= fb_q are queued (fb_list, FbEntry records,
+    // fb_count appended atomically, fb_cap entries) and propagated by the
+    // ray integrals (12-point Gauss-Legendre per layer) in a second pass
+    double fb_q;
+    void *fb_list;
+    unsigned long long *fb_count;
+    int64_t fb_cap;
+    double gl_x[12], gl_w[12];
     // atmospheric transmission (NULL: off): vertical optical depth on a
     // uniform (lambda, h) grid, [nl][nh], float (FP32) or double (FP64);
     // index = (value - first node) * scale
@@ -148,6 +159,7 @@ struct KParams {
         float gx0[2], gy0[2], inv_gcs[2];
         float prof_dx, prof_inv_dx;
         float trans_l0, trans_lscale, trans_h0, trans_hscale;
+        float fb_q;
         float hb[6], a[5], b[5], c[5], inv_c[5], t_top[5];
     } f;
 };
@@ -176,11 +188,24 @@ cudaError_t adjoint_pairs(bool fp32, int mode, const AdjParams &A, void *stream)
 void fill_float_constants(KParams &p);
 
 enum Mode : int { MODE_HITS = 0, MODE_TRACE = 1, MODE_YIELD = 2, MODE_SCREEN = 3 };
-// added to a Mode when the launch applies the transmission draw
+// added to a Mode when the launch applies the transmission draw, and when
+// it queues (hits) or integrates in place (trace) the bunches past the
+// tables' zenith range
 constexpr int kTransBit = 4;
+constexpr int kFbBit = 8;
 inline int kernel_mode(int mode, const KParams &p) {
-    return (p.trans && mode != MODE_YIELD) ? (mode | kTransBit) : mode;
+    int m = mode;
+    if (p.trans && mode != MODE_YIELD) m |= kTransBit;
+    if (p.fb_q > 0.0 && (mode == MODE_HITS || mode == MODE_TRACE)) m |= kFbBit;
+    return m;
 }
+// The fallback pass over the queued bunches (after a MODE_HITS launch with
+// fb_q > 0, on the same stream; reads the queue's count on the device).
+cudaError_t launch_fallback(bool fp32, bool tr, const KParams &p, int num_sms, void *stream);
+// Bytes of one fallback queue record.
+size_t fallback_record_bytes(bool fp32);
+// The 12-point Gauss-Legendre rule on [-1, 1] (host).
+void gauss_legendre12(double *x, double *w);
 
 // Launchers (cher_kernels.cu).  fp32 selects CHER_FP32_BULK.
 size_t kernel_smem_bytes(bool fp32, int block, const KParams &p);

@@ -336,7 +336,7 @@ struct BunchOut {
 template <class R>
 struct Consts {
     R h_obs, dH_max, eta_o, inv_np1o, q_max, inv_dht, inv_dq, inv_dh, lam_inv1, lam_dinv;
-    R gx0[2], gy0[2], inv_gcs[2], q_band;
+    R gx0[2], gy0[2], inv_gcs[2], q_band, fb_q;
     int H, Z, n_fine;
 };
 
@@ -358,7 +358,103 @@ __device__ __forceinline__ R eta_at(const KParams &p, const Consts<R> &c, R h) {
     return t0 + f * (t1 - t0);
 }
 
-template <class R, bool TR>
+// the per-launch constants of the bunch loop in the path's precision
+template <class R>
+__device__ __forceinline__ void make_consts(const KParams &p, Consts<R> &c, R &np1o) {
+    if constexpr (std::is_same<R, float>::value) {
+        c.h_obs = p.f.h_obs;
+        c.dH_max = p.f.dH_max;
+        c.eta_o = p.f.eta_o;
+        c.inv_np1o = p.f.inv_np1o;
+        c.q_max = p.f.q_max;
+        c.inv_dht = p.f.inv_dht;
+        c.inv_dq = p.f.inv_dq;
+        c.inv_dh = p.f.inv_dh;
+        c.lam_inv1 = p.f.lam_inv1;
+        c.lam_dinv = p.f.lam_dinv;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            c.gx0[g] = p.f.gx0[g];
+            c.gy0[g] = p.f.gy0[g];
+            c.inv_gcs[g] = p.f.inv_gcs[g];
+        }
+        c.q_band = p.f.q_band;
+        c.fb_q = p.f.fb_q;
+        np1o = p.f.np1o;
+    } else {
+        c.h_obs = p.h_obs;
+        c.dH_max = p.h_max - p.h_obs;
+        c.eta_o = p.eta_obs;
+        c.inv_np1o = 1.0 / (1.0 + p.eta_obs);
+        c.q_max = p.q_max;
+        c.inv_dht = p.inv_dht;
+        c.inv_dq = p.inv_dq;
+        c.inv_dh = p.inv_dh;
+        c.lam_inv1 = p.lam_inv1;
+        c.lam_dinv = p.lam_dinv;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            c.gx0[g] = p.grid[g].x0;
+            c.gy0[g] = p.grid[g].y0;
+            c.inv_gcs[g] = p.grid[g].inv_cs;
+        }
+        c.q_band = p.q_band;
+        c.fb_q = p.fb_q;
+        np1o = 1.0 + p.eta_obs;
+    }
+    c.H = p.H;
+    c.Z = p.Z;
+    c.n_fine = p.n_fine;
+}
+
+// ------------------------------------------------------------------------
+// Beyond-table fallback (the paper's scalar path for the photons that do
+// not fit the vectorised one, section 3.3.1): the ray integrals
+//   D = int tan(theta(h)) dh,  L = int n(h) / cos(theta(h)) dh  over
+//   [h_obs, h_e], n(h) sin(theta(h)) = n_obs sin(theta_obs),
+// in FP64 with the exact layered n(h), 12-point Gauss-Legendre on each
+// layer's part of the interval (the integrands are smooth inside a layer).
+// ------------------------------------------------------------------------
+__device__ __forceinline__ double eta_layer(const KParams &p, double h) {
+    if (!(h < p.atm.hb[5])) return 0.0;
+    double e = p.atm.eta_coef[0], ic = p.atm.inv_c[0];
+#pragma unroll
+    for (int l = 1; l < 5; ++l)
+        if (h >= p.atm.hb[l]) { e = p.atm.eta_coef[l]; ic = p.atm.inv_c[l]; }
+    return e * exp(-(h * ic));
+}
+
+__device__ void ray_integrals(const KParams &p, double h_e, double s_obs, double &D, double &L) {
+    const double K = (1.0 + eta_layer(p, p.h_obs)) * s_obs;
+    D = 0.0;
+    L = 0.0;
+    double a = p.h_obs;
+    for (int l = 0; l < 5 && a < h_e; ++l) {
+        const double top = l < 4 ? p.atm.hb[l + 1] : h_e;
+        if (!(top > a)) continue;
+        const double b = top < h_e ? top : h_e;
+        const double half = 0.5 * (b - a), mid = 0.5 * (a + b);
+        for (int q = 0; q < 12; ++q) {
+            const double n = 1.0 + eta_layer(p, mid + half * p.gl_x[q]);
+            const double sn = K / n;
+            const double inv_c = rsqrt(1.0 - sn * sn);
+            D += p.gl_w[q] * half * sn * inv_c;
+            L += p.gl_w[q] * half * n * inv_c;
+        }
+        a = b;
+    }
+}
+
+// One queued bunch: its emission point and time, the horizontal direction
+// and sine of its observation-level zenith, wavelength, photons and key.
+template <class R>
+struct alignas(16) FbEntry {
+    R xe, ye, he, dh, te, hx, hy, s_obs, lam, w;   // dh = h_e - h_obs
+    uint64_t key;                                  // the record key (step << 32 | j)
+    uint32_t step_hi;                              // bits 32.. of the global step index
+};
+
+template <class R, bool TR, int FB>
 __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c,
                                       const Seg<R> &S, int64_t gi, int j, BunchOut<R> &o) {
     const uint4 x = philox4x32_10(
@@ -405,7 +501,53 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c,
     const R rat = R(1) + (eta_e - c.eta_o) * c.inv_np1o;
     const R se2 = px * px + py * py;
     const R q = se2 * rat * rat;                    // sin^2(theta_obs)
-    if (!(q <= c.q_max)) { o.status = ST_ANGLE; return; }
+    if (!(q <= c.q_max)) {
+        if constexpr (FB != 0) {
+            if (q <= c.fb_q) {
+                // past the tables' range: the ray integrals, queued (FB 1,
+                // the hits kernel) or in place (FB 2, the trace kernel);
+                // a queued bunch carries emission point, time, horizontal
+                // direction and sin(theta_obs) in X, Y, t, cx, cy, cz, and
+                // h_e - h_obs in he
+                const R rse = rsqrt(se2 > R(1e-30) ? se2 : R(1e-30));
+                const R hx = px * rse, hy = py * rse, s_obs = sqrt(q);
+                const R xe = S.x0 + fl * S.ux, ye = S.y0 + fl * S.uy;
+                const R te = S.tseg + fl * S.inv_bc;
+                if constexpr (FB == 1) {
+                    o.X = xe; o.Y = ye; o.t = te; o.cx = hx; o.cy = hy; o.cz = s_obs;
+                    o.he = dH;
+                    o.status = ST_DEFER;
+                } else {
+                    double Df, Lf;
+                    ray_integrals(p, p.h_obs + static_cast<double>(dH),
+                                  static_cast<double>(s_obs), Df, Lf);
+                    const R co_fb = sqrt(R(1) - q);
+                    o.X = xe + static_cast<R>(Df) * hx;
+                    o.Y = ye + static_cast<R>(Df) * hy;
+                    o.t = te + static_cast<R>(Lf * (1.0 / kC));
+                    o.cx = s_obs * hx;
+                    o.cy = s_obs * hy;
+                    o.cz = -co_fb;
+                    o.status = ST_GROUND;
+                    if constexpr (TR) {
+                        const R tau = trans_tau<R>(p, o.lam, o.he);
+                        R P, u3;
+                        if constexpr (std::is_same<R, float>::value) {
+                            P = __expf(-(tau / co_fb));
+                            u3 = u01f(x.w);
+                        } else {
+                            P = exp(-(tau / co_fb));
+                            u3 = u01d(x.w);
+                        }
+                        if (!(u3 < P)) o.status = ST_ABSORBED;
+                    }
+                }
+                return;
+            }
+        }
+        o.status = ST_ANGLE;
+        return;
+    }
     const R omq = R(1) - q;
     const R sec = rsqrt(omq);              // 1 / cos(theta_obs)
     const R co = omq * sec;
@@ -584,12 +726,54 @@ __device__ __forceinline__ void flush_stat_signed(unsigned long long *stats, int
         atomicAdd(stats + idx, static_cast<unsigned long long>(static_cast<long long>(v)));
 }
 
+// Warp-aggregated compaction into the per-telescope buffers: per (warp,
+// telescope) one atomicAdd reserves the slots; the record is the crossing
+// of the arrival line with the horizontal plane through the sphere centre.
+// All 32 lanes call it (hm = 0 on lanes without a crossing).
+template <class R>
+__device__ __forceinline__ void record_hits(const KParams &p, const BunchOut<R> &o, unsigned hm,
+                                            int s0, int gsel, R w, uint64_t key, R np1o,
+                                            int lane, unsigned &st_hits, unsigned &st_over) {
+    for (;;) {
+        if (!__any_sync(kFull, hm != 0u)) break;
+        int tel = -1;
+        R tx = R(0), ty = R(0), tz = R(0);
+        if (hm) {
+            const int bit = __ffs(hm) - 1;
+            hm &= hm - 1u;
+            tel = cand_info<R>(p, gsel, s0 + bit, tx, ty, tz);
+            ++st_hits;
+        }
+        const unsigned grp = __match_any_sync(kFull, tel);
+        if (tel >= 0) {
+            const int leader = __ffs(grp) - 1;
+            const unsigned rank = __popc(grp & ((1u << lane) - 1u));
+            unsigned long long slot0 = 0;
+            if (lane == leader)
+                slot0 = atomicAdd(p.count + tel, static_cast<unsigned long long>(__popc(grp)));
+            slot0 = __shfl_sync(grp, slot0, leader);
+            const unsigned long long slot = slot0 + rank;
+            if (slot < static_cast<unsigned long long>(p.cap)) {
+                const R sl = tz / o.cz;       // to the plane through the centre
+                const int64_t r = static_cast<int64_t>(tel) * p.cap + static_cast<int64_t>(slot);
+                store4<R>(p.pos, r, o.X + sl * o.cx - tx, o.Y + sl * o.cy - ty, o.cx, o.cy);
+                store4<R>(p.tim, r, o.t + sl * np1o * R(1.0 / kC), o.he, w, o.lam);
+                p.key[r] = key;
+            } else {
+                ++st_over;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------------
 // The fused kernel.
 // ------------------------------------------------------------------------
 // TR: the atmospheric transmission draw is compiled in (a separate
-// instantiation: present but switched off it cost 2 % of the launch)
-template <class R, int BLOCK, int MODE, bool TR>
+// instantiation: present but switched off it cost 2 % of the launch).
+// FB: bunches past the tables' zenith range are queued for the fallback
+// pass (1, hits) or integrated in place (2, trace).
+template <class R, int BLOCK, int MODE, bool TR, int FB>
 __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / BLOCK : 1)
     k_gen_prop(const KParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -604,48 +788,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
 
     Consts<R> c;
     R np1o;
-    if constexpr (std::is_same<R, float>::value) {
-        c.h_obs = p.f.h_obs;
-        c.dH_max = p.f.dH_max;
-        c.eta_o = p.f.eta_o;
-        c.inv_np1o = p.f.inv_np1o;
-        c.q_max = p.f.q_max;
-        c.inv_dht = p.f.inv_dht;
-        c.inv_dq = p.f.inv_dq;
-        c.inv_dh = p.f.inv_dh;
-        c.lam_inv1 = p.f.lam_inv1;
-        c.lam_dinv = p.f.lam_dinv;
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-            c.gx0[g] = p.f.gx0[g];
-            c.gy0[g] = p.f.gy0[g];
-            c.inv_gcs[g] = p.f.inv_gcs[g];
-        }
-        c.q_band = p.f.q_band;
-        np1o = p.f.np1o;
-    } else {
-        c.h_obs = p.h_obs;
-        c.dH_max = p.h_max - p.h_obs;
-        c.eta_o = p.eta_obs;
-        c.inv_np1o = 1.0 / (1.0 + p.eta_obs);
-        c.q_max = p.q_max;
-        c.inv_dht = p.inv_dht;
-        c.inv_dq = p.inv_dq;
-        c.inv_dh = p.inv_dh;
-        c.lam_inv1 = p.lam_inv1;
-        c.lam_dinv = p.lam_dinv;
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-            c.gx0[g] = p.grid[g].x0;
-            c.gy0[g] = p.grid[g].y0;
-            c.inv_gcs[g] = p.grid[g].inv_cs;
-        }
-        c.q_band = p.q_band;
-        np1o = 1.0 + p.eta_obs;
-    }
-    c.H = p.H;
-    c.Z = p.Z;
-    c.n_fine = p.n_fine;
+    make_consts<R>(p, c, np1o);
 
     unsigned st_steps = 0, st_emit = 0, st_inval = 0, st_bunch = 0, st_up = 0, st_below = 0,
              st_above = 0, st_angle = 0, st_absorb = 0, st_hits = 0, st_over = 0;
@@ -787,7 +930,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             int j = 0;
             if (live) {
                 j = bidx - off[s];
-                bunch<R, TR>(p, c, seg[s], p.track_base + base + s, j, o);
+                bunch<R, TR, FB>(p, c, seg[s], p.track_base + base + s, j, o);
                 if (o.status != ST_GROUND) {       // rare: the drops
                     st_up += o.status == ST_UPWARD;
                     st_below += o.status == ST_BELOW;
@@ -816,6 +959,28 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                 }
                 continue;
             }
+            if constexpr (MODE == MODE_HITS && FB == 1) {
+                // past the tables' range: queue for the fallback pass
+                const bool dq = live && o.status == ST_DEFER;
+                const unsigned qm = __ballot_sync(kFull, dq);
+                if (qm) {
+                    const int leader = __ffs(qm) - 1;
+                    unsigned long long at0 = 0;
+                    if (lane == leader) at0 = atomicAdd(p.fb_count, static_cast<unsigned long long>(__popc(qm)));
+                    at0 = __shfl_sync(kFull, at0, leader);
+                    const unsigned long long at = at0 + __popc(qm & ((1u << lane) - 1u));
+                    if (dq && at < static_cast<unsigned long long>(p.fb_cap)) {
+                        FbEntry<R> e;
+                        e.xe = o.X; e.ye = o.Y; e.he = c.h_obs + o.he; e.dh = o.he; e.te = o.t;
+                        e.hx = o.cx; e.hy = o.cy; e.s_obs = o.cz; e.lam = o.lam;
+                        e.w = seg[s].w;
+                        const int64_t gstep = p.track_base + base + s;
+                        e.key = (static_cast<uint64_t>(gstep) << 32) | static_cast<uint32_t>(j);
+                        e.step_hi = static_cast<uint32_t>(static_cast<uint64_t>(gstep) >> 32);
+                        static_cast<FbEntry<R> *>(p.fb_list)[at] = e;
+                    }
+                }
+            }
             int s0 = 0, gsel = 0;
             unsigned hm = live ? sphere_hits<R>(p, c, o, s0, gsel) : 0u;
             if constexpr (MODE == MODE_TRACE) {
@@ -841,40 +1006,10 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                     p.t_first[gb] = first;
                 }
             } else {
-                // warp-aggregated compaction into the per-telescope buffers
                 const R w = live ? seg[s].w : R(0);
                 const uint64_t key = (static_cast<uint64_t>(p.track_base + base + s) << 32) |
                                      static_cast<uint32_t>(j);
-                for (;;) {
-                    if (!__any_sync(kFull, hm != 0u)) break;
-                    int tel = -1;
-                    R tx = R(0), ty = R(0), tz = R(0);
-                    if (hm) {
-                        const int bit = __ffs(hm) - 1;
-                        hm &= hm - 1u;
-                        tel = cand_info<R>(p, gsel, s0 + bit, tx, ty, tz);
-                        ++st_hits;
-                    }
-                    const unsigned grp = __match_any_sync(kFull, tel);
-                    if (tel >= 0) {
-                        const int leader = __ffs(grp) - 1;
-                        const unsigned rank = __popc(grp & ((1u << lane) - 1u));
-                        unsigned long long slot0 = 0;
-                        if (lane == leader)
-                            slot0 = atomicAdd(p.count + tel, static_cast<unsigned long long>(__popc(grp)));
-                        slot0 = __shfl_sync(grp, slot0, leader);
-                        const unsigned long long slot = slot0 + rank;
-                        if (slot < static_cast<unsigned long long>(p.cap)) {
-                            const R sl = tz / o.cz;       // to the plane through the centre
-                            const int64_t r = static_cast<int64_t>(tel) * p.cap + static_cast<int64_t>(slot);
-                            store4<R>(p.pos, r, o.X + sl * o.cx - tx, o.Y + sl * o.cy - ty, o.cx, o.cy);
-                            store4<R>(p.tim, r, o.t + sl * np1o * R(1.0 / kC), o.he, w, o.lam);
-                            p.key[r] = key;
-                        } else {
-                            ++st_over;
-                        }
-                    }
-                }
+                record_hits<R>(p, o, hm, s0, gsel, w, key, np1o, lane, st_hits, st_over);
             }
         }
         if (!p.tile_counter) break;
@@ -907,6 +1042,88 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
     }
 }
 
+// ------------------------------------------------------------------------
+// The fallback pass: one thread per queued bunch (warps walk the queue 32
+// entries at a time so that the compaction stays warp-synchronous).
+// ------------------------------------------------------------------------
+template <class R, bool TR>
+__global__ void __launch_bounds__(128) k_fallback(const KParams p) {
+    Consts<R> c;
+    R np1o;
+    make_consts<R>(p, c, np1o);
+    const int lane = threadIdx.x & 31;
+    const unsigned long long queued = *p.fb_count;
+    const unsigned long long cap = static_cast<unsigned long long>(p.fb_cap);
+    const int64_t n = static_cast<int64_t>(queued < cap ? queued : cap);
+    unsigned st_fb = 0, st_absorb = 0, st_hits = 0, st_over = 0;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    const int64_t wid = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (int64_t first = wid * 32; first < n; first += warps * 32) {
+        const int64_t e = first + lane;
+        const bool live = e < n;
+        BunchOut<R> o;
+        o.status = -1;
+        R w = R(0);
+        uint64_t key = 0;
+        if (live) {
+            const FbEntry<R> E = static_cast<const FbEntry<R> *>(p.fb_list)[e];
+            double D, L;
+            ray_integrals(p, p.h_obs + static_cast<double>(E.dh), static_cast<double>(E.s_obs),
+                          D, L);
+            const R co = sqrt(R(1) - E.s_obs * E.s_obs);
+            o.X = E.xe + static_cast<R>(D) * E.hx;
+            o.Y = E.ye + static_cast<R>(D) * E.hy;
+            o.t = E.te + static_cast<R>(L * (1.0 / kC));
+            o.cx = E.s_obs * E.hx;
+            o.cy = E.s_obs * E.hy;
+            o.cz = -co;
+            o.he = E.he;
+            o.lam = E.lam;
+            o.status = ST_GROUND;
+            w = E.w;
+            key = E.key;
+            const uint32_t step_hi = E.step_hi;
+            ++st_fb;
+            if constexpr (TR) {
+                // the bunch's fourth Philox word decides, as in the main pass
+                const uint4 x = philox4x32_10(
+                    make_uint4(static_cast<uint32_t>(key >> 32), step_hi, static_cast<uint32_t>(key),
+                               0u),
+                    p.key0, p.key1);
+                const R tau = trans_tau<R>(p, o.lam, o.he);
+                R P, u3;
+                if constexpr (std::is_same<R, float>::value) {
+                    P = __expf(-(tau / co));
+                    u3 = u01f(x.w);
+                } else {
+                    P = exp(-(tau / co));
+                    u3 = u01d(x.w);
+                }
+                if (!(u3 < P)) {
+                    o.status = ST_ABSORBED;
+                    ++st_absorb;
+                }
+            }
+        }
+        int s0 = 0, gsel = 0;
+        unsigned hm = live ? sphere_hits<R>(p, c, o, s0, gsel) : 0u;
+        record_hits<R>(p, o, hm, s0, gsel, w, key, np1o, lane, st_hits, st_over);
+    }
+    unsigned long long *S = p.stats;
+    if (S) {
+        // the main pass counted the queued bunches as reaching the ground
+        flush_stat(S, CHER_STAT_FALLBACK, st_fb);
+        flush_stat(S, CHER_STAT_ABSORBED, st_absorb);
+        flush_stat_signed(S, CHER_STAT_GROUND, -static_cast<int>(st_absorb));
+        flush_stat(S, CHER_STAT_HITS, st_hits);
+        flush_stat(S, CHER_STAT_OVERFLOW, st_over);
+        if (blockIdx.x == 0 && threadIdx.x == 0 && queued > cap) {
+            atomicAdd(S + CHER_STAT_FB_LOST, queued - cap);
+            atomicAdd(S + CHER_STAT_GROUND, ~(queued - cap) + 1ull);     // minus the lost
+        }
+    }
+}
+
 template <class R, int BLOCK>
 size_t smem_bytes(const KParams &p) {
     size_t b = sizeof(Seg<R>) * BLOCK + sizeof(int) * (BLOCK + 1 + 32);
@@ -915,41 +1132,52 @@ size_t smem_bytes(const KParams &p) {
 }
 
 template <class R, int BLOCK, int MODE>
-const void *kernel_ptr(bool tr) {
-    if constexpr (MODE == MODE_YIELD)
-        return reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false>);
-    else
-        return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true>)
-                  : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false>);
+const void *kernel_ptr(bool tr, bool fb) {
+    if constexpr (MODE == MODE_YIELD || MODE == MODE_SCREEN) {
+        if constexpr (MODE == MODE_YIELD)
+            return reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0>);
+        else
+            return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, 0>)
+                      : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0>);
+    } else {
+        constexpr int F = MODE == MODE_HITS ? 1 : 2;
+        if (fb)
+            return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, F>)
+                      : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, F>);
+        return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, 0>)
+                  : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0>);
+    }
 }
 
 template <class R, int MODE>
-const void *pick(int block, bool tr) {
+const void *pick(int block, bool tr, bool fb) {
     switch (block) {
-    case 128: return kernel_ptr<R, 128, MODE>(tr);
-    case 256: return kernel_ptr<R, 256, MODE>(tr);
-    case 512: return kernel_ptr<R, 512, MODE>(tr);
+    case 128: return kernel_ptr<R, 128, MODE>(tr, fb);
+    case 256: return kernel_ptr<R, 256, MODE>(tr, fb);
+    case 512: return kernel_ptr<R, 512, MODE>(tr, fb);
     }
     return nullptr;
 }
 
-// mode: a Mode, plus kTransBit for the instantiation with the transmission
+// mode: a Mode, plus kTransBit / kFbBit for the instantiations with the
+// transmission draw / the beyond-table fallback
 const void *pick_kernel(bool fp32, int block, int mode) {
     const bool tr = (mode & kTransBit) != 0;
-    mode &= ~kTransBit;
+    const bool fb = (mode & kFbBit) != 0;
+    mode &= ~(kTransBit | kFbBit);
     if (fp32) {
         switch (mode) {
-        case MODE_HITS: return pick<float, MODE_HITS>(block, tr);
-        case MODE_TRACE: return pick<float, MODE_TRACE>(block, tr);
-        case MODE_YIELD: return pick<float, MODE_YIELD>(block, tr);
-        case MODE_SCREEN: return pick<float, MODE_SCREEN>(block, tr);
+        case MODE_HITS: return pick<float, MODE_HITS>(block, tr, fb);
+        case MODE_TRACE: return pick<float, MODE_TRACE>(block, tr, fb);
+        case MODE_YIELD: return pick<float, MODE_YIELD>(block, tr, fb);
+        case MODE_SCREEN: return pick<float, MODE_SCREEN>(block, tr, fb);
         }
     } else {
         switch (mode) {
-        case MODE_HITS: return pick<double, MODE_HITS>(block, tr);
-        case MODE_TRACE: return pick<double, MODE_TRACE>(block, tr);
-        case MODE_YIELD: return pick<double, MODE_YIELD>(block, tr);
-        case MODE_SCREEN: return pick<double, MODE_SCREEN>(block, tr);
+        case MODE_HITS: return pick<double, MODE_HITS>(block, tr, fb);
+        case MODE_TRACE: return pick<double, MODE_TRACE>(block, tr, fb);
+        case MODE_YIELD: return pick<double, MODE_YIELD>(block, tr, fb);
+        case MODE_SCREEN: return pick<double, MODE_SCREEN>(block, tr, fb);
         }
     }
     return nullptr;
@@ -982,6 +1210,7 @@ void fill_float_constants(KParams &p) {
     p.f.dh = static_cast<float>(1.0 / p.inv_dh);
     p.f.eta_slope = static_cast<float>(p.eta_slope * 1.01);
     p.f.rcut2 = static_cast<float>(p.rcut2);
+    p.f.fb_q = static_cast<float>(p.fb_q);
     p.f.trans_l0 = static_cast<float>(p.trans_l0);
     p.f.trans_lscale = static_cast<float>(p.trans_lscale);
     p.f.trans_h0 = static_cast<float>(p.trans_h0);
@@ -1005,6 +1234,25 @@ __global__ void k_round_to_float(const double *in, float *out, int64_t n) {
         out[i] = d2f_rn(in[i]);
 }
 }  // namespace
+
+size_t fallback_record_bytes(bool fp32) {
+    static_assert(sizeof(FbEntry<float>) == 64 && sizeof(FbEntry<double>) == 96,
+                  "fallback queue records");
+    return fp32 ? sizeof(FbEntry<float>) : sizeof(FbEntry<double>);
+}
+
+cudaError_t launch_fallback(bool fp32, bool tr, const KParams &p, int num_sms, void *stream) {
+    const int grid = num_sms * 8;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (fp32) {
+        if (tr) k_fallback<float, true><<<grid, 128, 0, st>>>(p);
+        else k_fallback<float, false><<<grid, 128, 0, st>>>(p);
+    } else {
+        if (tr) k_fallback<double, true><<<grid, 128, 0, st>>>(p);
+        else k_fallback<double, false><<<grid, 128, 0, st>>>(p);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t round_to_float(const double *in, float *out, int64_t n, int num_sms, void *stream) {
     if (n <= 0) return cudaSuccess;

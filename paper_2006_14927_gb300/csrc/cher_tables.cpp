@@ -445,6 +445,15 @@ double greisen(double t, double y) {
 }
 }  // namespace
 
+void gauss_legendre12(double *x, double *w) {
+    static const GaussLegendre gl;
+    static_assert(GaussLegendre::N == 12, "the fallback integrator takes 12 nodes");
+    for (int q = 0; q < GaussLegendre::N; ++q) {
+        x[q] = gl.x[q];
+        w[q] = gl.w[q];
+    }
+}
+
 void greisen_cdf_host(double y, double t_g, int n_cdf, std::vector<double> &cdf) {
     static const GaussLegendre gl;
     cdf.assign(n_cdf, 0.0);
