@@ -417,13 +417,16 @@ cher_status cher_set_transmission(cher_ctx *ctx, const cher_transmission *table)
  * FP64, 12-point Gauss-Legendre on each layer's part -- instead of being
  * dropped (stats[CHER_STAT_ANGLE]).  The generation launch queues them and
  * a second kernel on the same stream propagates them (stats
- * [CHER_STAT_FALLBACK]); the queue holds max(2^20, n steps) bunches per
- * call, the rest counted in stats[CHER_STAT_FB_LOST].  Trace launches
- * integrate them in place.  The adjoint and the allocation-free launch do
- * not use it (those bunches stay dropped there).
- *   zenith_max_deg: 0 (off) or in (the tables' zenith range, 85].
+ * [CHER_STAT_FALLBACK]); the queue holds `queue_records` bunches per call
+ * (0: max(2^20, 4 x the call's steps); 64 B each in FP32, 96 B in FP64,
+ * allocated on the first call that needs them), the rest counted in
+ * stats[CHER_STAT_FB_LOST].  Trace launches integrate them in place.  The
+ * adjoint and the allocation-free launch do not use it (those bunches stay
+ * dropped there).
+ *   zenith_max_deg: 0 (off) or in (the tables' zenith range, 85];
+ *   queue_records : 0 or up to 2^34.
  * Errors: CHER_EINVAL. */
-cher_status cher_set_fallback(cher_ctx *ctx, double zenith_max_deg);
+cher_status cher_set_fallback(cher_ctx *ctx, double zenith_max_deg, int64_t queue_records);
 
 /* Replace the atmosphere and, if tables were built, rebuild them with the
  * same sizes (blocking).  Errors as cher_build_refraction_tables. */

@@ -109,7 +109,7 @@ SIGNATURES = {
                                         ctypes.POINTER(Output), ctypes.POINTER(Profile), _P]),
     "cher_round_to_float": (_S, [_P, _P, ctypes.c_int64, _P]),
     "cher_set_transmission": (_S, [_P, ctypes.POINTER(Transmission)]),
-    "cher_set_fallback": (_S, [_P, ctypes.c_double]),
+    "cher_set_fallback": (_S, [_P, ctypes.c_double, ctypes.c_int64]),
     "cher_generate_steps": (_S, [_P, ctypes.POINTER(Shower), ctypes.c_int32, ctypes.c_uint64, _S,
                                  ctypes.POINTER(StepBuffers), _P]),
     "cher_generate_propagate_noalloc": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
@@ -460,10 +460,12 @@ class Context:
                "cher_generate_steps")
         return out
 
-    def set_fallback(self, zenith_max_deg: float):
+    def set_fallback(self, zenith_max_deg: float, queue_records: int = 0):
         """Propagate bunches past the tables' zenith range, up to this
-        zenith, by the ray integrals (0: off)."""
-        _check(lib().cher_set_fallback(self._h, float(zenith_max_deg)), "cher_set_fallback")
+        zenith, by the ray integrals (0: off); queue_records bunches per call
+        (0: max(2^20, 4 x steps))."""
+        _check(lib().cher_set_fallback(self._h, float(zenith_max_deg), int(queue_records)),
+               "cher_set_fallback")
 
     def set_transmission(self, table: dict | None):
         """Atmospheric transmission: dict(tau=(n_lambda, n_height) vertical

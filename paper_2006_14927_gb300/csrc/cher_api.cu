@@ -62,6 +62,7 @@ struct cher_ctx {
     double trans_l0 = 0, trans_l1 = 0, trans_h0 = 0, trans_h1 = 0;
     // beyond-table fallback: zenith limit (deg, 0 off) and its queue
     double fb_deg = 0.0;
+    int64_t fb_records = 0;               // queue size per call (0: the default)
     void *d_fb = nullptr;
     int64_t fb_cap = 0;                   // bytes
     unsigned long long *d_fb_count = nullptr;
@@ -670,9 +671,10 @@ cher_status cher_generate_propagate_ex(cher_ctx *c, const cher_tracks *t, uint64
     p.stats = out->stats;
     const bool fb = p.fb_q > 0.0;
     if (fb) {
-        // the fallback queue: max(2^20, n) records, grown as needed
+        // the fallback queue: the set size or max(2^20, 4 n) records
         const size_t rec = cher::fallback_record_bytes(fp32);
-        const int64_t want = std::max<int64_t>(int64_t(1) << 20, t->n);
+        const int64_t want = c->fb_records > 0 ? c->fb_records
+                                               : std::max<int64_t>(int64_t(1) << 20, 4 * t->n);
         int64_t bytes_cap = c->fb_cap;
         if (static_cast<int64_t>(want * rec) > bytes_cap) {
             unsigned char *buf = static_cast<unsigned char *>(c->d_fb);
@@ -690,7 +692,7 @@ cher_status cher_generate_propagate_ex(cher_ctx *c, const cher_tracks *t, uint64
             return CHER_ECUDA;
         p.fb_list = c->d_fb;
         p.fb_count = c->d_fb_count;
-        p.fb_cap = c->fb_cap / static_cast<int64_t>(rec);
+        p.fb_cap = std::min<int64_t>(want, c->fb_cap / static_cast<int64_t>(rec));
     }
     if (prof) {
         p.prof = prof->profile;
@@ -710,8 +712,10 @@ cher_status cher_generate_propagate_ex(cher_ctx *c, const cher_tracks *t, uint64
     return CHER_OK;
 }
 
-cher_status cher_set_fallback(cher_ctx *c, double zenith_max_deg) {
+cher_status cher_set_fallback(cher_ctx *c, double zenith_max_deg, int64_t queue_records) {
     if (!c || !std::isfinite(zenith_max_deg)) return CHER_EINVAL;
+    if (queue_records < 0 || queue_records > (int64_t(1) << 34)) return CHER_EINVAL;
+    c->fb_records = queue_records;
     if (zenith_max_deg == 0.0) {
         c->fb_deg = 0.0;
         return CHER_OK;

@@ -80,6 +80,20 @@ def test_bunches_past_the_fallback_limit_stay_dropped(prec):
     ctx.close()
 
 
+def test_fallback_queue_overflow_is_counted():
+    """A queue far smaller than the bunches past the tables: the rest are
+    counted as lost, and the books still balance."""
+    sc = _scenario(61.0)
+    ctx = context(sc)
+    ctx.set_fallback(80.0, queue_records=1000)
+    tr = host_tracks(sc, FP32)
+    code, stats, out = gpu_hits(ctx, tr, sc["t_ref"], SEED, FP32, 200_000)
+    assert code == 0
+    assert int(stats[12]) == 1000 and int(stats[13]) > 1000
+    assert int(stats[8]) + int(stats[4:8].sum()) + int(stats[11]) + int(stats[13]) == int(stats[3])
+    ctx.close()
+
+
 def test_fallback_setting_is_checked():
     sc = _scenario(61.0)
     ctx = context(sc)
@@ -87,6 +101,8 @@ def test_fallback_setting_is_checked():
         with pytest.raises(P.CherError) as e:
             ctx.set_fallback(bad)
         assert e.value.code == 1
+    with pytest.raises(P.CherError):
+        ctx.set_fallback(70.0, queue_records=-5)
     ctx.set_fallback(70.0)
     ctx.set_fallback(0.0)
     ctx.close()
