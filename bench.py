@@ -45,9 +45,11 @@ UNIT = "bunches/s"
 WORKLOAD = "vertical_1tev"
 
 # ---------------------------------------------------------------------------
-# Algorithmic operation counts (derivation in DESIGN.md, "Roofline").
-# Per bunch, FP32/INT32 lane operations of the single-precision path, by
-# stage; per emitting step, the FP64 operations of the yield.
+# Algorithmic operation counts, from the algorithm as the oracle states it
+# (each add, mul, fma, compare, select, convert, shift or logic op = 1; each
+# sqrt, rsqrt or reciprocal = 1; implementation overhead excluded).  Per
+# bunch, FP32/INT32 lane operations of the single-precision path, by stage;
+# per emitting step, the FP64 operations of the yield.
 # ---------------------------------------------------------------------------
 OPS_PER_BUNCH_FP32 = {
     "sub_step_loop": 2,
@@ -69,11 +71,11 @@ FP64_OPS_PER_STEP = 34          # yield chain: 24 mul/add + 1 division (~10 ops)
 FP32_LANES_PER_SM = 128
 FP64_FMA_PER_SM_CLK = 2         # GB300: 1/64 of the FP32 rate (ncu: 2 DFMA/cycle/SM)
 
-# DRAM bytes (read + write) of one FP32 launch, from one ncu capture (the
-# summary in profiles/k_gen_prop_vertical_1tev.md: 128.25 MB read, 24.35 MB
-# written, 512 threads x 2 CTAs per SM).  Reported only for that workload at
-# full size and only while the kernel sources hash to what was profiled.
-TRAFFIC = {"vertical_1tev": (152_606_464, "a3cf0da2448c21c8")}
+# DRAM bytes (read + write) of one FP32 launch, from one ncu capture of the
+# full-size vertical workload (128.23 MB read, 24.68 MB written, 128 threads
+# x 8 CTAs per SM).  Reported only for that workload at full size and only
+# while the kernel sources hash to what was profiled.
+TRAFFIC = {"vertical_1tev": (152_903_168, "b1fd8a60ff30dd7f")}
 KERNEL_SOURCES = ("cher_kernels.cu", "cher_device.cuh", "cher_internal.h")
 
 

@@ -68,7 +68,8 @@ class _Cfg(ctypes.Structure):
                 ("trans_nl", ctypes.c_int), ("trans_nh", ctypes.c_int),
                 ("trans_l0", ctypes.c_double), ("trans_l1", ctypes.c_double),
                 ("trans_h0", ctypes.c_double), ("trans_h1", ctypes.c_double),
-                ("trans_tau", _dp), ("fb_sin2_max", ctypes.c_double)]
+                ("trans_tau", _dp), ("fb_sin2_max", ctypes.c_double),
+                ("disp_k", ctypes.c_int), ("disp_kappa", _dp), ("ax_hi", _dp), ("al_hi", _dp)]
 
 
 class _Tracks(ctypes.Structure):
@@ -145,6 +146,8 @@ def lib():
                                                   ctypes.c_double, _dp, _dp]
         L.orc_propagate_photon.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int] + \
             [ctypes.c_double] * 7 + [_dp]
+        L.orc_propagate_photon_k.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int] + \
+            [ctypes.c_double] * 8 + [_dp]
         L.orc_bunches.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Tracks),
                                   ctypes.c_uint64, _i64p, ctypes.c_int,
                                   ctypes.POINTER(_Out)]
@@ -282,6 +285,10 @@ class Model:
     # beyond-table fallback: bunches up to this observation-level zenith
     # (deg) past the tables' range take the ray integrals (0: off)
     fallback_deg: float = 0.0
+    # wavelength-dependent index: kappa at k (2..9) nodes uniform in 1/lambda
+    # from 1/lambda1 (node 0) to 1/lambda2, n(h, lambda) - 1 = eta(h) kappa,
+    # positive and not increasing along the nodes; None: constant index
+    dispersion: np.ndarray | None = None
     table_tol: float = 1e-13
     bf_tol: float = 1e-12
     eta_tab: np.ndarray = field(init=False, repr=False)
@@ -291,8 +298,22 @@ class Model:
     def __post_init__(self):
         self.telescopes = _f64(np.asarray(self.telescopes).reshape(-1, 4))
         self.eta_tab = eta_table(self.atm, self.h_max, self.n_fine)
-        self.ax, self.al = refraction_tables(self.atm, self.h_obs, self.h_max, self.H,
-                                             self.Z, self.theta_max_rad, self.table_tol)
+        if self.dispersion is not None:
+            kap = _f64(np.asarray(self.dispersion, float).ravel())
+            if not (2 <= kap.size <= 9) or not np.all(kap > 0) or np.any(np.diff(kap) > 0):
+                raise ValueError("dispersion: 2..9 positive, non-increasing kappa nodes")
+            self.dispersion = kap
+            # the tables of the band's two ends: n - 1 scaled by kappa
+            lo = dict(self.atm, n0_minus_1=float(self.atm["n0_minus_1"]) * kap[-1])
+            hi = dict(self.atm, n0_minus_1=float(self.atm["n0_minus_1"]) * kap[0])
+            self.ax, self.al = refraction_tables(lo, self.h_obs, self.h_max, self.H, self.Z,
+                                                 self.theta_max_rad, self.table_tol)
+            self.ax_hi, self.al_hi = refraction_tables(hi, self.h_obs, self.h_max, self.H,
+                                                       self.Z, self.theta_max_rad,
+                                                       self.table_tol)
+        else:
+            self.ax, self.al = refraction_tables(self.atm, self.h_obs, self.h_max, self.H,
+                                                 self.Z, self.theta_max_rad, self.table_tol)
         if self.t_ref is not None:
             self.t_ref = _f64(np.atleast_1d(self.t_ref))
 
@@ -321,6 +342,10 @@ class Model:
             C.t_ref = None
             C.n_showers = 0
         C.bf_tol = self.bf_tol
+        if self.dispersion is not None:
+            C.disp_k = int(self.dispersion.size)
+            C.disp_kappa = _ptr(self.dispersion)
+            C.ax_hi, C.al_hi = _ptr(self.ax_hi), _ptr(self.al_hi)
         if self.fallback_deg > 0.0:
             sf = math.sin(self.fallback_deg * 3.14159265358979323846 / 180.0)
             C.fb_sin2_max = sf * sf
@@ -438,11 +463,16 @@ class Model:
         del keep
         return prof
 
-    def propagate_photon(self, xe, ye, he, te, px, py, pz, variant=0):
+    def propagate_photon(self, xe, ye, he, te, px, py, pz, variant=0, kappa=None):
+        """One bunch to the ground; kappa scales n - 1 at its wavelength."""
         r = np.zeros(6)
         C = self._cfg()
-        st = lib().orc_propagate_photon(ctypes.byref(C), int(variant), xe, ye, he, te,
-                                        px, py, pz, _ptr(r))
+        if kappa is None:
+            st = lib().orc_propagate_photon(ctypes.byref(C), int(variant), xe, ye, he, te,
+                                            px, py, pz, _ptr(r))
+        else:
+            st = lib().orc_propagate_photon_k(ctypes.byref(C), int(variant), float(kappa), xe,
+                                              ye, he, te, px, py, pz, _ptr(r))
         return st, r
 
 

@@ -71,6 +71,7 @@
                              /* atmospheric transmission draw              */
 
 #define ORC_MAX_HITS 4       /* telescopes recorded per bunch               */
+#define ORC_DISP_MAX 9       /* nodes of a wavelength-dependent index       */
 
 /* Layered atmosphere: thickness T(h) = a_i + b_i exp(-h/c_i) in layer i,
  * h in [h_bound[i], h_bound[i+1]); density rho = -dT/dh; above h_bound[5]
@@ -115,6 +116,17 @@ typedef struct {
     /* sin^2(zenith) exceeds the tables' range but not fb_sin2_max are      */
     /* propagated by the ray integrals themselves (variant (B))            */
     double fb_sin2_max;
+    /* wavelength-dependent index (disp_k = 0: off):                       */
+    /*   n(h, lambda) - 1 = eta(h) kappa(lambda),                           */
+    /* kappa linear in the wavenumber 1/lambda between disp_k nodes, node m */
+    /* at 1/lambda_m = 1/lambda1 - m (1/lambda1 - 1/lambda2)/(disp_k - 1),  */
+    /* so node 0 is the short end of the band; kappa is positive and does   */
+    /* not increase with m (normal dispersion).  The refraction tables are  */
+    /* then (ax, al) for kappa[disp_k - 1] and (ax_hi, al_hi) for kappa[0], */
+    /* interpolated linearly in kappa.                                      */
+    int disp_k;
+    const double *disp_kappa;
+    const double *ax_hi, *al_hi;
 } orc_cfg;
 
 typedef struct {
@@ -266,6 +278,11 @@ double orc_eta_lookup(const double *tab, int n, double h_max, double h)
 typedef struct {
     int64_t nb;
     double w, N, s2, beta, eta;
+    /* with a wavelength-dependent index: gamma^2, beta^2 gamma^2, and per  */
+    /* piece of the band its share of the yield (integral / piece width)    */
+    /* and the radiating fraction of its width                              */
+    double gam2, bg2, psum, x_th;
+    double piece[ORC_DISP_MAX - 1], frac[ORC_DISP_MAX - 1];
 } orc_yield;
 
 static double orc_band_factor(const orc_cfg *C)
@@ -320,6 +337,108 @@ static int orc_step_yield_valid(const orc_cfg *C, double z0, double len, double 
     return 0;
 }
 
+/* Frank-Tamm with a wavelength-dependent index (an extension: the paper's
+ * CERENK takes n independent of the wavelength).  Per unit path,
+ *     dN/dL = 2 pi alpha int (1 - 1/(beta n(u))^2)_+ du,   u = 1/lambda.
+ * On a piece of the band where n(u) = 1 + eta kappa(u) is linear in u the
+ * integral has a closed form (the antiderivative of 1/(A + B u)^2 is
+ * -1/(B (A + B u))):
+ *     int_piece (1 - 1/(beta n)^2) du = width (1 - 1/(beta^2 n_a n_b)),
+ * n_a, n_b the index at the ends, and with e = n_a n_b - 1 = e_a + e_b + e_a e_b
+ * (e_a = eta kappa_a) the bracket is the cancellation-free
+ *     [e gamma^2 - (1 + e)] / [g (2 + g) (1 + e)],
+ * the constant-index sin^2 form with eta (2 + eta) replaced by e.  Only the
+ * part of the band where beta n > 1 radiates, i.e. eta kappa > x_th with
+ *     x_th = 1/beta - 1 = 1 / (gamma^2 beta (1 + beta));
+ * kappa falls along the nodes, so at most one piece is cut: its radiating
+ * part is the fraction (e_a - x_th) / (e_a - e_b) at its short-wavelength
+ * end, where the index runs from n_a down to 1/beta (e_b replaced by x_th).
+ *     N = L 2 pi alpha du sum_m frac_m S_m,  du = (1/lambda1 - 1/lambda2)/(k - 1),
+ * and nb = ceil(N / B) as for the constant index. */
+static double orc_disp_piece(double x, double y, double gam2, double bg2)
+{
+    double xy = x * y;
+    double xpy = x + y;
+    double e = xpy + xy;
+    double np = 1.0 + e;
+    double A = e * gam2;
+    double num = A - np;
+    double den = bg2 * np;
+    double S = num / den;
+    return (S > 0.0) ? S : 0.0;
+}
+
+static double orc_disp_band_factor(const orc_cfg *C)
+{
+    double two_pi_alpha = (2.0 * ORC_PI) * ORC_ALPHA;
+    double inv1 = 1.0e9 / C->lambda1_nm;
+    double inv2 = 1.0e9 / C->lambda2_nm;
+    double dinv = inv1 - inv2;
+    double du = dinv / (double)(C->disp_k - 1);
+    return two_pi_alpha * du;
+}
+
+static int orc_step_yield_disp(const orc_cfg *C, double z0, double len, double ekin,
+                               double uz, orc_yield *Y)
+{
+    double inv_me = 1.0 / ORC_ME_MEV;
+    double Kd = orc_disp_band_factor(C);
+    double inv_B = 1.0 / C->bunch_size;
+
+    double g = ekin * inv_me;
+    double gam = 1.0 + g;
+    double gam2 = gam * gam;
+    double half_len = 0.5 * len;
+    double dz = half_len * uz;
+    double hm = z0 + dz;
+    double eta = orc_eta_lookup(C->eta_tab, C->n_fine, C->h_max, hm);
+    double two_g = 2.0 + g;
+    double bg2 = g * two_g;
+    double beta = sqrt(bg2) / gam;
+    double onepb = 1.0 + beta;
+    double gb = gam2 * beta;
+    double gbb = gb * onepb;
+    double x_th = 1.0 / gbb;
+    Y->eta = eta;
+    Y->beta = beta;
+    Y->gam2 = gam2;
+    Y->bg2 = bg2;
+    Y->x_th = x_th;
+    double sum = 0.0;
+    for (int m = 0; m + 1 < C->disp_k; ++m) {
+        double ea = eta * C->disp_kappa[m];
+        double eb = eta * C->disp_kappa[m + 1];
+        double frac = 0.0, S = 0.0;
+        if (ea > x_th) {
+            if (eb >= x_th) {
+                frac = 1.0;
+                S = orc_disp_piece(ea, eb, gam2, bg2);
+            } else {
+                double d1 = ea - x_th;
+                double d2 = ea - eb;
+                frac = d1 / d2;
+                S = orc_disp_piece(ea, x_th, gam2, bg2);
+            }
+        }
+        double v = frac * S;
+        Y->frac[m] = frac;
+        Y->piece[m] = v;
+        sum = sum + v;
+    }
+    Y->psum = sum;
+    if (!(sum > 0.0)) return 0;             /* below threshold everywhere  */
+    double Ks = Kd * sum;
+    double N = len * Ks;
+    double q = N * inv_B;
+    if (!(q < 4194304.0)) return -1;
+    double nbd = ceil(q);
+    Y->s2 = sum / (double)(C->disp_k - 1);  /* band-averaged sin^2         */
+    Y->N = N;
+    Y->nb = (int64_t)nbd;
+    Y->w = (Y->nb > 0) ? N / nbd : 0.0;
+    return 0;
+}
+
 /* A step is valid when every field is finite, its length is not negative
  * and its kinetic energy is positive; an invalid step emits nothing. */
 static int orc_step_valid(const orc_tracks *T, int64_t i)
@@ -334,7 +453,10 @@ static int orc_step_valid(const orc_tracks *T, int64_t i)
 static int orc_step_yield(const orc_cfg *C, const orc_tracks *T, int64_t i, orc_yield *Y)
 {
     Y->nb = 0; Y->w = 0.0; Y->N = 0.0; Y->s2 = 0.0; Y->beta = 0.0; Y->eta = 0.0;
+    Y->psum = 0.0;
     if (!orc_step_valid(T, i)) return -1;
+    if (C->disp_k > 0)
+        return orc_step_yield_disp(C, T->z0[i], T->len[i], T->ekin[i], T->uz[i], Y);
     return orc_step_yield_valid(C, T->z0[i], T->len[i], T->ekin[i], T->uz[i], Y);
 }
 
@@ -505,12 +627,13 @@ static double orc_bilinear(const double *T, int Z, int j, int k, double a, doubl
 
 /* ======================================================================= */
 /* Propagation of one photon bunch to the observation level (RAYBND).      */
-/* variant 0 = (T) tables, 1 = (B) brute force.                             */
+/* variant 0 = (T) tables, 1 = (B) brute force.  kappa scales n - 1 at the */
+/* bunch's wavelength (1 for a wavelength-independent index).               */
 /* out: X, Y, t, cx, cy, cz.  Returns the status code.                      */
 /* ======================================================================= */
-int orc_propagate_photon(const orc_cfg *C, int variant, double xe, double ye,
-                         double he, double te, double px, double py, double pz,
-                         double *out)
+int orc_propagate_photon_k(const orc_cfg *C, int variant, double kappa, double xe,
+                           double ye, double he, double te, double px, double py,
+                           double pz, double *out)
 {
     /* rare conditions first (paper Alg. 2), each a counted drop */
     if (pz >= 0.0) return ORC_ST_UPWARD;
@@ -526,6 +649,11 @@ int orc_propagate_photon(const orc_cfg *C, int variant, double xe, double ye,
         eta_e = orc_eta_exact(&C->atm, he);
         eta_o = orc_eta_exact(&C->atm, C->h_obs);
     }
+    eta_e = kappa * eta_e;
+    eta_o = kappa * eta_o;
+    /* the atmosphere at this wavelength, for the ray integrals */
+    orc_atm Ak = C->atm;
+    Ak.n0_minus_1 = kappa * C->atm.n0_minus_1;
     /* Snell in flat layers: n(h_e) sin(theta_em) = n_obs sin(theta_obs) */
     double sin_obs = sin_em * (1.0 + eta_e) / (1.0 + eta_o);
     double q = sin_obs * sin_obs;
@@ -559,6 +687,15 @@ int orc_propagate_photon(const orc_cfg *C, int variant, double xe, double ye,
         double b = fk - (double)k;
         double Ax = orc_bilinear(C->ax, C->Z, j, k, a, b);
         double Al = orc_bilinear(C->al, C->Z, j, k, a, b);
+        if (C->disp_k > 0) {
+            /* linear in kappa between the tables of the band's two ends */
+            double k_lo = C->disp_kappa[C->disp_k - 1], k_hi = C->disp_kappa[0];
+            double wk = (k_hi > k_lo) ? (kappa - k_lo) / (k_hi - k_lo) : 0.0;
+            double Bx = orc_bilinear(C->ax_hi, C->Z, j, k, a, b);
+            double Bl = orc_bilinear(C->al_hi, C->Z, j, k, a, b);
+            Ax = Ax + wk * (Bx - Ax);
+            Al = Al + wk * (Bl - Al);
+        }
         /* dx = Ax tan sec^2, dl = Al sec^3 (see the table definition) */
         double sec = 1.0 / cos_obs;
         double tn = sin_obs * sec;
@@ -566,7 +703,7 @@ int orc_propagate_photon(const orc_cfg *C, int variant, double xe, double ye,
         D = dH * tn + Ax * tn * sec2;
         L = dH * sec + Al * sec2 * sec;
     } else {
-        if (orc_brute_ray(&C->atm, C->h_obs, he, sin_obs, C->bf_tol, &D, &L) != 0)
+        if (orc_brute_ray(&Ak, C->h_obs, he, sin_obs, C->bf_tol, &D, &L) != 0)
             return ORC_ST_ANGLE;
     }
     out[0] = xe + D * hx;
@@ -576,6 +713,13 @@ int orc_propagate_photon(const orc_cfg *C, int variant, double xe, double ye,
     out[4] = sin_obs * hy;
     out[5] = -cos_obs;
     return ORC_ST_GROUND;
+}
+
+int orc_propagate_photon(const orc_cfg *C, int variant, double xe, double ye,
+                         double he, double te, double px, double py, double pz,
+                         double *out)
+{
+    return orc_propagate_photon_k(C, variant, 1.0, xe, ye, he, te, px, py, pz, out);
 }
 
 /* ======================================================================= */
@@ -621,7 +765,71 @@ typedef struct {
     double xe, ye, he, te, px, py, pz, lam;
     double r[6];                      /* X, Y, t (before t_ref), cx, cy, cz */
     double tr_margin;                 /* u3 - P of the transmission draw, or NaN */
+    double kappa;                     /* (n - 1) scale at the bunch's wavelength */
 } orc_bunch1;
+
+/* The wavelength of a bunch under a wavelength-dependent index, from the
+ * step's spectrum (density 1 - 1/(beta n(u))^2 in u = 1/lambda over the
+ * radiating part of the band) by inversion of the deviate u2, counted from
+ * the short end of the band like the constant-index inversion: the piece m
+ * whose cumulative share first exceeds u2 * psum, then inside it the
+ * fraction t of its radiating width where
+ *     G(t) = t - t / (beta^2 n_a n(t)),  n(t) = n_a + b t,  b = n_end - n_a
+ * (the density's integral over [0, t] in units of that width) equals the
+ * remaining share D' = D / frac.  That is the quadratic
+ *     b t^2 + (n_a s_a^2 - D' b) t - D' n_a = 0,  s_a^2 = 1 - 1/(beta n_a)^2,
+ * whose root in [0, 1] is taken as t = 2 D' n_a / (P + sqrt(P^2 + 4 b D' n_a)),
+ * P = n_a s_a^2 - D' b (b <= 0, so P >= 0 and nothing cancels).  kappa and
+ * the wavenumber follow linearly; the Cherenkov angle is that of the
+ * bunch's index at the step midpoint: cos = 1/(beta n), sin^2 in the
+ * cancellation-free form. */
+static void orc_disp_sample(const orc_cfg *C, const orc_yield *Y, double u2, double *lam,
+                            double *kap, double *cos_c, double *sin_c)
+{
+    int K = C->disp_k;
+    double T = u2 * Y->psum;
+    int m = 0;
+    double acc = 0.0;
+    while (m < K - 2) {
+        double nxt = acc + Y->piece[m];
+        if (T < nxt) break;
+        acc = nxt;
+        ++m;
+    }
+    double eta = Y->eta;
+    double frac = Y->frac[m];
+    double ka = C->disp_kappa[m], kb = C->disp_kappa[m + 1];
+    double ea = eta * ka;
+    double x_end = (frac < 1.0) ? Y->x_th : eta * kb;
+    double D = T - acc;
+    if (D < 0.0) D = 0.0;
+    double Dp = (frac > 0.0) ? D / frac : 0.0;
+    double na = 1.0 + ea;
+    double eaa = ea * (2.0 + ea);
+    double s2a = (eaa * Y->gam2 - (1.0 + eaa)) / (Y->bg2 * (1.0 + eaa));
+    if (!(s2a > 0.0)) s2a = 0.0;
+    double b = x_end - ea;
+    double P = na * s2a - Dp * b;
+    double disc = P * P + 4.0 * b * Dp * na;
+    if (!(disc > 0.0)) disc = 0.0;
+    double den = P + sqrt(disc);
+    double t = (den > 0.0) ? (2.0 * Dp * na) / den : 0.0;
+    if (t > 1.0) t = 1.0;
+    if (!(t > 0.0)) t = 0.0;
+    double sm = t * frac;                 /* position inside the whole piece */
+    double k = ka + sm * (kb - ka);
+    double inv1 = 1.0 / C->lambda1_nm, inv2 = 1.0 / C->lambda2_nm;
+    double du = (inv1 - inv2) / (double)(K - 1);
+    double u = inv1 - ((double)m + sm) * du;
+    *lam = 1.0 / u;
+    *kap = k;
+    double e = eta * k;
+    double ee = e * (2.0 + e);
+    double s2 = (ee * Y->gam2 - (1.0 + ee)) / (Y->bg2 * (1.0 + ee));
+    if (!(s2 > 0.0)) s2 = 0.0;
+    *sin_c = sqrt(s2);
+    *cos_c = 1.0 / (Y->beta * (1.0 + e));
+}
 
 /* ======================================================================= */
 /* Atmospheric transmission (an extension: the paper's RAYBND only bends   */
@@ -657,8 +865,11 @@ static void orc_one_bunch(const orc_cfg *C, const orc_tracks *Tk, int64_t i, int
                           int64_t nb, const orc_yield *Y, int variant, orc_bunch1 *B)
 {
     double ux = Tk->ux[i], uy = Tk->uy[i], uz = Tk->uz[i];
-    double cos_c = 1.0 / (Y->beta * (1.0 + Y->eta));
-    double sin_c = sqrt(Y->s2);
+    double cos_c = 0.0, sin_c = 0.0;
+    if (C->disp_k == 0) {
+        cos_c = 1.0 / (Y->beta * (1.0 + Y->eta));
+        sin_c = sqrt(Y->s2);
+    }
     /* azimuth basis around the step direction */
     double e1x, e1y, e1z = 0.0;
     double rho2 = ux * ux + uy * uy;
@@ -680,9 +891,14 @@ static void orc_one_bunch(const orc_cfg *C, const orc_tracks *Tk, int64_t i, int
     /* sub-step j, emission point uniform inside it */
     double f = ((double)j + u0) / (double)nb;
     double phi = 2.0 * ORC_PI * u1;
-    /* 1/lambda^2 spectrum on [lambda1, lambda2] by inversion */
-    double inv1 = 1.0 / C->lambda1_nm, inv2 = 1.0 / C->lambda2_nm;
-    B->lam = 1.0 / (inv1 - u2 * (inv1 - inv2));
+    B->kappa = 1.0;
+    if (C->disp_k > 0) {
+        orc_disp_sample(C, Y, u2, &B->lam, &B->kappa, &cos_c, &sin_c);
+    } else {
+        /* 1/lambda^2 spectrum on [lambda1, lambda2] by inversion */
+        double inv1 = 1.0 / C->lambda1_nm, inv2 = 1.0 / C->lambda2_nm;
+        B->lam = 1.0 / (inv1 - u2 * (inv1 - inv2));
+    }
     double cp = cos(phi), sp = sin(phi);
     B->px = cos_c * ux + sin_c * (cp * e1x + sp * e2x);
     B->py = cos_c * uy + sin_c * (cp * e1y + sp * e2y);
@@ -693,8 +909,8 @@ static void orc_one_bunch(const orc_cfg *C, const orc_tracks *Tk, int64_t i, int
     B->ye = Tk->y0[i] + fl * uy;
     B->he = Tk->z0[i] + fl * uz;
     B->te = Tk->t0[i] + fl * inv_bc;
-    B->status = orc_propagate_photon(C, variant, B->xe, B->ye, B->he, B->te, B->px, B->py,
-                                     B->pz, B->r);
+    B->status = orc_propagate_photon_k(C, variant, B->kappa, B->xe, B->ye, B->he, B->te,
+                                       B->px, B->py, B->pz, B->r);
     B->tr_margin = NAN;
     if (B->status == ORC_ST_GROUND && C->trans_tau) {
         double tau = orc_trans_tau(C, B->lam, B->he);
@@ -725,9 +941,9 @@ int orc_bunches(const orc_cfg *C, const orc_tracks *Tk, uint64_t seed,
     orc_cfg Cs = *C;
     Cs.philox_key[0] = (uint32_t)(seed & 0xffffffffu);
     Cs.philox_key[1] = (uint32_t)(seed >> 32);
-    double np1_obs_T = 1.0 + orc_eta_lookup(C->eta_tab, C->n_fine, C->h_max, C->h_obs);
-    double np1_obs_B = 1.0 + orc_eta_exact(&C->atm, C->h_obs);
-    double np1_obs = (variant == 0) ? np1_obs_T : np1_obs_B;
+    double eta_obs_T = orc_eta_lookup(C->eta_tab, C->n_fine, C->h_max, C->h_obs);
+    double eta_obs_B = orc_eta_exact(&C->atm, C->h_obs);
+    double eta_obs = (variant == 0) ? eta_obs_T : eta_obs_B;
 
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < Tk->n; ++i) {
@@ -754,6 +970,7 @@ int orc_bunches(const orc_cfg *C, const orc_tracks *Tk, uint64_t seed,
             double t = B.r[2] - t_ref;
             O->X[bidx] = B.r[0]; O->Y[bidx] = B.r[1]; O->t[bidx] = t;
             O->cx[bidx] = B.r[3]; O->cy[bidx] = B.r[4]; O->cz[bidx] = B.r[5];
+            double np1_obs = 1.0 + B.kappa * eta_obs;
             O->nhit[bidx] = orc_telescopes(&Cs, B.r[0], B.r[1], t, B.r[3], B.r[4], B.r[5],
                                            np1_obs,
                                            O->hit_tel + ORC_MAX_HITS * bidx,
