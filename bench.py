@@ -340,6 +340,11 @@ def run_ours(args):
     ctx.set_transmission(workloads.synthetic_transmission(h_obs=sc["h_obs"], h_max=sc["h_max"]))
     r32t = measure(P.CHER_FP32_BULK, steps, max(3, min(warmup, 3)), autotune=False, reuse=r32)
     ctx.set_transmission(None)
+    # the wavelength-dependent index (Edlen's dispersion of standard air, 9 nodes)
+    ctx.set_dispersion(workloads.synthetic_dispersion(lambda1_nm=sc["lambda1_nm"],
+                                                      lambda2_nm=sc["lambda2_nm"]))
+    r32d = measure(P.CHER_FP32_BULK, steps, max(3, min(warmup, 3)), autotune=False, reuse=r32)
+    ctx.set_dispersion(None)
 
     def total(r):
         return reduce_over_ranks(sum(r["ms"]) / 1e3, float(r["stats"][3]) * len(r["ms"]),
@@ -569,6 +574,12 @@ def run_ours(args):
                          "overhead": statistics.mean(r32t["ms"]) / statistics.mean(r32["ms"]) - 1,
                          "absorbed_frac": float(r32t["stats"][11]) / float(r32t["stats"][3]),
                          "table": "synthetic Rayleigh + aerosol, 16 x 121"},
+        "dispersion": {"ms_per_step": statistics.mean(r32d["ms"]),
+                       "overhead": statistics.mean(r32d["ms"]) / statistics.mean(r32["ms"]) - 1,
+                       "value": float(r32d["stats"][3]) / (statistics.mean(r32d["ms"]) / 1e3),
+                       "unit": UNIT, "bunches_per_step": int(r32d["stats"][3]),
+                       "curve": "Edlen 1966 standard air, kappa = 1 at 400 nm, 9 nodes in "
+                                "1/lambda"},
         "profile": {"ms_per_step": statistics.mean(r32p["ms"]),
                     "overhead": statistics.mean(r32p["ms"]) / statistics.mean(r32["ms"]) - 1.0,
                     "bins": int(prof_t.shape[1]), "bin_gcm2": 10.0, "rows": n_rows,

@@ -414,11 +414,13 @@ cher_status cher_set_transmission(cher_ctx *ctx, const cher_transmission *table)
  * tables' range but within `zenith_max_deg` are propagated by the ray
  * integrals themselves -- n(h) sin(theta(h)) = n_obs sin(theta_obs) in the
  * layered atmosphere, D = int tan(theta) dh, L = int n / cos(theta) dh,
- * FP64, 12-point Gauss-Legendre on each layer's part -- instead of being
+ * 12-point Gauss-Legendre on each layer's part, in FP64 on the FP64 path
+ * and in FP32 on the FP32 path (there as the straight line at the arrival
+ * zenith plus the integrals of the small corrections) -- instead of being
  * dropped (stats[CHER_STAT_ANGLE]).  The generation launch queues them and
  * a second kernel on the same stream propagates them (stats
  * [CHER_STAT_FALLBACK]); the queue holds `queue_records` bunches per call
- * (0: max(2^20, 4 x the call's steps); 64 B each in FP32, 96 B in FP64,
+ * (0: max(2^20, 4 x the call's steps); 64 B each in FP32, 112 B in FP64,
  * allocated on the first call that needs them), the rest counted in
  * stats[CHER_STAT_FB_LOST].  Trace launches integrate them in place.  The
  * adjoint and the allocation-free launch do not use it (those bunches stay
@@ -427,6 +429,33 @@ cher_status cher_set_transmission(cher_ctx *ctx, const cher_transmission *table)
  *   queue_records : 0 or up to 2^34.
  * Errors: CHER_EINVAL. */
 cher_status cher_set_fallback(cher_ctx *ctx, double zenith_max_deg, int64_t queue_records);
+
+/* Wavelength-dependent index of refraction (an extension: the paper's
+ * CERENK and RAYBND take n independent of the wavelength).  With kappa set,
+ *     n(h, lambda) - 1 = (n(h) - 1) kappa(lambda),
+ * n(h) the atmosphere's index (n0_minus_1 at the reference wavelength) and
+ * kappa linear in the wavenumber 1/lambda between k nodes, node m at
+ *     1/lambda_m = 1/lambda_min - m (1/lambda_min - 1/lambda_max) / (k - 1)
+ * (node 0 at the band's short end).  Then, per step, the yield is the
+ * Frank-Tamm integral of 1 - 1/(beta n(lambda))^2 over the radiating part of
+ * the band (exact: a closed form on each linear piece, the Cherenkov
+ * threshold cutting at most one piece); per bunch, the wavelength inverts
+ * the step's spectrum with the third Philox deviate (from the short end,
+ * like the constant-index 1/lambda^2 draw), the Cherenkov cone, Snell's law
+ * and the sphere-plane time use the bunch's own index, and the refraction
+ * corrections are interpolated linearly in kappa between tables built for
+ * kappa[k-1] and kappa[0] (the context's table sizes; rebuilt with the
+ * tables by cher_build_refraction_tables and cher_set_atmosphere).
+ *   kappa : host, k values, finite, > 0 and not increasing with m (normal
+ *           dispersion: n falls towards long wavelengths), copied;
+ *           kappa[0] n0_minus_1 < 0.01;
+ *   k     : 2 .. CHER_DISPERSION_MAX_NODES; kappa NULL or k = 0 turns it off.
+ * Launches with it run 128-step tiles whatever cher_set_launch chose.  The
+ * read-out and its adjoint refuse a context with it (CHER_EINVAL).
+ * Blocking.  Errors: CHER_EINVAL, CHER_ESTATE (tables not built yet),
+ * CHER_ENOMEM, CHER_ECUDA. */
+#define CHER_DISPERSION_MAX_NODES 9
+cher_status cher_set_dispersion(cher_ctx *ctx, const double *kappa, int32_t k);
 
 /* Replace the atmosphere and, if tables were built, rebuild them with the
  * same sizes (blocking).  Errors as cher_build_refraction_tables. */

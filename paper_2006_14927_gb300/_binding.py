@@ -110,6 +110,7 @@ SIGNATURES = {
     "cher_round_to_float": (_S, [_P, _P, ctypes.c_int64, _P]),
     "cher_set_transmission": (_S, [_P, ctypes.POINTER(Transmission)]),
     "cher_set_fallback": (_S, [_P, ctypes.c_double, ctypes.c_int64]),
+    "cher_set_dispersion": (_S, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
     "cher_generate_steps": (_S, [_P, ctypes.POINTER(Shower), ctypes.c_int32, ctypes.c_uint64, _S,
                                  ctypes.POINTER(StepBuffers), _P]),
     "cher_generate_propagate_noalloc": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
@@ -482,6 +483,17 @@ class Context:
                          float(table["height_m"][1]),
                          tau.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         _check(lib().cher_set_transmission(self._h, ctypes.byref(T)), "cher_set_transmission")
+
+    def set_dispersion(self, kappa):
+        """Wavelength-dependent index: kappa at 2..9 nodes uniform in
+        1/lambda from the band's short end, n(h, lambda) - 1 = (n(h) - 1)
+        kappa; None turns it off."""
+        if kappa is None:
+            _check(lib().cher_set_dispersion(self._h, None, 0), "cher_set_dispersion")
+            return
+        k = np.ascontiguousarray(np.asarray(kappa, dtype=np.float64).ravel())
+        _check(lib().cher_set_dispersion(self._h, k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         int(k.size)), "cher_set_dispersion")
 
     def set_atmosphere(self, atm: dict):
         A = atmosphere_struct(atm)

@@ -71,6 +71,14 @@ struct cher_ctx {
     unsigned char *d_gen = nullptr;
     int64_t gen_cap = 0;
     std::map<std::pair<double, double>, std::vector<float>> cdf_cache;
+    // wavelength-dependent index: kappa at the nodes (disp_k = 0: off), its
+    // device copies, and the refraction tables of the band's two ends in
+    // the pair-interleaved layout, {kappa_lo entry, kappa_hi entry}
+    int32_t disp_k = 0;
+    double kap[cher::kDispMax] = {};
+    double *d_kap64 = nullptr;
+    float *d_kap32 = nullptr;
+    void *d_tabd64 = nullptr, *d_tabd32 = nullptr;
 };
 
 namespace {
@@ -100,6 +108,16 @@ void free_tables(cher_ctx *c) {
     cudaFree(c->d_sens);
     c->d_sens = nullptr;
     c->built = false;
+}
+
+void free_dispersion_tables(cher_ctx *c) {
+    cudaFree(c->d_kap64);
+    cudaFree(c->d_kap32);
+    cudaFree(c->d_tabd64);
+    cudaFree(c->d_tabd32);
+    c->d_kap64 = nullptr;
+    c->d_kap32 = nullptr;
+    c->d_tabd64 = c->d_tabd32 = nullptr;
 }
 
 void free_adjoint_scratch(cher_ctx *c) {
@@ -162,6 +180,54 @@ cher_status upload_grid(cher_ctx *c, int g) {
         (r = upload(&c->d_cand32[g], c32.data(), c32.size())) != CHER_OK ||
         (r = upload(&c->d_cand64[g], c64.data(), c64.size())) != CHER_OK)
         return r;
+    return CHER_OK;
+}
+
+// The refraction tables of kappa[k-1] (lo) and kappa[0] (hi): the context's
+// table shape with n - 1 scaled by kappa, interleaved per entry.
+cher_status build_dispersion_tables(cher_ctx *c) {
+    free_dispersion_tables(c);
+    if (c->disp_k == 0) return CHER_OK;
+    const double th = c->tab_zen * cher::kPi / 180.0;
+    cher::HostTables T[2];
+    for (int s = 0; s < 2; ++s) {
+        cher_atmosphere a = c->atm;
+        a.n0_minus_1 *= s == 0 ? c->kap[c->disp_k - 1] : c->kap[0];
+        const cher_status r = cher::build_tables(a, c->h_obs, 2, c->tab_H, c->tab_Z, th,
+                                                 c->tab_hmax, T[s]);
+        if (r != CHER_OK) return r;
+    }
+    const int H = T[0].H, Z = T[0].Z;
+    std::vector<double> t64(static_cast<size_t>(H) * (Z - 1) * 8);
+    std::vector<float> t32(t64.size());
+    for (int j = 0; j < H; ++j)
+        for (int k = 0; k < Z - 1; ++k) {
+            const size_t e = (static_cast<size_t>(j) * (Z - 1) + k) * 8;
+            const size_t a = static_cast<size_t>(j) * Z + k;
+            for (int s = 0; s < 2; ++s) {
+                t64[e + 4 * s + 0] = T[s].ax[a];
+                t64[e + 4 * s + 1] = T[s].al[a];
+                t64[e + 4 * s + 2] = T[s].ax[a + 1];
+                t64[e + 4 * s + 3] = T[s].al[a + 1];
+            }
+            for (int q = 0; q < 8; ++q) t32[e + q] = static_cast<float>(t64[e + q]);
+        }
+    float k32[cher::kDispMax];
+    for (int m = 0; m < cher::kDispMax; ++m) k32[m] = static_cast<float>(c->kap[m]);
+    double *d64 = nullptr;
+    float *d32 = nullptr;
+    cher_status r;
+    if ((r = upload(&c->d_kap64, c->kap, cher::kDispMax)) != CHER_OK ||
+        (r = upload(&c->d_kap32, k32, cher::kDispMax)) != CHER_OK ||
+        (r = upload(&d64, t64.data(), t64.size())) != CHER_OK ||
+        (r = upload(&d32, t32.data(), t32.size())) != CHER_OK) {
+        cudaFree(d64);
+        cudaFree(d32);
+        free_dispersion_tables(c);
+        return r;
+    }
+    c->d_tabd64 = d64;
+    c->d_tabd32 = d32;
     return CHER_OK;
 }
 
@@ -241,6 +307,25 @@ cher::KParams base_params(const cher_ctx *c, const cher_tracks *t, uint64_t seed
         const double sf = std::sin(c->fb_deg * 3.14159265358979323846 / 180.0);
         p.fb_q = sf * sf;
     }
+    if (c->disp_k > 0) {
+        p.disp_k = c->disp_k;
+        for (int m = 0; m < cher::kDispMax; ++m) p.kap[m] = c->kap[m];
+        p.kap64 = c->d_kap64;
+        p.kap32 = c->d_kap32;
+        // 2 pi alpha du, du = (1/lambda_min - 1/lambda_max) / (k - 1) in 1/m
+        const double two_pi_alpha = (2.0 * cher::kPi) * cher::kAlpha;
+        const double inv1 = 1.0e9 / c->opt.lambda_min_nm;
+        const double inv2 = 1.0e9 / c->opt.lambda_max_nm;
+        const double dinv = inv1 - inv2;
+        const double du = dinv / static_cast<double>(c->disp_k - 1);
+        p.disp_Kd = two_pi_alpha * du;
+        p.disp_u1 = 1.0 / c->opt.lambda_min_nm;
+        p.disp_du = (1.0 / c->opt.lambda_min_nm - 1.0 / c->opt.lambda_max_nm) /
+                    static_cast<double>(c->disp_k - 1);
+        p.kap_lo = c->kap[c->disp_k - 1];
+        p.kap_winv = c->kap[0] > p.kap_lo ? 1.0 / (c->kap[0] - p.kap_lo) : 0.0;
+        p.tabd = fp32 ? c->d_tabd32 : c->d_tabd64;
+    }
     if (c->d_trans64) {
         p.trans = fp32 ? static_cast<const void *>(c->d_trans32) : c->d_trans64;
         p.trans_nl = c->trans_nl;
@@ -256,7 +341,7 @@ cher::KParams base_params(const cher_ctx *c, const cher_tracks *t, uint64_t seed
 
 cher_status launch(cher_ctx *c, cher::KParams &p, bool fp32, int mode, bool persistent,
                    void *stream) {
-    const int block = c->block;
+    const int block = p.disp_k > 0 ? cher::kDispBlock : c->block;
     p.n_tiles = (p.n + block - 1) / block;
     if (p.n_tiles == 0) return CHER_OK;
     const size_t smem = cher::kernel_smem_bytes(fp32, block, p);
@@ -440,7 +525,7 @@ cher_status cher_build_refraction_tables(cher_ctx *c, int32_t n_heights, int32_t
     c->tab_Z = n_zenith;
     c->tab_zen = zenith_max_deg;
     c->tab_hmax = h_max;
-    return CHER_OK;
+    return build_dispersion_tables(c);
 }
 
 cher_status cher_set_atmosphere(cher_ctx *c, const cher_atmosphere *atm) {
@@ -495,6 +580,28 @@ cher_status cher_set_transmission(cher_ctx *c, const cher_transmission *tb) {
     c->trans_h0 = tb->h_min;
     c->trans_h1 = tb->h_max;
     return CHER_OK;
+}
+
+cher_status cher_set_dispersion(cher_ctx *c, const double *kappa, int32_t k) {
+    if (!c) return CHER_EINVAL;
+    if (!check_device(c)) return CHER_EINVAL;
+    if (!kappa || k == 0) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return CHER_ECUDA;
+        free_dispersion_tables(c);
+        c->disp_k = 0;
+        return CHER_OK;
+    }
+    if (k < 2 || k > cher::kDispMax) return CHER_EINVAL;
+    for (int m = 0; m < k; ++m)
+        if (!std::isfinite(kappa[m]) || !(kappa[m] > 0.0) || (m > 0 && kappa[m] > kappa[m - 1]))
+            return CHER_EINVAL;
+    if (!c->built) return CHER_ESTATE;
+    if (cudaDeviceSynchronize() != cudaSuccess) return CHER_ECUDA;
+    c->disp_k = k;
+    for (int m = 0; m < cher::kDispMax; ++m) c->kap[m] = m < k ? kappa[m] : 0.0;
+    const cher_status r = build_dispersion_tables(c);
+    if (r != CHER_OK) c->disp_k = 0;
+    return r;
 }
 
 cher_status cher_generate_steps(cher_ctx *c, const cher_shower *sh, int32_t n_showers,
@@ -607,6 +714,7 @@ cher_status cher_destroy(cher_ctx *c) {
     free_tables(c);
     free_adjoint_scratch(c);
     free_transmission(c);
+    free_dispersion_tables(c);
     cudaFree(c->d_gen);
     cudaFree(c->d_fb);
     cudaFree(c->d_fb_count);
@@ -705,7 +813,8 @@ cher_status cher_generate_propagate_ex(cher_ctx *c, const cher_tracks *t, uint64
     }
     cher_status r = launch(c, p, fp32, cher::MODE_HITS, true, stream);
     if (r != CHER_OK || !fb || p.n == 0) return r;
-    if (cher::launch_fallback(fp32, p.trans != nullptr, p, c->num_sms, stream) != cudaSuccess) {
+    if (cher::launch_fallback(fp32, p.trans != nullptr, p.disp_k > 0, p, c->num_sms, stream) !=
+        cudaSuccess) {
         cudaGetLastError();
         return CHER_ECUDA;
     }
@@ -898,6 +1007,7 @@ cher_status readout(cher_ctx *c, const cher_tracks *t, uint64_t seed, cher_preci
     if (!c || !tracks_ok(t)) return CHER_EINVAL;
     if (prec != CHER_FP64 && prec != CHER_FP32_BULK) return CHER_EINVAL;
     if (!(sigma > 0.0) || !std::isfinite(sigma)) return CHER_EINVAL;
+    if (c->disp_k > 0) return CHER_EINVAL;   // defined for a wavelength-independent index
     if (!c->built) return CHER_ESTATE;
     if (!check_device(c)) return CHER_EINVAL;
     if (t->n > 0x7fffffffLL) return CHER_ERANGE;
@@ -1209,7 +1319,7 @@ extern "C" cher_status cher_generate_propagate_noalloc(cher_ctx *c, const cher_t
     p.cap = out->cap_per_tel;
     p.count = out->count;
     p.stats = out->stats;
-    const int block = c->block;
+    const int block = p.disp_k > 0 ? cher::kDispBlock : c->block;
     p.n_tiles = (p.n + block - 1) / block;
     if (p.n_tiles == 0) return CHER_OK;
     const size_t smem = cher::kernel_smem_bytes(fp32, block, p);

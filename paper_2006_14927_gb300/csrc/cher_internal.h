@@ -26,6 +26,7 @@ enum : int32_t {
 };
 
 constexpr int kMaxCandPerCell = 32;   // telescope candidates in one grid cell
+constexpr int kDispMax = 9;           // nodes of a wavelength-dependent index
 
 // Host-side tables, all FP64 (step a0).
 struct HostTables {
@@ -149,6 +150,18 @@ struct KParams {
     const void *trans;
     int32_t trans_nl, trans_nh;
     double trans_l0, trans_lscale, trans_h0, trans_hscale;
+    // wavelength-dependent index (disp_k = 0: off): n - 1 = eta(h) kappa,
+    // kappa at disp_k nodes uniform in 1/lambda from 1/lambda_min (node 0),
+    // linear between them; the yield's band factor per piece disp_Kd =
+    // 2 pi alpha du (du in 1/m); tabd: the refraction tables of kappa at the
+    // band's two ends, entry (j, k) = {entry of kap_lo, entry of kap_hi} in
+    // the pair-interleaved layout of tab; weight (kappa - kap_lo) kap_winv
+    int32_t disp_k;
+    double kap[kDispMax];
+    const double *kap64;
+    const float *kap32;
+    double disp_Kd, disp_u1, disp_du, kap_lo, kap_winv;
+    const void *tabd;
     // the per-launch constants of the bunch loop, rounded to float on the
     // host: the FP32 path converts nothing from double on the device
     struct {
@@ -161,6 +174,8 @@ struct KParams {
         float trans_l0, trans_lscale, trans_h0, trans_hscale;
         float fb_q;
         float hb[6], a[5], b[5], c[5], inv_c[5], t_top[5];
+        float kap[kDispMax], disp_Kd, disp_u1, disp_du, kap_lo, kap_winv;
+        float eta_coef[5], gl_x[12], gl_w[12];
     } f;
 };
 
@@ -193,15 +208,21 @@ enum Mode : int { MODE_HITS = 0, MODE_TRACE = 1, MODE_YIELD = 2, MODE_SCREEN = 3
 // tables' zenith range
 constexpr int kTransBit = 4;
 constexpr int kFbBit = 8;
+// and when the index depends on the wavelength (instantiated for 128-step
+// tiles and the hits, trace and yield modes only)
+constexpr int kDispBit = 16;
+constexpr int kDispBlock = 128;
 inline int kernel_mode(int mode, const KParams &p) {
     int m = mode;
     if (p.trans && mode != MODE_YIELD) m |= kTransBit;
     if (p.fb_q > 0.0 && (mode == MODE_HITS || mode == MODE_TRACE)) m |= kFbBit;
+    if (p.disp_k > 0) m |= kDispBit;
     return m;
 }
 // The fallback pass over the queued bunches (after a MODE_HITS launch with
 // fb_q > 0, on the same stream; reads the queue's count on the device).
-cudaError_t launch_fallback(bool fp32, bool tr, const KParams &p, int num_sms, void *stream);
+cudaError_t launch_fallback(bool fp32, bool tr, bool disp, const KParams &p, int num_sms,
+                            void *stream);
 // Bytes of one fallback queue record.
 size_t fallback_record_bytes(bool fp32);
 // The 12-point Gauss-Legendre rule on [-1, 1] (host).

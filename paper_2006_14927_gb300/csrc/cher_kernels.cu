@@ -130,6 +130,257 @@ __device__ __forceinline__ void step_yield_screened(const KParams &p, bool other
     y.N = static_cast<float>(yd.N);
 }
 
+// ------------------------------------------------------------------------
+// a1 with a wavelength-dependent index, n(u) = 1 + eta kappa(u) with kappa
+// linear in the wavenumber u = 1/lambda between nodes.  On each piece the
+// Frank-Tamm integral of 1 - 1/(beta n)^2 is exact in closed form,
+//     width (1 - 1/(beta^2 n_a n_b)) = width [e gamma^2 - (1 + e)] / [g (2 + g) (1 + e)],
+//     e = e_a + e_b + e_a e_b,  e_a = eta kappa_a,
+// and the Cherenkov threshold eta kappa = x_th = 1 / (gamma^2 beta (1 + beta))
+// cuts at most one piece (kappa falls along the nodes), whose radiating
+// fraction (e_a - x_th) / (e_a - e_b) ends at the threshold.  The step keeps
+// the cumulative shares of the pieces for the bunches' wavelengths.
+// ------------------------------------------------------------------------
+template <class R>
+struct alignas(16) SegD {
+    R cdf[kDispMax - 1];     // cumulative shares (integral / piece width)
+    R eta, beta;             // at the step midpoint
+    R x_th;                  // the threshold's eta kappa, 1/beta - 1
+    R frac_cut;              // the piece the threshold cuts: its radiating fraction
+    int m_cut, pad;          // and index (disp_k - 1: none)
+};
+
+__device__ __forceinline__ double disp_piece(double x, double y, double gam2, double bg2) {
+    const double xy = __dmul_rn(x, y);
+    const double xpy = __dadd_rn(x, y);
+    const double e = __dadd_rn(xpy, xy);
+    const double np = __dadd_rn(1.0, e);
+    const double A = __dmul_rn(e, gam2);
+    const double num = __dsub_rn(A, np);
+    const double den = __dmul_rn(bg2, np);
+    const double S = __ddiv_rn(num, den);
+    return S > 0.0 ? S : 0.0;
+}
+
+// the exact FP64 chain (same operation order as the oracle)
+template <class R>
+__device__ __forceinline__ void step_yield_disp(const KParams &p, bool others_valid, double z0,
+                                                double len, double ekin, double uz, Yield &y,
+                                                SegD<R> &D) {
+    y.nb = 0;
+    y.valid = false;
+    y.N = y.s2 = y.g = y.gam = y.eta = 0.0;
+    if (!others_valid || !finite_d(z0) || !finite_d(len) || !finite_d(ekin) || !finite_d(uz) ||
+        len < 0.0 || ekin <= 0.0)
+        return;
+    const double g = __dmul_rn(ekin, p.inv_me);
+    const double gam = __dadd_rn(1.0, g);
+    const double gam2 = __dmul_rn(gam, gam);
+    const double half_len = __dmul_rn(0.5, len);
+    const double dz = __dmul_rn(half_len, uz);
+    const double hm = __dadd_rn(z0, dz);
+    const double eta = eta_exact_lookup(p, hm);
+    const double two_g = __dadd_rn(2.0, g);
+    const double bg2 = __dmul_rn(g, two_g);
+    const double beta = __ddiv_rn(__dsqrt_rn(bg2), gam);
+    const double onepb = __dadd_rn(1.0, beta);
+    const double gb = __dmul_rn(gam2, beta);
+    const double gbb = __dmul_rn(gb, onepb);
+    const double x_th = __ddiv_rn(1.0, gbb);
+    y.g = g;
+    y.gam = gam;
+    y.eta = eta;
+    y.valid = true;
+    double sum = 0.0, frac_cut = 1.0;
+    int m_cut = p.disp_k - 1;
+#pragma unroll
+    for (int m = 0; m < kDispMax - 1; ++m) {
+        if (m + 1 < p.disp_k) {
+            const double ea = __dmul_rn(eta, p.kap[m]);
+            const double eb = __dmul_rn(eta, p.kap[m + 1]);
+            double v = 0.0;
+            if (ea > x_th) {
+                if (eb >= x_th) {
+                    v = disp_piece(ea, eb, gam2, bg2);
+                } else {
+                    const double f = __ddiv_rn(__dsub_rn(ea, x_th), __dsub_rn(ea, eb));
+                    v = __dmul_rn(f, disp_piece(ea, x_th, gam2, bg2));
+                    m_cut = m;
+                    frac_cut = f;
+                }
+            }
+            sum = __dadd_rn(sum, v);
+            D.cdf[m] = static_cast<R>(sum);
+        }
+    }
+    D.eta = static_cast<R>(eta);
+    D.beta = static_cast<R>(beta);
+    D.x_th = static_cast<R>(x_th);
+    D.frac_cut = static_cast<R>(frac_cut);
+    D.m_cut = m_cut;
+    if (!(sum > 0.0)) return;                  // below threshold over the whole band
+    const double Ks = __dmul_rn(p.disp_Kd, sum);
+    const double N = __dmul_rn(len, Ks);
+    const double q = __dmul_rn(N, p.inv_B);
+    if (!(q < 4194304.0)) {
+        y.valid = false;
+        return;
+    }
+    y.nb = static_cast<int>(ceil(q));
+    y.N = N;
+    y.s2 = sum;
+}
+
+// The FP32 screen: every piece whole (every node clearly above the
+// threshold) and ceil(q) certain under the rounding bound, or every node
+// clearly below it; anything else (a cut piece, strong cancellation, an
+// integer within reach) takes the exact chain.
+__device__ __forceinline__ void step_yield_screened_disp(const KParams &p, bool others_valid,
+                                                         double z0, double len, double ekin,
+                                                         float uz, YieldF &y, SegD<float> &D) {
+    y.nb = 0;
+    y.valid = false;
+    y.g = y.eta = y.s2 = y.N = 0.0f;
+    if (!others_valid || !finite_d(z0) || !finite_d(len) || !finite_d(ekin) || !finite_f(uz) ||
+        d_negative(len) || d_not_positive(ekin))
+        return;
+    y.valid = true;
+    const float u = 5.9604645e-8f;                       // 2^-24
+    const float e = d2f_rn(ekin), L = d2f_rn(len);
+    const float z = d2f_rn(z0);
+    const float g = e * p.f.inv_me;
+    const float gam = 1.0f + g, gam2 = gam * gam;
+    const float hm = z + (0.5f * L) * uz;
+    float hc = fminf(fmaxf(hm, 0.0f), p.f.h_max);
+    const float x = hc * p.f.inv_dh;
+    int k = static_cast<int>(x);
+    k = k > p.n_fine - 2 ? p.n_fine - 2 : k;
+    const float f = x - static_cast<float>(k);
+    const float t0 = __ldg(p.eta32 + k), t1 = __ldg(p.eta32 + k + 1);
+    const float eta = t0 + f * (t1 - t0);
+    const float bg2 = g * (2.0f + g);
+    const float beta = sqrtf(bg2) / gam;
+    const float x_th = 1.0f / (gam2 * beta * (1.0f + beta));
+    const float d_eta = 6.0f * u * p.f.eta_slope * (fabsf(z) + L + p.f.dh) + 5.0f * u * eta;
+    const float tol_x = 64.0f * u * x_th;
+    const float e_hi = eta * p.f.kap[0], e_lo = eta * p.f.kap_lo;
+    const int K = p.disp_k;
+    if (e_hi + p.f.kap[0] * d_eta + 4.0f * u * e_hi < x_th - tol_x) return;   // below, surely
+    if (e_lo - p.f.kap_lo * d_eta - 4.0f * u * e_lo > x_th + tol_x) {
+        float sum = 0.0f, dsum = 0.0f;
+        bool mild = true;
+#pragma unroll
+        for (int m = 0; m < kDispMax - 1; ++m) {
+            if (m + 1 < K) {
+                const float ka = p.f.kap[m], kb = p.f.kap[m + 1];
+                const float ea = eta * ka, eb = eta * kb;
+                const float ee = (ea + eb) + ea * eb;
+                const float B = 1.0f + ee, A = ee * gam2;
+                const float num = A - B, den = bg2 * B;
+                const float S = num / den;
+                const float d_e = (ka + kb) * (1.0f + ee) * d_eta + 4.0f * u * ee;
+                const float d_A = gam2 * (d_e + 10.0f * u * ee);
+                const float d_B = d_e + 3.0f * u * B;
+                const float d_num = d_A + d_B + u * (A + B);
+                dsum += d_num / den + fabsf(S) * (12.0f * u + 2.0f * d_eta);
+                mild = mild && num >= 0.01f * (A + B);
+                sum += S;
+                D.cdf[m] = sum;
+            }
+        }
+        const float KL = p.f.disp_Kd * L;
+        const float q = KL * sum * p.f.inv_B;
+        const float E = 4.0f * (KL * p.f.inv_B * dsum +
+                                fabsf(q) * (8.0f + static_cast<float>(K)) * u) + 1e-30f;
+        const float lo = q - E, hi = q + E;
+        if (lo > 0.0f && ceilf(lo) == ceilf(hi) && mild && hi < 4.0e6f) {
+            y.nb = static_cast<int>(ceilf(hi));
+            y.g = g;
+            y.eta = eta;
+            y.s2 = sum;
+            y.N = KL * sum;
+            D.eta = eta;
+            D.beta = beta;
+            D.x_th = x_th;
+            D.frac_cut = 1.0f;
+            D.m_cut = K - 1;
+            return;
+        }
+    }
+    Yield yd;
+    step_yield_disp<float>(p, true, z0, len, ekin, static_cast<double>(uz), yd, D);
+    y.valid = yd.valid;
+    y.nb = yd.nb;
+    y.g = static_cast<float>(yd.g);
+    y.eta = static_cast<float>(yd.eta);
+    y.s2 = static_cast<float>(yd.s2);
+    y.N = static_cast<float>(yd.N);
+}
+
+// A bunch's wavelength from its step's spectrum (density 1 - 1/(beta n)^2
+// in u over the radiating part of the band) by inversion of u2 from the
+// band's short end: the piece m whose cumulative share first exceeds
+// u2 * total, then the fraction t of its radiating width where
+//     G(t) = t - t / (beta^2 n_a n(t)),  n(t) = n_a + b t
+// equals the remaining share D' (the quadratic b t^2 + (n_a s_a^2 - D' b) t
+// - D' n_a = 0, root 2 D' n_a / (P + sqrt(P^2 + 4 b D' n_a)), P = n_a s_a^2 -
+// D' b >= 0 since b <= 0).  Returns lambda, kappa and the cone of the
+// bunch's index at the step midpoint.  Near the threshold 1 - 1/(beta n)^2
+// cancels; with beta n - 1 = beta (eta kappa - x_th), x_th = 1/beta - 1,
+//     s^2 = b_d (2 + b_d) / (1 + b_d)^2,  cos = 1 - b_d / (1 + b_d),
+//     b_d = beta (eta kappa - x_th),
+// neither does, and the cosine keeps half an ulp through approximate
+// divisions.
+template <class R>
+__device__ __forceinline__ void disp_sample(const KParams &p, const SegD<R> &D, R u2, R &lam,
+                                            R &kap, R &cosc, R &sinc) {
+    const int K = p.disp_k;
+    const R T = u2 * D.cdf[K - 2];
+    int m = 0;
+#pragma unroll
+    for (int i = 0; i < kDispMax - 2; ++i) m += (i < K - 2 && !(T < D.cdf[i]));
+    const R acc = m > 0 ? D.cdf[m - 1] : R(0);
+    const bool cut = m == D.m_cut;
+    const R frac = cut ? D.frac_cut : R(1);
+    R ka, kb, u1, du;
+    if constexpr (std::is_same<R, float>::value) {
+        ka = __ldg(p.kap32 + m);
+        kb = __ldg(p.kap32 + m + 1);
+        u1 = p.f.disp_u1;
+        du = p.f.disp_du;
+    } else {
+        ka = __ldg(p.kap64 + m);
+        kb = __ldg(p.kap64 + m + 1);
+        u1 = p.disp_u1;
+        du = p.disp_du;
+    }
+    const R ea = D.eta * ka;
+    const R x_end = cut ? D.x_th : D.eta * kb;
+    R Dl = T - acc;
+    Dl = Dl > R(0) ? Dl : R(0);
+    const R Dp = cut ? (frac > R(0) ? Dl / frac : R(0)) : Dl;
+    const R na = R(1) + ea;
+    const R bda = D.beta * (ea - D.x_th);
+    R s2a = bda * (R(2) + bda) / ((R(1) + bda) * (R(1) + bda));
+    s2a = s2a > R(0) ? s2a : R(0);
+    const R b = x_end - ea;
+    const R P = na * s2a - Dp * b;
+    R disc = P * P + R(4) * b * Dp * na;
+    disc = disc > R(0) ? disc : R(0);
+    const R den = P + sqrt(disc);
+    R t = den > R(0) ? (R(2) * Dp * na) / den : R(0);
+    t = t < R(1) ? t : R(1);
+    t = t > R(0) ? t : R(0);
+    const R sm = t * frac;
+    kap = ka + sm * (kb - ka);
+    lam = R(1) / (u1 - (static_cast<R>(m) + sm) * du);
+    const R bd = D.beta * (D.eta * kap - D.x_th);
+    R s2 = bd * (R(2) + bd) / ((R(1) + bd) * (R(1) + bd));
+    s2 = s2 > R(0) ? s2 : R(0);
+    sinc = sqrt(s2);
+    cosc = R(1) - bd / (R(1) + bd);
+}
+
 template <class R>
 __device__ __forceinline__ R load_dir(const void *p, int64_t i) {
     return __ldg(static_cast<const R *>(p) + i);
@@ -187,7 +438,18 @@ __device__ __forceinline__ void prep_step(const KParams &p, int64_t i, const Y &
         const R g = static_cast<R>(y.g);
         const R beta = sqrt(g * (R(2) + g)) / (R(1) + g);
         const R inv_nb = R(1) / static_cast<R>(y.nb);
-        S.cosc = R(1) / (beta * (R(1) + static_cast<R>(y.eta)));
+        if constexpr (std::is_same<R, float>::value) {
+            // cos = 1/(beta n) = 1 - b_d / (1 + b_d), b_d = beta n - 1 = beta (eta - x_th),
+            // x_th = 1/beta - 1 = 1 / (gamma^2 beta (1 + beta)): half an ulp through the
+            // approximate divisions and square roots (1/(beta n) directly: ~6 ulp, which
+            // the arrival time at large zenith, ~1e5 ns of path, feels)
+            const float gam = 1.0f + g;
+            const float x_th = 1.0f / (gam * gam * beta * (1.0f + beta));
+            const float bd = beta * (y.eta - x_th);
+            S.cosc = 1.0f - bd / (1.0f + bd);
+        } else {
+            S.cosc = R(1) / (beta * (R(1) + static_cast<R>(y.eta)));
+        }
         S.sinc = sqrt(static_cast<R>(y.s2));
         S.inv_nb = inv_nb;
         S.inv_bc = R(1) / (beta * R(kC));
@@ -330,6 +592,8 @@ __device__ __forceinline__ R trans_tau(const KParams &p, R lam, R h) {
 template <class R>
 struct BunchOut {
     R X, Y, cx, cy, cz, t, he, lam;
+    R kap;               // (n - 1) scale at the bunch's wavelength
+    R c2;                // cos^2 of the arrival zenith (queued fallback bunches)
     int status;
 };
 
@@ -424,8 +688,9 @@ __device__ __forceinline__ double eta_layer(const KParams &p, double h) {
     return e * exp(-(h * ic));
 }
 
-__device__ void ray_integrals(const KParams &p, double h_e, double s_obs, double &D, double &L) {
-    const double K = (1.0 + eta_layer(p, p.h_obs)) * s_obs;
+__device__ void ray_integrals(const KParams &p, double h_e, double s_obs, double kap, double &D,
+                              double &L) {
+    const double K = (1.0 + kap * eta_layer(p, p.h_obs)) * s_obs;
     D = 0.0;
     L = 0.0;
     double a = p.h_obs;
@@ -435,7 +700,7 @@ __device__ void ray_integrals(const KParams &p, double h_e, double s_obs, double
         const double b = top < h_e ? top : h_e;
         const double half = 0.5 * (b - a), mid = 0.5 * (a + b);
         for (int q = 0; q < 12; ++q) {
-            const double n = 1.0 + eta_layer(p, mid + half * p.gl_x[q]);
+            const double n = 1.0 + kap * eta_layer(p, mid + half * p.gl_x[q]);
             const double sn = K / n;
             const double inv_c = rsqrt(1.0 - sn * sn);
             D += p.gl_w[q] * half * sn * inv_c;
@@ -445,18 +710,73 @@ __device__ void ray_integrals(const KParams &p, double h_e, double s_obs, double
     }
 }
 
-// One queued bunch: its emission point and time, the horizontal direction
-// and sine of its observation-level zenith, wavelength, photons and key.
+// The same integrals for the FP32 path, in FP32: the straight line at the
+// observation-level zenith plus the integrals of the corrections,
+//   D = dh tan(theta_o) + int (tan(theta) - tan(theta_o)),
+//   L = dh / cos(theta_o) + int (n / cos(theta) - 1 / cos(theta_o)),
+// whose integrands are small and written without cancellation: with
+// delta = (n_o - n) / n, sin(theta) = s_o (1 + delta) and
+//   cos_o - cos = s_o^2 delta (2 + delta) / (cos_o + cos),
+//   tan - tan_o = s_o [delta cos_o + (cos_o - cos)] / (cos cos_o),
+//   n / cos - 1 / cos_o = [(n - 1) cos_o + (cos_o - cos)] / (cos cos_o).
+// cos_o^2 comes in as computed from the vertical cosine (full relative
+// precision at large zenith).
+__device__ __forceinline__ float eta_layer_f(const KParams &p, float h) {
+    if (!(h < p.f.hb[5])) return 0.0f;
+    float e = p.f.eta_coef[0], ic = p.f.inv_c[0];
+#pragma unroll
+    for (int l = 1; l < 5; ++l)
+        if (h >= p.f.hb[l]) { e = p.f.eta_coef[l]; ic = p.f.inv_c[l]; }
+    return e * __expf(-(h * ic));
+}
+
+__device__ void ray_integrals_f(const KParams &p, float dh, float s_o, float c2o, float kap,
+                                float &D, float &L) {
+    const float c_o = sqrtf(c2o);
+    const float inv_co = 1.0f / c_o;
+    const float s2o = s_o * s_o;
+    const float eta_o = kap * eta_layer_f(p, p.f.h_obs);
+    const float h_e = p.f.h_obs + dh;
+    float Dc = 0.0f, Lc = 0.0f;
+    float a = p.f.h_obs;
+    for (int l = 0; l < 5 && a < h_e; ++l) {
+        const float top = l < 4 ? p.f.hb[l + 1] : h_e;
+        if (!(top > a)) continue;
+        const float b = top < h_e ? top : h_e;
+        const float half = 0.5f * (b - a), mid = 0.5f * (a + b);
+        float sx = 0.0f, sl = 0.0f;
+#pragma unroll 4
+        for (int q = 0; q < 12; ++q) {
+            const float eh = kap * eta_layer_f(p, mid + half * p.f.gl_x[q]);
+            const float del = (eta_o - eh) / (1.0f + eh);
+            const float g = s2o * (del * (2.0f + del));
+            const float c = sqrtf(c2o - g);
+            const float dc = g / (c_o + c);                 // cos_o - cos
+            const float inv = 1.0f / (c * c_o);
+            sx += p.f.gl_w[q] * ((s_o * (del * c_o + dc)) * inv);
+            sl += p.f.gl_w[q] * ((eh * c_o + dc) * inv);
+        }
+        Dc += half * sx;
+        Lc += half * sl;
+        a = b;
+    }
+    D = dh * s_o * inv_co + Dc;
+    L = dh * inv_co + Lc;
+}
+
+// One queued bunch: its emission point and time, the horizontal direction,
+// sine and squared cosine of its observation-level zenith, wavelength, its
+// index's scale kappa, photons and key.
 template <class R>
 struct alignas(16) FbEntry {
-    R xe, ye, he, dh, te, hx, hy, s_obs, lam, w;   // dh = h_e - h_obs
+    R xe, ye, he, dh, te, hx, hy, s_obs, c2, lam, w, kap;   // dh = h_e - h_obs
     uint64_t key;                                  // the record key (step << 32 | j)
     uint32_t step_hi;                              // bits 32.. of the global step index
 };
 
-template <class R, bool TR, int FB>
-__device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c,
-                                      const Seg<R> &S, int64_t gi, int j, BunchOut<R> &o) {
+template <class R, bool TR, int FB, bool DS>
+__device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, const Seg<R> &S,
+                                      const SegD<R> *SD, int64_t gi, int j, BunchOut<R> &o) {
     const uint4 x = philox4x32_10(
         make_uint4(static_cast<uint32_t>(gi), static_cast<uint32_t>(static_cast<uint64_t>(gi) >> 32),
                    static_cast<uint32_t>(j), 0u),
@@ -485,20 +805,31 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c,
     } else {
         sincospi(2.0 * u1, &sp, &cp);
     }
-    const R px = S.cosc * S.ux + S.sinc * (cp * S.e1x + sp * S.e2x);
-    const R py = S.cosc * S.uy + S.sinc * (cp * S.e1y + sp * S.e2y);
-    const R pz = S.cosc * S.uz + S.sinc * (sp * S.e2z);
-    // 1/lambda^2 spectrum by inversion
-    o.lam = R(1) / (c.lam_inv1 - u2 * c.lam_dinv);
+    R cosc = S.cosc, sinc = S.sinc;
+    o.kap = R(1);
+    if constexpr (DS) {
+        disp_sample<R>(p, *SD, u2, o.lam, o.kap, cosc, sinc);
+    } else {
+        // 1/lambda^2 spectrum by inversion
+        o.lam = R(1) / (c.lam_inv1 - u2 * c.lam_dinv);
+    }
+    const R px = cosc * S.ux + sinc * (cp * S.e1x + sp * S.e2x);
+    const R py = cosc * S.uy + sinc * (cp * S.e1y + sp * S.e2y);
+    const R pz = cosc * S.uz + sinc * (sp * S.e2z);
     const R dH = S.dz0 + fl * S.uz;                 // h_e - h_obs
     o.he = c.h_obs + dH;
     // rare conditions first (paper Alg. 2)
     if (!(pz < R(0))) { o.status = ST_UPWARD; return; }
     if (!(dH >= R(0))) { o.status = ST_BELOW; return; }
     if (!(dH <= c.dH_max)) { o.status = ST_ABOVE; return; }
-    // Snell: sin_obs = sin_em (1 + eta_e) / (1 + eta_o)
+    // Snell: sin_obs = sin_em (1 + kappa eta_e) / (1 + kappa eta_o)
     const R eta_e = eta_at<R>(p, c, o.he);
-    const R rat = R(1) + (eta_e - c.eta_o) * c.inv_np1o;
+    R rm1;                                          // rat - 1
+    if constexpr (DS)
+        rm1 = o.kap * (eta_e - c.eta_o) / (R(1) + o.kap * c.eta_o);
+    else
+        rm1 = (eta_e - c.eta_o) * c.inv_np1o;
+    const R rat = R(1) + rm1;
     const R se2 = px * px + py * py;
     const R q = se2 * rat * rat;                    // sin^2(theta_obs)
     if (!(q <= c.q_max)) {
@@ -511,20 +842,25 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c,
                 // h_e - h_obs in he
                 const R rse = rsqrt(se2 > R(1e-30) ? se2 : R(1e-30));
                 const R hx = px * rse, hy = py * rse, s_obs = sqrt(q);
+                const R c2 = R(1) - q;                                     // cos^2
                 const R xe = S.x0 + fl * S.ux, ye = S.y0 + fl * S.uy;
                 const R te = S.tseg + fl * S.inv_bc;
                 if constexpr (FB == 1) {
                     o.X = xe; o.Y = ye; o.t = te; o.cx = hx; o.cy = hy; o.cz = s_obs;
                     o.he = dH;
+                    o.c2 = c2;
                     o.status = ST_DEFER;
                 } else {
-                    double Df, Lf;
-                    ray_integrals(p, p.h_obs + static_cast<double>(dH),
-                                  static_cast<double>(s_obs), Df, Lf);
-                    const R co_fb = sqrt(R(1) - q);
-                    o.X = xe + static_cast<R>(Df) * hx;
-                    o.Y = ye + static_cast<R>(Df) * hy;
-                    o.t = te + static_cast<R>(Lf * (1.0 / kC));
+                    R Df, Lf;
+                    if constexpr (std::is_same<R, float>::value) {
+                        ray_integrals_f(p, dH, s_obs, c2, o.kap, Df, Lf);
+                    } else {
+                        ray_integrals(p, p.h_obs + dH, s_obs, o.kap, Df, Lf);
+                    }
+                    const R co_fb = sqrt(c2);
+                    o.X = xe + Df * hx;
+                    o.Y = ye + Df * hy;
+                    o.t = te + Lf * R(1.0 / kC);
                     o.cx = s_obs * hx;
                     o.cy = s_obs * hy;
                     o.cz = -co_fb;
@@ -561,7 +897,43 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c,
     kk = kk > c.Z - 2 ? c.Z - 2 : kk;
     const R b = fk - static_cast<R>(kk);
     R Ax, Al;
-    {
+    if constexpr (DS) {
+        // the tables of the band's two ends, linear in kappa
+        const size_t e0 = static_cast<size_t>(jj) * (c.Z - 1) + kk;
+        const size_t e1 = e0 + (c.Z - 1);
+        if constexpr (std::is_same<R, float>::value) {
+            const float wk = (o.kap - p.f.kap_lo) * p.f.kap_winv;
+            const float4 *T = static_cast<const float4 *>(p.tabd);
+            const float4 a0 = __ldg(T + 2 * e0), b0 = __ldg(T + 2 * e0 + 1);
+            const float4 a1 = __ldg(T + 2 * e1), b1 = __ldg(T + 2 * e1 + 1);
+            const float4 t0 = make_float4(a0.x + wk * (b0.x - a0.x), a0.y + wk * (b0.y - a0.y),
+                                          a0.z + wk * (b0.z - a0.z), a0.w + wk * (b0.w - a0.w));
+            const float4 t1 = make_float4(a1.x + wk * (b1.x - a1.x), a1.y + wk * (b1.y - a1.y),
+                                          a1.z + wk * (b1.z - a1.z), a1.w + wk * (b1.w - a1.w));
+            const float x0 = t0.x + a * (t1.x - t0.x), x1 = t0.z + a * (t1.z - t0.z);
+            const float l0 = t0.y + a * (t1.y - t0.y), l1 = t0.w + a * (t1.w - t0.w);
+            Ax = x0 + b * (x1 - x0);
+            Al = l0 + b * (l1 - l0);
+        } else {
+            const double wk = (o.kap - p.kap_lo) * p.kap_winv;
+            const double2 *T = static_cast<const double2 *>(p.tabd);
+            double v[2][4];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const size_t e = r ? e1 : e0;
+                const double2 la = __ldg(T + 4 * e), lb = __ldg(T + 4 * e + 1);
+                const double2 ha = __ldg(T + 4 * e + 2), hb = __ldg(T + 4 * e + 3);
+                v[r][0] = la.x + wk * (ha.x - la.x);
+                v[r][1] = la.y + wk * (ha.y - la.y);
+                v[r][2] = lb.x + wk * (hb.x - lb.x);
+                v[r][3] = lb.y + wk * (hb.y - lb.y);
+            }
+            const double x0 = v[0][0] + a * (v[1][0] - v[0][0]), x1 = v[0][2] + a * (v[1][2] - v[0][2]);
+            const double l0 = v[0][1] + a * (v[1][1] - v[0][1]), l1 = v[0][3] + a * (v[1][3] - v[0][3]);
+            Ax = x0 + b * (x1 - x0);
+            Al = l0 + b * (l1 - l0);
+        }
+    } else {
         const size_t e0 = static_cast<size_t>(jj) * (c.Z - 1) + kk;
         const size_t e1 = e0 + (c.Z - 1);
         if constexpr (std::is_same<R, float>::value) {
@@ -773,13 +1145,20 @@ __device__ __forceinline__ void record_hits(const KParams &p, const BunchOut<R> 
 // instantiation: present but switched off it cost 2 % of the launch).
 // FB: bunches past the tables' zenith range are queued for the fallback
 // pass (1, hits) or integrated in place (2, trace).
-template <class R, int BLOCK, int MODE, bool TR, int FB>
+// DS: the index depends on the wavelength (per-step spectra in shared memory).
+template <class R, int BLOCK>
+__host__ __device__ constexpr size_t segd_offset() {
+    return (sizeof(Seg<R>) * BLOCK + sizeof(int) * (BLOCK + 1 + 32) + 15) & ~size_t(15);
+}
+
+template <class R, int BLOCK, int MODE, bool TR, int FB, bool DS>
 __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / BLOCK : 1)
     k_gen_prop(const KParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     Seg<R> *seg = reinterpret_cast<Seg<R> *>(smem);
     int *off = reinterpret_cast<int *>(seg + BLOCK);          // BLOCK + 1
     int *wsum = off + BLOCK + 1;                                // BLOCK / 32
+    SegD<R> *segd = reinterpret_cast<SegD<R> *>(smem + segd_offset<R, BLOCK>());   // DS only
     __shared__ unsigned long long s_tile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // the candidate grids (a few KB) are read through L1; their sizes and
@@ -816,12 +1195,22 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             using YT = typename std::conditional<std::is_same<R, float>::value, YieldF,
                                                  Yield>::type;
             YT y;
-            if constexpr (std::is_same<YT, YieldF>::value)
+            if constexpr (DS) {
+                if constexpr (std::is_same<YT, YieldF>::value)
+                    step_yield_screened_disp(p, step_valid<R>(p, i), __ldg(p.z0 + i),
+                                             __ldg(p.len + i), __ldg(p.ekin + i),
+                                             load_dir<float>(p.uz, i), y, segd[tid]);
+                else
+                    step_yield_disp<R>(p, step_valid<R>(p, i), __ldg(p.z0 + i), __ldg(p.len + i),
+                                       __ldg(p.ekin + i), static_cast<double>(load_dir<R>(p.uz, i)),
+                                       y, segd[tid]);
+            } else if constexpr (std::is_same<YT, YieldF>::value) {
                 step_yield_screened(p, step_valid<R>(p, i), __ldg(p.z0 + i), __ldg(p.len + i),
                                     __ldg(p.ekin + i), load_dir<float>(p.uz, i), y);
-            else
+            } else {
                 step_yield(p, step_valid<R>(p, i), __ldg(p.z0 + i), __ldg(p.len + i),
                            __ldg(p.ekin + i), static_cast<double>(load_dir<R>(p.uz, i)), y);
+            }
             if constexpr (MODE == MODE_SCREEN) {
                 // the adjoint freezes the sub-step structure
                 const int nf = __ldg(p.nb_frozen + i);
@@ -930,7 +1319,8 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             int j = 0;
             if (live) {
                 j = bidx - off[s];
-                bunch<R, TR, FB>(p, c, seg[s], p.track_base + base + s, j, o);
+                bunch<R, TR, FB, DS>(p, c, seg[s], DS ? segd + s : nullptr,
+                                     p.track_base + base + s, j, o);
                 if (o.status != ST_GROUND) {       // rare: the drops
                     st_up += o.status == ST_UPWARD;
                     st_below += o.status == ST_BELOW;
@@ -972,8 +1362,9 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                     if (dq && at < static_cast<unsigned long long>(p.fb_cap)) {
                         FbEntry<R> e;
                         e.xe = o.X; e.ye = o.Y; e.he = c.h_obs + o.he; e.dh = o.he; e.te = o.t;
-                        e.hx = o.cx; e.hy = o.cy; e.s_obs = o.cz; e.lam = o.lam;
+                        e.hx = o.cx; e.hy = o.cy; e.s_obs = o.cz; e.c2 = o.c2; e.lam = o.lam;
                         e.w = seg[s].w;
+                        e.kap = o.kap;
                         const int64_t gstep = p.track_base + base + s;
                         e.key = (static_cast<uint64_t>(gstep) << 32) | static_cast<uint32_t>(j);
                         e.step_hi = static_cast<uint32_t>(static_cast<uint64_t>(gstep) >> 32);
@@ -1009,7 +1400,8 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                 const R w = live ? seg[s].w : R(0);
                 const uint64_t key = (static_cast<uint64_t>(p.track_base + base + s) << 32) |
                                      static_cast<uint32_t>(j);
-                record_hits<R>(p, o, hm, s0, gsel, w, key, np1o, lane, st_hits, st_over);
+                const R np1 = DS ? R(1) + o.kap * c.eta_o : np1o;
+                record_hits<R>(p, o, hm, s0, gsel, w, key, np1, lane, st_hits, st_over);
             }
         }
         if (!p.tile_counter) break;
@@ -1046,7 +1438,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
 // The fallback pass: one thread per queued bunch (warps walk the queue 32
 // entries at a time so that the compaction stays warp-synchronous).
 // ------------------------------------------------------------------------
-template <class R, bool TR>
+template <class R, bool TR, bool DS>
 __global__ void __launch_bounds__(128) k_fallback(const KParams p) {
     Consts<R> c;
     R np1o;
@@ -1067,18 +1459,21 @@ __global__ void __launch_bounds__(128) k_fallback(const KParams p) {
         uint64_t key = 0;
         if (live) {
             const FbEntry<R> E = static_cast<const FbEntry<R> *>(p.fb_list)[e];
-            double D, L;
-            ray_integrals(p, p.h_obs + static_cast<double>(E.dh), static_cast<double>(E.s_obs),
-                          D, L);
-            const R co = sqrt(R(1) - E.s_obs * E.s_obs);
-            o.X = E.xe + static_cast<R>(D) * E.hx;
-            o.Y = E.ye + static_cast<R>(D) * E.hy;
-            o.t = E.te + static_cast<R>(L * (1.0 / kC));
+            R D, L;
+            if constexpr (std::is_same<R, float>::value)
+                ray_integrals_f(p, E.dh, E.s_obs, E.c2, DS ? E.kap : 1.0f, D, L);
+            else
+                ray_integrals(p, p.h_obs + E.dh, E.s_obs, DS ? E.kap : 1.0, D, L);
+            const R co = sqrt(E.c2);
+            o.X = E.xe + D * E.hx;
+            o.Y = E.ye + D * E.hy;
+            o.t = E.te + L * R(1.0 / kC);
             o.cx = E.s_obs * E.hx;
             o.cy = E.s_obs * E.hy;
             o.cz = -co;
             o.he = E.he;
             o.lam = E.lam;
+            o.kap = DS ? E.kap : R(1);
             o.status = ST_GROUND;
             w = E.w;
             key = E.key;
@@ -1107,7 +1502,8 @@ __global__ void __launch_bounds__(128) k_fallback(const KParams p) {
         }
         int s0 = 0, gsel = 0;
         unsigned hm = live ? sphere_hits<R>(p, c, o, s0, gsel) : 0u;
-        record_hits<R>(p, o, hm, s0, gsel, w, key, np1o, lane, st_hits, st_over);
+        const R np1 = DS ? R(1) + o.kap * c.eta_o : np1o;
+        record_hits<R>(p, o, hm, s0, gsel, w, key, np1, lane, st_hits, st_over);
     }
     unsigned long long *S = p.stats;
     if (S) {
@@ -1126,58 +1522,72 @@ __global__ void __launch_bounds__(128) k_fallback(const KParams p) {
 
 template <class R, int BLOCK>
 size_t smem_bytes(const KParams &p) {
-    size_t b = sizeof(Seg<R>) * BLOCK + sizeof(int) * (BLOCK + 1 + 32);
-    b = (b + 15) & ~size_t(15);
+    size_t b = segd_offset<R, BLOCK>();
+    if (p.disp_k > 0) b += sizeof(SegD<R>) * BLOCK;
     return b;
 }
 
-template <class R, int BLOCK, int MODE>
-const void *kernel_ptr(bool tr, bool fb) {
+template <class R, int BLOCK, int MODE, bool DS>
+const void *kernel_ptr_ds(bool tr, bool fb) {
     if constexpr (MODE == MODE_YIELD || MODE == MODE_SCREEN) {
         if constexpr (MODE == MODE_YIELD)
-            return reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0>);
+            return reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0, DS>);
         else
-            return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, 0>)
-                      : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0>);
+            return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, 0, DS>)
+                      : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0, DS>);
     } else {
         constexpr int F = MODE == MODE_HITS ? 1 : 2;
         if (fb)
-            return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, F>)
-                      : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, F>);
-        return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, 0>)
-                  : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0>);
+            return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, F, DS>)
+                      : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, F, DS>);
+        return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, 0, DS>)
+                  : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0, DS>);
     }
 }
 
+template <class R, int BLOCK, int MODE>
+const void *kernel_ptr(bool tr, bool fb, bool ds) {
+    if (ds) {
+        // the wavelength-dependent index: 128-step tiles, no adjoint screening
+        if constexpr (BLOCK == kDispBlock && MODE != MODE_SCREEN)
+            return kernel_ptr_ds<R, BLOCK, MODE, true>(tr, fb);
+        else
+            return nullptr;
+    }
+    return kernel_ptr_ds<R, BLOCK, MODE, false>(tr, fb);
+}
+
 template <class R, int MODE>
-const void *pick(int block, bool tr, bool fb) {
+const void *pick(int block, bool tr, bool fb, bool ds) {
     switch (block) {
-    case 128: return kernel_ptr<R, 128, MODE>(tr, fb);
-    case 256: return kernel_ptr<R, 256, MODE>(tr, fb);
-    case 512: return kernel_ptr<R, 512, MODE>(tr, fb);
+    case 128: return kernel_ptr<R, 128, MODE>(tr, fb, ds);
+    case 256: return kernel_ptr<R, 256, MODE>(tr, fb, ds);
+    case 512: return kernel_ptr<R, 512, MODE>(tr, fb, ds);
     }
     return nullptr;
 }
 
-// mode: a Mode, plus kTransBit / kFbBit for the instantiations with the
-// transmission draw / the beyond-table fallback
+// mode: a Mode, plus kTransBit / kFbBit / kDispBit for the instantiations
+// with the transmission draw / the beyond-table fallback / the
+// wavelength-dependent index
 const void *pick_kernel(bool fp32, int block, int mode) {
     const bool tr = (mode & kTransBit) != 0;
     const bool fb = (mode & kFbBit) != 0;
-    mode &= ~(kTransBit | kFbBit);
+    const bool ds = (mode & kDispBit) != 0;
+    mode &= ~(kTransBit | kFbBit | kDispBit);
     if (fp32) {
         switch (mode) {
-        case MODE_HITS: return pick<float, MODE_HITS>(block, tr, fb);
-        case MODE_TRACE: return pick<float, MODE_TRACE>(block, tr, fb);
-        case MODE_YIELD: return pick<float, MODE_YIELD>(block, tr, fb);
-        case MODE_SCREEN: return pick<float, MODE_SCREEN>(block, tr, fb);
+        case MODE_HITS: return pick<float, MODE_HITS>(block, tr, fb, ds);
+        case MODE_TRACE: return pick<float, MODE_TRACE>(block, tr, fb, ds);
+        case MODE_YIELD: return pick<float, MODE_YIELD>(block, tr, fb, ds);
+        case MODE_SCREEN: return pick<float, MODE_SCREEN>(block, tr, fb, ds);
         }
     } else {
         switch (mode) {
-        case MODE_HITS: return pick<double, MODE_HITS>(block, tr, fb);
-        case MODE_TRACE: return pick<double, MODE_TRACE>(block, tr, fb);
-        case MODE_YIELD: return pick<double, MODE_YIELD>(block, tr, fb);
-        case MODE_SCREEN: return pick<double, MODE_SCREEN>(block, tr, fb);
+        case MODE_HITS: return pick<double, MODE_HITS>(block, tr, fb, ds);
+        case MODE_TRACE: return pick<double, MODE_TRACE>(block, tr, fb, ds);
+        case MODE_YIELD: return pick<double, MODE_YIELD>(block, tr, fb, ds);
+        case MODE_SCREEN: return pick<double, MODE_SCREEN>(block, tr, fb, ds);
         }
     }
     return nullptr;
@@ -1217,6 +1627,17 @@ void fill_float_constants(KParams &p) {
     p.f.trans_hscale = static_cast<float>(p.trans_hscale);
     p.f.prof_dx = static_cast<float>(p.prof_dx);
     p.f.prof_inv_dx = static_cast<float>(p.prof_inv_dx);
+    for (int m = 0; m < kDispMax; ++m) p.f.kap[m] = static_cast<float>(p.kap[m]);
+    p.f.disp_Kd = static_cast<float>(p.disp_Kd);
+    p.f.disp_u1 = static_cast<float>(p.disp_u1);
+    p.f.disp_du = static_cast<float>(p.disp_du);
+    p.f.kap_lo = static_cast<float>(p.kap_lo);
+    p.f.kap_winv = static_cast<float>(p.kap_winv);
+    for (int l = 0; l < 5; ++l) p.f.eta_coef[l] = static_cast<float>(p.atm.eta_coef[l]);
+    for (int q = 0; q < 12; ++q) {
+        p.f.gl_x[q] = static_cast<float>(p.gl_x[q]);
+        p.f.gl_w[q] = static_cast<float>(p.gl_w[q]);
+    }
     for (int l = 0; l < 6; ++l) p.f.hb[l] = static_cast<float>(p.atm.hb[l]);
     for (int l = 0; l < 5; ++l) {
         p.f.a[l] = static_cast<float>(p.atm.a[l]);
@@ -1236,21 +1657,28 @@ __global__ void k_round_to_float(const double *in, float *out, int64_t n) {
 }  // namespace
 
 size_t fallback_record_bytes(bool fp32) {
-    static_assert(sizeof(FbEntry<float>) == 64 && sizeof(FbEntry<double>) == 96,
+    static_assert(sizeof(FbEntry<float>) == 64 && sizeof(FbEntry<double>) == 112,
                   "fallback queue records");
     return fp32 ? sizeof(FbEntry<float>) : sizeof(FbEntry<double>);
 }
 
-cudaError_t launch_fallback(bool fp32, bool tr, const KParams &p, int num_sms, void *stream) {
+template <class R>
+void fallback_r(bool tr, bool disp, const KParams &p, int grid, cudaStream_t st) {
+    if (disp) {
+        if (tr) k_fallback<R, true, true><<<grid, 128, 0, st>>>(p);
+        else k_fallback<R, false, true><<<grid, 128, 0, st>>>(p);
+    } else {
+        if (tr) k_fallback<R, true, false><<<grid, 128, 0, st>>>(p);
+        else k_fallback<R, false, false><<<grid, 128, 0, st>>>(p);
+    }
+}
+
+cudaError_t launch_fallback(bool fp32, bool tr, bool disp, const KParams &p, int num_sms,
+                            void *stream) {
     const int grid = num_sms * 8;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (fp32) {
-        if (tr) k_fallback<float, true><<<grid, 128, 0, st>>>(p);
-        else k_fallback<float, false><<<grid, 128, 0, st>>>(p);
-    } else {
-        if (tr) k_fallback<double, true><<<grid, 128, 0, st>>>(p);
-        else k_fallback<double, false><<<grid, 128, 0, st>>>(p);
-    }
+    if (fp32) fallback_r<float>(tr, disp, p, grid, st);
+    else fallback_r<double>(tr, disp, p, grid, st);
     return cudaGetLastError();
 }
 

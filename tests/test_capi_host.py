@@ -99,3 +99,7 @@ def test_round_to_float_rejects_bad_arguments(L):
     assert L.cher_round_to_float(None, None, 5, None) == 1
     assert L.cher_round_to_float(None, None, -1, None) == 1
     assert L.cher_round_to_float(None, None, 0, None) == 0
+
+
+def test_dispersion_setter_rejects_a_missing_context(L):
+    assert L.cher_set_dispersion(None, None, 0) == 1
