@@ -69,7 +69,8 @@ class _Cfg(ctypes.Structure):
                 ("trans_l0", ctypes.c_double), ("trans_l1", ctypes.c_double),
                 ("trans_h0", ctypes.c_double), ("trans_h1", ctypes.c_double),
                 ("trans_tau", _dp), ("fb_sin2_max", ctypes.c_double),
-                ("disp_k", ctypes.c_int), ("disp_kappa", _dp), ("ax_hi", _dp), ("al_hi", _dp)]
+                ("disp_k", ctypes.c_int), ("disp_kappa", _dp), ("ax_hi", _dp), ("al_hi", _dp),
+                ("earth_radius", ctypes.c_double), ("ag", _dp), ("ag_hi", _dp)]
 
 
 class _Tracks(ctypes.Structure):
@@ -83,7 +84,7 @@ class _Out(ctypes.Structure):
                 ("px", _dp), ("py", _dp), ("pz", _dp), ("X", _dp), ("Y", _dp), ("t", _dp),
                 ("cx", _dp), ("cy", _dp), ("cz", _dp), ("lam", _dp), ("w", _dp),
                 ("nhit", _i32p), ("hit_tel", _i32p), ("hit_x", _dp), ("hit_y", _dp),
-                ("hit_t", _dp), ("tr_margin", _dp)]
+                ("hit_t", _dp), ("tr_margin", _dp), ("Zg", _dp)]
 
 
 _lib = None
@@ -148,6 +149,12 @@ def lib():
             [ctypes.c_double] * 7 + [_dp]
         L.orc_propagate_photon_k.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int] + \
             [ctypes.c_double] * 8 + [_dp]
+        L.orc_brute_ray_curved.argtypes = [ctypes.POINTER(_Atm)] + [ctypes.c_double] * 5 + \
+            [_dp, _dp]
+        L.orc_build_curved_tables.argtypes = [ctypes.POINTER(_Atm), ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                              _dp, _dp, _dp]
         L.orc_bunches.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Tracks),
                                   ctypes.c_uint64, _i64p, ctypes.c_int,
                                   ctypes.POINTER(_Out)]
@@ -250,6 +257,35 @@ def refraction_tables(atm, h_obs, h_max, H, Z, theta_max_rad, tol=1e-13):
     return ax, al
 
 
+def curved_tables(atm, earth_radius, h_obs, h_max, H, Z, theta_max_rad, tol=1e-13):
+    """Refraction tables of a curved atmosphere (corrections of the central
+    angle and of the two parts of the optical path to the straight line of
+    the same arrival zenith), on a zenith axis uniform in sec: ax, al, ag."""
+    A = _atm(atm)
+    ax = np.zeros((H, Z))
+    al = np.zeros((H, Z))
+    ag = np.zeros((H, Z))
+    rc = lib().orc_build_curved_tables(ctypes.byref(A), float(earth_radius), float(h_obs),
+                                       float(h_max), int(H), int(Z), float(theta_max_rad),
+                                       float(tol), _ptr(ax), _ptr(al), _ptr(ag))
+    if rc != 0:
+        raise ValueError("bad curved table arguments")
+    return ax, al, ag
+
+
+def brute_ray_curved(atm, earth_radius, h_obs, h_e, sin_obs, tol=1e-12):
+    """(B), curved: central angle phi and optical path l from h_obs to h_e."""
+    A = _atm(atm)
+    phi = ctypes.c_double()
+    l_ = ctypes.c_double()
+    rc = lib().orc_brute_ray_curved(ctypes.byref(A), float(earth_radius), float(h_obs),
+                                    float(h_e), float(sin_obs), float(tol), ctypes.byref(phi),
+                                    ctypes.byref(l_))
+    if rc != 0:
+        raise ValueError("bad ray")
+    return phi.value, l_.value
+
+
 def brute_ray(atm, h_obs, h_e, sin_obs, tol=1e-12):
     """(B): horizontal displacement x and optical path l from h_obs to h_e."""
     A = _atm(atm)
@@ -289,15 +325,27 @@ class Model:
     # from 1/lambda1 (node 0) to 1/lambda2, n(h, lambda) - 1 = eta(h) kappa,
     # positive and not increasing along the nodes; None: constant index
     dispersion: np.ndarray | None = None
+    # curved atmosphere: the Earth's radius in m (0: flat layers); positions
+    # are then Cartesian in the core frame and heights radial
+    earth_radius: float = 0.0
     table_tol: float = 1e-13
     bf_tol: float = 1e-12
     eta_tab: np.ndarray = field(init=False, repr=False)
     ax: np.ndarray = field(init=False, repr=False)
+    ag: np.ndarray | None = field(init=False, repr=False, default=None)
     al: np.ndarray = field(init=False, repr=False)
 
     def __post_init__(self):
         self.telescopes = _f64(np.asarray(self.telescopes).reshape(-1, 4))
         self.eta_tab = eta_table(self.atm, self.h_max, self.n_fine)
+
+        def tables(atm):
+            if self.earth_radius > 0.0:
+                return curved_tables(atm, self.earth_radius, self.h_obs, self.h_max, self.H,
+                                     self.Z, self.theta_max_rad, self.table_tol)
+            return refraction_tables(atm, self.h_obs, self.h_max, self.H, self.Z,
+                                     self.theta_max_rad, self.table_tol) + (None,)
+
         if self.dispersion is not None:
             kap = _f64(np.asarray(self.dispersion, float).ravel())
             if not (2 <= kap.size <= 9) or not np.all(kap > 0) or np.any(np.diff(kap) > 0):
@@ -306,14 +354,10 @@ class Model:
             # the tables of the band's two ends: n - 1 scaled by kappa
             lo = dict(self.atm, n0_minus_1=float(self.atm["n0_minus_1"]) * kap[-1])
             hi = dict(self.atm, n0_minus_1=float(self.atm["n0_minus_1"]) * kap[0])
-            self.ax, self.al = refraction_tables(lo, self.h_obs, self.h_max, self.H, self.Z,
-                                                 self.theta_max_rad, self.table_tol)
-            self.ax_hi, self.al_hi = refraction_tables(hi, self.h_obs, self.h_max, self.H,
-                                                       self.Z, self.theta_max_rad,
-                                                       self.table_tol)
+            self.ax, self.al, self.ag = tables(lo)
+            self.ax_hi, self.al_hi, self.ag_hi = tables(hi)
         else:
-            self.ax, self.al = refraction_tables(self.atm, self.h_obs, self.h_max, self.H,
-                                                 self.Z, self.theta_max_rad, self.table_tol)
+            self.ax, self.al, self.ag = tables(self.atm)
         if self.t_ref is not None:
             self.t_ref = _f64(np.atleast_1d(self.t_ref))
 
@@ -342,6 +386,10 @@ class Model:
             C.t_ref = None
             C.n_showers = 0
         C.bf_tol = self.bf_tol
+        C.earth_radius = float(self.earth_radius)
+        C.ag = _ptr(self.ag)
+        if self.dispersion is not None:
+            C.ag_hi = _ptr(self.ag_hi)
         if self.dispersion is not None:
             C.disp_k = int(self.dispersion.size)
             C.disp_kappa = _ptr(self.dispersion)
@@ -412,6 +460,7 @@ class Model:
         for k in ("hit_x", "hit_y", "hit_t"):
             out[k] = np.zeros((nbt, MAX_HITS))
         out["tr_margin"] = np.full(nbt, np.nan)
+        out["Zg"] = np.zeros(nbt)
         O = _Out()
         for k, v in out.items():
             setattr(O, k, _ptr(v, ctypes.c_int32 if v.dtype == np.int32 else ctypes.c_double))
@@ -464,8 +513,10 @@ class Model:
         return prof
 
     def propagate_photon(self, xe, ye, he, te, px, py, pz, variant=0, kappa=None):
-        """One bunch to the ground; kappa scales n - 1 at its wavelength."""
-        r = np.zeros(6)
+        """One bunch to the ground; kappa scales n - 1 at its wavelength.
+        r: X, Y, t, cx, cy, cz, arrival z - h_obs, cosine to the local
+        vertical, emission height."""
+        r = np.zeros(9)
         C = self._cfg()
         if kappa is None:
             st = lib().orc_propagate_photon(ctypes.byref(C), int(variant), xe, ye, he, te,

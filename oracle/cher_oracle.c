@@ -127,6 +127,17 @@ typedef struct {
     int disp_k;
     const double *disp_kappa;
     const double *ax_hi, *al_hi;
+    /* curved atmosphere (earth_radius = 0: flat layers).  Positions are   */
+    /* Cartesian in the core frame (z up, z = height a.s.l. on the core's   */
+    /* vertical); the Earth's centre is (0, 0, -earth_radius); a point's    */
+    /* height is its radial height |x - C| - earth_radius; rays keep        */
+    /* Bouguer's invariant n r sin(zeta) (zeta from the local vertical);   */
+    /* the observation level is the sphere r_o = earth_radius + h_obs.  The */
+    /* refraction tables are then the curved ones (orc_build_curved_tables). */
+    double earth_radius;
+    /* curved: the third table (the geometric part of the optical path),   */
+    /* and its twin at kappa[0] with a wavelength-dependent index          */
+    const double *ag, *ag_hi;
 } orc_cfg;
 
 typedef struct {
@@ -150,6 +161,7 @@ typedef struct {
     double *hit_x, *hit_y, *hit_t;    /* record in the telescope frame     */
     double *tr_margin;                /* u3 - P of the transmission draw (NaN */
                                       /* where none), optional              */
+    double *Zg;                       /* arrival z - h_obs (curved), optional */
 } orc_bunch_out;
 
 /* ======================================================================= */
@@ -297,9 +309,48 @@ static double orc_band_factor(const orc_cfg *C)
 
 static int orc_finite(double v) { return v == v && v - v == 0.0; }
 
+/* Height of a point in a curved atmosphere: |x - C| - R_E with the centre
+ * C = (0, 0, -R_E), written without cancellation:
+ *     sqrt(rho^2 + (z + R_E)^2) - R_E = z + rho^2 / (sqrt(rho^2 + (z + R_E)^2) + z + R_E). */
+static double orc_radial_height(double R_E, double x, double y, double z)
+{
+    double rho2 = x * x + y * y;
+    double Rp = z + R_E;
+    double r = sqrt(rho2 + Rp * Rp);
+    double den = r + Rp;
+    return z + rho2 / den;
+}
+
+/* The height at which a step's index is taken: its midpoint's (reading:
+ * the radial height in a curved atmosphere).  One IEEE operation per
+ * statement, like the rest of the yield. */
+static double orc_midpoint_height(const orc_cfg *C, const orc_tracks *T, int64_t i)
+{
+    double half_len = 0.5 * T->len[i];
+    double dz = half_len * T->uz[i];
+    double hm = T->z0[i] + dz;
+    if (C->earth_radius > 0.0) {
+        double dx = half_len * T->ux[i];
+        double xm = T->x0[i] + dx;
+        double dy = half_len * T->uy[i];
+        double ym = T->y0[i] + dy;
+        double xx = xm * xm;
+        double yy = ym * ym;
+        double rho2 = xx + yy;
+        double Rp = hm + C->earth_radius;
+        double RR = Rp * Rp;
+        double r2 = rho2 + RR;
+        double r = sqrt(r2);
+        double den = r + Rp;
+        double corr = rho2 / den;
+        hm = hm + corr;
+    }
+    return hm;
+}
+
 /* the yield of a step whose fields are all valid */
-static int orc_step_yield_valid(const orc_cfg *C, double z0, double len, double ekin,
-                                double uz, orc_yield *Y)
+static int orc_step_yield_valid(const orc_cfg *C, double hm, double len, double ekin,
+                                orc_yield *Y)
 {
     double inv_me = 1.0 / ORC_ME_MEV;
     double K = orc_band_factor(C);
@@ -308,9 +359,6 @@ static int orc_step_yield_valid(const orc_cfg *C, double z0, double len, double 
     double g = ekin * inv_me;               /* gamma - 1                   */
     double gam = 1.0 + g;
     double gam2 = gam * gam;
-    double half_len = 0.5 * len;
-    double dz = half_len * uz;
-    double hm = z0 + dz;                    /* midpoint height             */
     double eta = orc_eta_lookup(C->eta_tab, C->n_fine, C->h_max, hm);
     double np1 = 1.0 + eta;
     double np1sq = np1 * np1;
@@ -378,8 +426,8 @@ static double orc_disp_band_factor(const orc_cfg *C)
     return two_pi_alpha * du;
 }
 
-static int orc_step_yield_disp(const orc_cfg *C, double z0, double len, double ekin,
-                               double uz, orc_yield *Y)
+static int orc_step_yield_disp(const orc_cfg *C, double hm, double len, double ekin,
+                               orc_yield *Y)
 {
     double inv_me = 1.0 / ORC_ME_MEV;
     double Kd = orc_disp_band_factor(C);
@@ -388,9 +436,6 @@ static int orc_step_yield_disp(const orc_cfg *C, double z0, double len, double e
     double g = ekin * inv_me;
     double gam = 1.0 + g;
     double gam2 = gam * gam;
-    double half_len = 0.5 * len;
-    double dz = half_len * uz;
-    double hm = z0 + dz;
     double eta = orc_eta_lookup(C->eta_tab, C->n_fine, C->h_max, hm);
     double two_g = 2.0 + g;
     double bg2 = g * two_g;
@@ -455,9 +500,10 @@ static int orc_step_yield(const orc_cfg *C, const orc_tracks *T, int64_t i, orc_
     Y->nb = 0; Y->w = 0.0; Y->N = 0.0; Y->s2 = 0.0; Y->beta = 0.0; Y->eta = 0.0;
     Y->psum = 0.0;
     if (!orc_step_valid(T, i)) return -1;
+    double hm = orc_midpoint_height(C, T, i);
     if (C->disp_k > 0)
-        return orc_step_yield_disp(C, T->z0[i], T->len[i], T->ekin[i], T->uz[i], Y);
-    return orc_step_yield_valid(C, T->z0[i], T->len[i], T->ekin[i], T->uz[i], Y);
+        return orc_step_yield_disp(C, hm, T->len[i], T->ekin[i], Y);
+    return orc_step_yield_valid(C, hm, T->len[i], T->ekin[i], Y);
 }
 
 /* Per-step yield for every step: nb (bunches), w (photons per bunch),
@@ -490,6 +536,7 @@ typedef struct {
     double s_obs;     /* sin(theta_obs)                                    */
     double c_obs;     /* cos(theta_obs)                                    */
     int which;        /* integrand selector                                */
+    double floor;     /* relative noise floor of the adaptive rule         */
 } orc_ray;
 
 enum { F_TAN = 0, F_OPT = 1, F_TAN_CORR = 2, F_OPT_CORR = 3, F_RATIO = 4 };
@@ -510,6 +557,20 @@ static double orc_integrand(const orc_ray *R, double h)
     return 0.0;
 }
 
+/* Adaptive Simpson stops refining once the two estimates agree to the
+ * rounding noise of the integrand: the correction integrands of the tables
+ * (tan - tan_o) are differences of terms up to ~1/cos^3 larger, whose
+ * rounding at large zenith reaches ~1e-10 of the correction (80 degrees);
+ * a tolerance halved below that recurses towards the depth limit without
+ * gaining anything.  The floor, `rel` of the integrand's size over the
+ * interval (1e-9 for the tables' corrections, 1e-13 for the full integrands
+ * of the brute-force variant), changes an integral by at most `rel` of its
+ * size. */
+static double orc_noise_floor(double rel, double a, double b, double fa, double fm, double fb)
+{
+    return rel * (fabs(fa) + fabs(fm) + fabs(fb)) * (b - a);
+}
+
 static double orc_simpson_rec(const orc_ray *R, double a, double b, double fa,
                               double fm, double fb, double whole, double tol,
                               int depth)
@@ -520,7 +581,7 @@ static double orc_simpson_rec(const orc_ray *R, double a, double b, double fa,
     double left = (m - a) / 6.0 * (fa + 4.0 * flm + fm);
     double right = (b - m) / 6.0 * (fm + 4.0 * frm + fb);
     double delta = left + right - whole;
-    if (depth <= 0 || fabs(delta) <= 15.0 * tol)
+    if (depth <= 0 || fabs(delta) <= 15.0 * tol || fabs(delta) <= orc_noise_floor(R->floor, a, b, fa, fm, fb))
         return left + right + delta / 15.0;
     return orc_simpson_rec(R, a, m, fa, flm, fm, left, 0.5 * tol, depth - 1)
          + orc_simpson_rec(R, m, b, fm, frm, fb, right, 0.5 * tol, depth - 1);
@@ -558,6 +619,7 @@ int orc_brute_ray(const orc_atm *A, double h_obs, double h_e, double sin_obs,
     if (!(sin_obs >= 0.0 && sin_obs < 1.0) || h_e < h_obs) return -1;
     orc_ray R;
     R.A = A;
+    R.floor = 1e-13;
     R.np1_obs = 1.0 + orc_eta_exact(A, h_obs);
     R.s_obs = sin_obs;
     R.c_obs = sqrt(1.0 - sin_obs * sin_obs);
@@ -597,6 +659,7 @@ int orc_build_refraction_tables(const orc_atm *A, double h_obs, double h_max,
         double so = sqrt(q), co = sqrt(1.0 - so * so);
         orc_ray R;
         R.A = A; R.np1_obs = np1_obs; R.s_obs = so; R.c_obs = co;
+        R.floor = 1e-9;
         double dx = 0.0, dl = 0.0;
         ax[(size_t)0 * Z + k] = 0.0;
         al[(size_t)0 * Z + k] = 0.0;
@@ -610,6 +673,196 @@ int orc_build_refraction_tables(const orc_atm *A, double h_obs, double h_max,
             double c3 = co * co * co;
             ax[(size_t)j * Z + k] = (k == 0) ? dx : dx * c3 / so;
             al[(size_t)j * Z + k] = dl * c3;
+        }
+    }
+    return 0;
+}
+
+/* ======================================================================= */
+/* Curved atmosphere (an extension: the flat layers of RAYBND become       */
+/* spherical shells, for large zenith angles).  A ray in a spherically     */
+/* stratified medium stays in the plane through the Earth's centre and     */
+/* keeps Bouguer's invariant n(r) r sin(zeta(r)) = K, zeta the angle to the */
+/* local vertical.  Between the observation sphere r_o and the emission    */
+/* radius r_e it turns through the central angle and has the optical path  */
+/*     phi = int tan(zeta) / r dr,   L = int n / cos(zeta) dr,             */
+/* r = R_E + h, integrated over h layer by layer (adaptive Simpson).       */
+/* The tables hold corrections to the straight line that arrives at the    */
+/* same zenith (impact parameter b = r_o sin(zeta_o), sin(zeta_s) = b / r): */
+/*     dphi = int (tan(zeta) - tan(zeta_s)) / r dr,                        */
+/*     L - l_s = int (n - 1) / cos(zeta) dr + int (1/cos(zeta) - 1/cos(zeta_s)) dr, */
+/* three quantities, each divided by the path average along that line of   */
+/* its first-order angular factor (b r_o / (r^2 cos^3), 1 / cos and        */
+/* sin^2 / cos^3 of zeta_s), all closed forms (orc_curved_factors), so that */
+/* to first order in n - 1 each table is the path average of n_o / n - 1,  */
+/* n - 1 or n_o / n - 1: nearly independent of the angle.  The zenith axis */
+/* is uniform in sec(zeta_o) from 1 to sec(theta_max): what the path       */
+/* averages leave (the weights n - 1 are not uniform along a path whose    */
+/* zenith changes, by ~2 sin^2 h / r_o in cos^2) varies near grazing like  */
+/* 1 / cos^2, far from linear in sin^2 but near linear in sec.  For        */
+/* R_E -> infinity the three factors become tan / cos^2, 1 / cos and       */
+/* sin^2 / cos^3, the flat tables' normalisation.                          */
+/* ======================================================================= */
+typedef struct {
+    const orc_atm *A;
+    double R_E, K, b, no_ro;   /* invariant, reference impact parameter, n_o r_o */
+    double r_o;
+    int which;
+    double floor;
+} orc_cray;
+
+enum { C_PHI = 0, C_OPT = 1, C_PHI_CORR = 2, C_OPT_N1 = 3, C_OPT_GEO = 4, C_RATIO = 5,
+       C_RATIO_GEO = 6 };
+
+static double orc_cintegrand(const orc_cray *R, double h)
+{
+    double r = R->R_E + h;
+    double n = 1.0 + orc_eta_exact(R->A, h);
+    double s = R->K / (n * r);
+    double c = sqrt(1.0 - s * s);
+    double ss = R->b / r;
+    double cs = sqrt(1.0 - ss * ss);
+    switch (R->which) {
+    /* the central-angle integrands carry a factor r_o (metres of arc at the
+     * observation level), so that the absolute tolerance means the same as
+     * for the flat tables */
+    case C_PHI: return s / c * (R->r_o / r);
+    case C_OPT: return n / c;
+    case C_PHI_CORR: return (s / c - ss / cs) * (R->r_o / r);
+    case C_OPT_N1: return (n - 1.0) / c;
+    case C_OPT_GEO: return (s * s - ss * ss) / (c * cs * (c + cs));   /* 1/c - 1/cs */
+    case C_RATIO: return (R->no_ro / (n * r) - R->r_o / r) * R->r_o / r;
+    case C_RATIO_GEO: {                       /* small-angle limit of C_OPT_GEO / sin^2 */
+        double v = R->no_ro / (n * R->r_o);   /* n_o / n */
+        return 0.5 * (v * v - 1.0) * (R->r_o / r) * (R->r_o / r);
+    }
+    }
+    return 0.0;
+}
+
+static double orc_csimpson_rec(const orc_cray *R, double a, double b, double fa, double fm,
+                               double fb, double whole, double tol, int depth)
+{
+    double m = 0.5 * (a + b);
+    double lm = 0.5 * (a + m), rm = 0.5 * (m + b);
+    double flm = orc_cintegrand(R, lm), frm = orc_cintegrand(R, rm);
+    double left = (m - a) / 6.0 * (fa + 4.0 * flm + fm);
+    double right = (b - m) / 6.0 * (fm + 4.0 * frm + fb);
+    double delta = left + right - whole;
+    if (depth <= 0 || fabs(delta) <= 15.0 * tol || fabs(delta) <= orc_noise_floor(R->floor, a, b, fa, fm, fb))
+        return left + right + delta / 15.0;
+    return orc_csimpson_rec(R, a, m, fa, flm, fm, left, 0.5 * tol, depth - 1)
+         + orc_csimpson_rec(R, m, b, fm, frm, fb, right, 0.5 * tol, depth - 1);
+}
+
+static double orc_cintegrate(const orc_cray *R, double lo, double hi, double tol)
+{
+    double sum = 0.0, a = lo;
+    for (int i = 1; i <= 5; ++i) {
+        double hb = R->A->h_bound[i];
+        if (hb > a && hb < hi) {
+            double fa = orc_cintegrand(R, a), fb = orc_cintegrand(R, hb);
+            double m = 0.5 * (a + hb), fm = orc_cintegrand(R, m);
+            sum += orc_csimpson_rec(R, a, hb, fa, fm, fb, (hb - a) / 6.0 * (fa + 4.0 * fm + fb),
+                                    tol, 48);
+            a = hb;
+        }
+    }
+    if (hi > a) {
+        double fa = orc_cintegrand(R, a), fb = orc_cintegrand(R, hi);
+        double m = 0.5 * (a + hi), fm = orc_cintegrand(R, m);
+        sum += orc_csimpson_rec(R, a, hi, fa, fm, fb, (hi - a) / 6.0 * (fa + 4.0 * fm + fb),
+                                tol, 48);
+    }
+    return sum;
+}
+
+/* The path averages, along the straight line that arrives at the
+ * observation sphere (radius r_o) with sine s_o, between r_o and r_e
+ * (dH = r_e - r_o), of b r_o / (r^2 cos^3), 1 / cos and sin^2 / cos^3 of
+ * its zenith (u = r_o / r_e, c_e' its cosine at r_e, c_o at r_o):
+ *     G_phi = r_o (tan(zeta_o) - tan(zeta_e')) / dH
+ *           = r_o s_o (1 + u) / (r_e (c_e' + u c_o) c_o c_e'),
+ *     G_1   = (r_e c_e' - r_o c_o) / dH = (r_e + r_o) / (r_e c_e' + r_o c_o),
+ *     G_2   = G_1 s_o^2 u / (c_e' c_o)
+ * (from d tan/dr = -b / (r^2 cos^3), d (r cos)/dr = 1 / cos and
+ * d (r (1 - 2 sin^2) / cos)/dr = 1 / cos^3, written without cancellation;
+ * G_2 vanishes with s_o like s_o^2). */
+static void orc_curved_factors(double r_o, double r_e, double s_o, double *g_phi,
+                               double *g_1, double *g_2)
+{
+    double u = r_o / r_e;
+    double c_o = sqrt(1.0 - s_o * s_o);
+    double se = s_o * u;
+    double ce = sqrt(1.0 - se * se);
+    *g_phi = r_o * s_o * (1.0 + u) / (r_e * (ce + u * c_o) * c_o * ce);
+    *g_1 = (r_e + r_o) / (r_e * ce + r_o * c_o);
+    *g_2 = *g_1 * s_o * s_o * u / (ce * c_o);
+}
+
+/* (B), curved: central angle phi and optical path L of the ray that arrives
+ * at the observation sphere at local zenith asin(sin_obs), up to h_e. */
+int orc_brute_ray_curved(const orc_atm *A, double R_E, double h_obs, double h_e,
+                         double sin_obs, double tol, double *phi_out, double *l_out)
+{
+    if (!(sin_obs >= 0.0 && sin_obs < 1.0) || h_e < h_obs || !(R_E > 0.0)) return -1;
+    orc_cray R;
+    R.A = A;
+    R.floor = 1e-13;
+    R.R_E = R_E;
+    R.r_o = R_E + h_obs;
+    R.no_ro = (1.0 + orc_eta_exact(A, h_obs)) * R.r_o;
+    R.K = R.no_ro * sin_obs;
+    R.b = R.r_o * sin_obs;
+    R.which = C_PHI;
+    *phi_out = orc_cintegrate(&R, h_obs, h_e, tol) / R.r_o;
+    R.which = C_OPT;
+    *l_out = orc_cintegrate(&R, h_obs, h_e, tol);
+    return 0;
+}
+
+/* Curved tables over heights h_j (as the flat ones) and observation-level
+ * zeniths with sec(zeta_k) = 1 + k dsec, dsec = (sec(theta_max) - 1)/(Z-1),
+ * accumulated interval by interval. */
+int orc_build_curved_tables(const orc_atm *A, double R_E, double h_obs, double h_max,
+                            int H, int Z, double theta_max, double tol, double *ax,
+                            double *al, double *ag)
+{
+    if (H < 2 || Z < 2 || !(h_max > h_obs) || !(theta_max > 0.0)
+        || !(theta_max < 0.5 * ORC_PI) || !(R_E > 0.0))
+        return -1;
+    double dht = (h_max - h_obs) / (double)(H - 1);
+    double dsec = (1.0 / cos(theta_max) - 1.0) / (double)(Z - 1);
+    double r_o = R_E + h_obs;
+    double no_ro = (1.0 + orc_eta_exact(A, h_obs)) * r_o;
+    for (int k = 0; k < Z; ++k) {
+        double co = 1.0 / (1.0 + (double)k * dsec);
+        double so = sqrt((1.0 - co) * (1.0 + co));
+        orc_cray R;
+        R.A = A; R.R_E = R_E; R.r_o = r_o; R.no_ro = no_ro;
+        R.floor = 1e-9;
+        R.K = no_ro * so; R.b = r_o * so;
+        double dphi = 0.0, d1 = 0.0, d2 = 0.0;
+        ax[(size_t)0 * Z + k] = 0.0;
+        al[(size_t)0 * Z + k] = 0.0;
+        ag[(size_t)0 * Z + k] = 0.0;
+        for (int j = 1; j < H; ++j) {
+            double lo = h_obs + (double)(j - 1) * dht;
+            double hi = h_obs + (double)j * dht;
+            R.which = (k == 0) ? C_RATIO : C_PHI_CORR;
+            dphi += orc_cintegrate(&R, lo, hi, tol);
+            R.which = C_OPT_N1;
+            d1 += orc_cintegrate(&R, lo, hi, tol);
+            R.which = (k == 0) ? C_RATIO_GEO : C_OPT_GEO;
+            d2 += orc_cintegrate(&R, lo, hi, tol);
+            double r_e = R_E + hi;
+            double g_phi, g_1, g_2;
+            orc_curved_factors(r_o, r_e, so, &g_phi, &g_1, &g_2);
+            /* dphi carries r_o; at k = 0 the small-angle limits' integrals,
+             * divided by G_phi / s_o -> r_o / r_e and G_2 / s_o^2 -> r_o / r_e */
+            ax[(size_t)j * Z + k] = (k == 0) ? dphi * (r_e / r_o) : dphi / g_phi;
+            al[(size_t)j * Z + k] = d1 / g_1;
+            ag[(size_t)j * Z + k] = (k == 0) ? d2 * (r_e / r_o) : d2 / g_2;
         }
     }
     return 0;
@@ -629,12 +882,22 @@ static double orc_bilinear(const double *T, int Z, int j, int k, double a, doubl
 /* Propagation of one photon bunch to the observation level (RAYBND).      */
 /* variant 0 = (T) tables, 1 = (B) brute force.  kappa scales n - 1 at the */
 /* bunch's wavelength (1 for a wavelength-independent index).               */
-/* out: X, Y, t, cx, cy, cz.  Returns the status code.                      */
+/* out: X, Y, t, cx, cy, cz of the arrival, its z relative to h_obs (0 in  */
+/* flat layers), the cosine of its zenith to the local vertical, and the   */
+/* emission height.  Returns the status code.                               */
 /* ======================================================================= */
+static int orc_propagate_curved(const orc_cfg *C, int variant, double kappa, double xe,
+                                double ye, double ze, double te, double px, double py,
+                                double pz, double *out);
+
 int orc_propagate_photon_k(const orc_cfg *C, int variant, double kappa, double xe,
                            double ye, double he, double te, double px, double py,
                            double pz, double *out)
 {
+    if (C->earth_radius > 0.0)
+        return orc_propagate_curved(C, variant, kappa, xe, ye, he, te, px, py, pz, out);
+    out[6] = 0.0;
+    out[8] = he;
     /* rare conditions first (paper Alg. 2), each a counted drop */
     if (pz >= 0.0) return ORC_ST_UPWARD;
     if (he < C->h_obs) return ORC_ST_BELOW_OBS;
@@ -712,6 +975,129 @@ int orc_propagate_photon_k(const orc_cfg *C, int variant, double kappa, double x
     out[3] = sin_obs * hx;
     out[4] = sin_obs * hy;
     out[5] = -cos_obs;
+    out[7] = cos_obs;
+    return ORC_ST_GROUND;
+}
+
+/* Curved: the emission point's radial height and local vertical r^ (from
+ * the Earth's centre); cos and sin of the photon's angle to it (the sine as
+ * |p x r^|, exact at small angles); Bouguer's invariant for the arrival
+ * zenith, sin(zeta_o) = n_e r_e sin(zeta_e) / (n_o r_o); the central angle
+ * and optical path from the tables (corrections to the straight line of the
+ * same arrival zenith, whose central angle and length are closed forms) or
+ * from the integrals; then the arrival point
+ *     x_e + (r_o cos(phi) - r_e) r^ + r_o sin(phi) t^,
+ * t^ the horizontal direction of travel at the emission point, and the
+ * arrival direction -cos(zeta_o) r^_o + sin(zeta_o) t^_o in the rotated
+ * frame.  The same rare conditions, with radial heights and the outward
+ * cosine for "upward". */
+static int orc_propagate_curved(const orc_cfg *C, int variant, double kappa, double xe,
+                                double ye, double ze, double te, double px, double py,
+                                double pz, double *out)
+{
+    double R_E = C->earth_radius;
+    double Rp = ze + R_E;
+    double rho2 = xe * xe + ye * ye;
+    double r_e = sqrt(rho2 + Rp * Rp);
+    double he = ze + rho2 / (r_e + Rp);
+    out[8] = he;
+    double rx = xe / r_e, ry = ye / r_e, rz = Rp / r_e;
+    double ce = px * rx + py * ry + pz * rz;          /* cosine to the upward vertical */
+    if (ce >= 0.0) return ORC_ST_UPWARD;
+    if (he < C->h_obs) return ORC_ST_BELOW_OBS;
+    if (he > C->h_max) return ORC_ST_ABOVE_MAX;
+    double wx = py * rz - pz * ry, wy = pz * rx - px * rz, wz = px * ry - py * rx;
+    double se = sqrt(wx * wx + wy * wy + wz * wz);
+    double eta_e, eta_o;
+    if (variant == 0) {
+        eta_e = orc_eta_lookup(C->eta_tab, C->n_fine, C->h_max, he);
+        eta_o = orc_eta_lookup(C->eta_tab, C->n_fine, C->h_max, C->h_obs);
+    } else {
+        eta_e = orc_eta_exact(&C->atm, he);
+        eta_o = orc_eta_exact(&C->atm, C->h_obs);
+    }
+    eta_e = kappa * eta_e;
+    eta_o = kappa * eta_o;
+    orc_atm Ak = C->atm;
+    Ak.n0_minus_1 = kappa * C->atm.n0_minus_1;
+    double r_o = R_E + C->h_obs;
+    double dH = he - C->h_obs;
+    double s_o = se * (r_e / r_o) * ((1.0 + eta_e) / (1.0 + eta_o));
+    double q = s_o * s_o;
+    double smax = sin(C->theta_max);
+    double q_max = smax * smax;
+    int fallback = 0;
+    if (q > q_max) {
+        if (!(C->fb_sin2_max > 0.0) || !(q <= C->fb_sin2_max)) return ORC_ST_ANGLE;
+        fallback = 1;
+    }
+    double c_o = sqrt(1.0 - q);
+    double sphi, cphi, L;
+    if (variant == 0 && !fallback) {
+        double dht = (C->h_max - C->h_obs) / (double)(C->H - 1);
+        double dsec = (1.0 / cos(C->theta_max) - 1.0) / (double)(C->Z - 1);
+        double fj = dH / dht;
+        int j = (int)fj;
+        if (j > C->H - 2) j = C->H - 2;
+        double a = fj - (double)j;
+        double fk = (1.0 / c_o - 1.0) / dsec;
+        int k = (int)fk;
+        if (k > C->Z - 2) k = C->Z - 2;
+        double b = fk - (double)k;
+        double Ax = orc_bilinear(C->ax, C->Z, j, k, a, b);
+        double A1 = orc_bilinear(C->al, C->Z, j, k, a, b);
+        double A2 = orc_bilinear(C->ag, C->Z, j, k, a, b);
+        if (C->disp_k > 0) {
+            double k_lo = C->disp_kappa[C->disp_k - 1], k_hi = C->disp_kappa[0];
+            double wk = (k_hi > k_lo) ? (kappa - k_lo) / (k_hi - k_lo) : 0.0;
+            Ax = Ax + wk * (orc_bilinear(C->ax_hi, C->Z, j, k, a, b) - Ax);
+            A1 = A1 + wk * (orc_bilinear(C->al_hi, C->Z, j, k, a, b) - A1);
+            A2 = A2 + wk * (orc_bilinear(C->ag_hi, C->Z, j, k, a, b) - A2);
+        }
+        double g_phi, g_1, g_2;
+        orc_curved_factors(r_o, r_e, s_o, &g_phi, &g_1, &g_2);
+        double dphi = Ax * g_phi / r_o;
+        double dL = A1 * g_1 + A2 * g_2;
+        /* the straight line arriving at zeta_o: at r_e its angle to the
+         * vertical has sine s_o u, u = r_o / r_e; it turns through
+         * sin(phi_s) = s_o (1 - u^2) / (cos_e' + c_o u) and is
+         * dH (r_e + r_o) / (r_e cos_e' + r_o c_o) long */
+        double u = r_o / r_e;
+        double se2 = s_o * u;
+        double ce2 = sqrt(1.0 - se2 * se2);
+        double omu2 = (dH / r_e) * (1.0 + u);
+        double sps = s_o * omu2 / (ce2 + c_o * u);
+        double cps = ce2 * c_o + se2 * s_o;
+        double lref = dH * (r_e + r_o) / (r_e * ce2 + r_o * c_o);
+        sphi = sps * cos(dphi) + cps * sin(dphi);
+        cphi = cps * cos(dphi) - sps * sin(dphi);
+        L = lref + dL;
+    } else {
+        double phi;
+        if (orc_brute_ray_curved(&Ak, R_E, C->h_obs, he, s_o, C->bf_tol, &phi, &L) != 0)
+            return ORC_ST_ANGLE;
+        sphi = sin(phi);
+        cphi = cos(phi);
+    }
+    double tx = 0.0, ty = 0.0, tz = 0.0;              /* horizontal direction of travel */
+    if (se > 0.0) {
+        tx = (px - ce * rx) / se;
+        ty = (py - ce * ry) / se;
+        tz = (pz - ce * rz) / se;
+    }
+    double omc = sphi * sphi / (1.0 + cphi);          /* 1 - cos(phi) */
+    double dr = -dH - r_o * omc;                      /* r_o cos(phi) - r_e */
+    double dtn = r_o * sphi;
+    out[0] = xe + (dr * rx + dtn * tx);
+    out[1] = ye + (dr * ry + dtn * ty);
+    out[6] = (ze - C->h_obs) + (dr * rz + dtn * tz);
+    out[2] = te + L / ORC_C_M_PER_NS;
+    double rox = cphi * rx + sphi * tx, roy = cphi * ry + sphi * ty, roz = cphi * rz + sphi * tz;
+    double tox = cphi * tx - sphi * rx, toy = cphi * ty - sphi * ry, toz = cphi * tz - sphi * rz;
+    out[3] = -c_o * rox + s_o * tox;
+    out[4] = -c_o * roy + s_o * toy;
+    out[5] = -c_o * roz + s_o * toz;
+    out[7] = c_o;
     return ORC_ST_GROUND;
 }
 
@@ -729,7 +1115,7 @@ int orc_propagate_photon(const orc_cfg *C, int variant, double xe, double ye,
 /* taken where the line crosses the horizontal plane through the centre,   */
 /* relative to the centre; its time moves at c/n_obs along the line.       */
 /* ======================================================================= */
-static int orc_telescopes(const orc_cfg *C, double X, double Y, double t,
+static int orc_telescopes(const orc_cfg *C, double X, double Y, double Zg, double t,
                           double cx, double cy, double cz, double np1_obs,
                           int32_t *tel, double *rx, double *ry, double *rt)
 {
@@ -737,14 +1123,14 @@ static int orc_telescopes(const orc_cfg *C, double X, double Y, double t,
     for (int k = 0; k < C->n_tel; ++k) {
         double tx = C->tel[4 * k + 0], ty = C->tel[4 * k + 1];
         double tz = C->tel[4 * k + 2], tr = C->tel[4 * k + 3];
-        double dx = tx - X, dy = ty - Y, dz = tz;
+        double dx = tx - X, dy = ty - Y, dz = tz - Zg;
         double q0 = dy * cz - dz * cy;
         double q1 = dz * cx - dx * cz;
         double q2 = dx * cy - dy * cx;
         double d2 = q0 * q0 + q1 * q1 + q2 * q2;
         if (d2 <= tr * tr) {
             if (nh < ORC_MAX_HITS) {
-                double s = tz / cz;
+                double s = dz / cz;
                 tel[nh] = k;
                 rx[nh] = X + s * cx - tx;
                 ry[nh] = Y + s * cy - ty;
@@ -763,7 +1149,8 @@ static int orc_telescopes(const orc_cfg *C, double X, double Y, double t,
 typedef struct {
     int status;
     double xe, ye, he, te, px, py, pz, lam;
-    double r[6];                      /* X, Y, t (before t_ref), cx, cy, cz */
+    double r[9];                      /* X, Y, t (before t_ref), cx, cy, cz, */
+                                      /* z - h_obs, local cos, emission height */
     double tr_margin;                 /* u3 - P of the transmission draw, or NaN */
     double kappa;                     /* (n - 1) scale at the bunch's wavelength */
 } orc_bunch1;
@@ -911,10 +1298,13 @@ static void orc_one_bunch(const orc_cfg *C, const orc_tracks *Tk, int64_t i, int
     B->te = Tk->t0[i] + fl * inv_bc;
     B->status = orc_propagate_photon_k(C, variant, B->kappa, B->xe, B->ye, B->he, B->te,
                                        B->px, B->py, B->pz, B->r);
+    /* the emission height: radial in a curved atmosphere */
+    if (C->earth_radius > 0.0)
+        B->he = orc_radial_height(C->earth_radius, B->xe, B->ye, B->he);
     B->tr_margin = NAN;
     if (B->status == ORC_ST_GROUND && C->trans_tau) {
         double tau = orc_trans_tau(C, B->lam, B->he);
-        double cos_obs = -B->r[5];
+        double cos_obs = B->r[7];
         double P = exp(-(tau / cos_obs));
         double u3 = orc_u01(x[3]);
         B->tr_margin = u3 - P;
@@ -964,6 +1354,7 @@ int orc_bunches(const orc_cfg *C, const orc_tracks *Tk, uint64_t seed,
             if (O->tr_margin) O->tr_margin[bidx] = B.tr_margin;
             if (B.status != ORC_ST_GROUND) {
                 O->X[bidx] = O->Y[bidx] = O->t[bidx] = 0.0;
+                if (O->Zg) O->Zg[bidx] = 0.0;
                 O->cx[bidx] = O->cy[bidx] = O->cz[bidx] = 0.0;
                 continue;
             }
@@ -971,7 +1362,8 @@ int orc_bunches(const orc_cfg *C, const orc_tracks *Tk, uint64_t seed,
             O->X[bidx] = B.r[0]; O->Y[bidx] = B.r[1]; O->t[bidx] = t;
             O->cx[bidx] = B.r[3]; O->cy[bidx] = B.r[4]; O->cz[bidx] = B.r[5];
             double np1_obs = 1.0 + B.kappa * eta_obs;
-            O->nhit[bidx] = orc_telescopes(&Cs, B.r[0], B.r[1], t, B.r[3], B.r[4], B.r[5],
+            if (O->Zg) O->Zg[bidx] = B.r[6];
+            O->nhit[bidx] = orc_telescopes(&Cs, B.r[0], B.r[1], B.r[6], t, B.r[3], B.r[4], B.r[5],
                                            np1_obs,
                                            O->hit_tel + ORC_MAX_HITS * bidx,
                                            O->hit_x + ORC_MAX_HITS * bidx,
