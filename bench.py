@@ -647,10 +647,11 @@ def run_leg(args):
 
 
 def fallback_leg(dev, args):
-    """The beyond-table fallback on the 60-degree shower (2e6 steps, FP32):
-    refraction tables to 61 deg with the fallback up to 80 deg (about 9 % of
+    """Large zeniths on the 60-degree shower (2e6 steps, FP32): refraction
+    tables to 61 deg with the beyond-table fallback up to 80 deg (about 9 % of
     the bunches arrive past the tables and take the ray integrals), against
-    tables to 75 deg that cover every bunch."""
+    tables to 75 deg that cover every bunch, and the curved atmosphere
+    (Earth radius 6371 km) with its tables to 80 deg."""
     import torch
 
     import paper_2006_14927_gb300 as P
@@ -659,8 +660,11 @@ def fallback_leg(dev, args):
     dtr = P.device_tracks(sc["tracks"], P.CHER_FP32_BULK, device=dev, t_ref=sc["t_ref"])
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     res = {}
-    for name, theta, fb in (("tables_75deg", 75.0, 0.0), ("tables_61deg_fallback_80deg", 61.0, 80.0)):
+    for name, theta, fb, radius in (("tables_75deg", 75.0, 0.0, 0.0),
+                                    ("tables_61deg_fallback_80deg", 61.0, 80.0, 0.0),
+                                    ("curved_tables_80deg", 80.0, 0.0, 6.371e6)):
         ctx = P.Context(sc["atm"], sc["h_obs"], sc["telescopes"])
+        ctx.set_curved(radius)
         ctx.build_refraction_tables(1000, 64, theta, sc["h_max"])
         ctx.set_fallback(fb)
         out = ctx.alloc_hits(2_000_000, P.CHER_FP32_BULK, device=dev)

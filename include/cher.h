@@ -423,8 +423,8 @@ cher_status cher_set_transmission(cher_ctx *ctx, const cher_transmission *table)
  * (0: max(2^20, 4 x the call's steps); 64 B each in FP32, 112 B in FP64,
  * allocated on the first call that needs them), the rest counted in
  * stats[CHER_STAT_FB_LOST].  Trace launches integrate them in place.  The
- * adjoint and the allocation-free launch do not use it (those bunches stay
- * dropped there).
+ * adjoint, the allocation-free launch and the curved atmosphere do not use
+ * it (those bunches stay dropped there).
  *   zenith_max_deg: 0 (off) or in (the tables' zenith range, 85];
  *   queue_records : 0 or up to 2^34.
  * Errors: CHER_EINVAL. */
@@ -456,6 +456,28 @@ cher_status cher_set_fallback(cher_ctx *ctx, double zenith_max_deg, int64_t queu
  * CHER_ENOMEM, CHER_ECUDA. */
 #define CHER_DISPERSION_MAX_NODES 9
 cher_status cher_set_dispersion(cher_ctx *ctx, const double *kappa, int32_t k);
+
+/* Curved atmosphere (an extension for large zenith angles: the paper's
+ * RAYBND works in flat layers).  With an Earth radius R_E set, positions are
+ * Cartesian in the core frame (z up, z = height a.s.l. on the core's
+ * vertical), the Earth's centre is (0, 0, -R_E), a point's height is its
+ * radial height |x - C| - R_E (the steps' index is taken at the radial
+ * height of their midpoint), rays keep Bouguer's invariant n r sin(zeta)
+ * (zeta the angle to the local vertical) and end on the observation sphere
+ * r_o = R_E + h_obs.  The refraction tables become corrections of the
+ * central angle and of the optical path to the straight line with the same
+ * arrival zenith (three values per node, a zenith axis uniform in
+ * sec(zeta_o), the table sizes of the context) and are rebuilt now if built.
+ * Records: the arrival point (X, Y) on the observation sphere, which lies
+ * (X^2 + Y^2)/2R_E below the tangent plane; the sphere test and the record
+ * plane use that point; z_emit is the radial height; the transmission uses
+ * the local zenith.  Telescope z stays relative to the tangent plane at h_obs.
+ *   earth_radius_m: 0 (flat layers) or in [1e6, 1e8] m.
+ * Launches with it run 128-step tiles; the beyond-table fallback is off in
+ * it (build the tables up to 85 degrees instead); the read-out, its adjoint
+ * and the production profile refuse it (CHER_EINVAL).  Blocking.  Errors:
+ * CHER_EINVAL, CHER_ENOMEM, CHER_ECUDA (the previous geometry is kept). */
+cher_status cher_set_curved(cher_ctx *ctx, double earth_radius_m);
 
 /* Replace the atmosphere and, if tables were built, rebuild them with the
  * same sizes (blocking).  Errors as cher_build_refraction_tables. */
@@ -508,6 +530,15 @@ cher_status cher_trace_bunches(cher_ctx *ctx, const cher_tracks *tracks,
  * CHER_ESTATE before cher_build_refraction_tables. */
 cher_status cher_get_tables(const cher_ctx *ctx, double *eta, double *ax,
                             double *al);
+
+/* The curved atmosphere's host table builder on its own (no CUDA call):
+ * ax, al, ag [n_heights * n_zenith] (row-major, height first) as
+ * cher_set_curved builds them, zenith nodes uniform in sec.  Errors:
+ * CHER_EINVAL. */
+cher_status cher_build_curved_tables_host(const cher_atmosphere *atm, double earth_radius_m,
+                                          double h_obs, int32_t n_heights, int32_t n_zenith,
+                                          double zenith_max_deg, double h_max, double *ax,
+                                          double *al, double *ag);
 
 /* The host table builder on its own (no CUDA call): fills eta[n_fine],
  * ax[n_heights * n_zenith], al[n_heights * n_zenith] exactly as

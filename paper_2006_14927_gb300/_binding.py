@@ -111,6 +111,7 @@ SIGNATURES = {
     "cher_set_transmission": (_S, [_P, ctypes.POINTER(Transmission)]),
     "cher_set_fallback": (_S, [_P, ctypes.c_double, ctypes.c_int64]),
     "cher_set_dispersion": (_S, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
+    "cher_set_curved": (_S, [_P, ctypes.c_double]),
     "cher_generate_steps": (_S, [_P, ctypes.POINTER(Shower), ctypes.c_int32, ctypes.c_uint64, _S,
                                  ctypes.POINTER(StepBuffers), _P]),
     "cher_generate_propagate_noalloc": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
@@ -126,6 +127,10 @@ SIGNATURES = {
     "cher_trace_bunches": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S, _P,
                                 ctypes.POINTER(Trace), _P]),
     "cher_get_tables": (_S, [_P, _P, _P, _P]),
+    "cher_build_curved_tables_host": (_S, [ctypes.POINTER(Atmosphere), ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
     "cher_build_tables_host": (_S, [ctypes.POINTER(Atmosphere), ctypes.c_double, ctypes.c_int32,
                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                     ctypes.c_double, _P, _P, _P]),
@@ -185,6 +190,19 @@ def build_tables_host(atm: dict, h_obs: float, n_fine: int, n_heights: int, n_ze
                                         float(h_max), eta.ctypes.data, ax.ctypes.data,
                                         al.ctypes.data), "cher_build_tables_host")
     return eta, ax, al
+
+
+def build_curved_tables_host(atm: dict, earth_radius_m: float, h_obs: float, n_heights: int,
+                             n_zenith: int, zenith_max_deg: float, h_max: float):
+    """The curved atmosphere's host tables (no CUDA call): ax, al, ag."""
+    out = [np.zeros((n_heights, n_zenith)) for _ in range(3)]
+    A = atmosphere_struct(atm)
+    _check(lib().cher_build_curved_tables_host(ctypes.byref(A), float(earth_radius_m),
+                                               float(h_obs), int(n_heights), int(n_zenith),
+                                               float(zenith_max_deg), float(h_max),
+                                               *[o.ctypes.data for o in out]),
+           "cher_build_curved_tables_host")
+    return tuple(out)
 
 
 def build_sensitivity_host(atm: dict, h_obs: float, n_fine: int, n_heights: int,
@@ -494,6 +512,10 @@ class Context:
         k = np.ascontiguousarray(np.asarray(kappa, dtype=np.float64).ravel())
         _check(lib().cher_set_dispersion(self._h, k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                          int(k.size)), "cher_set_dispersion")
+
+    def set_curved(self, earth_radius_m: float):
+        """Curved atmosphere with this Earth radius (m); 0 for flat layers."""
+        _check(lib().cher_set_curved(self._h, float(earth_radius_m)), "cher_set_curved")
 
     def set_atmosphere(self, atm: dict):
         A = atmosphere_struct(atm)

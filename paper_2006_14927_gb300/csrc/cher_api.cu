@@ -76,6 +76,8 @@ struct cher_ctx {
     // the pair-interleaved layout, {kappa_lo entry, kappa_hi entry}
     int32_t disp_k = 0;
     double kap[cher::kDispMax] = {};
+    // curved atmosphere: the Earth's radius (0: flat layers)
+    double earth_radius = 0.0;
     double *d_kap64 = nullptr;
     float *d_kap32 = nullptr;
     void *d_tabd64 = nullptr, *d_tabd32 = nullptr;
@@ -183,6 +185,23 @@ cher_status upload_grid(cher_ctx *c, int g) {
     return CHER_OK;
 }
 
+// Device layout of one table set: per entry (j, k < Z-1) the pair
+// {ax_k, al_k, ax_k+1, al_k+1} and, in a curved atmosphere, {ag_k, ag_k+1, 0, 0}.
+size_t entry_values(const cher::HostTables &T) { return T.earth_radius > 0.0 ? 8 : 4; }
+
+void pack_entry(const cher::HostTables &T, int j, int k, double *out) {
+    const size_t a = static_cast<size_t>(j) * T.Z + k;
+    out[0] = T.ax[a];
+    out[1] = T.al[a];
+    out[2] = T.ax[a + 1];
+    out[3] = T.al[a + 1];
+    if (T.earth_radius > 0.0) {
+        out[4] = T.ag[a];
+        out[5] = T.ag[a + 1];
+        out[6] = out[7] = 0.0;
+    }
+}
+
 // The refraction tables of kappa[k-1] (lo) and kappa[0] (hi): the context's
 // table shape with n - 1 scaled by kappa, interleaved per entry.
 cher_status build_dispersion_tables(cher_ctx *c) {
@@ -194,23 +213,18 @@ cher_status build_dispersion_tables(cher_ctx *c) {
         cher_atmosphere a = c->atm;
         a.n0_minus_1 *= s == 0 ? c->kap[c->disp_k - 1] : c->kap[0];
         const cher_status r = cher::build_tables(a, c->h_obs, 2, c->tab_H, c->tab_Z, th,
-                                                 c->tab_hmax, T[s]);
+                                                 c->tab_hmax, T[s], c->earth_radius);
         if (r != CHER_OK) return r;
     }
     const int H = T[0].H, Z = T[0].Z;
-    std::vector<double> t64(static_cast<size_t>(H) * (Z - 1) * 8);
+    const size_t per = entry_values(T[0]);
+    std::vector<double> t64(static_cast<size_t>(H) * (Z - 1) * 2 * per);
     std::vector<float> t32(t64.size());
     for (int j = 0; j < H; ++j)
         for (int k = 0; k < Z - 1; ++k) {
-            const size_t e = (static_cast<size_t>(j) * (Z - 1) + k) * 8;
-            const size_t a = static_cast<size_t>(j) * Z + k;
-            for (int s = 0; s < 2; ++s) {
-                t64[e + 4 * s + 0] = T[s].ax[a];
-                t64[e + 4 * s + 1] = T[s].al[a];
-                t64[e + 4 * s + 2] = T[s].ax[a + 1];
-                t64[e + 4 * s + 3] = T[s].al[a + 1];
-            }
-            for (int q = 0; q < 8; ++q) t32[e + q] = static_cast<float>(t64[e + q]);
+            const size_t e = (static_cast<size_t>(j) * (Z - 1) + k) * 2 * per;
+            for (int s = 0; s < 2; ++s) pack_entry(T[s], j, k, &t64[e + per * s]);
+            for (size_t q = 0; q < 2 * per; ++q) t32[e + q] = static_cast<float>(t64[e + q]);
         }
     float k32[cher::kDispMax];
     for (int m = 0; m < cher::kDispMax; ++m) k32[m] = static_cast<float>(c->kap[m]);
@@ -303,7 +317,13 @@ cher::KParams base_params(const cher_ctx *c, const cher_tracks *t, uint64_t seed
                             (c->atm.b[0] / c->atm.c[0]);
     }
     cher::gauss_legendre12(p.gl_x, p.gl_w);
-    if (c->fb_deg > c->tab_zen && c->built) {
+    if (c->earth_radius > 0.0) {
+        p.earth_radius = c->earth_radius;
+        p.r_o = c->earth_radius + c->h_obs;
+        p.inv_ro = 1.0 / p.r_o;
+        p.inv_dsec = c->T.inv_dsec;
+    }
+    if (c->fb_deg > c->tab_zen && c->built && c->earth_radius == 0.0) {
         const double sf = std::sin(c->fb_deg * 3.14159265358979323846 / 180.0);
         p.fb_q = sf * sf;
     }
@@ -341,7 +361,7 @@ cher::KParams base_params(const cher_ctx *c, const cher_tracks *t, uint64_t seed
 
 cher_status launch(cher_ctx *c, cher::KParams &p, bool fp32, int mode, bool persistent,
                    void *stream) {
-    const int block = p.disp_k > 0 ? cher::kDispBlock : c->block;
+    const int block = (p.disp_k > 0 || p.earth_radius > 0.0) ? cher::kDispBlock : c->block;
     p.n_tiles = (p.n + block - 1) / block;
     if (p.n_tiles == 0) return CHER_OK;
     const size_t smem = cher::kernel_smem_bytes(fp32, block, p);
@@ -452,15 +472,31 @@ cher_status cher_build_refraction_tables(cher_ctx *c, int32_t n_heights, int32_t
     cher::HostTables T;
     const double th = zenith_max_deg * cher::kPi / 180.0;
     cher_status s = cher::build_tables(c->atm, c->h_obs, c->opt.n_fine, n_heights, n_zenith, th,
-                                       h_max, T);
+                                       h_max, T, c->earth_radius);
     if (s != CHER_OK) return s;
     // candidate grids for two zenith bands: photons steeper than 25 degrees
-    // (the bulk of a near-vertical shower) see a much smaller reach
+    // (the bulk of a near-vertical shower) see a much smaller reach.  In a
+    // curved atmosphere the ground point lies up to rho^2 / 2R_E below the
+    // tangent plane and the local vertical is tilted by up to rho / R_E
+    // (rho: the telescopes' distance from the core plus their reach): the
+    // spheres' heights and the zenith range grow by that much for the grid.
+    std::vector<cher_telescope> tg(c->tel);
+    double tilt = 0.0;
+    if (c->earth_radius > 0.0) {
+        double rho_max = 0.0;
+        for (const cher_telescope &q : c->tel)
+            rho_max = std::max(rho_max, std::hypot(q.x, q.y) + q.r);
+        rho_max += 1000.0;
+        tilt = rho_max / c->earth_radius;
+        for (cher_telescope &q : tg)
+            q.z = std::fabs(q.z) + rho_max * rho_max / (2.0 * c->earth_radius);
+    }
     cher::HostGrid G[2];
     const double th_band = std::min(th, 25.0 * cher::kPi / 180.0);
-    s = cher::build_grid(c->tel.data(), static_cast<int32_t>(c->tel.size()), th_band, G[0]);
+    s = cher::build_grid(tg.data(), static_cast<int32_t>(tg.size()), th_band + tilt, G[0]);
     if (s != CHER_OK) return s;
-    s = cher::build_grid(c->tel.data(), static_cast<int32_t>(c->tel.size()), th, G[1]);
+    s = cher::build_grid(tg.data(), static_cast<int32_t>(tg.size()),
+                         std::min(th + tilt, 85.0 * cher::kPi / 180.0), G[1]);
     if (s != CHER_OK) return s;
     if (static_cast<double>(n_heights) * n_zenith * 32.0 > 4.0e9) return CHER_ERANGE;
     free_tables(c);
@@ -474,17 +510,14 @@ cher_status cher_build_refraction_tables(cher_ctx *c, int32_t n_heights, int32_t
         c->eta_slope = std::max(c->eta_slope, std::fabs(c->T.eta[k + 1] - c->T.eta[k]) * c->T.inv_dh);
 
     const int H = c->T.H, Z = c->T.Z;
-    std::vector<double> t64(static_cast<size_t>(H) * (Z - 1) * 4);
+    const size_t per = entry_values(c->T);
+    std::vector<double> t64(static_cast<size_t>(H) * (Z - 1) * per);
     std::vector<float> t32(t64.size());
     for (int j = 0; j < H; ++j)
         for (int k = 0; k < Z - 1; ++k) {
-            const size_t e = (static_cast<size_t>(j) * (Z - 1) + k) * 4;
-            const size_t a = static_cast<size_t>(j) * Z + k;
-            t64[e + 0] = c->T.ax[a];
-            t64[e + 1] = c->T.al[a];
-            t64[e + 2] = c->T.ax[a + 1];
-            t64[e + 3] = c->T.al[a + 1];
-            for (int q = 0; q < 4; ++q) t32[e + q] = static_cast<float>(t64[e + q]);
+            const size_t e = (static_cast<size_t>(j) * (Z - 1) + k) * per;
+            pack_entry(c->T, j, k, &t64[e]);
+            for (size_t q = 0; q < per; ++q) t32[e + q] = static_cast<float>(t64[e + q]);
         }
     std::vector<float> e32(c->T.eta.begin(), c->T.eta.end());
     const size_t nt = c->tel.size();
@@ -580,6 +613,27 @@ cher_status cher_set_transmission(cher_ctx *c, const cher_transmission *tb) {
     c->trans_h0 = tb->h_min;
     c->trans_h1 = tb->h_max;
     return CHER_OK;
+}
+
+cher_status cher_set_curved(cher_ctx *c, double earth_radius_m) {
+    if (!c || !std::isfinite(earth_radius_m)) return CHER_EINVAL;
+    if (earth_radius_m != 0.0 && !(earth_radius_m >= 1.0e6 && earth_radius_m <= 1.0e8))
+        return CHER_EINVAL;
+    if (!check_device(c)) return CHER_EINVAL;
+    const double old = c->earth_radius;
+    c->earth_radius = earth_radius_m;
+    if (!c->built) return CHER_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        c->earth_radius = old;
+        return CHER_ECUDA;
+    }
+    const cher_status s = cher_build_refraction_tables(c, c->tab_H, c->tab_Z, c->tab_zen,
+                                                       c->tab_hmax);
+    if (s != CHER_OK) {
+        c->earth_radius = old;
+        cher_build_refraction_tables(c, c->tab_H, c->tab_Z, c->tab_zen, c->tab_hmax);
+    }
+    return s;
 }
 
 cher_status cher_set_dispersion(cher_ctx *c, const double *kappa, int32_t k) {
@@ -754,6 +808,7 @@ cher_status cher_generate_propagate_ex(cher_ctx *c, const cher_tracks *t, uint64
                  reinterpret_cast<uintptr_t>(prof->axis_cos) % alignof(double) ||
                  int64_t(std::max(t->n_showers, 1)) * prof->n_bins > 0x7fffffffLL))
         return CHER_EINVAL;
+    if (prof && c->earth_radius > 0.0) return CHER_EINVAL;   // depths of flat layers
     if (prec != CHER_FP64 && prec != CHER_FP32_BULK) return CHER_EINVAL;
     if (!c->built) return CHER_ESTATE;
     if (!check_device(c)) return CHER_EINVAL;
@@ -917,6 +972,23 @@ cher_status cher_build_tables_host(const cher_atmosphere *atm, double h_obs, int
     return CHER_OK;
 }
 
+cher_status cher_build_curved_tables_host(const cher_atmosphere *atm, double earth_radius_m,
+                                          double h_obs, int32_t n_heights, int32_t n_zenith,
+                                          double zenith_max_deg, double h_max, double *ax,
+                                          double *al, double *ag) {
+    if (!atm || !ax || !al || !ag || !(earth_radius_m >= 1.0e6 && earth_radius_m <= 1.0e8))
+        return CHER_EINVAL;
+    cher::HostTables T;
+    const cher_status s = cher::build_tables(*atm, h_obs, 2, n_heights, n_zenith,
+                                             zenith_max_deg * cher::kPi / 180.0, h_max, T,
+                                             earth_radius_m);
+    if (s != CHER_OK) return s;
+    std::copy(T.ax.begin(), T.ax.end(), ax);
+    std::copy(T.al.begin(), T.al.end(), al);
+    std::copy(T.ag.begin(), T.ag.end(), ag);
+    return CHER_OK;
+}
+
 cher_status cher_autotune(cher_ctx *c, const cher_tracks *t, uint64_t seed, cher_precision prec,
                           const cher_output *out, const char *cache_path, void *stream) {
     if (!c || !tracks_ok(t) || !out) return CHER_EINVAL;
@@ -1008,6 +1080,7 @@ cher_status readout(cher_ctx *c, const cher_tracks *t, uint64_t seed, cher_preci
     if (prec != CHER_FP64 && prec != CHER_FP32_BULK) return CHER_EINVAL;
     if (!(sigma > 0.0) || !std::isfinite(sigma)) return CHER_EINVAL;
     if (c->disp_k > 0) return CHER_EINVAL;   // defined for a wavelength-independent index
+    if (c->earth_radius > 0.0) return CHER_EINVAL;   // and for flat layers
     if (!c->built) return CHER_ESTATE;
     if (!check_device(c)) return CHER_EINVAL;
     if (t->n > 0x7fffffffLL) return CHER_ERANGE;
@@ -1319,7 +1392,7 @@ extern "C" cher_status cher_generate_propagate_noalloc(cher_ctx *c, const cher_t
     p.cap = out->cap_per_tel;
     p.count = out->count;
     p.stats = out->stats;
-    const int block = p.disp_k > 0 ? cher::kDispBlock : c->block;
+    const int block = (p.disp_k > 0 || p.earth_radius > 0.0) ? cher::kDispBlock : c->block;
     p.n_tiles = (p.n + block - 1) / block;
     if (p.n_tiles == 0) return CHER_OK;
     const size_t smem = cher::kernel_smem_bytes(fp32, block, p);

@@ -109,8 +109,30 @@ __device__ __forceinline__ bool step_valid(const KParams &p, int64_t i) {
            finite_r<R>(__ldg(static_cast<const R *>(p.uy) + i));
 }
 
+// In a curved atmosphere the index is taken at the radial height of the
+// step's midpoint, |x_m - C| - R_E = h_m + rho^2 / (sqrt(rho^2 + (h_m + R_E)^2) + h_m + R_E),
+// in the oracle's order.  xy = {x0, y0, ux, uy}.
+__device__ __forceinline__ double curved_midpoint(const KParams &p, double hm, double half_len,
+                                                  const double *xy) {
+    const double dx = __dmul_rn(half_len, xy[2]);
+    const double xm = __dadd_rn(xy[0], dx);
+    const double dy = __dmul_rn(half_len, xy[3]);
+    const double ym = __dadd_rn(xy[1], dy);
+    const double xx = __dmul_rn(xm, xm);
+    const double yy = __dmul_rn(ym, ym);
+    const double rho2 = __dadd_rn(xx, yy);
+    const double Rp = __dadd_rn(hm, p.earth_radius);
+    const double RR = __dmul_rn(Rp, Rp);
+    const double r2 = __dadd_rn(rho2, RR);
+    const double r = __dsqrt_rn(r2);
+    const double den = __dadd_rn(r, Rp);
+    const double corr = __ddiv_rn(rho2, den);
+    return __dadd_rn(hm, corr);
+}
+
 __device__ __forceinline__ void step_yield(const KParams &p, bool others_valid, double z0,
-                                           double len, double ekin, double uz, Yield &y) {
+                                           double len, double ekin, double uz, Yield &y,
+                                           const double *xy = nullptr) {
     y.nb = 0;
     y.valid = false;
     y.N = y.s2 = y.g = y.gam = y.eta = 0.0;
@@ -122,7 +144,8 @@ __device__ __forceinline__ void step_yield(const KParams &p, bool others_valid, 
     const double gam2 = __dmul_rn(gam, gam);
     const double half_len = __dmul_rn(0.5, len);
     const double dz = __dmul_rn(half_len, uz);
-    const double hm = __dadd_rn(z0, dz);
+    double hm = __dadd_rn(z0, dz);
+    if (xy) hm = curved_midpoint(p, hm, half_len, xy);
     const double eta = eta_exact_lookup(p, hm);
     const double np1 = __dadd_rn(1.0, eta);
     const double np1sq = __dmul_rn(np1, np1);

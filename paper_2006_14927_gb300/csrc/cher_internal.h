@@ -36,6 +36,12 @@ struct HostTables {
     int32_t H = 0, Z = 0;
     double theta_max = 0, dht = 0, inv_dht = 0, q_max = 0, dq = 0, inv_dq = 0;
     std::vector<double> ax, al;          // [H][Z]
+    // curved atmosphere (earth_radius > 0): zenith nodes uniform in sec,
+    // sec_k = 1 + k dsec, and a third table (the geometric part of the
+    // optical-path correction); ax, al, ag normalised by the path averages
+    // of their first-order factors along the straight reference line
+    double earth_radius = 0, dsec = 0, inv_dsec = 0;
+    std::vector<double> ag;              // [H][Z]
 };
 
 // Ground grid of telescope candidates (step a4).
@@ -49,7 +55,7 @@ struct HostGrid {
 // Build eta, ax, al (table definitions in cher_tables.cpp).
 cher_status build_tables(const cher_atmosphere &atm, double h_obs, int32_t n_fine,
                          int32_t H, int32_t Z, double theta_max, double h_max,
-                         HostTables &out);
+                         HostTables &out, double earth_radius = 0.0);
 // Eta lookup in the fine table, one IEEE operation per statement (the same
 // rounding as the device lookup that decides the bunch count).
 double eta_lookup(const HostTables &t, double h);
@@ -162,6 +168,12 @@ struct KParams {
     const float *kap32;
     double disp_Kd, disp_u1, disp_du, kap_lo, kap_winv;
     const void *tabd;
+    // curved atmosphere (earth_radius = 0: flat layers): r_o = R_E + h_obs;
+    // the tables' zenith axis is uniform in sec (inv_dsec) and an entry holds
+    // two more values (the geometric part of the optical path): entry (j, k)
+    // = {ax_k, al_k, ax_k+1, al_k+1}, {ag_k, ag_k+1, 0, 0} (and with kappa,
+    // that pair for kap_lo then for kap_hi)
+    double earth_radius, r_o, inv_ro, inv_dsec;
     // the per-launch constants of the bunch loop, rounded to float on the
     // host: the FP32 path converts nothing from double on the device
     struct {
@@ -176,6 +188,7 @@ struct KParams {
         float hb[6], a[5], b[5], c[5], inv_c[5], t_top[5];
         float kap[kDispMax], disp_Kd, disp_u1, disp_du, kap_lo, kap_winv;
         float eta_coef[5], gl_x[12], gl_w[12];
+        float earth_radius, r_o, inv_ro, inv_dsec;
     } f;
 };
 
@@ -208,15 +221,18 @@ enum Mode : int { MODE_HITS = 0, MODE_TRACE = 1, MODE_YIELD = 2, MODE_SCREEN = 3
 // tables' zenith range
 constexpr int kTransBit = 4;
 constexpr int kFbBit = 8;
-// and when the index depends on the wavelength (instantiated for 128-step
-// tiles and the hits, trace and yield modes only)
+// and when the index depends on the wavelength, and in a curved atmosphere
+// (both instantiated for 128-step tiles and the hits, trace and yield modes
+// only; the curved atmosphere without the beyond-table fallback)
 constexpr int kDispBit = 16;
+constexpr int kCurvBit = 32;
 constexpr int kDispBlock = 128;
 inline int kernel_mode(int mode, const KParams &p) {
     int m = mode;
     if (p.trans && mode != MODE_YIELD) m |= kTransBit;
     if (p.fb_q > 0.0 && (mode == MODE_HITS || mode == MODE_TRACE)) m |= kFbBit;
     if (p.disp_k > 0) m |= kDispBit;
+    if (p.earth_radius > 0.0) m |= kCurvBit;
     return m;
 }
 // The fallback pass over the queued bunches (after a MODE_HITS launch with

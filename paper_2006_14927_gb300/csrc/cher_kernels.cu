@@ -69,9 +69,23 @@ __device__ __forceinline__ bool d_not_positive(double v) {
     return b < 0 || b == 0;
 }
 
+// The FP32 radial midpoint height in a curved atmosphere (xyf = {x0, y0,
+// ux, uy}); its rounding (a few ulp of the correction) joins the bound.
+__device__ __forceinline__ float curved_midpoint_f(const KParams &p, float hm, float L,
+                                                   const float *xyf, float &err) {
+    const float half = 0.5f * L;
+    const float xm = xyf[0] + half * xyf[2], ym = xyf[1] + half * xyf[3];
+    const float rho2 = xm * xm + ym * ym;
+    const float Rp = hm + p.f.earth_radius;
+    const float corr = rho2 / (sqrtf(rho2 + Rp * Rp) + Rp);
+    err = 32.0f * 5.9604645e-8f * corr;
+    return hm + corr;
+}
+
 __device__ __forceinline__ void step_yield_screened(const KParams &p, bool others_valid,
                                                     double z0, double len, double ekin, float uz,
-                                                    YieldF &y) {
+                                                    YieldF &y, const float *xyf = nullptr,
+                                                    const double *xyd = nullptr) {
     y.nb = 0;
     y.valid = false;
     y.g = y.eta = y.s2 = y.N = 0.0f;
@@ -84,7 +98,9 @@ __device__ __forceinline__ void step_yield_screened(const KParams &p, bool other
     const float z = d2f_rn(z0);
     const float g = e * p.f.inv_me;
     const float gam = 1.0f + g, gam2 = gam * gam;
-    const float hm = z + (0.5f * L) * uz;
+    float hm = z + (0.5f * L) * uz;
+    float curv_err = 0.0f;
+    if (xyf) hm = curved_midpoint_f(p, hm, L, xyf, curv_err);
     float hc = fminf(fmaxf(hm, 0.0f), p.f.h_max);
     const float x = hc * p.f.inv_dh;
     int k = static_cast<int>(x);
@@ -102,7 +118,8 @@ __device__ __forceinline__ void step_yield_screened(const KParams &p, bool other
     const float KL = p.f.K * L;
     const float q = KL * s2 * p.f.inv_B;
     // rounding-error bound (first order, each term padded)
-    const float d_eta = 6.0f * u * p.f.eta_slope * (fabsf(z) + L + p.f.dh) + 5.0f * u * eta;
+    const float d_eta = p.f.eta_slope * (6.0f * u * (fabsf(z) + L + p.f.dh) + curv_err) +
+                        5.0f * u * eta;
     const float d_a = (2.0f + 2.0f * eta) * d_eta + 3.0f * u * a;
     const float d_A = gam2 * (d_a + 10.0f * u * a);
     const float d_B = 2.0f * np1 * d_eta + 3.0f * u * np1sq;
@@ -121,7 +138,7 @@ __device__ __forceinline__ void step_yield_screened(const KParams &p, bool other
     }
     // exact FP64 chain (rare)
     Yield yd;
-    step_yield(p, true, z0, len, ekin, static_cast<double>(uz), yd);
+    step_yield(p, true, z0, len, ekin, static_cast<double>(uz), yd, xyd);
     y.valid = yd.valid;
     y.nb = yd.nb;
     y.g = static_cast<float>(yd.g);
@@ -166,7 +183,7 @@ __device__ __forceinline__ double disp_piece(double x, double y, double gam2, do
 template <class R>
 __device__ __forceinline__ void step_yield_disp(const KParams &p, bool others_valid, double z0,
                                                 double len, double ekin, double uz, Yield &y,
-                                                SegD<R> &D) {
+                                                SegD<R> &D, const double *xy = nullptr) {
     y.nb = 0;
     y.valid = false;
     y.N = y.s2 = y.g = y.gam = y.eta = 0.0;
@@ -178,7 +195,8 @@ __device__ __forceinline__ void step_yield_disp(const KParams &p, bool others_va
     const double gam2 = __dmul_rn(gam, gam);
     const double half_len = __dmul_rn(0.5, len);
     const double dz = __dmul_rn(half_len, uz);
-    const double hm = __dadd_rn(z0, dz);
+    double hm = __dadd_rn(z0, dz);
+    if (xy) hm = curved_midpoint(p, hm, half_len, xy);
     const double eta = eta_exact_lookup(p, hm);
     const double two_g = __dadd_rn(2.0, g);
     const double bg2 = __dmul_rn(g, two_g);
@@ -237,7 +255,9 @@ __device__ __forceinline__ void step_yield_disp(const KParams &p, bool others_va
 // integer within reach) takes the exact chain.
 __device__ __forceinline__ void step_yield_screened_disp(const KParams &p, bool others_valid,
                                                          double z0, double len, double ekin,
-                                                         float uz, YieldF &y, SegD<float> &D) {
+                                                         float uz, YieldF &y, SegD<float> &D,
+                                                         const float *xyf = nullptr,
+                                                         const double *xyd = nullptr) {
     y.nb = 0;
     y.valid = false;
     y.g = y.eta = y.s2 = y.N = 0.0f;
@@ -250,7 +270,9 @@ __device__ __forceinline__ void step_yield_screened_disp(const KParams &p, bool 
     const float z = d2f_rn(z0);
     const float g = e * p.f.inv_me;
     const float gam = 1.0f + g, gam2 = gam * gam;
-    const float hm = z + (0.5f * L) * uz;
+    float hm = z + (0.5f * L) * uz;
+    float curv_err = 0.0f;
+    if (xyf) hm = curved_midpoint_f(p, hm, L, xyf, curv_err);
     float hc = fminf(fmaxf(hm, 0.0f), p.f.h_max);
     const float x = hc * p.f.inv_dh;
     int k = static_cast<int>(x);
@@ -261,7 +283,8 @@ __device__ __forceinline__ void step_yield_screened_disp(const KParams &p, bool 
     const float bg2 = g * (2.0f + g);
     const float beta = sqrtf(bg2) / gam;
     const float x_th = 1.0f / (gam2 * beta * (1.0f + beta));
-    const float d_eta = 6.0f * u * p.f.eta_slope * (fabsf(z) + L + p.f.dh) + 5.0f * u * eta;
+    const float d_eta = p.f.eta_slope * (6.0f * u * (fabsf(z) + L + p.f.dh) + curv_err) +
+                        5.0f * u * eta;
     const float tol_x = 64.0f * u * x_th;
     const float e_hi = eta * p.f.kap[0], e_lo = eta * p.f.kap_lo;
     const int K = p.disp_k;
@@ -308,7 +331,7 @@ __device__ __forceinline__ void step_yield_screened_disp(const KParams &p, bool 
         }
     }
     Yield yd;
-    step_yield_disp<float>(p, true, z0, len, ekin, static_cast<double>(uz), yd, D);
+    step_yield_disp<float>(p, true, z0, len, ekin, static_cast<double>(uz), yd, D, xyd);
     y.valid = yd.valid;
     y.nb = yd.nb;
     y.g = static_cast<float>(yd.g);
@@ -594,6 +617,7 @@ struct BunchOut {
     R X, Y, cx, cy, cz, t, he, lam;
     R kap;               // (n - 1) scale at the bunch's wavelength
     R c2;                // cos^2 of the arrival zenith (queued fallback bunches)
+    R zg;                // arrival z - h_obs (curved atmosphere; 0 in flat layers)
     int status;
 };
 
@@ -774,7 +798,166 @@ struct alignas(16) FbEntry {
     uint32_t step_hi;                              // bits 32.. of the global step index
 };
 
-template <class R, bool TR, int FB, bool DS>
+// ------------------------------------------------------------------------
+// a3 in a curved atmosphere (spherical shells around C = (0, 0, -R_E) in the
+// core frame, Bouguer's invariant n r sin(zeta)): the emission point's
+// radial height and local vertical; the photon's angle to it (sine as
+// |p x r^|, exact at small angles); sin(zeta_o) = sin(zeta_e) (r_e / r_o)
+// (n_e / n_o); the central angle and optical path of the straight line that
+// arrives at zeta_o (closed forms, below) plus the tables' corrections
+// (central angle; (n - 1) and geometric parts of the optical path, each
+// times the path average of its first-order factor along that line); the
+// arrival point x_e + (r_o cos(phi) - r_e) r^ + r_o sin(phi) t^ and
+// direction -cos(zeta_o) r^_o + sin(zeta_o) t^_o in the plane of the centre.
+// Every difference of nearly equal terms is written out: h_e - h_obs =
+// (z - h_obs) + rho^2 / (r_e + z + R_E), 1 - u = (h_e - h_obs) / r_e,
+// cos_e'^2 = cos_o^2 + sin_o^2 (1 - u)(1 + u), 1 - cos(phi) = sin^2 / (1 + cos).
+// ------------------------------------------------------------------------
+template <class R, bool TR, bool DS>
+__device__ __forceinline__ void propagate_curved(const KParams &p, const Consts<R> &c,
+                                                 const Seg<R> &S, R fl, R px, R py, R pz,
+                                                 uint32_t w3, BunchOut<R> &o) {
+    R r_o, inv_ro, inv_dsec;
+    if constexpr (std::is_same<R, float>::value) {
+        r_o = p.f.r_o;
+        inv_ro = p.f.inv_ro;
+        inv_dsec = p.f.inv_dsec;
+    } else {
+        r_o = p.r_o;
+        inv_ro = p.inv_ro;
+        inv_dsec = p.inv_dsec;
+    }
+    const R xe = S.x0 + fl * S.ux, ye = S.y0 + fl * S.uy;
+    const R dze = S.dz0 + fl * S.uz;                     // z - h_obs in the core frame
+    const R Rp = dze + r_o;
+    const R rho2 = xe * xe + ye * ye;
+    const R r_e = sqrt(rho2 + Rp * Rp);
+    const R dH = dze + rho2 / (r_e + Rp);                // radial height above h_obs
+    o.he = c.h_obs + dH;
+    const R inv_re = R(1) / r_e;
+    const R rx = xe * inv_re, ry = ye * inv_re, rz = Rp * inv_re;
+    const R ce = px * rx + py * ry + pz * rz;           // cosine to the upward vertical
+    if (!(ce < R(0))) { o.status = ST_UPWARD; return; }
+    if (!(dH >= R(0))) { o.status = ST_BELOW; return; }
+    if (!(dH <= c.dH_max)) { o.status = ST_ABOVE; return; }
+    const R wx = py * rz - pz * ry, wy = pz * rx - px * rz, wz = px * ry - py * rx;
+    const R se2 = wx * wx + wy * wy + wz * wz;
+    const R eta_e = eta_at<R>(p, c, o.he);
+    R rm1;
+    if constexpr (DS)
+        rm1 = o.kap * (eta_e - c.eta_o) / (R(1) + o.kap * c.eta_o);
+    else
+        rm1 = (eta_e - c.eta_o) * c.inv_np1o;
+    const R gb = (R(1) + dH * inv_ro) * (R(1) + rm1);
+    const R q = se2 * gb * gb;                           // sin^2(zeta_o)
+    if (!(q <= c.q_max)) { o.status = ST_ANGLE; return; }
+    const R omq = R(1) - q;
+    const R sec = rsqrt(omq);
+    const R co = omq * sec;
+    const R so = sqrt(q);
+    // one cell: heights in rows, zeniths uniform in sec
+    const R fj = dH * c.inv_dht;
+    int jj = static_cast<int>(fj);
+    jj = jj > c.H - 2 ? c.H - 2 : jj;
+    const R a = fj - static_cast<R>(jj);
+    const R fk = (sec - R(1)) * inv_dsec;
+    int kk = static_cast<int>(fk);
+    kk = kk > c.Z - 2 ? c.Z - 2 : kk;
+    const R b = fk - static_cast<R>(kk);
+    const size_t e0 = static_cast<size_t>(jj) * (c.Z - 1) + kk;
+    const size_t e1 = e0 + (c.Z - 1);
+    R v[2][6];                  // rows jj, jj + 1: ax_k, al_k, ax_k1, al_k1, ag_k, ag_k1
+    if constexpr (std::is_same<R, float>::value) {
+        const float4 *T = static_cast<const float4 *>(DS ? p.tabd : p.tab);
+        const int per = DS ? 4 : 2;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const size_t e = r ? e1 : e0;
+            float4 A = __ldg(T + per * e), B = __ldg(T + per * e + 1);
+            if constexpr (DS) {
+                const float wk = (o.kap - p.f.kap_lo) * p.f.kap_winv;
+                const float4 A2 = __ldg(T + per * e + 2), B2 = __ldg(T + per * e + 3);
+                A = make_float4(A.x + wk * (A2.x - A.x), A.y + wk * (A2.y - A.y),
+                                A.z + wk * (A2.z - A.z), A.w + wk * (A2.w - A.w));
+                B = make_float4(B.x + wk * (B2.x - B.x), B.y + wk * (B2.y - B.y), 0.0f, 0.0f);
+            }
+            v[r][0] = A.x; v[r][1] = A.y; v[r][2] = A.z; v[r][3] = A.w;
+            v[r][4] = B.x; v[r][5] = B.y;
+        }
+    } else {
+        const double2 *T = static_cast<const double2 *>(DS ? p.tabd : p.tab);
+        const int per = DS ? 8 : 4;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const size_t e = r ? e1 : e0;
+            double2 A = __ldg(T + per * e), B = __ldg(T + per * e + 1);
+            double2 C = __ldg(T + per * e + 2);
+            if constexpr (DS) {
+                const double wk = (o.kap - p.kap_lo) * p.kap_winv;
+                const double2 A2 = __ldg(T + per * e + 4), B2 = __ldg(T + per * e + 5);
+                const double2 C2 = __ldg(T + per * e + 6);
+                A = make_double2(A.x + wk * (A2.x - A.x), A.y + wk * (A2.y - A.y));
+                B = make_double2(B.x + wk * (B2.x - B.x), B.y + wk * (B2.y - B.y));
+                C = make_double2(C.x + wk * (C2.x - C.x), C.y + wk * (C2.y - C.y));
+            }
+            v[r][0] = A.x; v[r][1] = A.y; v[r][2] = B.x; v[r][3] = B.y;
+            v[r][4] = C.x; v[r][5] = C.y;
+        }
+    }
+    R t3[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) t3[m] = v[0][m] + a * (v[1][m] - v[0][m]);
+    const R Ax = t3[0] + b * (t3[2] - t3[0]);
+    const R A1 = t3[1] + b * (t3[3] - t3[1]);
+    const R A2 = t3[4] + b * (t3[5] - t3[4]);
+    // the straight line arriving at zeta_o
+    const R u = R(1) / (R(1) + dH * inv_ro);            // r_o / r_e
+    const R omu = dH * inv_re;                           // 1 - u
+    const R ce2 = sqrt(omq + q * omu * (R(1) + u));     // its cosine at r_e
+    const R g1 = (R(1) + u) / (ce2 + u * co);
+    const R gphi = u * so * g1 / (co * ce2);
+    const R g2 = g1 * q * u / (ce2 * co);
+    const R dphi = Ax * gphi * inv_ro;
+    const R L = dH * g1 + A1 * g1 + A2 * g2;
+    const R sps = so * omu * g1;                         // sin of its central angle
+    const R cps = ce2 * co + q * u;
+    const R hd = R(0.5) * dphi * dphi;
+    const R sphi = sps * (R(1) - hd) + cps * dphi;
+    const R cphi = cps * (R(1) - hd) - sps * dphi;
+    const R omc = sphi * sphi / (R(1) + cphi);
+    // the horizontal direction of travel at the emission point
+    const R rse = rsqrt(se2 > R(1e-30) ? se2 : R(1e-30));
+    const R tx = (px - ce * rx) * rse, ty = (py - ce * ry) * rse, tz = (pz - ce * rz) * rse;
+    const R dr = -dH - r_o * omc;                        // r_o cos(phi) - r_e
+    const R dtn = r_o * sphi;
+    o.X = xe + (dr * rx + dtn * tx);
+    o.Y = ye + (dr * ry + dtn * ty);
+    o.zg = dze + (dr * rz + dtn * tz);
+    o.t = S.tseg + fl * S.inv_bc + L * R(1.0 / kC);
+    const R rox = cphi * rx + sphi * tx, roy = cphi * ry + sphi * ty, roz = cphi * rz + sphi * tz;
+    const R tox = cphi * tx - sphi * rx, toy = cphi * ty - sphi * ry, toz = cphi * tz - sphi * rz;
+    o.cx = so * tox - co * rox;
+    o.cy = so * toy - co * roy;
+    o.cz = so * toz - co * roz;
+    if constexpr (TR) {
+        const R tau = trans_tau<R>(p, o.lam, o.he);
+        R P, u3;
+        if constexpr (std::is_same<R, float>::value) {
+            P = __expf(-(tau * sec));
+            u3 = u01f(w3);
+        } else {
+            P = exp(-(tau / co));
+            u3 = u01d(w3);
+        }
+        if (!(u3 < P)) {
+            o.status = ST_ABSORBED;
+            return;
+        }
+    }
+    o.status = ST_GROUND;
+}
+
+template <class R, bool TR, int FB, bool DS, bool CV = false>
 __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, const Seg<R> &S,
                                       const SegD<R> *SD, int64_t gi, int j, BunchOut<R> &o) {
     const uint4 x = philox4x32_10(
@@ -816,6 +999,11 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
     const R px = cosc * S.ux + sinc * (cp * S.e1x + sp * S.e2x);
     const R py = cosc * S.uy + sinc * (cp * S.e1y + sp * S.e2y);
     const R pz = cosc * S.uz + sinc * (sp * S.e2z);
+    o.zg = R(0);
+    if constexpr (CV) {
+        propagate_curved<R, TR, DS>(p, c, S, fl, px, py, pz, x.w, o);
+        return;
+    }
     const R dH = S.dz0 + fl * S.uz;                 // h_e - h_obs
     o.he = c.h_obs + dH;
     // rare conditions first (paper Alg. 2)
@@ -988,7 +1176,7 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
 
 // Candidate spheres of the bunch's grid cell: bit m of the mask is cell
 // entry s0 + m of grid g (chosen by the arrival zenith).
-template <class R>
+template <class R, bool CV = false>
 __device__ __forceinline__ unsigned sphere_hits(const KParams &p, const Consts<R> &c,
                                                 const BunchOut<R> &o, int &s0,
                                                 int &g) {
@@ -1017,7 +1205,7 @@ __device__ __forceinline__ unsigned sphere_hits(const KParams &p, const Consts<R
         const int s1 = __ldg(cs + cell + 1);
         for (int m = s0; m < s1; ++m) {
             const float4 T = __ldg(cd + m);
-            const float dx = T.x - o.X, dy = T.y - o.Y, dz = T.z;
+            const float dx = T.x - o.X, dy = T.y - o.Y, dz = CV ? T.z - o.zg : T.z;
             const float q0 = dy * o.cz - dz * o.cy;
             const float q1 = dz * o.cx - dx * o.cz;
             const float q2 = dx * o.cy - dy * o.cx;
@@ -1030,7 +1218,7 @@ __device__ __forceinline__ unsigned sphere_hits(const KParams &p, const Consts<R
         const double2 *T = static_cast<const double2 *>(g ? p.grid[1].cand64 : p.grid[0].cand64);
         for (int m = s0; m < s1; ++m) {
             const double2 A = __ldg(T + 2 * m), B = __ldg(T + 2 * m + 1);
-            const double dx = A.x - o.X, dy = A.y - o.Y, dz = B.x;
+            const double dx = A.x - o.X, dy = A.y - o.Y, dz = CV ? B.x - o.zg : B.x;
             const double q0 = dy * o.cz - dz * o.cy;
             const double q1 = dz * o.cx - dx * o.cz;
             const double q2 = dx * o.cy - dy * o.cx;
@@ -1126,7 +1314,7 @@ __device__ __forceinline__ void record_hits(const KParams &p, const BunchOut<R> 
             slot0 = __shfl_sync(grp, slot0, leader);
             const unsigned long long slot = slot0 + rank;
             if (slot < static_cast<unsigned long long>(p.cap)) {
-                const R sl = tz / o.cz;       // to the plane through the centre
+                const R sl = (tz - o.zg) / o.cz;   // to the plane through the centre
                 const int64_t r = static_cast<int64_t>(tel) * p.cap + static_cast<int64_t>(slot);
                 store4<R>(p.pos, r, o.X + sl * o.cx - tx, o.Y + sl * o.cy - ty, o.cx, o.cy);
                 store4<R>(p.tim, r, o.t + sl * np1o * R(1.0 / kC), o.he, w, o.lam);
@@ -1151,7 +1339,8 @@ __host__ __device__ constexpr size_t segd_offset() {
     return (sizeof(Seg<R>) * BLOCK + sizeof(int) * (BLOCK + 1 + 32) + 15) & ~size_t(15);
 }
 
-template <class R, int BLOCK, int MODE, bool TR, int FB, bool DS>
+// CV: a curved atmosphere (radial heights, spherical shells).
+template <class R, int BLOCK, int MODE, bool TR, int FB, bool DS, bool CV>
 __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / BLOCK : 1)
     k_gen_prop(const KParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1195,21 +1384,36 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             using YT = typename std::conditional<std::is_same<R, float>::value, YieldF,
                                                  Yield>::type;
             YT y;
+            // in a curved atmosphere the yield needs the midpoint's horizontal place
+            double xyd[4];
+            float xyf[4];
+            if constexpr (CV) {
+                xyd[0] = __ldg(p.x0 + i);
+                xyd[1] = __ldg(p.y0 + i);
+                xyd[2] = static_cast<double>(load_dir<R>(p.ux, i));
+                xyd[3] = static_cast<double>(load_dir<R>(p.uy, i));
+                xyf[0] = d2f_rn(xyd[0]);
+                xyf[1] = d2f_rn(xyd[1]);
+                xyf[2] = static_cast<float>(load_dir<R>(p.ux, i));
+                xyf[3] = static_cast<float>(load_dir<R>(p.uy, i));
+            }
+            const double *pxyd = CV ? xyd : nullptr;
+            const float *pxyf = CV ? xyf : nullptr;
             if constexpr (DS) {
                 if constexpr (std::is_same<YT, YieldF>::value)
                     step_yield_screened_disp(p, step_valid<R>(p, i), __ldg(p.z0 + i),
                                              __ldg(p.len + i), __ldg(p.ekin + i),
-                                             load_dir<float>(p.uz, i), y, segd[tid]);
+                                             load_dir<float>(p.uz, i), y, segd[tid], pxyf, pxyd);
                 else
                     step_yield_disp<R>(p, step_valid<R>(p, i), __ldg(p.z0 + i), __ldg(p.len + i),
                                        __ldg(p.ekin + i), static_cast<double>(load_dir<R>(p.uz, i)),
-                                       y, segd[tid]);
+                                       y, segd[tid], pxyd);
             } else if constexpr (std::is_same<YT, YieldF>::value) {
                 step_yield_screened(p, step_valid<R>(p, i), __ldg(p.z0 + i), __ldg(p.len + i),
-                                    __ldg(p.ekin + i), load_dir<float>(p.uz, i), y);
+                                    __ldg(p.ekin + i), load_dir<float>(p.uz, i), y, pxyf, pxyd);
             } else {
                 step_yield(p, step_valid<R>(p, i), __ldg(p.z0 + i), __ldg(p.len + i),
-                           __ldg(p.ekin + i), static_cast<double>(load_dir<R>(p.uz, i)), y);
+                           __ldg(p.ekin + i), static_cast<double>(load_dir<R>(p.uz, i)), y, pxyd);
             }
             if constexpr (MODE == MODE_SCREEN) {
                 // the adjoint freezes the sub-step structure
@@ -1316,11 +1520,12 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             s_cur = __shfl_sync(kFull, s, 31);
             BunchOut<R> o;
             o.status = -1;
+            o.zg = R(0);
             int j = 0;
             if (live) {
                 j = bidx - off[s];
-                bunch<R, TR, FB, DS>(p, c, seg[s], DS ? segd + s : nullptr,
-                                     p.track_base + base + s, j, o);
+                bunch<R, TR, FB, DS, CV>(p, c, seg[s], DS ? segd + s : nullptr,
+                                         p.track_base + base + s, j, o);
                 if (o.status != ST_GROUND) {       // rare: the drops
                     st_up += o.status == ST_UPWARD;
                     st_below += o.status == ST_BELOW;
@@ -1373,7 +1578,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                 }
             }
             int s0 = 0, gsel = 0;
-            unsigned hm = live ? sphere_hits<R>(p, c, o, s0, gsel) : 0u;
+            unsigned hm = live ? sphere_hits<R, CV>(p, c, o, s0, gsel) : 0u;
             if constexpr (MODE == MODE_TRACE) {
                 st_hits += __popc(hm);
                 if (live) {
@@ -1455,6 +1660,7 @@ __global__ void __launch_bounds__(128) k_fallback(const KParams p) {
         const bool live = e < n;
         BunchOut<R> o;
         o.status = -1;
+        o.zg = R(0);
         R w = R(0);
         uint64_t key = 0;
         if (live) {
@@ -1527,67 +1733,78 @@ size_t smem_bytes(const KParams &p) {
     return b;
 }
 
-template <class R, int BLOCK, int MODE, bool DS>
+template <class R, int BLOCK, int MODE, bool DS, bool CV>
 const void *kernel_ptr_ds(bool tr, bool fb) {
     if constexpr (MODE == MODE_YIELD || MODE == MODE_SCREEN) {
         if constexpr (MODE == MODE_YIELD)
-            return reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0, DS>);
+            return reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0, DS, CV>);
         else
-            return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, 0, DS>)
-                      : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0, DS>);
+            return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, 0, DS, CV>)
+                      : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0, DS, CV>);
+    } else if constexpr (CV) {
+        // the curved atmosphere has no beyond-table fallback
+        if (fb) return nullptr;
+        return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, 0, DS, CV>)
+                  : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0, DS, CV>);
     } else {
         constexpr int F = MODE == MODE_HITS ? 1 : 2;
         if (fb)
-            return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, F, DS>)
-                      : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, F, DS>);
-        return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, 0, DS>)
-                  : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0, DS>);
+            return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, F, DS, CV>)
+                      : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, F, DS, CV>);
+        return tr ? reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, true, 0, DS, CV>)
+                  : reinterpret_cast<const void *>(&k_gen_prop<R, BLOCK, MODE, false, 0, DS, CV>);
     }
 }
 
 template <class R, int BLOCK, int MODE>
-const void *kernel_ptr(bool tr, bool fb, bool ds) {
-    if (ds) {
-        // the wavelength-dependent index: 128-step tiles, no adjoint screening
-        if constexpr (BLOCK == kDispBlock && MODE != MODE_SCREEN)
-            return kernel_ptr_ds<R, BLOCK, MODE, true>(tr, fb);
-        else
+const void *kernel_ptr(bool tr, bool fb, bool ds, bool cv) {
+    if (ds || cv) {
+        // the wavelength-dependent index and the curved atmosphere: 128-step
+        // tiles, no adjoint screening
+        if constexpr (BLOCK == kDispBlock && MODE != MODE_SCREEN) {
+            if (cv)
+                return ds ? kernel_ptr_ds<R, BLOCK, MODE, true, true>(tr, fb)
+                          : kernel_ptr_ds<R, BLOCK, MODE, false, true>(tr, fb);
+            return kernel_ptr_ds<R, BLOCK, MODE, true, false>(tr, fb);
+        } else {
             return nullptr;
+        }
     }
-    return kernel_ptr_ds<R, BLOCK, MODE, false>(tr, fb);
+    return kernel_ptr_ds<R, BLOCK, MODE, false, false>(tr, fb);
 }
 
 template <class R, int MODE>
-const void *pick(int block, bool tr, bool fb, bool ds) {
+const void *pick(int block, bool tr, bool fb, bool ds, bool cv) {
     switch (block) {
-    case 128: return kernel_ptr<R, 128, MODE>(tr, fb, ds);
-    case 256: return kernel_ptr<R, 256, MODE>(tr, fb, ds);
-    case 512: return kernel_ptr<R, 512, MODE>(tr, fb, ds);
+    case 128: return kernel_ptr<R, 128, MODE>(tr, fb, ds, cv);
+    case 256: return kernel_ptr<R, 256, MODE>(tr, fb, ds, cv);
+    case 512: return kernel_ptr<R, 512, MODE>(tr, fb, ds, cv);
     }
     return nullptr;
 }
 
-// mode: a Mode, plus kTransBit / kFbBit / kDispBit for the instantiations
-// with the transmission draw / the beyond-table fallback / the
-// wavelength-dependent index
+// mode: a Mode, plus kTransBit / kFbBit / kDispBit / kCurvBit for the
+// instantiations with the transmission draw / the beyond-table fallback /
+// the wavelength-dependent index / the curved atmosphere
 const void *pick_kernel(bool fp32, int block, int mode) {
     const bool tr = (mode & kTransBit) != 0;
     const bool fb = (mode & kFbBit) != 0;
     const bool ds = (mode & kDispBit) != 0;
-    mode &= ~(kTransBit | kFbBit | kDispBit);
+    const bool cv = (mode & kCurvBit) != 0;
+    mode &= ~(kTransBit | kFbBit | kDispBit | kCurvBit);
     if (fp32) {
         switch (mode) {
-        case MODE_HITS: return pick<float, MODE_HITS>(block, tr, fb, ds);
-        case MODE_TRACE: return pick<float, MODE_TRACE>(block, tr, fb, ds);
-        case MODE_YIELD: return pick<float, MODE_YIELD>(block, tr, fb, ds);
-        case MODE_SCREEN: return pick<float, MODE_SCREEN>(block, tr, fb, ds);
+        case MODE_HITS: return pick<float, MODE_HITS>(block, tr, fb, ds, cv);
+        case MODE_TRACE: return pick<float, MODE_TRACE>(block, tr, fb, ds, cv);
+        case MODE_YIELD: return pick<float, MODE_YIELD>(block, tr, fb, ds, cv);
+        case MODE_SCREEN: return pick<float, MODE_SCREEN>(block, tr, fb, ds, cv);
         }
     } else {
         switch (mode) {
-        case MODE_HITS: return pick<double, MODE_HITS>(block, tr, fb, ds);
-        case MODE_TRACE: return pick<double, MODE_TRACE>(block, tr, fb, ds);
-        case MODE_YIELD: return pick<double, MODE_YIELD>(block, tr, fb, ds);
-        case MODE_SCREEN: return pick<double, MODE_SCREEN>(block, tr, fb, ds);
+        case MODE_HITS: return pick<double, MODE_HITS>(block, tr, fb, ds, cv);
+        case MODE_TRACE: return pick<double, MODE_TRACE>(block, tr, fb, ds, cv);
+        case MODE_YIELD: return pick<double, MODE_YIELD>(block, tr, fb, ds, cv);
+        case MODE_SCREEN: return pick<double, MODE_SCREEN>(block, tr, fb, ds, cv);
         }
     }
     return nullptr;
@@ -1634,6 +1851,10 @@ void fill_float_constants(KParams &p) {
     p.f.kap_lo = static_cast<float>(p.kap_lo);
     p.f.kap_winv = static_cast<float>(p.kap_winv);
     for (int l = 0; l < 5; ++l) p.f.eta_coef[l] = static_cast<float>(p.atm.eta_coef[l]);
+    p.f.earth_radius = static_cast<float>(p.earth_radius);
+    p.f.r_o = static_cast<float>(p.r_o);
+    p.f.inv_ro = static_cast<float>(p.inv_ro);
+    p.f.inv_dsec = static_cast<float>(p.inv_dsec);
     for (int q = 0; q < 12; ++q) {
         p.f.gl_x[q] = static_cast<float>(p.gl_x[q]);
         p.f.gl_w[q] = static_cast<float>(p.gl_w[q]);

@@ -122,6 +122,89 @@ struct RayIntegrand {
     }
 };
 
+// The curved atmosphere's integrands (spherical shells, Bouguer's
+// invariant n r sin(zeta) = n_o r_o s_o): at height h, with w = r_o / r and
+// v = n_o / n (v - 1 = (eta_o - eta) / (1 + eta)), the ray's sine is
+// s = s_o v w and the straight reference line's s_s = s_o w, and
+//   tan(zeta) - tan(zeta_s) = s_o w [(v - 1) c_s + (c_s - c)] / (c c_s),
+//   1/c - 1/c_s = (c_s - c) / (c c_s),  c_s - c = s_o^2 w^2 (v - 1)(v + 1) / (c_s + c),
+// so the three corrections (central angle times r_o, the (n - 1) part and
+// the geometric part of the optical path) are free of cancellation:
+//   g_phi = w (tan - tan_s),  g_1 = (n - 1) / c,  g_2 = 1/c - 1/c_s.
+// At s_o = 0 the tables hold their limits divided by s_o and s_o^2:
+//   w^2 (v - 1)  and  w^2 (v - 1)(v + 1) / 2.
+struct CurvedIntegrand {
+    const Layered *A;
+    double R_E, r_o, eta_o, so;
+    void operator()(double h, double &gp, double &g1, double &g2) const {
+        const double eta = eta_of(*A, h);
+        const double vm1 = (eta_o - eta) / (1.0 + eta);
+        const double v = 1.0 + vm1;
+        const double w = r_o / (R_E + h);
+        if (so == 0.0) {
+            gp = w * w * vm1;
+            g1 = eta;
+            g2 = 0.5 * w * w * vm1 * (v + 1.0);
+            return;
+        }
+        const double ss = so * w, s = ss * v;
+        const double cs = std::sqrt((1.0 - ss) * (1.0 + ss));
+        const double c = std::sqrt((1.0 - s) * (1.0 + s));
+        const double dc = so * so * w * w * vm1 * (v + 1.0) / (cs + c);   // c_s - c
+        gp = w * so * w * (vm1 * cs + dc) / (c * cs);
+        g1 = eta / c;
+        g2 = dc / (c * cs);
+    }
+};
+
+// Path averages of the three first-order factors along the straight line
+// that arrives at r_o with sine s_o, up to r_e (u = r_o / r_e, c_e' its
+// cosine at r_e, from c_e'^2 = c_o^2 + s_o^2 (1 - u)(1 + u)):
+//   G_phi = u s_o (1 + u) / ((c_e' + u c_o) c_o c_e'),  G_1 = (1 + u) / (c_e' + u c_o),
+//   G_2 = G_1 s_o^2 u / (c_e' c_o).
+void curved_factors(double r_o, double r_e, double so, double co, double &g_phi, double &g_1,
+                    double &g_2) {
+    const double u = r_o / r_e;
+    const double ce = std::sqrt(co * co + so * so * ((r_e - r_o) / r_e) * (1.0 + u));
+    g_1 = (1.0 + u) / (ce + u * co);
+    g_phi = u * so * g_1 / (co * ce);
+    g_2 = g_1 * so * so * u / (ce * co);
+}
+
+void integrate_piece_c(const CurvedIntegrand &f, const GaussLegendre &gl, double lo, double hi,
+                       double &ip, double &i1, double &i2) {
+    const double m = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
+    double sp = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int i = 0; i < GaussLegendre::N; ++i) {
+        double gp, g1, g2;
+        f(m + hw * gl.x[i], gp, g1, g2);
+        sp += gl.w[i] * gp;
+        s1 += gl.w[i] * g1;
+        s2 += gl.w[i] * g2;
+    }
+    ip = sp * hw;
+    i1 = s1 * hw;
+    i2 = s2 * hw;
+}
+
+void integrate_c(const CurvedIntegrand &f, const GaussLegendre &gl, double lo, double hi,
+                 double &ip, double &i1, double &i2) {
+    ip = i1 = i2 = 0.0;
+    double a = lo;
+    for (int i = 1; i <= 5; ++i) {
+        const double hb = f.A->hb[i];
+        if (hb > a && hb < hi) {
+            double p, q1, q2;
+            integrate_piece_c(f, gl, a, hb, p, q1, q2);
+            ip += p; i1 += q1; i2 += q2;
+            a = hb;
+        }
+    }
+    double p, q1, q2;
+    integrate_piece_c(f, gl, a, hi, p, q1, q2);
+    ip += p; i1 += q1; i2 += q2;
+}
+
 void integrate_piece(const RayIntegrand &f, const GaussLegendre &gl, double lo, double hi,
                      double &ix, double &il) {
     const double m = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
@@ -186,7 +269,8 @@ double eta_lookup(const HostTables &t, double h) {
 }
 
 cher_status build_tables(const cher_atmosphere &atm, double h_obs, int32_t n_fine, int32_t H,
-                         int32_t Z, double theta_max, double h_max, HostTables &T) {
+                         int32_t Z, double theta_max, double h_max, HostTables &T,
+                         double earth_radius) {
     if (!atm_valid(atm)) return CHER_EINVAL;
     if (n_fine < 2 || n_fine > (1 << 20)) return CHER_EINVAL;
     if (H < 2 || H > 65536 || Z < 2 || Z > 4096) return CHER_EINVAL;
@@ -222,8 +306,49 @@ cher_status build_tables(const cher_atmosphere &atm, double h_obs, int32_t n_fin
     T.al.assign(static_cast<size_t>(H) * Z, 0.0);
     const double eta_o = eta_of(A, h_obs);
     static const GaussLegendre gl;
+    T.earth_radius = earth_radius;
+    if (earth_radius > 0.0) {
+        T.dsec = (1.0 / std::cos(theta_max) - 1.0) / static_cast<double>(Z - 1);
+        T.inv_dsec = 1.0 / T.dsec;
+        T.ag.assign(static_cast<size_t>(H) * Z, 0.0);
+    }
+
+    auto column_curved = [&](int k) {
+        const double co = 1.0 / (1.0 + static_cast<double>(k) * T.dsec);
+        const double so = std::sqrt((1.0 - co) * (1.0 + co));
+        const double r_o = earth_radius + h_obs;
+        CurvedIntegrand f{&A, earth_radius, r_o, eta_o, k == 0 ? 0.0 : so};
+        double cp = 0.0, c1 = 0.0, c2 = 0.0;
+        for (int j = 1; j < H; ++j) {
+            const double lo = h_obs + static_cast<double>(j - 1) * T.dht;
+            const double hi = h_obs + static_cast<double>(j) * T.dht;
+            double ip, i1, i2;
+            integrate_c(f, gl, lo, hi, ip, i1, i2);
+            cp += ip;
+            c1 += i1;
+            c2 += i2;
+            const double r_e = earth_radius + hi;
+            const size_t a = static_cast<size_t>(j) * Z + k;
+            if (k == 0) {
+                // the limits at s_o = 0: G_phi / s_o, G_2 / s_o^2 -> u, G_1 -> 1
+                T.ax[a] = cp * (r_e / r_o);
+                T.al[a] = c1;
+                T.ag[a] = c2 * (r_e / r_o);
+            } else {
+                double g_phi, g_1, g_2;
+                curved_factors(r_o, r_e, so, co, g_phi, g_1, g_2);
+                T.ax[a] = cp / g_phi;
+                T.al[a] = c1 / g_1;
+                T.ag[a] = c2 / g_2;
+            }
+        }
+    };
 
     auto column = [&](int k) {
+        if (earth_radius > 0.0) {
+            column_curved(k);
+            return;
+        }
         const double q = static_cast<double>(k) * T.dq;
         const double so = std::sqrt(q);
         RayIntegrand f{&A, eta_o, so, std::sqrt((1.0 - so) * (1.0 + so))};

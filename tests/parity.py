@@ -113,12 +113,24 @@ def borderline_status(M: oracle.Model, o: dict, precision: int) -> np.ndarray:
     """Bunches whose oracle drop decision is within the path's precision."""
     t = TOL[precision]
     he = o["he"]
-    near = np.abs(o["pz"]) < t["edge_pz"]
-    near |= np.abs(he - M.h_obs) < t["edge_m"]
-    near |= np.abs(he - M.h_max) < t["edge_m"]
     kap = bunch_kappa(M, o)
     ratio = (1 + kap * _eta_interp(M, he)) / (1 + kap * _eta_interp(M, M.h_obs))
-    q = (o["px"] ** 2 + o["py"] ** 2) * ratio ** 2
+    R = getattr(M, "earth_radius", 0.0)
+    if R > 0.0:
+        # curved: the local vertical at the emission point (he is radial)
+        rho2 = o["xe"] ** 2 + o["ye"] ** 2
+        zc = np.sqrt(np.maximum((R + he) ** 2 - rho2, 0.0))
+        rv = np.stack([o["xe"], o["ye"], zc], 1) / (R + he)[:, None]
+        pv = np.stack([o["px"], o["py"], o["pz"]], 1)
+        ce = np.sum(pv * rv, 1)
+        se2 = np.sum(np.cross(pv, rv) ** 2, 1)
+        near = np.abs(ce) < t["edge_pz"]
+        q = se2 * ((R + he) / (R + M.h_obs)) ** 2 * ratio ** 2
+    else:
+        near = np.abs(o["pz"]) < t["edge_pz"]
+        q = (o["px"] ** 2 + o["py"] ** 2) * ratio ** 2
+    near |= np.abs(he - M.h_obs) < t["edge_m"]
+    near |= np.abs(he - M.h_max) < t["edge_m"]
     q_max = math.sin(M.theta_max_rad) ** 2
     near |= np.abs(q - q_max) < t["edge_q"]
     if "tr_margin" in o:       # the transmission draw u3 < P
@@ -134,7 +146,8 @@ def sphere_distance(M: oracle.Model, o: dict) -> np.ndarray:
     out = np.full((len(g), T.shape[0]), np.inf)
     if not g.any():
         return out
-    P0 = np.stack([o["X"][g], o["Y"][g], np.zeros(g.sum())], 1)
+    zg = o["Zg"][g] if "Zg" in o else np.zeros(g.sum())
+    P0 = np.stack([o["X"][g], o["Y"][g], zg], 1)
     D = np.stack([o["cx"][g], o["cy"][g], o["cz"][g]], 1)
     for k, (tx, ty, tz, tr) in enumerate(T):
         d = np.array([tx, ty, tz])[None, :] - P0

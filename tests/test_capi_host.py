@@ -63,6 +63,19 @@ def test_host_tables_match_oracle(H, Z, zen, hmax):
     assert np.max(np.abs(al - M.al)) < 1e-9
 
 
+@pytest.mark.parametrize("H,Z,zen", [(200, 32, 80.0), (60, 16, 60.0)])
+def test_host_curved_tables_match_oracle(H, Z, zen):
+    """The library's curved tables (12-point Gauss-Legendre per interval)
+    against the oracle's (adaptive Simpson): the same three normalised
+    corrections on the same sec-uniform zenith nodes."""
+    atm = workloads.us_standard_atmosphere()
+    ax, al, ag = P.build_curved_tables_host(atm, 6.371e6, 2200.0, H, Z, zen, 60000.0)
+    M = oracle.Model(atm, 2200.0, np.array([[0, 0, 0, 12.0]]), H=H, Z=Z, theta_max_deg=zen,
+                     h_max=60000.0, earth_radius=6.371e6)
+    for mine, theirs in ((ax, M.ax), (al, M.al), (ag, M.ag)):
+        assert np.max(np.abs(mine - theirs)) < 1e-8 * max(1.0, np.abs(theirs).max())
+
+
 def test_host_tables_reject_bad_ranges():
     atm = workloads.us_standard_atmosphere()
     with pytest.raises(P.CherError):
