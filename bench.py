@@ -72,10 +72,10 @@ FP32_LANES_PER_SM = 128
 FP64_FMA_PER_SM_CLK = 2         # GB300: 1/64 of the FP32 rate (ncu: 2 DFMA/cycle/SM)
 
 # DRAM bytes (read + write) of one FP32 launch, from one ncu capture of the
-# full-size vertical workload (128.25 MB read, 24.81 MB written, 128 threads
+# full-size vertical workload (128.24 MB read, 24.61 MB written, 128 threads
 # x 8 CTAs per SM).  Reported only for that workload at full size and only
 # while the kernel sources hash to what was profiled.
-TRAFFIC = {"vertical_1tev": (153_054_720, "356cfecfc7e7f435")}
+TRAFFIC = {"vertical_1tev": (152_848_128, "39115b047db898fb")}
 KERNEL_SOURCES = ("cher_kernels.cu", "cher_device.cuh", "cher_internal.h")
 
 

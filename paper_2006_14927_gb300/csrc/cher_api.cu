@@ -270,6 +270,10 @@ cher::KParams base_params(const cher_ctx *c, const cher_tracks *t, uint64_t seed
     p.track_base = t->track_base;
     p.key0 = static_cast<uint32_t>(seed & 0xffffffffu);
     p.key1 = static_cast<uint32_t>(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        p.rk0[r] = p.key0 + static_cast<uint32_t>(r) * 0x9E3779B9u;
+        p.rk1[r] = p.key1 + static_cast<uint32_t>(r) * 0xBB67AE85u;
+    }
     p.inv_me = c->inv_me;
     p.K = c->K;
     p.inv_B = c->inv_B;

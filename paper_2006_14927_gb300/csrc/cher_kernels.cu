@@ -960,10 +960,10 @@ __device__ __forceinline__ void propagate_curved(const KParams &p, const Consts<
 template <class R, bool TR, int FB, bool DS, bool CV = false>
 __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, const Seg<R> &S,
                                       const SegD<R> *SD, int64_t gi, int j, BunchOut<R> &o) {
-    const uint4 x = philox4x32_10(
+    const uint4 x = philox4x32_10_rk(
         make_uint4(static_cast<uint32_t>(gi), static_cast<uint32_t>(static_cast<uint64_t>(gi) >> 32),
                    static_cast<uint32_t>(j), 0u),
-        p.key0, p.key1);
+        p.rk0, p.rk1);
     R u0, u1, u2;
     if constexpr (std::is_same<R, float>::value) {
         u0 = u01f(x.x);

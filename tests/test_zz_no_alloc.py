@@ -57,6 +57,32 @@ def test_noalloc_matches_regular_entry_point(prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("feature", ["dispersion", "curved", "both"])
+def test_noalloc_with_the_index_and_geometry_options(feature):
+    """The 128-step instantiations of the wavelength-dependent index and the
+    curved atmosphere through the allocation-free entry point (their larger
+    shared-memory tiles and forced tile size come from the same launch
+    preparation)."""
+    P.build()
+    sc = workloads.inclined_20tev(n=20_011)
+    sc["H"], sc["Z"], sc["theta_max_deg"] = 200, 32, 80.0
+    ctx = context(sc)
+    if feature in ("dispersion", "both"):
+        ctx.set_dispersion(workloads.synthetic_dispersion())
+    if feature in ("curved", "both"):
+        ctx.set_curved(6.371e6)
+    prec = FP32
+    dev = P.device_tracks(host_tracks(sc, prec), prec, t_ref=sc["t_ref"])
+    ref_stats, ref = _run(ctx, dev, prec, 200_000, noalloc=False)
+    assert ref_stats[9] > 0
+    stats, rec = _run(ctx, dev, prec, 200_000, noalloc=True)
+    assert np.array_equal(stats, ref_stats)
+    assert np.array_equal(rec["key"], ref["key"])
+    for k in ("x", "y", "t", "lam"):
+        np.testing.assert_array_equal(rec[k], ref[k])
+    ctx.close()
+
+
 def test_noalloc_refuses_oversized_input():
     P.build()
     sc = workloads.plain_fp64(n=10)
