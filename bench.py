@@ -72,10 +72,10 @@ FP32_LANES_PER_SM = 128
 FP64_FMA_PER_SM_CLK = 2         # GB300: 1/64 of the FP32 rate (ncu: 2 DFMA/cycle/SM)
 
 # DRAM bytes (read + write) of one FP32 launch, from one ncu capture of the
-# full-size vertical workload (128.24 MB read, 24.61 MB written, 128 threads
+# full-size vertical workload (128.26 MB read, 24.89 MB written, 128 threads
 # x 8 CTAs per SM).  Reported only for that workload at full size and only
 # while the kernel sources hash to what was profiled.
-TRAFFIC = {"vertical_1tev": (152_848_128, "39115b047db898fb")}
+TRAFFIC = {"vertical_1tev": (153_143_040, "06768c0b4907450b")}
 KERNEL_SOURCES = ("cher_kernels.cu", "cher_device.cuh", "cher_internal.h")
 
 

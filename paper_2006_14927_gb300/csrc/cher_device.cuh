@@ -33,18 +33,6 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// The same rounds with the key of round r given (k0 + r W0, k1 + r W1).
-__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t *rk0,
-                                                  const uint32_t *rk1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ rk0[r], lo1, hi0 ^ c.w ^ rk1[r], lo0);
-    }
-    return c;
-}
-
 // uniform deviates in (0, 1)
 __device__ __forceinline__ double u01d(uint32_t x) {
     return (static_cast<double>(x) + 0.5) * (1.0 / 4294967296.0);

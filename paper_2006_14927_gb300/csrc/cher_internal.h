@@ -78,8 +78,8 @@ struct KParams {
     int64_t n, track_base;
     uint32_t key0, key1;
     // Philox round keys, rk0[r] = key0 + r W0 and rk1[r] = key1 + r W1: uniform
-    // over the launch, so the bunch loop reads them from the parameter bank
-    // instead of advancing the key every round
+    // over the launch, so the bunch loop (philox_bunch) reads them from the
+    // parameter bank instead of advancing the key every round
     uint32_t rk0[10], rk1[10];
     // yield constants (FP64, same rounding as the host)
     double inv_me, K, inv_B;

@@ -44,6 +44,9 @@ struct alignas(16) Seg {
     R x0, y0, dz0, tseg;   // dz0 = z0 - h_obs, tseg = t0 - t_ref (FP64 differences)
     R inv_bc, w;
     int nb, pad;
+    // the parts of the first two Philox rounds that depend on the step only
+    // (philox_bunch)
+    uint32_t ph_a, ph_b, ph_c, ph_d;
 };
 
 // ------------------------------------------------------------------------
@@ -421,6 +424,20 @@ __device__ __forceinline__ void prep_step(const KParams &p, int64_t i, const Y &
     }
     S.nb = y.nb;
     S.pad = 0;
+    {
+        // counter (lo(g), hi(g), j, 0): round 1 multiplies word 0 (the step's)
+        // and word 2 (j); round 2 multiplies round 1's word 2, which is the
+        // step's again
+        const uint64_t g = static_cast<uint64_t>(p.track_base + i);
+        const uint32_t glo = static_cast<uint32_t>(g), ghi = static_cast<uint32_t>(g >> 32);
+        const uint32_t lo0 = 0xD2511F53u * glo, hi0 = __umulhi(0xD2511F53u, glo);
+        const uint32_t w2 = hi0 ^ p.rk1[0];                      // c1.z (c.w = 0)
+        const uint32_t lo1 = 0xCD9E8D57u * w2, hi1 = __umulhi(0xCD9E8D57u, w2);
+        S.ph_a = ghi ^ p.rk0[0];         // round 1: c1.x = hi(M1 j) ^ ph_a
+        S.ph_b = hi1 ^ p.rk0[1];         // round 2: c2.x = ph_b ^ c1.y
+        S.ph_c = lo1;                    //          c2.y
+        S.ph_d = lo0 ^ p.rk1[1];         //          c2.z = hi(M0 c1.x) ^ ph_d
+    }
     S.ux = ux;
     S.uy = uy;
     S.uz = uz;
@@ -957,13 +974,30 @@ __device__ __forceinline__ void propagate_curved(const KParams &p, const Consts<
     o.status = ST_GROUND;
 }
 
+// Philox4x32-10 of the bunch's counter (lo(g), hi(g), j, 0), g the global
+// step index, with the step's share of the first two rounds taken from the
+// step constants (prep_step): round 1 multiplies counter word 0 (the
+// step's) and word 2 (j); round 2 multiplies round 1's word 2, which is the
+// step's again.  Same words as philox4x32_10.
+template <class R>
+__device__ __forceinline__ uint4 philox_bunch(const KParams &p, const Seg<R> &S, uint32_t j) {
+    const uint32_t lo1 = 0xCD9E8D57u * j, hi1 = __umulhi(0xCD9E8D57u, j);
+    const uint32_t c1x = hi1 ^ S.ph_a, c1y = lo1;
+    const uint32_t lo0 = 0xD2511F53u * c1x, hi0 = __umulhi(0xD2511F53u, c1x);
+    uint4 c = make_uint4(S.ph_b ^ c1y, S.ph_c, hi0 ^ S.ph_d, lo0);
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        const uint32_t a0 = 0xD2511F53u * c.x, b0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t a1 = 0xCD9E8D57u * c.z, b1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(b1 ^ c.y ^ p.rk0[r], a1, b0 ^ c.w ^ p.rk1[r], a0);
+    }
+    return c;
+}
+
 template <class R, bool TR, int FB, bool DS, bool CV = false>
 __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, const Seg<R> &S,
-                                      const SegD<R> *SD, int64_t gi, int j, BunchOut<R> &o) {
-    const uint4 x = philox4x32_10_rk(
-        make_uint4(static_cast<uint32_t>(gi), static_cast<uint32_t>(static_cast<uint64_t>(gi) >> 32),
-                   static_cast<uint32_t>(j), 0u),
-        p.rk0, p.rk1);
+                                      const SegD<R> *SD, int j, BunchOut<R> &o) {
+    const uint4 x = philox_bunch<R>(p, S, static_cast<uint32_t>(j));
     R u0, u1, u2;
     if constexpr (std::is_same<R, float>::value) {
         u0 = u01f(x.x);
@@ -1524,8 +1558,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             int j = 0;
             if (live) {
                 j = bidx - off[s];
-                bunch<R, TR, FB, DS, CV>(p, c, seg[s], DS ? segd + s : nullptr,
-                                         p.track_base + base + s, j, o);
+                bunch<R, TR, FB, DS, CV>(p, c, seg[s], DS ? segd + s : nullptr, j, o);
                 if (o.status != ST_GROUND) {       // rare: the drops
                     st_up += o.status == ST_UPWARD;
                     st_below += o.status == ST_BELOW;
