@@ -398,6 +398,14 @@ def run_ours(args):
                  torch.empty_like(h_key).pin_memory())]
         h_cnts = [h_cnt, torch.empty_like(h_cnt).pin_memory()]
         h_sts = [h_st, torch.empty_like(h_st).pin_memory()]
+        # the records of a step are packed on the device (cher_pack_records)
+        # and come down in one copy per array
+        pk = [dict(pos=torch.empty((n_rec, 4), dtype=torch.float32, device=dev),
+                   tim=torch.empty((n_rec, 4), dtype=torch.float32, device=dev),
+                   key=torch.empty(n_rec, dtype=torch.int64, device=dev),
+                   offset=torch.empty(n_tel + 1, dtype=torch.int64, device=dev))
+              for _ in range(2)]
+        h_offs = [torch.empty(n_tel + 1, dtype=torch.int64).pin_memory() for _ in range(2)]
         up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
         comp = torch.cuda.current_stream()
         ev = {k: [torch.cuda.Event(), torch.cuda.Event()] for k in ("up", "kern", "cnt", "down")}
@@ -414,27 +422,26 @@ def run_ours(args):
             comp.wait_event(ev["down"][b])             # out b's records are down
             ctx.generate_propagate(sets[b], 11, prec, outs[b], track_base=track_base)
             ev["kern"][b].record(comp)
+            ctx.pack_records(outs[b], pk[b], stream=comp)
             h_cnts[b].copy_(outs[b].count, non_blocking=True)
             h_sts[b].copy_(outs[b].stats, non_blocking=True)
+            h_offs[b].copy_(pk[b]["offset"], non_blocking=True)
             ev["cnt"][b].record(comp)
 
         def download(b):
             ev["cnt"][b].synchronize()                  # this step's counts on the host
-            nbytes = h_cnts[b].numel() * 8 + h_sts[b].numel() * 8
+            nbytes = (h_cnts[b].numel() + h_sts[b].numel() + h_offs[b].numel()) * 8
+            total = int(h_offs[b][-1])
+            if total > n_rec:
+                raise RuntimeError("host record buffer too small")
             with torch.cuda.stream(down):
-                down.wait_event(ev["kern"][b])
+                down.wait_event(ev["cnt"][b])           # the packed records are written
                 hp, ht, hk = hrec[b]
-                o_ = 0
-                for k_ in range(n_tel):
-                    c = min(int(h_cnts[b][k_]), cap)
-                    if o_ + c > n_rec:
-                        raise RuntimeError("host record buffer too small")
-                    if c > 0:
-                        hp[o_:o_ + c].copy_(outs[b].pos[k_, :c], non_blocking=True)
-                        ht[o_:o_ + c].copy_(outs[b].tim[k_, :c], non_blocking=True)
-                        hk[o_:o_ + c].copy_(outs[b].key[k_, :c], non_blocking=True)
-                        nbytes += c * 40
-                        o_ += c
+                if total > 0:
+                    hp[:total].copy_(pk[b]["pos"][:total], non_blocking=True)
+                    ht[:total].copy_(pk[b]["tim"][:total], non_blocking=True)
+                    hk[:total].copy_(pk[b]["key"][:total], non_blocking=True)
+                nbytes += total * 40
                 ev["down"][b].record(down)
             return nbytes
 
@@ -474,21 +481,20 @@ def run_ours(args):
             def gen_step():
                 dg = ctx.generate_steps(showers, 11, prec)
                 ctx.generate_propagate(dg, 11, prec, out)
+                ctx.pack_records(out, pk[0])
                 h_cnt.copy_(out.count, non_blocking=True)
                 h_st.copy_(out.stats, non_blocking=True)
+                h_offs[0].copy_(pk[0]["offset"], non_blocking=True)
                 torch.cuda.current_stream().synchronize()
-                nbytes = h_cnt.numel() * 8 + h_st.numel() * 8
-                o_ = 0
-                for k_ in range(n_tel):
-                    c = min(int(h_cnt[k_]), cap)
-                    if o_ + c > n_rec:
-                        raise RuntimeError("host record buffer too small")
-                    if c > 0:
-                        h_pos[o_:o_ + c].copy_(out.pos[k_, :c], non_blocking=True)
-                        h_tim[o_:o_ + c].copy_(out.tim[k_, :c], non_blocking=True)
-                        h_key[o_:o_ + c].copy_(out.key[k_, :c], non_blocking=True)
-                        nbytes += c * 40
-                        o_ += c
+                nbytes = (h_cnt.numel() + h_st.numel() + h_offs[0].numel()) * 8
+                total = int(h_offs[0][-1])
+                if total > n_rec:
+                    raise RuntimeError("host record buffer too small")
+                if total > 0:
+                    h_pos[:total].copy_(pk[0]["pos"][:total], non_blocking=True)
+                    h_tim[:total].copy_(pk[0]["tim"][:total], non_blocking=True)
+                    h_key[:total].copy_(pk[0]["key"][:total], non_blocking=True)
+                nbytes += total * 40
                 torch.cuda.current_stream().synchronize()
                 return nbytes, int(h_st[3])
 

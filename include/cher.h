@@ -457,6 +457,25 @@ cher_status cher_set_fallback(cher_ctx *ctx, double zenith_max_deg, int64_t queu
 #define CHER_DISPERSION_MAX_NODES 9
 cher_status cher_set_dispersion(cher_ctx *ctx, const double *kappa, int32_t k);
 
+/* Pack the records of every telescope contiguously, telescope after
+ * telescope (the order within a telescope as written), so that they come
+ * down in one copy per array instead of one per telescope (TELOUT's output,
+ * paper Appendix A, is one stream of records).
+ *   out         : the buffers and counts of a generation launch (device);
+ *                 counts are clipped to cap_per_tel;
+ *   prec        : the precision the launch wrote (record layout: 16 B or 32 B
+ *                 for pos and tim);
+ *   max_records : room in the destinations (records);
+ *   dst_pos, dst_tim, dst_key: device, max_records records each;
+ *   tel_offset  : device, n_tel + 1 int64: the first packed record of each
+ *                 telescope; tel_offset[n_tel] is the total, which may exceed
+ *                 max_records (the records past it are not copied).
+ * Asynchronous on `stream` (after the launch that wrote `out`).  Errors:
+ * CHER_EINVAL, CHER_ECUDA. */
+cher_status cher_pack_records(cher_ctx *ctx, const cher_output *out, cher_precision prec,
+                              int64_t max_records, void *dst_pos, void *dst_tim,
+                              uint64_t *dst_key, int64_t *tel_offset, void *stream);
+
 /* Curved atmosphere (an extension for large zenith angles: the paper's
  * RAYBND works in flat layers).  With an Earth radius R_E set, positions are
  * Cartesian in the core frame (z up, z = height a.s.l. on the core's

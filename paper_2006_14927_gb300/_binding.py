@@ -112,6 +112,9 @@ SIGNATURES = {
     "cher_set_fallback": (_S, [_P, ctypes.c_double, ctypes.c_int64]),
     "cher_set_dispersion": (_S, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
     "cher_set_curved": (_S, [_P, ctypes.c_double]),
+    "cher_pack_records": (_S, [_P, ctypes.POINTER(Output), ctypes.c_int, ctypes.c_int64,
+                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_void_p, ctypes.c_void_p]),
     "cher_generate_steps": (_S, [_P, ctypes.POINTER(Shower), ctypes.c_int32, ctypes.c_uint64, _S,
                                  ctypes.POINTER(StepBuffers), _P]),
     "cher_generate_propagate_noalloc": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
@@ -512,6 +515,30 @@ class Context:
         k = np.ascontiguousarray(np.asarray(kappa, dtype=np.float64).ravel())
         _check(lib().cher_set_dispersion(self._h, k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                          int(k.size)), "cher_set_dispersion")
+
+    def pack_records(self, out: "HitBuffers", dst: dict | None = None, stream=None):
+        """Every telescope's records packed contiguously on the device:
+        dict(pos, tim, key, offset) with offset[k] the first record of
+        telescope k and offset[n_tel] the total.  `dst` (the same keys,
+        preallocated) is reused when given; records past its room are not
+        copied (offset[n_tel] still tells the total)."""
+        torch = _torch()
+        dev = out.pos.device
+        if dst is None:
+            total = int(torch.clamp(out.count, max=out.cap).sum().item())
+            dt = out.pos.dtype
+            dst = dict(pos=torch.empty((total, 4), dtype=dt, device=dev),
+                       tim=torch.empty((total, 4), dtype=dt, device=dev),
+                       key=torch.empty(total, dtype=torch.int64, device=dev),
+                       offset=torch.empty(self.n_tel + 1, dtype=torch.int64, device=dev))
+        o = out.struct()
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        _check(lib().cher_pack_records(self._h, ctypes.byref(o), int(out.precision),
+                                       int(dst["key"].shape[0]), dst["pos"].data_ptr(),
+                                       dst["tim"].data_ptr(), dst["key"].data_ptr(),
+                                       dst["offset"].data_ptr(), ctypes.c_void_p(st.cuda_stream)),
+               "cher_pack_records")
+        return dst
 
     def set_curved(self, earth_radius_m: float):
         """Curved atmosphere with this Earth radius (m); 0 for flat layers."""

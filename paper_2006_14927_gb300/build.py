@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcher.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["cher_kernels.cu", "cher_adjoint.cu", "cher_api.cu", "cher_generator.cu",
+SOURCES = ["cher_kernels.cu", "cher_adjoint.cu", "cher_api.cu", "cher_generator.cu", "cher_pack.cu",
            "cher_tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

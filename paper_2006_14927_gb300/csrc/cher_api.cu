@@ -619,6 +619,27 @@ cher_status cher_set_transmission(cher_ctx *c, const cher_transmission *tb) {
     return CHER_OK;
 }
 
+cher_status cher_pack_records(cher_ctx *c, const cher_output *out, cher_precision prec,
+                              int64_t max_records, void *dst_pos, void *dst_tim,
+                              uint64_t *dst_key, int64_t *tel_offset, void *stream) {
+    if (!c || !out || max_records < 0 || bad_ptr(tel_offset)) return CHER_EINVAL;
+    if (prec != CHER_FP64 && prec != CHER_FP32_BULK) return CHER_EINVAL;
+    if (bad_ptr(out->count) || out->cap_per_tel < 0) return CHER_EINVAL;
+    if (out->cap_per_tel > 0 && (bad_ptr(out->pos) || bad_ptr(out->tim) || bad_ptr(out->key)))
+        return CHER_EINVAL;
+    if (max_records > 0 && (bad_ptr(dst_pos) || bad_ptr(dst_tim) || bad_ptr(dst_key)))
+        return CHER_EINVAL;
+    if (!check_device(c)) return CHER_EINVAL;
+    if (cher::pack_records(prec == CHER_FP32_BULK, out->pos, out->tim, out->key, out->count,
+                           out->cap_per_tel, static_cast<int>(c->tel.size()), max_records,
+                           dst_pos, dst_tim, dst_key, tel_offset, c->num_sms,
+                           stream) != cudaSuccess) {
+        cudaGetLastError();
+        return CHER_ECUDA;
+    }
+    return CHER_OK;
+}
+
 cher_status cher_set_curved(cher_ctx *c, double earth_radius_m) {
     if (!c || !std::isfinite(earth_radius_m)) return CHER_EINVAL;
     if (earth_radius_m != 0.0 && !(earth_radius_m >= 1.0e6 && earth_radius_m <= 1.0e8))

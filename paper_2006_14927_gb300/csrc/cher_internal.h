@@ -274,6 +274,12 @@ cudaError_t generate_steps(const GenParams &g, int num_sms, void *stream);
 // The Greisen profile's CDF on n_cdf uniform nodes of [0, t_g] (host, FP64).
 void greisen_cdf_host(double y, double t_g, int n_cdf, std::vector<double> &cdf);
 
+// The records of every telescope packed contiguously (cher_pack.cu).
+cudaError_t pack_records(bool fp32, const void *pos, const void *tim, const uint64_t *key,
+                         const unsigned long long *count, int64_t cap, int n_tel, int64_t max_rec,
+                         void *dpos, void *dtim, uint64_t *dkey, int64_t *off, int num_sms,
+                         void *stream);
+
 // The FP32 path's double -> float rounding over an array (grid-stride).
 cudaError_t round_to_float(const double *in, float *out, int64_t n, int num_sms, void *stream);
 cudaError_t kernel_prepare(bool fp32, int block, int mode, size_t smem);
