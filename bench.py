@@ -799,9 +799,24 @@ def cpu_baseline(workload: str = WORKLOAD):
         nb += len(o["status"])
         reps += 1
     dt = time.perf_counter() - t0
-    return {"value": nb / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{workload}: {n} steps ({nb // reps} bunches), repeated {reps} times, "
-                      f"FP64 table variant, OpenMP over steps"}
+    cores = oracle.num_threads()
+    res = {"value": nb / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{workload}: {n} steps ({nb // reps} bunches), repeated {reps} times, "
+                     f"FP64 table variant, OpenMP over steps"}
+    # the same single-threaded, on a fifth of the sample for about 3 s
+    sub = {k: v[: n // 5] for k, v in sc["tracks"].items()}
+    oracle.set_num_threads(1)
+    t0 = time.perf_counter()
+    reps1, nb1 = 0, 0
+    while time.perf_counter() - t0 < 3.0 or reps1 < 1:
+        nb1 += len(M.bunches(sub, 7)["status"])
+        reps1 += 1
+    dt1 = time.perf_counter() - t0
+    oracle.set_num_threads(cores)
+    res["one_core"] = {"value": nb1 / dt1, "unit": UNIT, "cores": 1,
+                       "sample": f"{n // 5} steps ({nb1 // reps1} bunches), repeated {reps1} "
+                                 f"times, single-threaded"}
+    return res
 
 
 def main():

@@ -548,3 +548,8 @@ def hit_records(out: dict, track_base: int = 0):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """OpenMP threads of the oracle's parallel loops (timing only)."""
+    lib().orc_set_num_threads(int(n))

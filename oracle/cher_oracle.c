@@ -1643,3 +1643,15 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* The number of OpenMP threads of the next parallel loops (timing only; no
+ * effect without OpenMP). */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
