@@ -95,6 +95,15 @@ def _traffic(workload: str, scale: float):
     return t[0]
 
 
+# The same capture's pipe utilisation and issue activity (percent of peak),
+# reported beside the operation counts under the same source-hash guard.
+NCU_PIPES = {"alu": 41.9, "fma": 37.1, "fp64": 4.0, "issue_active": 76.4, "dram": 2.35}
+
+
+def _ncu_pipes(workload: str, scale: float):
+    return dict(NCU_PIPES) if _traffic(workload, scale) is not None else None
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -596,6 +605,8 @@ def run_ours(args):
                      "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32/INT32 lanes x "
                                     f"{mhz:.0f} MHz ({src} max clock)",
                      "ops_per_bunch": OPS_PER_BUNCH,
+                     "ops_by_stage": dict(OPS_PER_BUNCH_FP32),
+                     "ncu_pct_of_peak": _ncu_pipes(args.workload, args.scale),
                      "roofline_ms": 1e3 * max(t_alu, t_fp64),
                      "fp64_yield_ms_at_peak": 1e3 * t_fp64,
                      "launch_ms": 1e3 * per_launch_s},
