@@ -978,18 +978,21 @@ __device__ __forceinline__ void propagate_curved(const KParams &p, const Consts<
 // step index, with the step's share of the first two rounds taken from the
 // step constants (prep_step): round 1 multiplies counter word 0 (the
 // step's) and word 2 (j); round 2 multiplies round 1's word 2, which is the
-// step's again.  Same words as philox4x32_10.
+// step's again.  Same words as philox4x32_10; each product is taken whole
+// (64 bits) so that its two halves come from one multiply.
 template <class R>
 __device__ __forceinline__ uint4 philox_bunch(const KParams &p, const Seg<R> &S, uint32_t j) {
-    const uint32_t lo1 = 0xCD9E8D57u * j, hi1 = __umulhi(0xCD9E8D57u, j);
-    const uint32_t c1x = hi1 ^ S.ph_a, c1y = lo1;
-    const uint32_t lo0 = 0xD2511F53u * c1x, hi0 = __umulhi(0xD2511F53u, c1x);
-    uint4 c = make_uint4(S.ph_b ^ c1y, S.ph_c, hi0 ^ S.ph_d, lo0);
+    const uint64_t w1 = static_cast<uint64_t>(0xCD9E8D57u) * j;
+    const uint32_t c1x = static_cast<uint32_t>(w1 >> 32) ^ S.ph_a, c1y = static_cast<uint32_t>(w1);
+    const uint64_t w0 = static_cast<uint64_t>(0xD2511F53u) * c1x;
+    uint4 c = make_uint4(S.ph_b ^ c1y, S.ph_c, static_cast<uint32_t>(w0 >> 32) ^ S.ph_d,
+                         static_cast<uint32_t>(w0));
 #pragma unroll
     for (int r = 2; r < 10; ++r) {
-        const uint32_t a0 = 0xD2511F53u * c.x, b0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t a1 = 0xCD9E8D57u * c.z, b1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(b1 ^ c.y ^ p.rk0[r], a1, b0 ^ c.w ^ p.rk1[r], a0);
+        const uint64_t m0 = static_cast<uint64_t>(0xD2511F53u) * c.x;
+        const uint64_t m1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
+        c = make_uint4(static_cast<uint32_t>(m1 >> 32) ^ c.y ^ p.rk0[r], static_cast<uint32_t>(m1),
+                       static_cast<uint32_t>(m0 >> 32) ^ c.w ^ p.rk1[r], static_cast<uint32_t>(m0));
     }
     return c;
 }

@@ -497,8 +497,10 @@ cher_status build_grid(const cher_telescope *tel, int32_t n_tel, double theta_ma
     // at a horizontal distance of at most |z| tan(theta_max) + r / cos(theta_max)
     // from the centre (the distance from the centre to the line is at least
     // cos(theta) times the horizontal distance in the plane of the centre); a
-    // margin covers single-precision ground points.  Cells of the size of the
-    // largest reach; a sphere is listed in every cell its reach disc touches.
+    // margin covers single-precision ground points.  Cells of half the largest
+    // reach (fewer false candidates per cell than cells of the full reach, and
+    // the grid still fits L1); a sphere is listed in every cell its reach disc
+    // touches.
     std::vector<double> reach(n_tel);
     double rmax = 0.0, xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
     for (int k = 0; k < n_tel; ++k) {
@@ -511,7 +513,7 @@ cher_status build_grid(const cher_telescope *tel, int32_t n_tel, double theta_ma
         ymin = std::min(ymin, tel[k].y - reach[k]);
         ymax = std::max(ymax, tel[k].y + reach[k]);
     }
-    double cs = rmax;
+    double cs = rmax * 0.5;
     for (int attempt = 0; attempt < 24; ++attempt) {
         const double ex = xmax - xmin, ey = ymax - ymin;
         const double nxd = std::ceil(ex / cs), nyd = std::ceil(ey / cs);
