@@ -398,7 +398,10 @@ def run_ours(args):
         # input up and its records back inside the timed region: step k+1's
         # inputs go up (copy stream) and step k-1's records come down (second
         # copy stream) while step k's kernel runs; two input sets, two output
-        # buffers and two host record buffers.
+        # buffers and two host record buffers.  Step k-1's download waits
+        # until step k's kernel has started: a download already in flight when
+        # the kernel's inputs landed held the kernel back until it ended
+        # (seen on GB300 as kernel starts lined up with download ends).
         sets = [dtr, {k: torch.empty_like(v) for k, v in dtr.items()}]
         sets[1]["t_ref"].copy_(dtr["t_ref"])
         outs = [out, ctx.alloc_hits(cap, prec, device=dev)]
@@ -417,7 +420,8 @@ def run_ours(args):
         h_offs = [torch.empty(n_tel + 1, dtype=torch.int64).pin_memory() for _ in range(2)]
         up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
         comp = torch.cuda.current_stream()
-        ev = {k: [torch.cuda.Event(), torch.cuda.Event()] for k in ("up", "kern", "cnt", "down")}
+        ev = {k: [torch.cuda.Event(), torch.cuda.Event()]
+              for k in ("up", "kern", "cnt", "down", "start")}
 
         def upload(b):
             with torch.cuda.stream(up):
@@ -429,6 +433,7 @@ def run_ours(args):
         def launch_step(b):
             comp.wait_event(ev["up"][b])
             comp.wait_event(ev["down"][b])             # out b's records are down
+            ev["start"][b].record(comp)
             ctx.generate_propagate(sets[b], 11, prec, outs[b], track_base=track_base)
             ev["kern"][b].record(comp)
             ctx.pack_records(outs[b], pk[b], stream=comp)
@@ -445,6 +450,7 @@ def run_ours(args):
                 raise RuntimeError("host record buffer too small")
             with torch.cuda.stream(down):
                 down.wait_event(ev["cnt"][b])           # the packed records are written
+                down.wait_event(ev["start"][1 - b])     # the next step's kernel has started
                 hp, ht, hk = hrec[b]
                 if total > 0:
                     hp[:total].copy_(pk[b]["pos"][:total], non_blocking=True)
@@ -478,7 +484,8 @@ def run_ours(args):
         te, _ = reduce_over_ranks(te, 0.0, world, dev)
         e2e = {"value": b32 / len(r32["ms"]) * steps / te, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "pipelined": "step k+1 up and step k-1 down during step k's kernel"}
+               "pipelined": "step k+1 up and step k-1 down during step k's kernel "
+                            "(each download starts once the next kernel has)"}
 
         # end to end from shower parameters: the steps come from the device
         # generator (same shower, same step count), only the parameters and
