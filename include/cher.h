@@ -261,8 +261,10 @@ cher_status cher_generate_propagate_ex(cher_ctx *ctx, const cher_tracks *tracks,
  *                 time the axis reaches h_obs), 8-byte aligned.
  * The context holds the per-call tables in its scratch: calls on one
  * context must not overlap on different streams.  Asynchronous on
- * `stream` after a blocking upload.  Errors: CHER_EINVAL, CHER_ERANGE,
- * CHER_ENOMEM, CHER_ECUDA. */
+ * `stream`: the tables (a few KB per shower) go up from the context's
+ * pinned staging, and a call first waits, on the host, for the previous
+ * call's upload to have read that staging.  Errors: CHER_EINVAL,
+ * CHER_ERANGE, CHER_ENOMEM, CHER_ECUDA. */
 typedef struct cher_shower {
     double e0_mev;
     double zenith, azimuth;

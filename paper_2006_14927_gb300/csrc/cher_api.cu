@@ -71,6 +71,12 @@ struct cher_ctx {
     unsigned char *d_gen = nullptr;
     int64_t gen_cap = 0;
     std::map<std::pair<double, double>, std::vector<float>> cdf_cache;
+    // pinned staging of those tables (the upload is asynchronous; the event
+    // marks when the last upload has read the staging, before it is reused)
+    unsigned char *h_gen = nullptr;
+    int64_t h_gen_cap = 0;
+    cudaEvent_t gen_ev = nullptr;
+    bool gen_ev_pending = false;
     // wavelength-dependent index: kappa at the nodes (disp_k = 0: off), its
     // device copies, and the refraction tables of the band's two ends in
     // the pair-interleaved layout, {kappa_lo entry, kappa_hi entry}
@@ -752,23 +758,46 @@ cher_status cher_generate_steps(cher_ctx *c, const cher_shower *sh, int32_t n_sh
         }
         std::copy(it->second.begin(), it->second.end(), cdf.begin() + static_cast<size_t>(s) * kCdf);
     }
-    // one scratch block: shower constants | offsets | tables
+    // one scratch block: shower constants | offsets | tables, staged in pinned
+    // host memory (with t_ref after it) and uploaded in one asynchronous copy
     const size_t o_first = (sizeof(cher::GenShower) * n_showers + 15) & ~size_t(15);
     const size_t o_cdf = (o_first + sizeof(int64_t) * (n_showers + 1) + 15) & ~size_t(15);
     const size_t bytes = o_cdf + sizeof(float) * cdf.size();
+    const size_t o_tref = (bytes + 15) & ~size_t(15);
+    const size_t staged = o_tref + sizeof(double) * n_showers;
     cher_status r;
     if ((r = grow(&c->d_gen, c->gen_cap, static_cast<int64_t>(bytes))) != CHER_OK) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (cudaMemcpyAsync(c->d_gen, G.data(), sizeof(cher::GenShower) * n_showers,
-                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(c->d_gen + o_first, first.data(), sizeof(int64_t) * (n_showers + 1),
-                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(c->d_gen + o_cdf, cdf.data(), sizeof(float) * cdf.size(),
-                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(out->t_ref, t_ref.data(), sizeof(double) * n_showers,
-                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
+    if (!c->gen_ev && cudaEventCreateWithFlags(&c->gen_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        c->gen_ev = nullptr;
         return CHER_ECUDA;
+    }
+    // the previous call's upload has read the staging before it is rewritten
+    if (c->gen_ev_pending && cudaEventSynchronize(c->gen_ev) != cudaSuccess) return CHER_ECUDA;
+    c->gen_ev_pending = false;
+    if (static_cast<int64_t>(staged) > c->h_gen_cap) {
+        cudaFreeHost(c->h_gen);
+        c->h_gen = nullptr;
+        c->h_gen_cap = 0;
+        void *h = nullptr;
+        if (cudaHostAlloc(&h, staged, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return CHER_ENOMEM;
+        }
+        c->h_gen = static_cast<unsigned char *>(h);
+        c->h_gen_cap = static_cast<int64_t>(staged);
+    }
+    std::memcpy(c->h_gen, G.data(), sizeof(cher::GenShower) * n_showers);
+    std::memcpy(c->h_gen + o_first, first.data(), sizeof(int64_t) * (n_showers + 1));
+    std::memcpy(c->h_gen + o_cdf, cdf.data(), sizeof(float) * cdf.size());
+    std::memcpy(c->h_gen + o_tref, t_ref.data(), sizeof(double) * n_showers);
+    if (cudaMemcpyAsync(c->d_gen, c->h_gen, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(out->t_ref, c->h_gen + o_tref, sizeof(double) * n_showers,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaEventRecord(c->gen_ev, st) != cudaSuccess)
+        return CHER_ECUDA;
+    c->gen_ev_pending = true;
     cher::GenParams g;
     g.showers = reinterpret_cast<const cher::GenShower *>(c->d_gen);
     g.first = reinterpret_cast<const int64_t *>(c->d_gen + o_first);
@@ -794,6 +823,11 @@ cher_status cher_destroy(cher_ctx *c) {
     free_adjoint_scratch(c);
     free_transmission(c);
     free_dispersion_tables(c);
+    if (c->gen_ev) {
+        cudaEventSynchronize(c->gen_ev);
+        cudaEventDestroy(c->gen_ev);
+    }
+    cudaFreeHost(c->h_gen);
     cudaFree(c->d_gen);
     cudaFree(c->d_fb);
     cudaFree(c->d_fb_count);

@@ -120,3 +120,23 @@ def test_generator_rejects_bad_showers():
     empty = ctx.generate_steps([dict(SHOWERS[0], n=0)], SEED, FP32)
     assert empty["x0"].numel() == 0
     ctx.close()
+
+
+def test_back_to_back_calls_keep_their_tables():
+    """The per-call tables go up asynchronously from one pinned staging: calls
+    queued back to back on a stream, with different shower lists and no
+    synchronisation in between, give what each gives alone."""
+    import torch
+    sc, ctx = _ctx()
+    lists = [SHOWERS, [SHOWERS[2], SHOWERS[0]], [dict(SHOWERS[1], n=5000)], SHOWERS[:1]]
+    alone = []
+    for sh in lists:
+        d = ctx.generate_steps(sh, SEED, FP32)
+        torch.cuda.synchronize()
+        alone.append({k: v.clone() for k, v in d.items()})
+    queued = [ctx.generate_steps(sh, SEED, FP32) for sh in lists]
+    torch.cuda.synchronize()
+    for a, q in zip(alone, queued):
+        for k in a:
+            assert torch.equal(a[k], q[k]), k
+    ctx.close()
