@@ -1326,11 +1326,13 @@ __device__ __forceinline__ void flush_stat_signed(unsigned long long *stats, int
 // Warp-aggregated compaction into the per-telescope buffers: per (warp,
 // telescope) one atomicAdd reserves the slots; the record is the crossing
 // of the arrival line with the horizontal plane through the sphere centre.
-// All 32 lanes call it (hm = 0 on lanes without a crossing).
-template <class R>
+// All 32 lanes call it (hm = 0 on lanes without a crossing).  The photon
+// weight and record key come from weight_key(w, key), called on the hit
+// path only (about 2 % of bunches need them).
+template <class R, class KW>
 __device__ __forceinline__ void record_hits(const KParams &p, const BunchOut<R> &o, unsigned hm,
-                                            int s0, int gsel, R w, uint64_t key, R np1o,
-                                            int lane, unsigned &st_hits, unsigned &st_over) {
+                                            int s0, int gsel, KW weight_key, R np1o, int lane,
+                                            unsigned &st_hits, unsigned &st_over) {
     for (;;) {
         if (!__any_sync(kFull, hm != 0u)) break;
         int tel = -1;
@@ -1351,6 +1353,9 @@ __device__ __forceinline__ void record_hits(const KParams &p, const BunchOut<R> 
             slot0 = __shfl_sync(grp, slot0, leader);
             const unsigned long long slot = slot0 + rank;
             if (slot < static_cast<unsigned long long>(p.cap)) {
+                R w;
+                uint64_t key;
+                weight_key(w, key);          // only on the (rare) hit path
                 const R sl = (tz - o.zg) / o.cz;   // to the plane through the centre
                 const int64_t r = static_cast<int64_t>(tel) * p.cap + static_cast<int64_t>(slot);
                 store4<R>(p.pos, r, o.X + sl * o.cx - tx, o.Y + sl * o.cy - ty, o.cx, o.cy);
@@ -1638,11 +1643,15 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                     p.t_first[gb] = first;
                 }
             } else {
-                const R w = live ? seg[s].w : R(0);
-                const uint64_t key = (static_cast<uint64_t>(p.track_base + base + s) << 32) |
-                                     static_cast<uint32_t>(j);
                 const R np1 = DS ? R(1) + o.kap * c.eta_o : np1o;
-                record_hits<R>(p, o, hm, s0, gsel, w, key, np1, lane, st_hits, st_over);
+                const int64_t gstep = p.track_base + base + s;
+                const Seg<R> *sp = seg + s;
+                record_hits<R>(p, o, hm, s0, gsel,
+                               [sp, gstep, j](R &w_, uint64_t &k_) {
+                                   w_ = sp->w;
+                                   k_ = (static_cast<uint64_t>(gstep) << 32) | static_cast<uint32_t>(j);
+                               },
+                               np1, lane, st_hits, st_over);
             }
         }
         if (!p.tile_counter) break;
@@ -1745,7 +1754,8 @@ __global__ void __launch_bounds__(128) k_fallback(const KParams p) {
         int s0 = 0, gsel = 0;
         unsigned hm = live ? sphere_hits<R>(p, c, o, s0, gsel) : 0u;
         const R np1 = DS ? R(1) + o.kap * c.eta_o : np1o;
-        record_hits<R>(p, o, hm, s0, gsel, w, key, np1, lane, st_hits, st_over);
+        record_hits<R>(p, o, hm, s0, gsel, [w, key](R &w_, uint64_t &k_) { w_ = w; k_ = key; },
+                       np1, lane, st_hits, st_over);
     }
     unsigned long long *S = p.stats;
     if (S) {
