@@ -72,10 +72,10 @@ FP32_LANES_PER_SM = 128
 FP64_FMA_PER_SM_CLK = 2         # GB300: 1/64 of the FP32 rate (ncu: 2 DFMA/cycle/SM)
 
 # DRAM bytes (read + write) of one FP32 launch, from one ncu capture of the
-# full-size vertical workload (128.21 MB read, 25.00 MB written, 128 threads
+# full-size vertical workload (128.21 MB read, 24.99 MB written, 128 threads
 # x 8 CTAs per SM).  Reported only for that workload at full size and only
 # while the kernel sources hash to what was profiled.
-TRAFFIC = {"vertical_1tev": (153_202_688, "70ed9a1df8740dda")}
+TRAFFIC = {"vertical_1tev": (153_202_688, "fcf7956156bb18a7")}
 KERNEL_SOURCES = ("cher_kernels.cu", "cher_device.cuh", "cher_internal.h")
 
 
@@ -97,7 +97,7 @@ def _traffic(workload: str, scale: float):
 
 # The same capture's pipe utilisation and issue activity (percent of peak),
 # reported beside the operation counts under the same source-hash guard.
-NCU_PIPES = {"alu": 41.4, "fma": 35.6, "fp64": 4.0, "issue_active": 74.3, "dram": 2.39}
+NCU_PIPES = {"alu": 41.0, "fma": 35.0, "fp64": 4.0, "issue_active": 73.3, "dram": 2.39}
 
 
 def _ncu_pipes(workload: str, scale: float):

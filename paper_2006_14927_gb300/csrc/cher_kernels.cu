@@ -997,7 +997,7 @@ __device__ __forceinline__ uint4 philox_bunch(const KParams &p, const Seg<R> &S,
     return c;
 }
 
-template <class R, bool TR, int FB, bool DS, bool CV = false>
+template <class R, bool TR, int FB, bool DS, bool CV = false, bool LAZY = false>
 __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, const Seg<R> &S,
                                       const SegD<R> *SD, int j, BunchOut<R> &o) {
     const uint4 x = philox_bunch<R>(p, S, static_cast<uint32_t>(j));
@@ -1029,6 +1029,9 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
     o.kap = R(1);
     if constexpr (DS) {
         disp_sample<R>(p, *SD, u2, o.lam, o.kap, cosc, sinc);
+    } else if constexpr (LAZY) {
+        // the deviate; the record forms lambda (the hit path only)
+        o.lam = u2;
     } else {
         // 1/lambda^2 spectrum by inversion
         o.lam = R(1) / (c.lam_inv1 - u2 * c.lam_dinv);
@@ -1159,8 +1162,9 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
             Al = l0 + b * (l1 - l0);
         }
     } else {
-        const size_t e0 = static_cast<size_t>(jj) * (c.Z - 1) + kk;
-        const size_t e1 = e0 + (c.Z - 1);
+        // (H <= 65536, Z <= 4096: the entry index fits 32 bits)
+        const int e0 = jj * (c.Z - 1) + kk;
+        const int e1 = e0 + (c.Z - 1);
         if constexpr (std::is_same<R, float>::value) {
             const float4 *T = static_cast<const float4 *>(p.tab);
             const float4 t0 = __ldg(T + e0), t1 = __ldg(T + e1);
@@ -1327,8 +1331,10 @@ __device__ __forceinline__ void flush_stat_signed(unsigned long long *stats, int
 // telescope) one atomicAdd reserves the slots; the record is the crossing
 // of the arrival line with the horizontal plane through the sphere centre.
 // All 32 lanes call it (hm = 0 on lanes without a crossing).  The photon
-// weight and record key come from weight_key(w, key), called on the hit
-// path only (about 2 % of bunches need them).
+// weight, record key and wavelength come from weight_key(w, key, lambda),
+// called on the hit path only (about 2 % of bunches need them; in the plain
+// hits instantiation the bunch carries the spectrum's deviate and lambda is
+// formed there).
 template <class R, class KW>
 __device__ __forceinline__ void record_hits(const KParams &p, const BunchOut<R> &o, unsigned hm,
                                             int s0, int gsel, KW weight_key, R np1o, int lane,
@@ -1353,13 +1359,13 @@ __device__ __forceinline__ void record_hits(const KParams &p, const BunchOut<R> 
             slot0 = __shfl_sync(grp, slot0, leader);
             const unsigned long long slot = slot0 + rank;
             if (slot < static_cast<unsigned long long>(p.cap)) {
-                R w;
+                R w, lam;
                 uint64_t key;
-                weight_key(w, key);          // only on the (rare) hit path
+                weight_key(w, key, lam);     // only on the (rare) hit path
                 const R sl = (tz - o.zg) / o.cz;   // to the plane through the centre
                 const int64_t r = static_cast<int64_t>(tel) * p.cap + static_cast<int64_t>(slot);
                 store4<R>(p.pos, r, o.X + sl * o.cx - tx, o.Y + sl * o.cy - ty, o.cx, o.cy);
-                store4<R>(p.tim, r, o.t + sl * np1o * R(1.0 / kC), o.he, w, o.lam);
+                store4<R>(p.tim, r, o.t + sl * np1o * R(1.0 / kC), o.he, w, lam);
                 p.key[r] = key;
             } else {
                 ++st_over;
@@ -1566,7 +1572,8 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             int j = 0;
             if (live) {
                 j = bidx - off[s];
-                bunch<R, TR, FB, DS, CV>(p, c, seg[s], DS ? segd + s : nullptr, j, o);
+                constexpr bool kLazy = MODE == MODE_HITS && !TR && FB == 0 && !DS && !CV;
+                bunch<R, TR, FB, DS, CV, kLazy>(p, c, seg[s], DS ? segd + s : nullptr, j, o);
                 if (o.status != ST_GROUND) {       // rare: the drops
                     st_up += o.status == ST_UPWARD;
                     st_below += o.status == ST_BELOW;
@@ -1646,10 +1653,13 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                 const R np1 = DS ? R(1) + o.kap * c.eta_o : np1o;
                 const int64_t gstep = p.track_base + base + s;
                 const Seg<R> *sp = seg + s;
+                constexpr bool kLazy = MODE == MODE_HITS && !TR && FB == 0 && !DS && !CV;
+                const R lam_o = o.lam, li1 = c.lam_inv1, ldi = c.lam_dinv;
                 record_hits<R>(p, o, hm, s0, gsel,
-                               [sp, gstep, j](R &w_, uint64_t &k_) {
+                               [sp, gstep, j, lam_o, li1, ldi](R &w_, uint64_t &k_, R &l_) {
                                    w_ = sp->w;
                                    k_ = (static_cast<uint64_t>(gstep) << 32) | static_cast<uint32_t>(j);
+                                   l_ = kLazy ? R(1) / (li1 - lam_o * ldi) : lam_o;
                                },
                                np1, lane, st_hits, st_over);
             }
@@ -1754,7 +1764,9 @@ __global__ void __launch_bounds__(128) k_fallback(const KParams p) {
         int s0 = 0, gsel = 0;
         unsigned hm = live ? sphere_hits<R>(p, c, o, s0, gsel) : 0u;
         const R np1 = DS ? R(1) + o.kap * c.eta_o : np1o;
-        record_hits<R>(p, o, hm, s0, gsel, [w, key](R &w_, uint64_t &k_) { w_ = w; k_ = key; },
+        const R lam_o = o.lam;
+        record_hits<R>(p, o, hm, s0, gsel,
+                       [w, key, lam_o](R &w_, uint64_t &k_, R &l_) { w_ = w; k_ = key; l_ = lam_o; },
                        np1, lane, st_hits, st_over);
     }
     unsigned long long *S = p.stats;
