@@ -457,10 +457,13 @@ class Context:
                "cher_graph_create")
         return Graph(h, (dev_tracks, out))
 
-    def generate_steps(self, showers, seed: int, precision: int, device="cuda", stream=None):
+    def generate_steps(self, showers, seed: int, precision: int, device="cuda", stream=None,
+                       out=None):
         """Device step arrays of parameterised showers (cher_generate_steps):
         `showers` is a sequence of dicts with e0_mev, zenith, azimuth,
-        core_x, core_y, n.  Returns the dict generate_propagate takes."""
+        core_x, core_y, n.  Returns the dict generate_propagate takes; `out`,
+        a dict returned by an earlier call with the same total step count,
+        shower count and precision, is written again instead of allocating."""
         torch = _torch()
         arr = (Shower * len(showers))()
         for k, s in enumerate(showers):
@@ -468,12 +471,17 @@ class Context:
                             float(s["core_x"]), float(s["core_y"]), int(s["n"]))
         n = sum(max(int(s["n"]), 0) for s in showers)    # (a negative count: EINVAL below)
         ddt = torch.float32 if precision == CHER_FP32_BULK else torch.float64
-        out = {k: torch.empty(n, dtype=torch.float64, device=device)
-               for k in ("x0", "y0", "z0", "t0", "len", "ekin")}
-        for k in ("ux", "uy", "uz"):
-            out[k] = torch.empty(n, dtype=ddt, device=device)
-        out["shower"] = torch.empty(n, dtype=torch.int32, device=device)
-        out["t_ref"] = torch.empty(len(showers), dtype=torch.float64, device=device)
+        if out is not None:
+            if (out["x0"].numel() != n or out["t_ref"].numel() != len(showers)
+                    or out["ux"].dtype != ddt):
+                raise ValueError("generate_steps: `out` does not match these showers")
+        else:
+            out = {k: torch.empty(n, dtype=torch.float64, device=device)
+                   for k in ("x0", "y0", "z0", "t0", "len", "ekin")}
+            for k in ("ux", "uy", "uz"):
+                out[k] = torch.empty(n, dtype=ddt, device=device)
+            out["shower"] = torch.empty(n, dtype=torch.int32, device=device)
+            out["t_ref"] = torch.empty(len(showers), dtype=torch.float64, device=device)
         B = StepBuffers(*[out[k].data_ptr() for k in ("x0", "y0", "z0", "t0", "len", "ekin", "ux",
                                                      "uy", "uz", "shower", "t_ref")])
         _check(lib().cher_generate_steps(self._h, arr, len(showers), ctypes.c_uint64(seed),

@@ -140,3 +140,22 @@ def test_back_to_back_calls_keep_their_tables():
         for k in a:
             assert torch.equal(a[k], q[k]), k
     ctx.close()
+
+
+def test_reused_outputs_match_fresh_ones():
+    """`out=` writes an earlier call's arrays again: the same steps as a fresh
+    call; a mismatched dict is refused before anything is launched."""
+    import torch
+    sc, ctx = _ctx()
+    fresh = ctx.generate_steps(SHOWERS, SEED, FP32)
+    buf = ctx.generate_steps(SHOWERS, SEED + 1, FP32)
+    again = ctx.generate_steps(SHOWERS, SEED, FP32, out=buf)
+    torch.cuda.synchronize()
+    assert again is buf
+    for k in fresh:
+        assert torch.equal(fresh[k], again[k]), k
+    with pytest.raises(ValueError):
+        ctx.generate_steps(SHOWERS[:2], SEED, FP32, out=buf)
+    with pytest.raises(ValueError):
+        ctx.generate_steps(SHOWERS, SEED, FP64, out=buf)
+    ctx.close()
