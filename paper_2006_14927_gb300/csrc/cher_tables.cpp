@@ -499,8 +499,8 @@ cher_status build_grid(const cher_telescope *tel, int32_t n_tel, double theta_ma
     // cos(theta) times the horizontal distance in the plane of the centre); a
     // margin covers single-precision ground points.  Cells of half the largest
     // reach (fewer false candidates per cell than cells of the full reach, and
-    // the grid still fits L1); a sphere is listed in every cell its reach disc
-    // touches.
+    // the grid still fits L1), or of the full reach where half would pass the
+    // cell limit; a sphere is listed in every cell its reach disc touches.
     std::vector<double> reach(n_tel);
     double rmax = 0.0, xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
     for (int k = 0; k < n_tel; ++k) {
@@ -514,10 +514,20 @@ cher_status build_grid(const cher_telescope *tel, int32_t n_tel, double theta_ma
         ymax = std::max(ymax, tel[k].y + reach[k]);
     }
     double cs = rmax * 0.5;
+    bool widened = false;
     for (int attempt = 0; attempt < 24; ++attempt) {
         const double ex = xmax - xmin, ey = ymax - ymin;
         const double nxd = std::ceil(ex / cs), nyd = std::ceil(ey / cs);
-        if (nxd * nyd > double(1 << 22)) return CHER_ERANGE;
+        if (nxd * nyd > double(1 << 22)) {
+            // too many cells of half the reach for this extent: cells of the
+            // full reach, once (the same limit then applies as to them)
+            if (!widened && cs < rmax) {
+                cs = rmax;
+                widened = true;
+                continue;
+            }
+            return CHER_ERANGE;
+        }
         g.nx = std::max(1, static_cast<int>(nxd));
         g.ny = std::max(1, static_cast<int>(nyd));
         g.x0 = xmin;
