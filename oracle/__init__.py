@@ -137,7 +137,7 @@ def lib():
                                           ctypes.c_int, _dp]
         L.orc_eta_lookup.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
         L.orc_eta_lookup.restype = ctypes.c_double
-        L.orc_segment_yield.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Tracks), _i32p,
+        L.orc_segment_yield.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Tracks), _i64p,
                                         _dp, _dp, _i32p]
         L.orc_brute_ray.argtypes = [ctypes.POINTER(_Atm), ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double, _dp, _dp]
@@ -414,12 +414,12 @@ class Model:
     def segment_yield(self, tracks: dict):
         T, keep = self._tracks(tracks)
         n = T.n
-        nb = np.zeros(n, np.int32)
+        nb = np.zeros(n, np.int64)
         w = np.zeros(n)
         s2 = np.zeros(n)
         valid = np.zeros(n, np.int32)
         C = self._cfg()
-        lib().orc_segment_yield(ctypes.byref(C), ctypes.byref(T), _ptr(nb, ctypes.c_int32),
+        lib().orc_segment_yield(ctypes.byref(C), ctypes.byref(T), _ptr(nb, ctypes.c_int64),
                                 _ptr(w), _ptr(s2), _ptr(valid, ctypes.c_int32))
         del keep
         return nb, w, s2, valid.astype(bool)

@@ -376,7 +376,6 @@ static int orc_step_yield_valid(const orc_cfg *C, double hm, double len, double 
     double Ks2 = K * s2;
     double N = len * Ks2;
     double q = N * inv_B;
-    if (!(q < 4194304.0)) return -1;           /* more than 2^22 bunches */
     double nbd = ceil(q);
     Y->s2 = s2;
     Y->N = N;
@@ -475,7 +474,6 @@ static int orc_step_yield_disp(const orc_cfg *C, double hm, double len, double e
     double Ks = Kd * sum;
     double N = len * Ks;
     double q = N * inv_B;
-    if (!(q < 4194304.0)) return -1;
     double nbd = ceil(q);
     Y->s2 = sum / (double)(C->disp_k - 1);  /* band-averaged sin^2         */
     Y->N = N;
@@ -508,13 +506,13 @@ static int orc_step_yield(const orc_cfg *C, const orc_tracks *T, int64_t i, orc_
 
 /* Per-step yield for every step: nb (bunches), w (photons per bunch),
  * s2 (sin^2 of the Cherenkov angle) and a validity flag (1 valid). */
-void orc_segment_yield(const orc_cfg *C, const orc_tracks *T, int32_t *nb, double *w,
+void orc_segment_yield(const orc_cfg *C, const orc_tracks *T, int64_t *nb, double *w,
                        double *s2, int32_t *valid)
 {
     for (int64_t i = 0; i < T->n; ++i) {
         orc_yield Y;
         int ok = orc_step_yield(C, T, i, &Y);
-        nb[i] = (int32_t)Y.nb;
+        nb[i] = Y.nb;
         if (w) w[i] = Y.w;
         if (s2) s2[i] = Y.s2;
         if (valid) valid[i] = (ok == 0);

@@ -170,6 +170,26 @@ def test_frank_tamm_ultrarelativistic_sea_level():
     assert 43.0 < per_m < 43.5
 
 
+def test_no_bunch_count_limit_in_the_oracle():
+    """The Frank-Tamm count has no upper limit: a 200 km step at sea-level
+    density (about 8.7e6 photons, 1.7e6 bunches) and a 2000 km one (17e6
+    bunches, past 2^22) both get nb = ceil(N / B) of the textbook N, valid."""
+    M = _model()
+    n = 1.0 + oracle.eta_exact(M.atm, 0.0)[0]
+    e = 1.0e7
+    gam = (e + ME) / ME
+    beta = math.sqrt(1.0 - 1.0 / gam ** 2)
+    for L in (2.0e5, 2.0e6):
+        tr = dict(z0=np.array([0.5 * L * 1e-9]), len=np.array([L]), ekin=np.array([e]),
+                  uz=np.array([-1e-9]))
+        nb, w, s2, valid = M.segment_yield(tr)
+        N = L * 2 * math.pi * ALPHA * (1 - 1 / (beta * n) ** 2) * (1 / 300e-9 - 1 / 600e-9)
+        assert valid[0]
+        assert nb[0] == math.ceil(N / 5.0)
+        assert nb[0] * w[0] == pytest.approx(N, rel=1e-9)
+    assert nb[0] > 2 ** 22
+
+
 def test_invalid_steps_are_flagged():
     M = _model()
     tr = dict(z0=np.array([1e4, np.nan, 1e4, 1e4]), len=np.array([5.0, 5.0, -1.0, 5.0]),
@@ -442,3 +462,69 @@ def test_density_read_out_is_the_gaussian_sum():
             assert U[k] == pytest.approx(np.sum(out["w"][g] * G * out["t"][g]), rel=1e-12,
                                          abs=1e-300)
         assert S.sum() > 0
+
+
+# --------------------------------------------------------------------------
+# a4/a5: the record at the plane through the sphere centre, in closed form
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("rho2", [0.5, 1.0])
+def test_record_plane_closed_form(rho2):
+    """Two slabs of constant index (n1 below hb, n2 above; rho2 = 1 makes
+    them one uniform medium, a straight line at c/n): a photon emitted at
+    x_e, h_e > hb along p runs straight at zenith theta2 down to hb, is
+    refracted there (n2 sin theta2 = n1 sin theta1) and runs straight at
+    theta1 through the horizontal plane z_p = h_obs + tz of a sphere centre.
+    There, relative to the centre (at the origin),
+        x = x_e + h_x [(h_e - hb) tan theta2 + (hb - z_p) tan theta1],
+        t = t_e + [n2 (h_e - hb) / cos theta2 + n1 (hb - z_p) / cos theta1] / c,
+    with (h_x, h_y) the horizontal unit vector of p, and (c_x, c_y) =
+    sin theta1 (h_x, h_y).  Each record field is checked against this to
+    rounding.  With n1 - 1 = 0.5 %, a record time taken at c instead of c/n1
+    along the line, or a step back along the line of the wrong sign, is off
+    by 0.1 - 1 ns."""
+    hb, h_obs, tz, n0m1 = 3000.0, 2200.0, 40.0, 0.005
+    atm = _slab_atm(1.0, rho2, hb, n0m1=n0m1)
+    n1 = 1.0 + n0m1
+    n2 = 1.0 + n0m1 * rho2
+    ns = 48
+    rng = np.random.default_rng(7)
+    th = np.radians(rng.uniform(5.0, 25.0, ns))
+    ph = rng.uniform(0.0, 2 * math.pi, ns)
+    tr = dict(x0=rng.uniform(-50, 50, ns), y0=rng.uniform(-50, 50, ns),
+              z0=rng.uniform(4000.0, 6000.0, ns), t0=rng.uniform(0.0, 100.0, ns),
+              len=np.full(ns, 4.0), ekin=np.full(ns, 1000.0),
+              ux=np.sin(th) * np.cos(ph), uy=np.sin(th) * np.sin(ph), uz=-np.cos(th))
+    tel = np.array([[0.0, 0.0, tz, 3000.0]])     # every downward bunch crosses it
+    for variant in (1, 0):
+        M = oracle.Model(atm, h_obs, tel, H=401, Z=64, h_max=43000.0, theta_max_deg=70.0,
+                         n_fine=20001)
+        out = M.bunches(tr, seed=5, variant=variant)
+        g = out["status"] == oracle.ST_GROUND
+        assert g.sum() > 100 and np.all(out["nhit"][g] == 1)
+        rec = oracle.hit_records(out)
+        b = rec["bunch"]
+        assert len(b) == g.sum()
+        xe, ye, he, te = out["xe"][b], out["ye"][b], out["he"][b], out["te"][b]
+        px, py, pz = out["px"][b], out["py"][b], out["pz"][b]
+        s2 = np.hypot(px, py)
+        hx, hy = px / s2, py / s2
+        c2 = -pz
+        s1 = n2 / n1 * s2
+        c1 = np.sqrt(1.0 - s1 * s1)
+        zp = h_obs + tz
+        assert np.all(he > hb)
+        D = (he - hb) * s2 / c2 + (hb - zp) * s1 / c1
+        L = n2 * (he - hb) / c2 + n1 * (hb - zp) / c1
+        ex, ey, et = xe + hx * D, ye + hy * D, te + L / C
+        # (B) integrates the slabs exactly; (T) interpolates its tables
+        tol_x, tol_t = (1e-9, 1e-9) if variant == 1 else (1e-5, 1e-4)
+        np.testing.assert_allclose(rec["x"], ex, rtol=0, atol=tol_x)
+        np.testing.assert_allclose(rec["y"], ey, rtol=0, atol=tol_x)
+        np.testing.assert_allclose(rec["t"], et, rtol=0, atol=tol_t)
+        np.testing.assert_allclose(rec["cx"], s1 * hx, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(rec["cy"], s1 * hy, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(rec["zem"], he, rtol=0, atol=0)
+        # the record time precedes the ground time by the stretch of line
+        # between the plane and the ground, run at c / n1
+        tg = out["t"][b]
+        np.testing.assert_allclose(tg - rec["t"], n1 * tz / c1 / C, rtol=0, atol=1e-9)
