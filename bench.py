@@ -1,16 +1,20 @@
 #!/usr/bin/env python
 """Throughput of the Cherenkov bunch hot path: bunches generated and
-propagated per second.
+propagated per second, FP32-bulk and FP64 paths, against the ALU roofline.
 
-Workload (default): one 1 TeV vertical gamma-like shower, 2e6 e+- steps,
-19 telescope spheres, refraction tables 1000 x 64 up to 70 deg (seeded,
-synthetic: see workloads/).  A step of the benchmark is one call of
-cher_generate_propagate over all 2e6 steps: every bunch generated, refracted,
-propagated, tested against the spheres and the crossings compacted.
+Workload (default): 256 showers (primary energies log-uniform 10 GeV -
+10 TeV, zenith 0-40 deg), 2e8 e+- steps in one persistent launch replayed
+from its captured CUDA graph, 100 telescope spheres over 2 x 2 km, refraction
+tables 1000 x 64 up to 70 deg (seeded, synthetic: see workloads/).  A step of
+the benchmark is one launch over all 2e8 steps: every bunch generated,
+refracted, propagated, tested against the spheres and the crossings
+compacted.  The same line carries the 20 TeV shower at 60 deg (1e8 steps,
+tables 4000 x 256 to 75 deg) and the 1 TeV vertical shower (2e6 steps) as
+legs with their own roofline, and the FP64 path of each.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun (N > 1) every rank simulates its own shower (independent
+Under torchrun (N > 1) every rank simulates its own showers (independent
 showers: weak scaling, no collective on the data path); the value is the
 bunches of all ranks over the slowest rank's time.  `--impl reference`
 times the FP64 CPU oracle on a bounded sample of the same workload.
@@ -39,21 +43,26 @@ WORKLOAD_TEXT = {
     "inclined_20tev": "inclined_20tev: 20 TeV shower at 60 deg zenith, 1e8 steps per GPU, "
                       "100 spheres over 2 x 2 km, tables 4000 x 256 to 75 deg",
     "batched_256": "batched_256: 256 showers (10 GeV - 10 TeV, zenith 0-40 deg), 2e8 steps per "
-                   "GPU in one persistent launch, 100 spheres over 2 x 2 km",
+                   "GPU in one persistent launch replayed from its CUDA graph, 100 spheres over "
+                   "2 x 2 km, tables 1000 x 64 to 70 deg",
 }
 UNIT = "bunches/s"
-WORKLOAD = "vertical_1tev"
+WORKLOAD = "batched_256"
 
 # ---------------------------------------------------------------------------
 # Algorithmic operation counts, from the algorithm as the oracle states it
 # (each add, mul, fma, compare, select, convert, shift or logic op = 1; each
-# sqrt, rsqrt or reciprocal = 1; implementation overhead excluded).  Per
-# bunch, FP32/INT32 lane operations of the single-precision path, by stage;
-# per emitting step, the FP64 operations of the yield.
+# sqrt, rsqrt or reciprocal = 1; implementation overhead excluded), with the
+# work that depends only on the step counted once per step and the work that
+# depends only on the launch (the Philox key schedule, 18 adds) not counted.
+# Per bunch, FP32/INT32 lane operations of the single-precision path by
+# stage; per step, the same for the step's own work.
 # ---------------------------------------------------------------------------
 OPS_PER_BUNCH_FP32 = {
     "sub_step_loop": 2,
-    "philox4x32_10": 98,        # 10 x (2 mul.lo + 2 mul.hi + 4 xor) + 9 x 2 key adds
+    "philox4x32_10": 71,        # rounds 3-10: 8 x (2 mul.lo + 2 mul.hi + 4 xor); rounds
+                                # 1-2: the bunch index's share (M1 j: 2 mul + 1 xor; M0 of
+                                # round 1's word 0: 2 mul + 2 xor)
     "deviates": 9,              # 3 x (shift, convert, fma)
     "emission": 36,             # sub-step fraction, sin/cos of the azimuth, cone, lambda, height
     "rare_conditions": 3,
@@ -63,19 +72,30 @@ OPS_PER_BUNCH_FP32 = {
     "grid_and_sphere": 24,      # grid cell, one line-sphere test
     "output_counters": 8,       # amortised compaction and counters
 }
-OPS_PER_BUNCH = sum(OPS_PER_BUNCH_FP32.values())          # 242
+OPS_PER_BUNCH = sum(OPS_PER_BUNCH_FP32.values())          # 215
+OPS_PER_STEP_FP32 = {
+    "validity": 11,             # nine finiteness tests, len >= 0, E_kin > 0
+    "yield": 50,                # n(h) lookup, sin^2, N / B, its rounding bound, ceil
+    "philox_step_share": 8,     # rounds 1-2: the step index's share (2 x (2 mul + 2 xor))
+    "step_constants": 32,       # 5 roundings, 2 FP64 differences, azimuth basis, cone,
+                                # 1/nb, 1/(beta c), photons per bunch
+    "scan": 12,                 # the tile's prefix sum of nb, per step
+}
+OPS_PER_STEP = sum(OPS_PER_STEP_FP32.values())            # 113
 # the floating-point part (everything but Philox), which the FP64 path runs
-# on the FP64 pipe
-FP64_OPS_PER_BUNCH = OPS_PER_BUNCH - OPS_PER_BUNCH_FP32["philox4x32_10"]
-FP64_OPS_PER_STEP = 34          # yield chain: 24 mul/add + 1 division (~10 ops)
+# on the FP64 pipe, per bunch and per step (the yield chain, 34, and the
+# step constants, 30, in FP64)
+FP64_OPS_PER_BUNCH = OPS_PER_BUNCH - OPS_PER_BUNCH_FP32["philox4x32_10"]     # 144
+FP64_OPS_PER_STEP = 64
 FP32_LANES_PER_SM = 128
 FP64_FMA_PER_SM_CLK = 2         # GB300: 1/64 of the FP32 rate (ncu: 2 DFMA/cycle/SM)
 
-# DRAM bytes (read + write) of one FP32 launch, from one ncu capture of the
-# full-size vertical workload (128.21 MB read, 24.99 MB written, 128 threads
-# x 8 CTAs per SM).  Reported only for that workload at full size and only
-# while the kernel sources hash to what was profiled.
-TRAFFIC = {"vertical_1tev": (153_202_688, "fcf7956156bb18a7")}
+# DRAM bytes (read + write) per step of one FP32 launch, from ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum of the fused kernel, 128
+# threads x 8 CTAs per SM) of each workload at 2e6 steps, scaled to a launch
+# by its steps (the inputs, 64 B per step, dominate and scale with them).
+# Reported only while the kernel sources hash to what was profiled.
+TRAFFIC_PER_STEP = {}
 KERNEL_SOURCES = ("cher_kernels.cu", "cher_device.cuh", "cher_internal.h")
 
 
@@ -88,20 +108,37 @@ def _kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic(workload: str, scale: float):
-    t = TRAFFIC.get(workload)
-    if t is None or scale != 1.0 or _kernel_hash() != t[1]:
+def _traffic(workload: str, steps: int):
+    t = TRAFFIC_PER_STEP.get(workload)
+    if t is None or _kernel_hash() != t[1]:
         return None
-    return t[0]
+    return int(round(t[0] * steps))
 
 
-# The same capture's pipe utilisation and issue activity (percent of peak),
-# reported beside the operation counts under the same source-hash guard.
-NCU_PIPES = {"alu": 41.0, "fma": 35.0, "fp64": 4.0, "issue_active": 73.3, "dram": 2.39}
+def alu_roofline(bunches: float, steps: float, ms: float, sm_count: int, mhz: float):
+    """FP32-path roofline: algorithmic lane operations per launch over the
+    mean launch time, against the FP32/INT32 lanes x clock (an issue-rate
+    bound derived from the unit counts, not a measured peak)."""
+    ops = OPS_PER_BUNCH * bunches + OPS_PER_STEP * steps
+    peak = sm_count * FP32_LANES_PER_SM * mhz * 1e6
+    achieved = ops / (ms / 1e3)
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+            "frac": achieved / peak, "ops_per_bunch": OPS_PER_BUNCH,
+            "ops_per_step": OPS_PER_STEP, "launch_ms": ms,
+            "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32/INT32 lanes x "
+                           f"{mhz:.0f} MHz max clock (issue-rate bound)"}
 
 
-def _ncu_pipes(workload: str, scale: float):
-    return dict(NCU_PIPES) if _traffic(workload, scale) is not None else None
+def fp64_roofline(bunches: float, steps: float, ms: float, sm_count: int, mhz: float):
+    """FP64-path roofline: the floating-point operations on the FP64 pipe."""
+    ops = FP64_OPS_PER_BUNCH * bunches + FP64_OPS_PER_STEP * steps
+    peak = sm_count * FP64_FMA_PER_SM_CLK * mhz * 1e6
+    achieved = ops / (ms / 1e3)
+    return {"bound": "fp64", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+            "frac": achieved / peak, "ops_per_bunch": FP64_OPS_PER_BUNCH,
+            "ops_per_step": FP64_OPS_PER_STEP,
+            "peak_source": f"derived: {sm_count} SMs x {FP64_FMA_PER_SM_CLK} FP64 lanes x "
+                           f"{mhz:.0f} MHz"}
 
 
 def _peaks():
@@ -192,17 +229,29 @@ def reduce_over_ranks(t_local: float, bunches_local: float, world: int, device):
     return float(t.item()), float(b.item())
 
 
+def _sample_workload(workload: str, n: int = 20_000):
+    """A bounded sample of a workload for the CPU oracle: its generator at n
+    steps (the 256-shower batch keeps its 256 showers, with n steps split
+    among them in proportion to energy as in the full batch)."""
+    import workloads
+    if workload == "batched_256":
+        return workloads.batched_256(total=n), f"the 256 showers of batched_256 with {n} steps"
+    if workload in ("plain_fp64", "adjoint_300gev"):
+        sc = workloads.WORKLOADS[workload]()
+        return sc, f"{workload}: all {len(sc['tracks']['x0'])} steps"
+    return workloads.WORKLOADS[workload](n=n), f"{workload}: its first {n} steps"
+
+
 def run_reference(args):
     """The FP64 CPU oracle on a bounded sample of the same workload."""
     rank, world, _ = _env_rank()
     if rank != 0:
         return
     import oracle
-    import workloads
     oracle.build()
-    sample_steps = 20_000
-    sc = workloads.vertical_1tev(n=sample_steps)
-    M = oracle.Model(sc["atm"], sc["h_obs"], sc["telescopes"], t_ref=sc["t_ref"])
+    sc, what = _sample_workload(args.workload)
+    M = oracle.Model(sc["atm"], sc["h_obs"], sc["telescopes"], h_max=sc["h_max"], H=sc["H"],
+                     Z=sc["Z"], theta_max_deg=sc["theta_max_deg"], t_ref=sc["t_ref"])
     tr = sc["tracks"]
     for _ in range(args.warmup):
         M.bunches(tr, 7)
@@ -218,14 +267,138 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"{WORKLOAD} sample: first {sample_steps} of 2e6 steps",
+            "config": {"workload": f"{args.workload} sample: {what}",
                        "precision": "fp64 oracle (table variant)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{sample_steps} steps ({nb // args.steps} bunches) "
-                                       f"of the 1 TeV vertical shower per step"},
+                             "sample": f"{what} ({nb // args.steps} bunches) per step, "
+                                       f"OpenMP over steps"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _make_workload(wl: str, scale: float, rank: int):
+    import workloads
+    if wl == "vertical_1tev":
+        n_req = int(2_000_000 * scale)
+        seed, track_base = shard(rank, n_req, 2)
+        return workloads.vertical_1tev(n=n_req, seed=seed), track_base
+    if wl == "inclined_20tev":
+        n_req = int(100_000_000 * scale)
+        seed, track_base = shard(rank, n_req, 5)
+        return workloads.inclined_20tev(n=n_req, seed=seed), track_base
+    if wl == "batched_256":
+        n_req = int(200_000_000 * scale)
+        seed, track_base = shard(rank, n_req, 3)
+        return workloads.batched_256(total=n_req, seed=seed), track_base
+    sc = workloads.WORKLOADS[wl]()
+    return sc, rank * len(sc["tracks"]["x0"])
+
+
+def _cap(wl: str, scale: float, cap_arg):
+    """Records per telescope: the densest telescope of each workload fits
+    (the batch: 12e6 x 100 telescopes x 40 B = 48 GB of the 288 GB)."""
+    if cap_arg:
+        return cap_arg
+    full = {"vertical_1tev": 600_000, "batched_256": 12_000_000}.get(wl, 8_000_000)
+    return full if wl == "vertical_1tev" else max(200_000, int(full * scale))
+
+
+class Bench:
+    """Timing of one workload on one context (CUDA events on the launching
+    stream, L2 flushed by a 256 MiB write between timed launches)."""
+
+    def __init__(self, P, dev, sc, wl, scale, cap, track_base, barrier):
+        import torch
+        self.P, self.dev, self.sc, self.wl = P, dev, sc, wl
+        self.track_base, self.barrier, self.cap = track_base, barrier, cap
+        self.n = len(sc["tracks"]["x0"])
+        t0 = time.perf_counter()
+        self.ctx = P.Context(sc["atm"], sc["h_obs"], sc["telescopes"])
+        self.ctx.build_refraction_tables(sc["H"], sc["Z"], sc["theta_max_deg"], sc["h_max"])
+        self.table_s = time.perf_counter() - t0
+        self.flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+        self.stream = torch.cuda.current_stream()
+        self.bufs = {}
+
+    def buffers(self, prec):
+        if prec not in self.bufs:
+            P = self.P
+            dtr = P.device_tracks(self.sc["tracks"], prec, device=self.dev, t_ref=self.sc["t_ref"])
+            self.bufs[prec] = (dtr, self.ctx.alloc_hits(self.cap, prec, device=self.dev))
+        return self.bufs[prec]
+
+    def release(self, prec):
+        import torch
+        self.bufs.pop(prec, None)
+        torch.cuda.empty_cache()
+
+    def measure(self, prec, steps, warmup, launch=None, graph=False, prof=None):
+        """Mean-free list of per-launch times (ms), the stats of the last
+        launch and the wall time of the timed loop."""
+        import torch
+        dtr, out = self.buffers(prec)
+        ctx = self.ctx
+        pkw = {} if prof is None else dict(profile=prof[0], bin_gcm2=prof[1], axis_cos=prof[2])
+        if launch is not None:
+            ctx.set_launch(*launch)
+
+        def once():
+            ctx.generate_propagate(dtr, 11, prec, out, track_base=self.track_base, **pkw)
+
+        g = None
+        if graph:
+            g = ctx.graph(dtr, 11, prec, out, track_base=self.track_base)
+            once = g.launch                      # noqa: F811 (the graph replaces the call)
+        for _ in range(warmup):
+            once()
+        code, stats = ctx.sync_status(out)
+        if code not in (0, 6):                   # 6: a buffer overflowed (counted)
+            raise RuntimeError(f"status {code} in warm-up")
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        self.barrier()
+        w0 = time.perf_counter()
+        for k in range(steps):
+            self.flush.fill_(k & 0xff)           # evict L2 between timed launches
+            ev[k][0].record(self.stream)
+            once()
+            ev[k][1].record(self.stream)
+        self.barrier()
+        wall = time.perf_counter() - w0
+        ms = [a.elapsed_time(b) for a, b in ev]
+        code, stats = ctx.sync_status(out)
+        if g is not None:
+            g.close()
+        return dict(ms=ms, wall=wall, stats=stats, code=code)
+
+
+def workload_leg(P, dev, wl, scale, cap_arg, steps, warmup, launch, sm_count, mhz, barrier):
+    """One more workload in the same run: FP32 (the autotuned shape of the
+    main workload, regular launches) and FP64, each with its roofline."""
+    import torch
+    sc, tb = _make_workload(wl, scale, 0)
+    B = Bench(P, dev, sc, wl, scale, _cap(wl, scale, cap_arg), tb, barrier)
+    r32 = B.measure(P.CHER_FP32_BULK, steps, warmup, launch=launch)
+    B.release(P.CHER_FP32_BULK)
+    r64 = B.measure(P.CHER_FP64, max(3, steps // 4), 3, launch=launch)
+    B.release(P.CHER_FP64)
+    n = B.n
+    b32, b64 = float(r32["stats"][3]), float(r64["stats"][3])
+    ms32, ms64 = statistics.mean(r32["ms"]), statistics.mean(r64["ms"])
+    rl = alu_roofline(b32, n, ms32, sm_count, mhz)
+    rl["traffic"] = _traffic(wl, n)
+    res = {"value": b32 / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32,
+           "bunches_per_step": int(b32), "steps_per_gpu": n, "roofline": rl,
+           "fp64": {"value": b64 / (ms64 / 1e3), "ms_per_step": ms64,
+                    "roofline": fp64_roofline(b64, n, ms64, sm_count, mhz)},
+           "fp32_over_fp64": (b32 / ms32) / (b64 / ms64),
+           "overflowed_records": int(r32["stats"][10]), "table_build_s": B.table_s,
+           "workload": WORKLOAD_TEXT.get(wl, wl)}
+    B.ctx.close()
+    del B
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_ours(args):
@@ -243,396 +416,161 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     P.build()
-    stream = torch.cuda.current_stream()
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    # ---- workload (each rank its own shower: weak scaling) ----------------
+    # ---- workload (each rank its own showers: weak scaling) ---------------
     wl = args.workload
-    if wl == "vertical_1tev":
-        n_req = int(2_000_000 * args.scale)
-        seed, track_base = shard(rank, n_req, 2)
-        sc = workloads.vertical_1tev(n=n_req, seed=seed)
-    elif wl == "inclined_20tev":
-        n_req = int(100_000_000 * args.scale)
-        seed, track_base = shard(rank, n_req, 5)
-        sc = workloads.inclined_20tev(n=n_req, seed=seed)
-    elif wl == "batched_256":
-        n_req = int(200_000_000 * args.scale)
-        seed, track_base = shard(rank, n_req, 3)
-        sc = workloads.batched_256(total=n_req, seed=seed)
-    else:
-        sc = workloads.WORKLOADS[wl]()
-        track_base = rank * len(sc["tracks"]["x0"])
-    n = len(sc["tracks"]["x0"])
-    t0 = time.perf_counter()
-    ctx = P.Context(sc["atm"], sc["h_obs"], sc["telescopes"])
-    ctx.build_refraction_tables(sc["H"], sc["Z"], sc["theta_max_deg"], sc["h_max"])
-    table_s = time.perf_counter() - t0
-    # records per telescope: the densest telescope of each workload fits
-    # (batched: 12e6 x 100 telescopes x 40 B = 48 GB of the 288 GB)
-    cap_full = {"vertical_1tev": 600_000, "batched_256": 12_000_000}.get(args.workload,
-                                                                         8_000_000)
-    cap = args.cap or (cap_full if args.workload == "vertical_1tev" else
-                       max(200_000, int(cap_full * args.scale)))
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-
-    def measure(prec, steps, warmup, autotune, prof=None, reuse=None):
-        if reuse is not None:
-            dtr, out = reuse["dtr"], reuse["out"]
-        else:
-            dtr = P.device_tracks(sc["tracks"], prec, device=dev, t_ref=sc["t_ref"])
-            out = ctx.alloc_hits(cap, prec, device=dev)
-        pkw = {} if prof is None else dict(profile=prof[0], bin_gcm2=prof[1], axis_cos=prof[2])
-        if autotune and args.launch is None:
-            ctx.autotune(dtr, 11, prec, out)
-        elif args.launch is not None:
-            ctx.set_launch(*(int(v) for v in args.launch.split(",")))
-        for _ in range(warmup):
-            ctx.generate_propagate(dtr, 11, prec, out, track_base=track_base, **pkw)
-        code, stats = ctx.sync_status(out)
-        if code not in (0, 6):                      # 6: a buffer overflowed (counted)
-            raise RuntimeError(f"status {code} in warm-up")
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)]
-        barrier()
-        w0 = time.perf_counter()
-        for k in range(steps):
-            flush.fill_(k & 0xff)                   # evict L2 between timed steps
-            ev[k][0].record(stream)
-            ctx.generate_propagate(dtr, 11, prec, out, track_base=track_base, **pkw)
-            ev[k][1].record(stream)
-        barrier()
-        wall = time.perf_counter() - w0
-        ms = [a.elapsed_time(b) for a, b in ev]
-        code, stats = ctx.sync_status(out)
-        return dict(ms=ms, wall=wall, stats=stats, dtr=dtr, out=out, code=code)
-
+    sc, track_base = _make_workload(wl, args.scale, rank)
+    cap = _cap(wl, args.scale, args.cap)
+    B = Bench(P, dev, sc, wl, args.scale, cap, track_base, barrier)
+    ctx, n = B.ctx, B.n
     steps, warmup = args.steps, args.warmup
-    with ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
-                      if os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0].isdigit()
-                      else 0) as clk:
-        r32 = measure(P.CHER_FP32_BULK, steps, warmup, autotune=True)
-    clocks = clk.summary()
+    FP32, FP64 = P.CHER_FP32_BULK, P.CHER_FP64
+
+    # autotuned launch shape (or the one given), then the headline: the
+    # persistent launch replayed from its captured graph
+    qprec = FP64 if (args.quick and args.prec == "fp64") else FP32
+    dtr_q, out_q = B.buffers(qprec)
+    if args.launch is not None:
+        ctx.set_launch(*(int(v) for v in args.launch.split(",")))
+    else:
+        ctx.autotune(dtr_q, 11, qprec, out_q)
     launch = ctx.get_launch()
+    table_s = B.table_s
+    gpu = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+    with ClockSampler(int(gpu) if gpu.isdigit() else 0) as clk:
+        rg = B.measure(qprec, steps, warmup, graph=not args.quick)
+    clocks = clk.summary()
     if args.sweep and rank == 0:
-        for shape in [(128, 1), (128, 2), (128, 4), (128, 6), (256, 1), (256, 2), (256, 3),
-                      (256, 4), (512, 1), (512, 2), (128, 0), (256, 0)]:
-            args.launch = f"{shape[0]},{shape[1]}"
-            r = measure(P.CHER_FP32_BULK, 5, 2, autotune=False)
+        for shape in [(128, 1), (128, 2), (128, 4), (128, 6), (128, 8), (256, 1), (256, 2),
+                      (256, 3), (256, 4), (512, 1), (512, 2), (128, 0), (256, 0)]:
+            r = B.measure(FP32, 5, 2, launch=shape)
             t = statistics.median(r["ms"])
             print(json.dumps({"sweep": shape, "ms": t,
                               "bunches_per_s": float(r["stats"][3]) / (t / 1e3)}), flush=True)
-        args.launch = f"{launch[0]},{launch[1]}"
         ctx.set_launch(*launch)
     if args.quick:
-        t = sum(r32["ms"]) / 1e3
+        t = sum(rg["ms"]) / 1e3
         if rank == 0:
-            print(json.dumps({"quick": True, "value": float(r32["stats"][3]) * len(r32["ms"]) / t,
-                              "unit": UNIT, "ms_per_step": 1e3 * t / len(r32["ms"]),
+            print(json.dumps({"quick": True, "workload": wl,
+                              "value": float(rg["stats"][3]) * len(rg["ms"]) / t,
+                              "unit": UNIT, "ms_per_step": 1e3 * t / len(rg["ms"]),
                               "launch": launch, "clocks": clocks}), flush=True)
         if world > 1:
             torch.distributed.destroy_process_group()
         return
-    r64 = measure(P.CHER_FP64, max(3, steps // 4), max(3, min(warmup, 3)), autotune=False)
+    # the same launch without the graph (one C-ABI call per launch)
+    r32 = B.measure(FP32, steps, 3, launch=launch)
     # the longitudinal production profile (CERLDE) in the same launch:
     # 10 g/cm^2 bins to 2000 g/cm^2 of slant depth, one row per shower
+    legs_steps = max(3, steps // 4)
     n_rows = max(len(sc["t_ref"]), 1)
     prof_t = torch.zeros((n_rows, 200), dtype=torch.float64, device=dev)
     axis_cos = np.cos(np.asarray(sc.get("axis_zenith_rad", np.zeros(n_rows)), float))
-    r32p = measure(P.CHER_FP32_BULK, steps, max(3, min(warmup, 3)), autotune=False,
-                   prof=(prof_t, 10.0, axis_cos), reuse=r32)
+    r32p = B.measure(FP32, legs_steps, 3, prof=(prof_t, 10.0, axis_cos))
     # the atmospheric transmission draw (synthetic Rayleigh + aerosol table)
     ctx.set_transmission(workloads.synthetic_transmission(h_obs=sc["h_obs"], h_max=sc["h_max"]))
-    r32t = measure(P.CHER_FP32_BULK, steps, max(3, min(warmup, 3)), autotune=False, reuse=r32)
+    r32t = B.measure(FP32, legs_steps, 3)
     ctx.set_transmission(None)
     # the wavelength-dependent index (Edlen's dispersion of standard air, 9 nodes)
     ctx.set_dispersion(workloads.synthetic_dispersion(lambda1_nm=sc["lambda1_nm"],
                                                       lambda2_nm=sc["lambda2_nm"]))
-    r32d = measure(P.CHER_FP32_BULK, steps, max(3, min(warmup, 3)), autotune=False, reuse=r32)
+    r32d = B.measure(FP32, legs_steps, 3)
     ctx.set_dispersion(None)
+    ctx.set_launch(*launch)
+    # the FP64 path (its own buffers; the batch's FP64 records take 96 GB)
+    r64 = B.measure(FP64, legs_steps, 3)
+    B.release(FP64)
 
     def total(r):
         return reduce_over_ranks(sum(r["ms"]) / 1e3, float(r["stats"][3]) * len(r["ms"]),
                                  world, dev)
 
+    tg, bg = total(rg)
     t32, b32 = total(r32)
     t64, b64 = total(r64)
-    v32, v64 = b32 / t32, b64 / t64
-    # the FP64 leg's device buffers are done with (the batched workload's
-    # FP64 records alone take 86 GB)
-    r64["out"] = r64["dtr"] = None
-    torch.cuda.empty_cache()
+    vg, v32, v64 = bg / tg, b32 / t32, b64 / t64
 
     # ---- end to end: host buffers through the C ABI ---------------------
-    e2e = None
-    e2e_gen = None
-    gen_leg = None
-    if not args.no_e2e:
-        prec = P.CHER_FP32_BULK
-        host = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory()
-                for k, v in sc["tracks"].items() if k != "shower"}
-        host["ux"], host["uy"], host["uz"] = (host[k].to(torch.float32).pin_memory()
-                                              for k in ("ux", "uy", "uz"))
-        host["shower"] = torch.as_tensor(
-            np.ascontiguousarray(sc["tracks"]["shower"]).view(np.int32)).pin_memory()
-        dtr = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
-        dtr["t_ref"] = torch.as_tensor(sc["t_ref"], dtype=torch.float64, device=dev)
-        out = r32["out"]
-        n_tel = ctx.n_tel
-        h_cnt = torch.empty(n_tel, dtype=torch.int64).pin_memory()
-        h_st = torch.empty(P.NSTATS, dtype=torch.int64).pin_memory()
-        # host records packed telescope after telescope: room for the FP32
-        # leg's crossings (the same seed gives the same records every step;
-        # the copies below refuse to truncate)
-        n_rec = int(int(r32["stats"][9]) * 1.1) + 4096
-        h_pos = torch.empty((n_rec, 4), dtype=torch.float32).pin_memory()
-        h_tim = torch.empty((n_rec, 4), dtype=torch.float32).pin_memory()
-        h_key = torch.empty(n_rec, dtype=torch.int64).pin_memory()
-        h2d = sum(v.numel() * v.element_size() for v in host.values())
+    e2e = None if args.no_e2e else e2e_leg(P, B, r32, steps, warmup, world, dev)
+    B.release(FP32)
 
-        # A three-stage pipeline over steps, every step still copying its whole
-        # input up and its records back inside the timed region: step k+1's
-        # inputs go up (copy stream) and step k-1's records come down (second
-        # copy stream) while step k's kernel runs; two input sets, two output
-        # buffers and two host record buffers.  Step k-1's download waits
-        # until step k's kernel has started: a download already in flight when
-        # the kernel's inputs landed held the kernel back until it ended
-        # (seen on GB300 as kernel starts lined up with download ends).
-        sets = [dtr, {k: torch.empty_like(v) for k, v in dtr.items()}]
-        sets[1]["t_ref"].copy_(dtr["t_ref"])
-        outs = [out, ctx.alloc_hits(cap, prec, device=dev)]
-        hrec = [(h_pos, h_tim, h_key),
-                (torch.empty_like(h_pos).pin_memory(), torch.empty_like(h_tim).pin_memory(),
-                 torch.empty_like(h_key).pin_memory())]
-        h_cnts = [h_cnt, torch.empty_like(h_cnt).pin_memory()]
-        h_sts = [h_st, torch.empty_like(h_st).pin_memory()]
-        # the records of a step are packed on the device (cher_pack_records)
-        # and come down in one copy per array
-        pk = [dict(pos=torch.empty((n_rec, 4), dtype=torch.float32, device=dev),
-                   tim=torch.empty((n_rec, 4), dtype=torch.float32, device=dev),
-                   key=torch.empty(n_rec, dtype=torch.int64, device=dev),
-                   offset=torch.empty(n_tel + 1, dtype=torch.int64, device=dev))
-              for _ in range(2)]
-        h_offs = [torch.empty(n_tel + 1, dtype=torch.int64).pin_memory() for _ in range(2)]
-        up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-        comp = torch.cuda.current_stream()
-        ev = {k: [torch.cuda.Event(), torch.cuda.Event()]
-              for k in ("up", "kern", "cnt", "down", "start")}
-
-        def upload(b):
-            with torch.cuda.stream(up):
-                up.wait_event(ev["kern"][b])            # the last kernel on set b is done
-                for k, v in host.items():
-                    sets[b][k].copy_(v, non_blocking=True)
-                ev["up"][b].record(up)
-
-        def launch_step(b):
-            comp.wait_event(ev["up"][b])
-            comp.wait_event(ev["down"][b])             # out b's records are down
-            ev["start"][b].record(comp)
-            ctx.generate_propagate(sets[b], 11, prec, outs[b], track_base=track_base)
-            ev["kern"][b].record(comp)
-            ctx.pack_records(outs[b], pk[b], stream=comp)
-            h_cnts[b].copy_(outs[b].count, non_blocking=True)
-            h_sts[b].copy_(outs[b].stats, non_blocking=True)
-            h_offs[b].copy_(pk[b]["offset"], non_blocking=True)
-            ev["cnt"][b].record(comp)
-
-        def download(b):
-            ev["cnt"][b].synchronize()                  # this step's counts on the host
-            nbytes = (h_cnts[b].numel() + h_sts[b].numel() + h_offs[b].numel()) * 8
-            total = int(h_offs[b][-1])
-            if total > n_rec:
-                raise RuntimeError("host record buffer too small")
-            with torch.cuda.stream(down):
-                down.wait_event(ev["cnt"][b])           # the packed records are written
-                down.wait_event(ev["start"][1 - b])     # the next step's kernel has started
-                hp, ht, hk = hrec[b]
-                if total > 0:
-                    hp[:total].copy_(pk[b]["pos"][:total], non_blocking=True)
-                    ht[:total].copy_(pk[b]["tim"][:total], non_blocking=True)
-                    hk[:total].copy_(pk[b]["key"][:total], non_blocking=True)
-                nbytes += total * 40
-                ev["down"][b].record(down)
-            return nbytes
-
-        def run(n_steps):
-            nbytes = 0
-            upload(0)
-            for k in range(n_steps):
-                b = k % 2
-                if k + 1 < n_steps:
-                    upload(1 - b)
-                launch_step(b)
-                if k >= 1:
-                    nbytes = download(1 - b)
-            nbytes = download((n_steps - 1) % 2)
-            down.synchronize()
-            comp.synchronize()
-            return nbytes
-
-        run(max(2, warmup // 2))
-        barrier()
-        e0 = time.perf_counter()
-        d2h = run(steps)
-        barrier()
-        te = time.perf_counter() - e0
-        te, _ = reduce_over_ranks(te, 0.0, world, dev)
-        e2e = {"value": b32 / len(r32["ms"]) * steps / te, "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "pipelined": "step k+1 up and step k-1 down during step k's kernel "
-                            "(each download starts once the next kernel has)"}
-
-        # end to end from shower parameters: the steps come from the device
-        # generator (same shower, same step count), only the parameters and
-        # its depth table go to the device
-        if args.workload == "vertical_1tev" and world == 1:
-            showers = [dict(e0_mev=1.0e6, zenith=0.0, azimuth=0.0, core_x=0.0, core_y=0.0,
-                            n=int(len(sc["tracks"]["x0"])))]
-
-            gen_buf = ctx.generate_steps(showers, 11, prec)
-
-            def gen_step():
-                dg = ctx.generate_steps(showers, 11, prec, out=gen_buf)
-                ctx.generate_propagate(dg, 11, prec, out)
-                ctx.pack_records(out, pk[0])
-                h_cnt.copy_(out.count, non_blocking=True)
-                h_st.copy_(out.stats, non_blocking=True)
-                h_offs[0].copy_(pk[0]["offset"], non_blocking=True)
-                torch.cuda.current_stream().synchronize()
-                nbytes = (h_cnt.numel() + h_st.numel() + h_offs[0].numel()) * 8
-                total = int(h_offs[0][-1])
-                if total > n_rec:
-                    raise RuntimeError("host record buffer too small")
-                if total > 0:
-                    h_pos[:total].copy_(pk[0]["pos"][:total], non_blocking=True)
-                    h_tim[:total].copy_(pk[0]["tim"][:total], non_blocking=True)
-                    h_key[:total].copy_(pk[0]["key"][:total], non_blocking=True)
-                nbytes += total * 40
-                torch.cuda.current_stream().synchronize()
-                return nbytes, int(h_st[3])
-
-            for _ in range(max(1, warmup // 2)):
-                gen_step()
-            g0 = time.perf_counter()
-            gb = 0
-            for _ in range(steps):
-                gd2h, gbunch = gen_step()
-                gb += gbunch
-            tg = time.perf_counter() - g0
-            # the generator alone (CUDA events around the whole call, whose
-            # table upload blocks): 64 B of steps written per step
-            gms = []
-            for _ in range(steps):
-                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a_.record()
-                ctx.generate_steps(showers, 11, prec, out=gen_buf)
-                b_.record()
-                torch.cuda.synchronize()
-                gms.append(a_.elapsed_time(b_))
-            g_ms = statistics.median(gms)
-            peaks_, _src = _peaks()
-            g_gbs = showers[0]["n"] * 64 / (g_ms / 1e3) / 1e9
-            gen_leg = {"ms_per_call": g_ms, "steps_per_s": showers[0]["n"] / (g_ms / 1e3),
-                       "roofline": {"bound": "hbm", "achieved": g_gbs,
-                                    "peak": float(peaks_.get("hbm_gbs", 6800.0)), "unit": "GB/s",
-                                    "frac": g_gbs / float(peaks_.get("hbm_gbs", 6800.0)),
-                                    "bytes_per_step": 64}}
-            e2e_gen = {"value": gb / tg, "unit": UNIT,
-                       "h2d_bytes_per_step": 64 + 16 + 4 * 1024 + 8,
-                       "d2h_bytes_per_step": int(gd2h), "steps_generated": showers[0]["n"],
-                       "bunches_per_step": gb // steps,
-                       "note": "steps from cher_generate_steps (Philox draws, not the "
-                               "host workload's)"}
-
+    peaks, src = _peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    legs = {}
+    if world == 1 and not args.no_legs and wl == "batched_256" and args.scale == 1.0:
+        ctx.close()
+        del B, ctx
+        torch.cuda.empty_cache()
+        for other in ("inclined_20tev", "vertical_1tev"):
+            legs[other] = workload_leg(P, dev, other, 1.0, None, steps, warmup, launch,
+                                       sm_count, mhz, barrier)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
 
     # ---- roofline of the dominant kernel (ALU bound) ----------------------
-    peaks, src = _peaks()
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = sm_count * FP32_LANES_PER_SM * mhz * 1e6          # lane ops/s
-    fp64_peak = sm_count * FP64_FMA_PER_SM_CLK * mhz * 1e6
-    st = r32["stats"]
-    bunches = float(st[3])
-    emitting = float(st[1])
-    per_launch_s = statistics.mean(r32["ms"]) / 1e3
-    ops = bunches * OPS_PER_BUNCH
-    achieved = ops / per_launch_s
-    t_alu = ops / alu_peak
-    t_fp64 = emitting * FP64_OPS_PER_STEP / fp64_peak
-    cpu = cpu_baseline(args.workload) if world == 1 else None
+    st = rg["stats"]
+    bunches, steps_n = float(st[3]), float(st[0])
+    ms_g = statistics.mean(rg["ms"])
+    rl = alu_roofline(bunches, steps_n, ms_g, sm_count, mhz)
+    rl["traffic"] = _traffic(wl, n) if args.scale == 1.0 else None
+    ms64 = statistics.mean(r64["ms"])
+    rl64 = fp64_roofline(float(r64["stats"][3]), steps_n, ms64, sm_count, mhz)
+    # the FP64 path beside the FP32 one inside the roofline object as well
+    rl["fp64_path"] = {"value": v64, "frac": rl64["frac"], "fp32_over_fp64": vg / v64}
+    cpu = cpu_baseline(wl) if world == 1 else None
     line = {
-        "metric": METRIC, "value": v32, "unit": UNIT, "n_gpus": world, "steps": steps,
-        "warmup": warmup, "ms_per_step": 1e3 * t32 / len(r32["ms"]),
+        "metric": METRIC, "value": vg, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": 1e3 * tg / len(rg["ms"]),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT.get(args.workload, args.workload) +
+        "fp64": {"value": v64, "unit": UNIT, "ms_per_step": 1e3 * t64 / len(r64["ms"]),
+                 "steps": len(r64["ms"]), "roofline": rl64},
+        "fp32_over_fp64": vg / v64,
+        "gpu_launches": len(rg["ms"]),
+        "config": {"workload": WORKLOAD_TEXT.get(wl, wl) +
                                (f" (scale {args.scale})" if args.scale != 1.0 else ""),
                    "steps_per_gpu": n, "n_showers": int(len(sc["t_ref"])),
                    "precision": "fp32_bulk (FP64 yield)", "bunches_per_step": int(bunches),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "launch": {"block": launch[0], "ctas_per_sm": launch[1],
-                              "persistent": launch[1] > 0},
+                              "persistent": launch[1] > 0, "graph": True},
                    "table_build_s": table_s},
-        "fp64": {"value": v64, "unit": UNIT, "ms_per_step": 1e3 * t64 / len(r64["ms"]),
-                 "steps": len(r64["ms"]),
-                 "roofline": {"bound": "fp64", "unit": "Tops/s",
-                              "achieved": float(r64["stats"][3]) * FP64_OPS_PER_BUNCH /
-                              (statistics.mean(r64["ms"]) / 1e3) / 1e12,
-                              "peak": fp64_peak / 1e12,
-                              "frac": float(r64["stats"][3]) * FP64_OPS_PER_BUNCH /
-                              (statistics.mean(r64["ms"]) / 1e3) / fp64_peak,
-                              "ops_per_bunch": FP64_OPS_PER_BUNCH,
-                              "peak_source": f"{sm_count} SMs x {FP64_FMA_PER_SM_CLK} FP64 "
-                                             f"lanes x {mhz:.0f} MHz"}},
-        "fp32_over_fp64": v32 / v64,
-        "transmission": {"ms_per_step": statistics.mean(r32t["ms"]),
-                         "overhead": statistics.mean(r32t["ms"]) / statistics.mean(r32["ms"]) - 1,
-                         "absorbed_frac": float(r32t["stats"][11]) / float(r32t["stats"][3]),
-                         "table": "synthetic Rayleigh + aerosol, 16 x 121"},
-        "dispersion": {"ms_per_step": statistics.mean(r32d["ms"]),
-                       "overhead": statistics.mean(r32d["ms"]) / statistics.mean(r32["ms"]) - 1,
-                       "value": float(r32d["stats"][3]) / (statistics.mean(r32d["ms"]) / 1e3),
-                       "unit": UNIT, "bunches_per_step": int(r32d["stats"][3]),
-                       "curve": "Edlen 1966 standard air, kappa = 1 at 400 nm, 9 nodes in "
-                                "1/lambda"},
-        "profile": {"ms_per_step": statistics.mean(r32p["ms"]),
-                    "overhead": statistics.mean(r32p["ms"]) / statistics.mean(r32["ms"]) - 1.0,
-                    "bins": int(prof_t.shape[1]), "bin_gcm2": 10.0, "rows": n_rows,
-                    "depth": "slant" if np.any(axis_cos < 1.0) else "vertical"},
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
-                     "unit": "Tops/s", "frac": achieved / alu_peak,
-                     "traffic": _traffic(args.workload, args.scale),
-                     "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32/INT32 lanes x "
-                                    f"{mhz:.0f} MHz ({src} max clock)",
-                     "ops_per_bunch": OPS_PER_BUNCH,
-                     "ops_by_stage": dict(OPS_PER_BUNCH_FP32),
-                     "ncu_pct_of_peak": _ncu_pipes(args.workload, args.scale),
-                     "roofline_ms": 1e3 * max(t_alu, t_fp64),
-                     "fp64_yield_ms_at_peak": 1e3 * t_fp64,
-                     "launch_ms": 1e3 * per_launch_s},
-        "overflowed_records": int(r32["stats"][10]),
-        "gpu_launches": len(r32["ms"]),
+        "roofline": rl,
         "clocks": clocks,
         "e2e": e2e,
+        "regular_launch": {"value": v32, "ms_per_step": 1e3 * t32 / len(r32["ms"]),
+                           "note": "one cher_generate_propagate call per launch, no graph"},
+        "overflowed_records": int(rg["stats"][10]),
     }
-    if e2e_gen is not None:
-        line["e2e_generated"] = e2e_gen
-        line["generator"] = gen_leg
     if cpu is not None:
         line["cpu_baseline"] = cpu
-    if args.workload == "vertical_1tev" and args.scale == 1.0 and world == 1:
-        line["graph"] = graph_leg(ctx, r32, steps, flush, stream)
+    ms32 = statistics.mean(r32["ms"])
+    line["features"] = {
+        "profile": {"overhead": statistics.mean(r32p["ms"]) / ms32 - 1.0,
+                    "bins": int(prof_t.shape[1]), "bin_gcm2": 10.0, "rows": n_rows},
+        "transmission": {"overhead": statistics.mean(r32t["ms"]) / ms32 - 1,
+                         "absorbed_frac": float(r32t["stats"][11]) / float(r32t["stats"][3])},
+        "dispersion": {"overhead": statistics.mean(r32d["ms"]) / ms32 - 1,
+                       "value": float(r32d["stats"][3]) / (statistics.mean(r32d["ms"]) / 1e3)}}
+    for k, v in legs.items():
+        line[k] = v
+    if world == 1 and not args.no_legs and wl == "batched_256" and args.scale == 1.0:
         line["adjoint"] = adjoint_leg(dev, steps)
         line["adjoint"]["cpu_baseline"] = cpu_baseline_readout()
+        line["e2e_generated"] = generated_leg(P, dev, steps, warmup)
+    # the headline figures once more at the end of the line
+    line["summary"] = {"fp32": vg, "fp32_frac": rl["frac"], "fp64": v64,
+                       "fp64_frac": rl64["frac"], "fp32_over_fp64": vg / v64,
+                       **{f"{k}_fp32_frac": v["roofline"]["frac"] for k, v in legs.items()},
+                       **{f"{k}_fp64_frac": v["fp64"]["roofline"]["frac"] for k, v in legs.items()}}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -713,27 +651,196 @@ def fallback_leg(dev, args):
     return res
 
 
-def graph_leg(ctx, r32, steps, flush, stream):
-    """The same FP32 launch replayed from a captured CUDA graph (counter
-    clears and the persistent kernel in one graph launch)."""
+def e2e_leg(P, B, r32, steps, warmup, world, dev):
+    """The same metric end to end through the C ABI: every step copies its
+    whole input up from pinned host memory and its records, counts and
+    statistics back, inside the timed region.  A three-stage pipeline over
+    steps: step k+1's inputs go up (copy stream) and step k-1's records come
+    down (second copy stream) while step k's kernel runs; two input sets, two
+    output buffers and two host record buffers.  Step k-1's download waits
+    until step k's kernel has started (a download already in flight when the
+    kernel's inputs landed held the kernel back until it ended)."""
+    import torch
+    sc, ctx, cap, track_base = B.sc, B.ctx, B.cap, B.track_base
+    prec = P.CHER_FP32_BULK
+    dtr, out = B.buffers(prec)
+    host = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory()
+            for k, v in sc["tracks"].items() if k != "shower"}
+    host["ux"], host["uy"], host["uz"] = (host[k].to(torch.float32).pin_memory()
+                                          for k in ("ux", "uy", "uz"))
+    host["shower"] = torch.as_tensor(
+        np.ascontiguousarray(sc["tracks"]["shower"]).view(np.int32)).pin_memory()
+    dtr = {k: v for k, v in dtr.items()}
+    n_tel = ctx.n_tel
+    # host records packed telescope after telescope: room for the crossings
+    # of the timed launches (the same seed gives the same records every step;
+    # the copies below refuse to truncate)
+    n_rec = int(int(r32["stats"][9]) * 1.1) + 4096
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    sets = [dtr, {k: torch.empty_like(v) for k, v in dtr.items()}]
+    sets[1]["t_ref"].copy_(dtr["t_ref"])
+    outs = [out, ctx.alloc_hits(cap, prec, device=dev)]
+    hrec = [tuple(torch.empty(shape, dtype=dt).pin_memory()
+                  for shape, dt in (((n_rec, 4), torch.float32), ((n_rec, 4), torch.float32),
+                                    (n_rec, torch.int64)))
+            for _ in range(2)]
+    h_cnts = [torch.empty(n_tel, dtype=torch.int64).pin_memory() for _ in range(2)]
+    h_sts = [torch.empty(P.NSTATS, dtype=torch.int64).pin_memory() for _ in range(2)]
+    # the records of a step are packed on the device (cher_pack_records)
+    # and come down in one copy per array
+    pk = [dict(pos=torch.empty((n_rec, 4), dtype=torch.float32, device=dev),
+               tim=torch.empty((n_rec, 4), dtype=torch.float32, device=dev),
+               key=torch.empty(n_rec, dtype=torch.int64, device=dev),
+               offset=torch.empty(n_tel + 1, dtype=torch.int64, device=dev))
+          for _ in range(2)]
+    h_offs = [torch.empty(n_tel + 1, dtype=torch.int64).pin_memory() for _ in range(2)]
+    up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    comp = torch.cuda.current_stream()
+    ev = {k: [torch.cuda.Event(), torch.cuda.Event()]
+          for k in ("up", "kern", "cnt", "down", "start")}
+
+    def upload(b):
+        with torch.cuda.stream(up):
+            up.wait_event(ev["kern"][b])            # the last kernel on set b is done
+            for k, v in host.items():
+                sets[b][k].copy_(v, non_blocking=True)
+            ev["up"][b].record(up)
+
+    def launch_step(b):
+        comp.wait_event(ev["up"][b])
+        comp.wait_event(ev["down"][b])             # out b's records are down
+        ev["start"][b].record(comp)
+        ctx.generate_propagate(sets[b], 11, prec, outs[b], track_base=track_base)
+        ev["kern"][b].record(comp)
+        ctx.pack_records(outs[b], pk[b], stream=comp)
+        h_cnts[b].copy_(outs[b].count, non_blocking=True)
+        h_sts[b].copy_(outs[b].stats, non_blocking=True)
+        h_offs[b].copy_(pk[b]["offset"], non_blocking=True)
+        ev["cnt"][b].record(comp)
+
+    def download(b):
+        ev["cnt"][b].synchronize()                  # this step's counts on the host
+        nbytes = (h_cnts[b].numel() + h_sts[b].numel() + h_offs[b].numel()) * 8
+        total = int(h_offs[b][-1])
+        if total > n_rec:
+            raise RuntimeError("host record buffer too small")
+        with torch.cuda.stream(down):
+            down.wait_event(ev["cnt"][b])           # the packed records are written
+            down.wait_event(ev["start"][1 - b])     # the next step's kernel has started
+            hp, ht, hk = hrec[b]
+            if total > 0:
+                hp[:total].copy_(pk[b]["pos"][:total], non_blocking=True)
+                ht[:total].copy_(pk[b]["tim"][:total], non_blocking=True)
+                hk[:total].copy_(pk[b]["key"][:total], non_blocking=True)
+            nbytes += total * 40
+            ev["down"][b].record(down)
+        return nbytes
+
+    def run(n_steps):
+        nbytes = 0
+        upload(0)
+        for k in range(n_steps):
+            b = k % 2
+            if k + 1 < n_steps:
+                upload(1 - b)
+            launch_step(b)
+            if k >= 1:
+                nbytes = download(1 - b)
+        nbytes = download((n_steps - 1) % 2)
+        down.synchronize()
+        comp.synchronize()
+        return nbytes
+
+    run(max(2, warmup // 2))
+    B.barrier()
+    e0 = time.perf_counter()
+    d2h = run(steps)
+    B.barrier()
+    te = time.perf_counter() - e0
+    te, _ = reduce_over_ranks(te, 0.0, world, dev)
+    bunches = float(r32["stats"][3])
+    del outs, sets, pk
+    return {"value": bunches * steps / te, "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "pipelined": "step k+1 up and step k-1 down during step k's kernel "
+                         "(each download starts once the next kernel has)"}
+
+
+def generated_leg(P, dev, steps, warmup):
+    """End to end from shower parameters: the 1 TeV vertical shower's 2e6
+    steps come from the device generator (cher_generate_steps), only the
+    shower parameters and its depth table go up, the packed records come
+    down; and the generator alone (64 B of steps written per step)."""
     import torch
 
-    import paper_2006_14927_gb300 as P
-    g = ctx.graph(r32["dtr"], 11, P.CHER_FP32_BULK, r32["out"])
-    for _ in range(3):
-        g.launch()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(steps)]
-    for k in range(steps):
-        flush.fill_(k & 0xff)
-        ev[k][0].record(stream)
-        g.launch()
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    g.close()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    return {"ms_per_step": statistics.mean(ms),
-            "value": float(r32["stats"][3]) / (statistics.mean(ms) / 1e3), "unit": UNIT}
+    import workloads
+    sc = workloads.vertical_1tev(n=10)
+    ctx = P.Context(sc["atm"], sc["h_obs"], sc["telescopes"])
+    ctx.build_refraction_tables(sc["H"], sc["Z"], sc["theta_max_deg"], sc["h_max"])
+    prec = P.CHER_FP32_BULK
+    n = 2_000_000
+    showers = [dict(e0_mev=1.0e6, zenith=0.0, azimuth=0.0, core_x=0.0, core_y=0.0, n=n)]
+    out = ctx.alloc_hits(600_000, prec, device=dev)
+    gen_buf = ctx.generate_steps(showers, 11, prec)
+    n_rec = 19 * 600_000
+    pk = dict(pos=torch.empty((n_rec, 4), dtype=torch.float32, device=dev),
+              tim=torch.empty((n_rec, 4), dtype=torch.float32, device=dev),
+              key=torch.empty(n_rec, dtype=torch.int64, device=dev),
+              offset=torch.empty(20, dtype=torch.int64, device=dev))
+    h_pos = torch.empty((n_rec, 4), dtype=torch.float32).pin_memory()
+    h_tim = torch.empty((n_rec, 4), dtype=torch.float32).pin_memory()
+    h_key = torch.empty(n_rec, dtype=torch.int64).pin_memory()
+    h_cnt = torch.empty(19, dtype=torch.int64).pin_memory()
+    h_st = torch.empty(P.NSTATS, dtype=torch.int64).pin_memory()
+    h_off = torch.empty(20, dtype=torch.int64).pin_memory()
+
+    def gen_step():
+        dg = ctx.generate_steps(showers, 11, prec, out=gen_buf)
+        ctx.generate_propagate(dg, 11, prec, out)
+        ctx.pack_records(out, pk)
+        h_cnt.copy_(out.count, non_blocking=True)
+        h_st.copy_(out.stats, non_blocking=True)
+        h_off.copy_(pk["offset"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        nbytes = (h_cnt.numel() + h_st.numel() + h_off.numel()) * 8
+        total = min(int(h_off[-1]), n_rec)
+        if total > 0:
+            h_pos[:total].copy_(pk["pos"][:total], non_blocking=True)
+            h_tim[:total].copy_(pk["tim"][:total], non_blocking=True)
+            h_key[:total].copy_(pk["key"][:total], non_blocking=True)
+        nbytes += total * 40
+        torch.cuda.current_stream().synchronize()
+        return nbytes, int(h_st[3])
+
+    for _ in range(max(1, warmup // 2)):
+        gen_step()
+    g0 = time.perf_counter()
+    gb = 0
+    for _ in range(steps):
+        gd2h, gbunch = gen_step()
+        gb += gbunch
+    tg = time.perf_counter() - g0
+    gms = []
+    for _ in range(steps):
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record()
+        ctx.generate_steps(showers, 11, prec, out=gen_buf)
+        b_.record()
+        torch.cuda.synchronize()
+        gms.append(a_.elapsed_time(b_))
+    g_ms = statistics.median(gms)
+    peaks_, _src = _peaks()
+    g_gbs = n * 64 / (g_ms / 1e3) / 1e9
+    ctx.close()
+    return {"value": gb / tg, "unit": UNIT, "h2d_bytes_per_step": 64 + 16 + 4 * 1024 + 8,
+            "d2h_bytes_per_step": int(gd2h), "steps_generated": n,
+            "bunches_per_step": gb // steps,
+            "generator": {"ms_per_call": g_ms, "steps_per_s": n / (g_ms / 1e3),
+                          "roofline": {"bound": "hbm", "achieved": g_gbs,
+                                       "peak": float(peaks_.get("hbm_gbs", 6800.0)),
+                                       "unit": "GB/s",
+                                       "frac": g_gbs / float(peaks_.get("hbm_gbs", 6800.0)),
+                                       "bytes_per_step": 64}}}
 
 
 def adjoint_leg(dev, steps):
@@ -796,19 +903,12 @@ def cpu_baseline_readout(n: int = 20000):
 
 
 def cpu_baseline(workload: str = WORKLOAD):
-    """The oracle as it stands on this host's cores, bounded sample: the
-    workload's generator with its first 20 000 steps."""
+    """The oracle as it stands on this host's cores, on a bounded sample of
+    the workload (its generator at 20 000 steps), repeated for about 10 s;
+    and single-threaded on a fifth of the sample for about 3 s."""
     import oracle
-    import workloads
     oracle.build()
-    n = 20_000
-    if workload == "batched_256":
-        sc = workloads.batched_256(total=n)
-    elif workload in ("plain_fp64", "adjoint_300gev"):
-        sc = workloads.WORKLOADS[workload]()
-        n = len(sc["tracks"]["x0"])
-    else:
-        sc = workloads.WORKLOADS[workload](n=n)
+    sc, what = _sample_workload(workload)
     M = oracle.Model(sc["atm"], sc["h_obs"], sc["telescopes"], h_max=sc["h_max"], H=sc["H"],
                      Z=sc["Z"], theta_max_deg=sc["theta_max_deg"], t_ref=sc["t_ref"])
     M.bunches(sc["tracks"], 7)
@@ -821,9 +921,9 @@ def cpu_baseline(workload: str = WORKLOAD):
     dt = time.perf_counter() - t0
     cores = oracle.num_threads()
     res = {"value": nb / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"{workload}: {n} steps ({nb // reps} bunches), repeated {reps} times, "
+           "sample": f"{what} ({nb // reps} bunches), repeated {reps} times, "
                      f"FP64 table variant, OpenMP over steps"}
-    # the same single-threaded, on a fifth of the sample for about 3 s
+    n = len(sc["tracks"]["x0"])
     sub = {k: v[: n // 5] for k, v in sc["tracks"].items()}
     oracle.set_num_threads(1)
     t0 = time.perf_counter()
@@ -834,8 +934,8 @@ def cpu_baseline(workload: str = WORKLOAD):
     dt1 = time.perf_counter() - t0
     oracle.set_num_threads(cores)
     res["one_core"] = {"value": nb1 / dt1, "unit": UNIT, "cores": 1,
-                       "sample": f"{n // 5} steps ({nb1 // reps1} bunches), repeated {reps1} "
-                                 f"times, single-threaded"}
+                       "sample": f"the first {n // 5} steps of that sample ({nb1 // reps1} "
+                                 f"bunches), repeated {reps1} times, single-threaded"}
     return res
 
 
@@ -846,16 +946,21 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true",
-                    help="FP32 device timing only (no FP64, end-to-end or CPU legs)")
+                    help="device timing of regular launches only (no graph, FP64 leg, "
+                         "end-to-end, other workloads or CPU legs)")
+    ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32",
+                    help="precision of the --quick timing")
     ap.add_argument("--launch", default=None,
                     help="block,ctas_per_sm instead of the autotuner's choice")
     ap.add_argument("--cap", type=int, default=None, help="records per telescope")
     ap.add_argument("--sweep", action="store_true", help="time a set of launch shapes")
-    ap.add_argument("--workload", default="vertical_1tev",
+    ap.add_argument("--workload", default=WORKLOAD,
                     choices=["vertical_1tev", "inclined_20tev", "batched_256", "plain_fp64",
                              "adjoint_300gev"])
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the workload's steps")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the other workloads, the adjoint and the generator legs")
     ap.add_argument("--leg", choices=["all", "generator", "adjoint", "fallback"], default="all",
                     help="run one secondary leg alone (for profiling captures)")
     args = ap.parse_args()

@@ -9,20 +9,33 @@ import bench
 
 
 def test_operation_count_is_the_stage_table():
-    assert bench.OPS_PER_BUNCH == sum(bench.OPS_PER_BUNCH_FP32.values()) == 242
-    assert bench.FP64_OPS_PER_BUNCH == 242 - bench.OPS_PER_BUNCH_FP32["philox4x32_10"]
+    assert bench.OPS_PER_BUNCH == sum(bench.OPS_PER_BUNCH_FP32.values()) == 215
+    assert bench.OPS_PER_STEP == sum(bench.OPS_PER_STEP_FP32.values()) == 113
+    # Philox per bunch: 8 full rounds plus the bunch index's share of the
+    # first two (the key schedule is per launch, the step's share per step)
+    assert bench.OPS_PER_BUNCH_FP32["philox4x32_10"] == 8 * 8 + 3 + 4
+    assert bench.OPS_PER_STEP_FP32["philox_step_share"] == 2 * (2 + 2)
+    assert bench.FP64_OPS_PER_BUNCH == 215 - bench.OPS_PER_BUNCH_FP32["philox4x32_10"]
+
+
+def test_rooflines_from_the_counts():
+    r = bench.alu_roofline(6.4e7, 2e6, 0.8, 152, 2070.0)
+    ops = 215 * 6.4e7 + 113 * 2e6
+    assert abs(r["achieved"] - ops / 0.8e-3 / 1e12) < 1e-9
+    assert abs(r["peak"] - 152 * 128 * 2.07e9 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert r["peak_source"].startswith("derived")
+    f = bench.fp64_roofline(6.4e7, 2e6, 18.0, 152, 2070.0)
+    assert abs(f["frac"] - (144 * 6.4e7 + 64 * 2e6) / 18e-3 / (152 * 2 * 2.07e9)) < 1e-12
 
 
 def test_traffic_only_for_the_profiled_sources(monkeypatch):
-    value, digest = bench.TRAFFIC["vertical_1tev"]
-    monkeypatch.setattr(bench, "_kernel_hash", lambda: digest)
-    assert bench._traffic("vertical_1tev", 1.0) == value
-    assert bench._ncu_pipes("vertical_1tev", 1.0) == bench.NCU_PIPES
-    assert bench._traffic("vertical_1tev", 0.5) is None          # another size
-    assert bench._traffic("inclined_20tev", 1.0) is None         # not profiled
-    monkeypatch.setattr(bench, "_kernel_hash", lambda: "0" * 16)  # sources changed
-    assert bench._traffic("vertical_1tev", 1.0) is None
-    assert bench._ncu_pipes("vertical_1tev", 1.0) is None
+    monkeypatch.setattr(bench, "TRAFFIC_PER_STEP", {"vertical_1tev": (76.5, "ab" * 8)})
+    monkeypatch.setattr(bench, "_kernel_hash", lambda: "ab" * 8)
+    assert bench._traffic("vertical_1tev", 2_000_000) == 153_000_000   # scaled by steps
+    assert bench._traffic("inclined_20tev", 1) is None                 # not profiled
+    monkeypatch.setattr(bench, "_kernel_hash", lambda: "0" * 16)        # sources changed
+    assert bench._traffic("vertical_1tev", 2_000_000) is None
 
 
 def test_kernel_hash_covers_the_kernel_sources():
