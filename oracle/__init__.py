@@ -161,6 +161,9 @@ def lib():
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_density.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Tracks), ctypes.c_uint64,
                                   _i32p, ctypes.c_double, _dp, _dp]
+        L.orc_density_grad.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Tracks),
+                                       ctypes.c_uint64, _i32p, ctypes.c_double, _dp, _dp,
+                                       ctypes.c_double, _dp, _dp, _dp, _dp]
         L.orc_profile.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Tracks), _dp,
                                   ctypes.c_double, ctypes.c_int, _dp]
         L.orc_generate_steps.argtypes = [ctypes.POINTER(_Shower), ctypes.c_int, ctypes.c_double,
@@ -491,6 +494,29 @@ class Model:
             raise ValueError("orc_density failed")
         del keep
         return S, U
+
+    def density_grad(self, tracks: dict, seed: int, nb_frozen, sigma: float, gD, gT,
+                     track_base: int = 0):
+        """The read-out S, U and the gradients of L = sum gD S + gT U / S by
+        forward-mode dual numbers (flat layers, constant index, table
+        variant): grad_atm (15: a, b, c) and grad_steps (6, n: x0, y0, z0,
+        ux, uy, uz)."""
+        T, keep = self._tracks(tracks, track_base)
+        nb = np.ascontiguousarray(nb_frozen, dtype=np.int32)
+        n_tel = self.telescopes.shape[0]
+        S, U = np.zeros(n_tel), np.zeros(n_tel)
+        gD = _f64(np.asarray(gD, float).reshape(n_tel))
+        gT = _f64(np.asarray(gT, float).reshape(n_tel))
+        ga = np.zeros(15)
+        gs = np.zeros((6, len(nb)))
+        C = self._cfg()
+        rc = lib().orc_density_grad(ctypes.byref(C), ctypes.byref(T), ctypes.c_uint64(seed),
+                                    _ptr(nb, ctypes.c_int32), float(sigma), _ptr(gD), _ptr(gT),
+                                    float(self.table_tol), _ptr(S), _ptr(U), _ptr(ga), _ptr(gs))
+        if rc != 0:
+            raise ValueError("orc_density_grad failed")
+        del keep
+        return S, U, ga, gs
 
     # ---- longitudinal production profile (CERLDE) --------------------------
     def profile(self, tracks: dict, bin_gcm2: float, n_bins: int, axis_cos=None):

@@ -1653,3 +1653,496 @@ void orc_set_num_threads(int n)
     (void)n;
 #endif
 }
+
+/* ======================================================================= */
+/* Reference gradient of the read-out by forward-mode dual numbers (no     */
+/* counterpart in the paper: the reference for the library's adjoint).    */
+/* Every quantity carries its value and its derivatives with respect to    */
+/* ORC_NG inputs: the six of the step it belongs to (x0, y0, z0, u_x, u_y, */
+/* u_z) and the ten atmosphere parameters n depends on (b_0..b_4,          */
+/* c_0..c_4; n does not depend on a_i, so dL/da_i = 0).  The arithmetic is */
+/* the table variant's (T), statement by statement and in the same order,  */
+/* so the values are the oracle's own: the derivative of an adaptive       */
+/* integral is that of the quadrature it chose (the same nodes), the       */
+/* derivative of a table lookup that of the interpolation inside the cell  */
+/* it chose; the bunch counts are frozen (w = N / nb).  For                */
+/*   L = sum_k gD_k S_k + gT_k Tbar_k,  Tbar_k = U_k / S_k,               */
+/* dL/dS_k = gD_k - gT_k U_k / S_k^2 and dL/dU_k = gT_k / S_k.             */
+/* Flat layers, constant index.                                             */
+/* ======================================================================= */
+#define ORC_NG 16
+enum { ORC_G_X0 = 0, ORC_G_Y0, ORC_G_Z0, ORC_G_UX, ORC_G_UY, ORC_G_UZ, ORC_G_B0 = 6,
+       ORC_G_C0 = 11 };
+
+typedef struct {
+    double v;
+    double d[ORC_NG];
+} orc_dual;
+
+static orc_dual od_c(double v)
+{
+    orc_dual r;
+    r.v = v;
+    for (int i = 0; i < ORC_NG; ++i) r.d[i] = 0.0;
+    return r;
+}
+
+static orc_dual od_var(double v, int i)
+{
+    orc_dual r = od_c(v);
+    r.d[i] = 1.0;
+    return r;
+}
+
+static orc_dual od_add(orc_dual a, orc_dual b)
+{
+    orc_dual r;
+    r.v = a.v + b.v;
+    for (int i = 0; i < ORC_NG; ++i) r.d[i] = a.d[i] + b.d[i];
+    return r;
+}
+
+static orc_dual od_sub(orc_dual a, orc_dual b)
+{
+    orc_dual r;
+    r.v = a.v - b.v;
+    for (int i = 0; i < ORC_NG; ++i) r.d[i] = a.d[i] - b.d[i];
+    return r;
+}
+
+static orc_dual od_mul(orc_dual a, orc_dual b)
+{
+    orc_dual r;
+    r.v = a.v * b.v;
+    for (int i = 0; i < ORC_NG; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+    return r;
+}
+
+/* a / b: d(a/b) = (da - (a/b) db) / b */
+static orc_dual od_div(orc_dual a, orc_dual b)
+{
+    orc_dual r;
+    r.v = a.v / b.v;
+    for (int i = 0; i < ORC_NG; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
+    return r;
+}
+
+/* constant on the left of a product, a sum, a quotient; quotient by a constant */
+static orc_dual od_cmul(double s, orc_dual a)
+{
+    orc_dual r;
+    r.v = s * a.v;
+    for (int i = 0; i < ORC_NG; ++i) r.d[i] = s * a.d[i];
+    return r;
+}
+
+static orc_dual od_cadd(double s, orc_dual a)
+{
+    orc_dual r = a;
+    r.v = s + a.v;
+    return r;
+}
+
+static orc_dual od_csub(double s, orc_dual a)
+{
+    orc_dual r;
+    r.v = s - a.v;
+    for (int i = 0; i < ORC_NG; ++i) r.d[i] = -a.d[i];
+    return r;
+}
+
+static orc_dual od_subc(orc_dual a, double s)
+{
+    orc_dual r = a;
+    r.v = a.v - s;
+    return r;
+}
+
+static orc_dual od_divc(orc_dual a, double s)
+{
+    orc_dual r;
+    r.v = a.v / s;
+    for (int i = 0; i < ORC_NG; ++i) r.d[i] = a.d[i] / s;
+    return r;
+}
+
+static orc_dual od_cdiv(double s, orc_dual b)
+{
+    orc_dual r;
+    r.v = s / b.v;
+    for (int i = 0; i < ORC_NG; ++i) r.d[i] = -r.v * b.d[i] / b.v;
+    return r;
+}
+
+static orc_dual od_neg(orc_dual a)
+{
+    orc_dual r;
+    r.v = -a.v;
+    for (int i = 0; i < ORC_NG; ++i) r.d[i] = -a.d[i];
+    return r;
+}
+
+static orc_dual od_sqrt(orc_dual a)
+{
+    orc_dual r;
+    r.v = sqrt(a.v);
+    for (int i = 0; i < ORC_NG; ++i) r.d[i] = a.d[i] / (2.0 * r.v);
+    return r;
+}
+
+static orc_dual od_exp(orc_dual a)
+{
+    orc_dual r;
+    r.v = exp(a.v);
+    for (int i = 0; i < ORC_NG; ++i) r.d[i] = r.v * a.d[i];
+    return r;
+}
+
+/* rho(h) = (b_i / c_i) exp(-h / c_i) in layer i, b_i and c_i as variables */
+static orc_dual od_rho(const orc_atm *A, orc_dual h)
+{
+    if (h.v >= A->h_bound[5]) return od_c(0.0);
+    int i = orc_layer(A, h.v);
+    orc_dual b = od_var(A->b[i], ORC_G_B0 + i);
+    orc_dual c = od_var(A->c[i], ORC_G_C0 + i);
+    orc_dual r = od_div(b, c);
+    orc_dual e = od_exp(od_neg(od_div(h, c)));
+    return od_mul(r, e);
+}
+
+/* eta(h) = n0_minus_1 rho(h) / rho(0) */
+static orc_dual od_eta_exact(const orc_atm *A, orc_dual h)
+{
+    orc_dual rho0 = od_rho(A, od_c(0.0));
+    orc_dual rho = od_rho(A, h);
+    orc_dual q = od_div(rho, rho0);
+    return od_cmul(A->n0_minus_1, q);
+}
+
+static orc_dual od_eta_lookup(const orc_dual *tab, int n, double h_max, orc_dual h)
+{
+    double dh = h_max / (double)(n - 1);
+    double inv_dh = 1.0 / dh;
+    orc_dual hc = h;
+    if (hc.v < 0.0) hc = od_c(0.0);
+    if (hc.v > h_max) hc = od_c(h_max);
+    orc_dual x = od_cmul(inv_dh, hc);
+    int k = (int)x.v;
+    if (k > n - 2) k = n - 2;
+    orc_dual f = od_subc(x, (double)k);
+    orc_dual d = od_sub(tab[k + 1], tab[k]);
+    orc_dual fd = od_mul(f, d);
+    return od_add(tab[k], fd);
+}
+
+/* the ray-integral integrands of the tables (orc_integrand) in duals */
+typedef struct {
+    const orc_atm *A;
+    orc_dual np1_obs;
+    double s_obs, c_obs;
+    int which;
+    double floor;
+} orc_dray;
+
+static orc_dual od_integrand(const orc_dray *R, double h)
+{
+    orc_dual eta = od_eta_exact(R->A, od_c(h));
+    orc_dual np1 = od_cadd(1.0, eta);
+    orc_dual s = od_div(od_mul(R->np1_obs, od_c(R->s_obs)), np1);
+    orc_dual c = od_sqrt(od_csub(1.0, od_mul(s, s)));
+    switch (R->which) {
+    case F_TAN_CORR: return od_subc(od_div(s, c), R->s_obs / R->c_obs);
+    case F_OPT_CORR: return od_subc(od_div(np1, c), 1.0 / R->c_obs);
+    case F_RATIO: return od_subc(od_div(R->np1_obs, np1), 1.0);
+    }
+    return od_c(0.0);
+}
+
+/* adaptive Simpson in duals: every decision on the values, as orc_simpson_rec */
+static orc_dual od_simpson_rec(const orc_dray *R, double a, double b, orc_dual fa, orc_dual fm,
+                               orc_dual fb, orc_dual whole, double tol, int depth)
+{
+    double m = 0.5 * (a + b);
+    double lm = 0.5 * (a + m), rm = 0.5 * (m + b);
+    orc_dual flm = od_integrand(R, lm), frm = od_integrand(R, rm);
+    orc_dual left = od_cmul((m - a) / 6.0, od_add(od_add(fa, od_cmul(4.0, flm)), fm));
+    orc_dual right = od_cmul((b - m) / 6.0, od_add(od_add(fm, od_cmul(4.0, frm)), fb));
+    orc_dual delta = od_sub(od_add(left, right), whole);
+    if (depth <= 0 || fabs(delta.v) <= 15.0 * tol
+        || fabs(delta.v) <= orc_noise_floor(R->floor, a, b, fa.v, fm.v, fb.v))
+        return od_add(od_add(left, right), od_divc(delta, 15.0));
+    return od_add(od_simpson_rec(R, a, m, fa, flm, fm, left, 0.5 * tol, depth - 1),
+                  od_simpson_rec(R, m, b, fm, frm, fb, right, 0.5 * tol, depth - 1));
+}
+
+static orc_dual od_simpson(const orc_dray *R, double a, double b, double tol)
+{
+    if (b <= a) return od_c(0.0);
+    orc_dual fa = od_integrand(R, a), fb = od_integrand(R, b);
+    double m = 0.5 * (a + b);
+    orc_dual fm = od_integrand(R, m);
+    orc_dual whole = od_cmul((b - a) / 6.0, od_add(od_add(fa, od_cmul(4.0, fm)), fb));
+    return od_simpson_rec(R, a, b, fa, fm, fb, whole, tol, 48);
+}
+
+static orc_dual od_integrate(const orc_dray *R, double lo, double hi, double tol)
+{
+    orc_dual sum = od_c(0.0);
+    double a = lo;
+    for (int i = 1; i <= 5; ++i) {
+        double hb = R->A->h_bound[i];
+        if (hb > a && hb < hi) {
+            sum = od_add(sum, od_simpson(R, a, hb, tol));
+            a = hb;
+        }
+    }
+    return od_add(sum, od_simpson(R, a, hi, tol));
+}
+
+/* orc_build_refraction_tables in duals */
+static void od_build_tables(const orc_atm *A, double h_obs, double h_max, int H, int Z,
+                            double theta_max, double tol, orc_dual *ax, orc_dual *al)
+{
+    double dht = (h_max - h_obs) / (double)(H - 1);
+    double smax = sin(theta_max);
+    double dq = smax * smax / (double)(Z - 1);
+    orc_dual np1_obs = od_cadd(1.0, od_eta_exact(A, od_c(h_obs)));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < Z; ++k) {
+        double q = (double)k * dq;
+        double so = sqrt(q), co = sqrt(1.0 - so * so);
+        orc_dray R;
+        R.A = A; R.np1_obs = np1_obs; R.s_obs = so; R.c_obs = co;
+        R.floor = 1e-9;
+        orc_dual dx = od_c(0.0), dl = od_c(0.0);
+        ax[(size_t)0 * Z + k] = od_c(0.0);
+        al[(size_t)0 * Z + k] = od_c(0.0);
+        for (int j = 1; j < H; ++j) {
+            double lo = h_obs + (double)(j - 1) * dht;
+            double hi = h_obs + (double)j * dht;
+            R.which = (k == 0) ? F_RATIO : F_TAN_CORR;
+            dx = od_add(dx, od_integrate(&R, lo, hi, tol));
+            R.which = F_OPT_CORR;
+            dl = od_add(dl, od_integrate(&R, lo, hi, tol));
+            double c3 = co * co * co;
+            ax[(size_t)j * Z + k] = (k == 0) ? dx : od_divc(od_cmul(c3, dx), so);
+            al[(size_t)j * Z + k] = od_cmul(c3, dl);
+        }
+    }
+}
+
+static orc_dual od_bilinear(const orc_dual *T, int Z, int j, int k, orc_dual a, orc_dual b)
+{
+    orc_dual t00 = T[(size_t)j * Z + k], t01 = T[(size_t)j * Z + k + 1];
+    orc_dual t10 = T[(size_t)(j + 1) * Z + k], t11 = T[(size_t)(j + 1) * Z + k + 1];
+    orc_dual v0 = od_add(t00, od_mul(a, od_sub(t10, t00)));
+    orc_dual v1 = od_add(t01, od_mul(a, od_sub(t11, t01)));
+    return od_add(v0, od_mul(b, od_sub(v1, v0)));
+}
+
+typedef struct {
+    const orc_dual *eta, *ax, *al;
+    orc_dual eta_obs;
+} orc_dtabs;
+
+/* One bunch in duals (orc_one_bunch + the (T) propagation, flat layers):
+ * its ground point X, Y, arrival time t (before t_ref) and photons w.
+ * Returns 1 when it reaches the ground. */
+static int od_bunch(const orc_cfg *C, const orc_dtabs *D, const orc_tracks *Tk, int64_t i,
+                    int64_t j, int64_t nb, orc_dual *X, orc_dual *Y, orc_dual *t, orc_dual *w)
+{
+    orc_dual x0 = od_var(Tk->x0[i], ORC_G_X0), y0 = od_var(Tk->y0[i], ORC_G_Y0);
+    orc_dual z0 = od_var(Tk->z0[i], ORC_G_Z0);
+    orc_dual ux = od_var(Tk->ux[i], ORC_G_UX), uy = od_var(Tk->uy[i], ORC_G_UY);
+    orc_dual uz = od_var(Tk->uz[i], ORC_G_UZ);
+    double len = Tk->len[i];
+    /* the yield (orc_step_yield_valid), nb frozen */
+    double inv_me = 1.0 / ORC_ME_MEV;
+    double K = orc_band_factor(C);
+    double g = Tk->ekin[i] * inv_me;
+    double gam = 1.0 + g;
+    double gam2 = gam * gam;
+    double half_len = 0.5 * len;
+    orc_dual hm = od_add(z0, od_cmul(half_len, uz));
+    orc_dual eta = od_eta_lookup(D->eta, C->n_fine, C->h_max, hm);
+    orc_dual np1 = od_cadd(1.0, eta);
+    orc_dual np1sq = od_mul(np1, np1);
+    orc_dual two_eta = od_cadd(2.0, eta);
+    orc_dual a = od_mul(eta, two_eta);
+    orc_dual b = od_mul(a, od_c(gam2));
+    orc_dual num = od_sub(b, np1sq);
+    double two_g = 2.0 + g;
+    double bg2 = g * two_g;
+    orc_dual den = od_cmul(bg2, np1sq);
+    orc_dual s2 = od_div(num, den);
+    if (!(s2.v > 0.0)) return 0;
+    double beta = sqrt(bg2) / gam;
+    orc_dual N = od_cmul(len, od_cmul(K, s2));
+    *w = od_divc(N, (double)nb);
+    /* emission (orc_one_bunch) */
+    orc_dual cos_c = od_cdiv(1.0, od_cmul(beta, od_cadd(1.0, eta)));
+    orc_dual sin_c = od_sqrt(s2);
+    orc_dual e1x, e1y, e1z = od_c(0.0);
+    orc_dual rho2 = od_add(od_mul(ux, ux), od_mul(uy, uy));
+    if (rho2.v > 1e-20) {
+        orc_dual r = od_sqrt(rho2);
+        e1x = od_div(od_neg(uy), r);
+        e1y = od_div(ux, r);
+    } else {
+        e1x = od_c(1.0);
+        e1y = od_c(0.0);
+    }
+    orc_dual e2x = od_sub(od_mul(uy, e1z), od_mul(uz, e1y));
+    orc_dual e2y = od_sub(od_mul(uz, e1x), od_mul(ux, e1z));
+    orc_dual e2z = od_sub(od_mul(ux, e1y), od_mul(uy, e1x));
+    int64_t gi = Tk->track_base + i;
+    uint32_t ctr[4] = { (uint32_t)((uint64_t)gi & 0xffffffffu),
+                        (uint32_t)((uint64_t)gi >> 32), (uint32_t)j, 0u };
+    uint32_t xw[4];
+    orc_philox4x32_10(ctr, C->philox_key, xw);
+    double u0 = orc_u01(xw[0]), u1 = orc_u01(xw[1]);
+    double f = ((double)j + u0) / (double)nb;
+    double phi = 2.0 * ORC_PI * u1;
+    double cp = cos(phi), sp = sin(phi);
+    orc_dual px = od_add(od_mul(cos_c, ux),
+                         od_mul(sin_c, od_add(od_cmul(cp, e1x), od_cmul(sp, e2x))));
+    orc_dual py = od_add(od_mul(cos_c, uy),
+                         od_mul(sin_c, od_add(od_cmul(cp, e1y), od_cmul(sp, e2y))));
+    orc_dual pz = od_add(od_mul(cos_c, uz),
+                         od_mul(sin_c, od_add(od_cmul(cp, e1z), od_cmul(sp, e2z))));
+    double fl = f * len;
+    double inv_bc = 1.0 / (beta * ORC_C_M_PER_NS);
+    orc_dual xe = od_add(x0, od_cmul(fl, ux));
+    orc_dual ye = od_add(y0, od_cmul(fl, uy));
+    orc_dual he = od_add(z0, od_cmul(fl, uz));
+    double te = Tk->t0[i] + fl * inv_bc;
+    /* propagation (orc_propagate_photon_k, variant (T), kappa = 1) */
+    if (pz.v >= 0.0 || he.v < C->h_obs || he.v > C->h_max) return 0;
+    orc_dual sin_em = od_sqrt(od_add(od_mul(px, px), od_mul(py, py)));
+    orc_dual eta_e = od_eta_lookup(D->eta, C->n_fine, C->h_max, he);
+    orc_dual sin_obs = od_div(od_mul(sin_em, od_cadd(1.0, eta_e)), od_cadd(1.0, D->eta_obs));
+    orc_dual q = od_mul(sin_obs, sin_obs);
+    double smax = sin(C->theta_max);
+    double q_max = smax * smax;
+    if (q.v > q_max) return 0;
+    orc_dual cos_obs = od_sqrt(od_csub(1.0, q));
+    orc_dual dH = od_subc(he, C->h_obs);
+    orc_dual hx = od_c(0.0), hy = od_c(0.0);
+    if (sin_em.v > 0.0) { hx = od_div(px, sin_em); hy = od_div(py, sin_em); }
+    double dht = (C->h_max - C->h_obs) / (double)(C->H - 1);
+    double dq = q_max / (double)(C->Z - 1);
+    orc_dual fj = od_divc(dH, dht);
+    int jj = (int)fj.v;
+    if (jj > C->H - 2) jj = C->H - 2;
+    orc_dual aa = od_subc(fj, (double)jj);
+    orc_dual fk = od_divc(q, dq);
+    int kk = (int)fk.v;
+    if (kk > C->Z - 2) kk = C->Z - 2;
+    orc_dual bb = od_subc(fk, (double)kk);
+    orc_dual Ax = od_bilinear(D->ax, C->Z, jj, kk, aa, bb);
+    orc_dual Al = od_bilinear(D->al, C->Z, jj, kk, aa, bb);
+    orc_dual sec = od_cdiv(1.0, cos_obs);
+    orc_dual tn = od_mul(sin_obs, sec);
+    orc_dual sec2 = od_mul(sec, sec);
+    orc_dual Dh = od_add(od_mul(dH, tn), od_mul(od_mul(Ax, tn), sec2));
+    orc_dual Lp = od_add(od_mul(dH, sec), od_mul(od_mul(Al, sec2), sec));
+    *X = od_add(xe, od_mul(Dh, hx));
+    *Y = od_add(ye, od_mul(Dh, hy));
+    *t = od_cadd(te, od_divc(Lp, ORC_C_M_PER_NS));
+    return 1;
+}
+
+/* S, U of the read-out and the gradients of L: grad_atm[15] (a_0..a_4,
+ * b_0..b_4, c_0..c_4), grad_steps[6 n] (dL/dx0, dL/dy0, dL/dz0, dL/dux,
+ * dL/duy, dL/duz, six arrays of n).  table_tol is the tolerance the tables
+ * were built with.  Returns 0, or -1 on bad arguments or a configuration it
+ * does not cover (curved, dispersion, fallback, transmission). */
+int orc_density_grad(const orc_cfg *C, const orc_tracks *Tk, uint64_t seed,
+                     const int32_t *nb_frozen, double sigma, const double *gD,
+                     const double *gT, double table_tol, double *S, double *U,
+                     double *grad_atm, double *grad_steps)
+{
+    if (!C || !Tk || !nb_frozen || !gD || !gT || !S || !U || !grad_atm || !grad_steps
+        || !(sigma > 0.0) || C->earth_radius > 0.0 || C->disp_k > 0 || C->fb_sin2_max > 0.0
+        || C->trans_tau)
+        return -1;
+    orc_cfg Cs = *C;
+    Cs.philox_key[0] = (uint32_t)(seed & 0xffffffffu);
+    Cs.philox_key[1] = (uint32_t)(seed >> 32);
+    size_t nt = (size_t)C->H * C->Z;
+    orc_dual *eta = malloc(sizeof(orc_dual) * (size_t)C->n_fine);
+    orc_dual *ax = malloc(sizeof(orc_dual) * nt), *al = malloc(sizeof(orc_dual) * nt);
+    int n_tel = C->n_tel;
+    orc_dual *SU = malloc(sizeof(orc_dual) * 2 * (size_t)(n_tel > 0 ? n_tel : 1));
+    if (!eta || !ax || !al || !SU) {
+        free(eta); free(ax); free(al); free(SU);
+        return -1;
+    }
+    double dh = C->h_max / (double)(C->n_fine - 1);
+    for (int k = 0; k < C->n_fine; ++k) eta[k] = od_eta_exact(&C->atm, od_c((double)k * dh));
+    od_build_tables(&C->atm, C->h_obs, C->h_max, C->H, C->Z, C->theta_max, table_tol, ax, al);
+    orc_dtabs D;
+    D.eta = eta; D.ax = ax; D.al = al;
+    D.eta_obs = od_eta_lookup(eta, C->n_fine, C->h_max, od_c(C->h_obs));
+    double norm = 1.0 / (2.0 * ORC_PI * sigma * sigma);
+    double rcut2 = 36.0 * sigma * sigma;
+    for (int k = 0; k < 2 * n_tel; ++k) SU[k] = od_c(0.0);
+    /* pass 1: S and U with their atmosphere tangents (the step tangents of
+     * different steps are different variables and are not summed here) */
+    for (int pass = 0; pass < 2; ++pass) {
+        double dLdS[4096], dLdU[4096];
+        if (pass == 1) {
+            if (n_tel > 4096) break;
+            for (int k = 0; k < n_tel; ++k) {
+                double s = SU[k].v, u = SU[n_tel + k].v;
+                dLdS[k] = gD[k];
+                dLdU[k] = 0.0;
+                if (s > 0.0) {
+                    dLdS[k] = gD[k] - gT[k] * u / (s * s);
+                    dLdU[k] = gT[k] / s;
+                }
+            }
+            for (int q = 0; q < 15; ++q) grad_atm[q] = 0.0;
+            for (int q = 0; q < 10; ++q) {
+                double gq = 0.0;
+                for (int k = 0; k < n_tel; ++k)
+                    gq += dLdS[k] * SU[k].d[ORC_G_B0 + q] + dLdU[k] * SU[n_tel + k].d[ORC_G_B0 + q];
+                grad_atm[5 + q] = gq;
+            }
+        }
+        for (int64_t i = 0; i < Tk->n; ++i) {
+            double gs[6] = { 0, 0, 0, 0, 0, 0 };
+            int64_t nb = nb_frozen[i];
+            if (nb > 0 && orc_step_valid(Tk, i)) {
+                double t_ref = orc_t_ref(&Cs, Tk, i);
+                for (int64_t j = 0; j < nb; ++j) {
+                    orc_dual X, Y, t, w;
+                    if (!od_bunch(&Cs, &D, Tk, i, j, nb, &X, &Y, &t, &w)) continue;
+                    t = od_subc(t, t_ref);
+                    for (int k = 0; k < n_tel; ++k) {
+                        orc_dual dx = od_subc(X, C->tel[4 * k + 0]);
+                        orc_dual dy = od_subc(Y, C->tel[4 * k + 1]);
+                        orc_dual r2 = od_add(od_mul(dx, dx), od_mul(dy, dy));
+                        if (!(r2.v < rcut2)) continue;
+                        orc_dual G = od_cmul(norm, od_exp(od_divc(od_neg(r2), 2.0 * sigma * sigma)));
+                        orc_dual wG = od_mul(w, G);
+                        orc_dual wGt = od_mul(wG, t);
+                        if (pass == 0) {
+                            SU[k] = od_add(SU[k], wG);
+                            SU[n_tel + k] = od_add(SU[n_tel + k], wGt);
+                        } else {
+                            for (int m = 0; m < 6; ++m)
+                                gs[m] += dLdS[k] * wG.d[m] + dLdU[k] * wGt.d[m];
+                        }
+                    }
+                }
+            }
+            if (pass == 1)
+                for (int m = 0; m < 6; ++m) grad_steps[(size_t)m * (size_t)Tk->n + (size_t)i] = gs[m];
+        }
+    }
+    int ok = n_tel <= 4096;
+    for (int k = 0; k < n_tel; ++k) { S[k] = SU[k].v; U[k] = SU[n_tel + k].v; }
+    free(eta); free(ax); free(al); free(SU);
+    return ok ? 0 : -1;
+}
