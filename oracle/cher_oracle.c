@@ -2113,9 +2113,22 @@ int orc_density_grad(const orc_cfg *C, const orc_tracks *Tk, uint64_t seed,
         for (int64_t i = 0; i < Tk->n; ++i) {
             double gs[6] = { 0, 0, 0, 0, 0, 0 };
             int64_t nb = nb_frozen[i];
-            if (nb > 0 && orc_step_valid(Tk, i)) {
+            orc_yield Yv;
+            if (nb > 0 && orc_step_yield(&Cs, Tk, i, &Yv) == 0 && Yv.s2 > 0.0) {
                 double t_ref = orc_t_ref(&Cs, Tk, i);
                 for (int64_t j = 0; j < nb; ++j) {
+                    /* the bunch's values first (the same arithmetic): the
+                     * dual numbers only where it lands within the cut of a
+                     * centre, as nothing else contributes */
+                    orc_bunch1 B;
+                    orc_one_bunch(&Cs, Tk, i, j, nb, &Yv, 0, &B);
+                    if (B.status != ORC_ST_GROUND) continue;
+                    int near = 0;
+                    for (int k = 0; k < n_tel && !near; ++k) {
+                        double ex = B.r[0] - C->tel[4 * k + 0], ey = B.r[1] - C->tel[4 * k + 1];
+                        near = ex * ex + ey * ey < rcut2;
+                    }
+                    if (!near) continue;
                     orc_dual X, Y, t, w;
                     if (!od_bunch(&Cs, &D, Tk, i, j, nb, &X, &Y, &t, &w)) continue;
                     t = od_subc(t, t_ref);
