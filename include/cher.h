@@ -294,8 +294,18 @@ cher_status cher_generate_steps(cher_ctx *ctx, const cher_shower *showers, int32
  * Errors: CHER_EINVAL (NULL array with n > 0, n < 0), CHER_ECUDA. */
 cher_status cher_round_to_float(const double *in, float *out, int64_t n, void *stream);
 
-/* The same hot path as cher_generate_propagate (same kernel, same results)
- * for callers that must not allocate device memory when they run it: code
+/* The float pair the FP32 path splits its FP64 time and height differences
+ * into (t0 - t_ref and z0 - h_obs, tens of km and ~1e5 ns), so that its
+ * arrival time is summed in float-float: hi = the rounding above and lo the
+ * float nearest to in - hi (0 where that would not be a normal float), on
+ * the integer pipes.  The paper has no counterpart; exposed for its test.
+ * in, hi, lo: device arrays of n elements (n >= 0), 8- and 4-byte aligned;
+ * asynchronous on `stream`.  Errors: CHER_EINVAL, CHER_ECUDA. */
+cher_status cher_split_to_float(const double *in, float *hi, float *lo, int64_t n,
+                                void *stream);
+
+/* The same hot path as cher_generate_propagate (same kernel, same results;
+ * see below for the one configuration it refuses) for callers that must not allocate device memory when they run it: code
  * that runs while a stream of the process is being captured into a CUDA
  * graph in global mode (where cudaMalloc is refused), pipelines whose device
  * memory is all held by another allocator (a framework's caching pool), and
@@ -311,7 +321,12 @@ cher_status cher_round_to_float(const double *in, float *out, int64_t n, void *s
  * calls that overlap on the GPU (different streams, or several contexts)
  * race on it and must be serialised by the caller.  A step count above
  * 2^40, the library-wide limit, is refused with CHER_ERANGE before anything
- * is launched.  Other errors as cher_generate_propagate. */
+ * is launched.  A context whose beyond-table fallback is active
+ * (cher_set_fallback past the tables' zenith range, flat layers) is refused
+ * with CHER_EINVAL before anything is launched: that fallback queues its
+ * bunches in memory the context allocates, and without it those bunches
+ * would be dropped where cher_generate_propagate propagates them.  Other
+ * errors as cher_generate_propagate. */
 cher_status cher_generate_propagate_noalloc(cher_ctx *ctx, const cher_tracks *tracks,
                                             uint64_t seed, cher_precision prec,
                                             const cher_output *out, void *stream);
@@ -341,8 +356,10 @@ cher_status cher_sync_status(cher_ctx *ctx, const cher_output *out,
 
 /* Launch shape of cher_generate_propagate.  block_threads in {128, 256,
  * 512} is also the number of steps per tile; ctas_per_sm in 1..8 sets the
- * persistent grid (0 = one CTA per tile, no persistence).  The defaults
- * come from cher_autotune or are 256 / 3.  Errors: CHER_EINVAL. */
+ * persistent grid (0 = one CTA per tile, no persistence).  A new context
+ * starts at 128 / 8 (the shape cher_autotune settles on for the FP32 path on
+ * GB300: 32 resident warps per SM); cher_autotune replaces it.  Errors:
+ * CHER_EINVAL. */
 cher_status cher_set_launch(cher_ctx *ctx, int32_t block_threads,
                             int32_t ctas_per_sm);
 cher_status cher_get_launch(const cher_ctx *ctx, int32_t *block_threads,

@@ -108,6 +108,7 @@ SIGNATURES = {
     "cher_generate_propagate_ex": (_S, [_P, ctypes.POINTER(Tracks), ctypes.c_uint64, _S,
                                         ctypes.POINTER(Output), ctypes.POINTER(Profile), _P]),
     "cher_round_to_float": (_S, [_P, _P, ctypes.c_int64, _P]),
+    "cher_split_to_float": (_S, [_P, _P, _P, ctypes.c_int64, _P]),
     "cher_set_transmission": (_S, [_P, ctypes.POINTER(Transmission)]),
     "cher_set_fallback": (_S, [_P, ctypes.c_double, ctypes.c_int64]),
     "cher_set_dispersion": (_S, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
@@ -327,7 +328,9 @@ class Context:
                "cher_build_refraction_tables")
         self.H, self.Z = int(n_heights), int(n_zenith)
 
-    def set_launch(self, block_threads=256, ctas_per_sm=3):
+    def set_launch(self, block_threads, ctas_per_sm):
+        """Steps per tile (128, 256 or 512) and persistent CTAs per SM (0: one
+        CTA per tile); a new context starts at 128 / 8."""
         _check(lib().cher_set_launch(self._h, int(block_threads), int(ctas_per_sm)),
                "cher_set_launch")
 
@@ -472,9 +475,18 @@ class Context:
         n = sum(max(int(s["n"]), 0) for s in showers)    # (a negative count: EINVAL below)
         ddt = torch.float32 if precision == CHER_FP32_BULK else torch.float64
         if out is not None:
-            if (out["x0"].numel() != n or out["t_ref"].numel() != len(showers)
-                    or out["ux"].dtype != ddt):
-                raise ValueError("generate_steps: `out` does not match these showers")
+            # every array the kernel writes: size, dtype, contiguity, device
+            want = {k: (n, torch.float64) for k in ("x0", "y0", "z0", "t0", "len", "ekin")}
+            want.update({k: (n, ddt) for k in ("ux", "uy", "uz")})
+            want["shower"] = (n, torch.int32)
+            want["t_ref"] = (len(showers), torch.float64)
+            cur = torch.device("cuda", torch.cuda.current_device())
+            for k, (cnt, dt) in want.items():
+                v = out.get(k) if isinstance(out, dict) else None
+                if (v is None or not isinstance(v, torch.Tensor) or v.numel() != cnt
+                        or v.dtype != dt or not v.is_contiguous() or v.device != cur):
+                    raise ValueError(f"generate_steps: out[{k!r}] must be a contiguous {dt} "
+                                     f"tensor of {cnt} elements on {cur}")
         else:
             out = {k: torch.empty(n, dtype=torch.float64, device=device)
                    for k in ("x0", "y0", "z0", "t0", "len", "ekin")}
@@ -611,6 +623,20 @@ def round_to_float(x):
     _check(lib().cher_round_to_float(x.data_ptr(), y.data_ptr(), x.numel(),
                                      ctypes.c_void_p(_stream_ptr(None))), "cher_round_to_float")
     return y
+
+
+def split_to_float(x):
+    """The FP32 path's float pair (hi, lo) of a device float64 tensor
+    (cher_split_to_float)."""
+    torch = _torch()
+    x = x.contiguous()
+    if x.dtype != torch.float64 or not x.is_cuda:
+        raise ValueError("a CUDA float64 tensor is needed")
+    hi = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    lo = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    _check(lib().cher_split_to_float(x.data_ptr(), hi.data_ptr(), lo.data_ptr(), x.numel(),
+                                     ctypes.c_void_p(_stream_ptr(None))), "cher_split_to_float")
+    return hi, lo
 
 
 class Graph:

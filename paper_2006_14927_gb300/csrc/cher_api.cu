@@ -31,6 +31,7 @@ struct cher_ctx {
     double q_band = 0;
     double eta_obs = 0;
     double eta_slope = 0;                 // max |eta[k+1] - eta[k]| / dh
+    double eta_jump = 0;                  // see KParams::eta_jump
     double *d_eta64 = nullptr;
     float *d_eta32 = nullptr;
     void *d_tab64 = nullptr, *d_tab32 = nullptr;
@@ -289,6 +290,7 @@ cher::KParams base_params(const cher_ctx *c, const cher_tracks *t, uint64_t seed
     p.eta64 = c->d_eta64;
     p.eta32 = c->d_eta32;
     p.eta_slope = c->eta_slope;
+    p.eta_jump = c->eta_jump;
     p.h_obs = c->h_obs;
     p.eta_obs = c->eta_obs;
     p.H = c->T.H;
@@ -518,6 +520,19 @@ cher_status cher_build_refraction_tables(cher_ctx *c, int32_t n_heights, int32_t
     c->eta_slope = 0.0;
     for (int k = 0; k + 1 < c->T.n_fine; ++k)
         c->eta_slope = std::max(c->eta_slope, std::fabs(c->T.eta[k + 1] - c->T.eta[k]) * c->T.inv_dh);
+    // the largest relative step of eta between nodes inside a layer (the
+    // density jumps at the boundaries; a cell that holds one is left out)
+    c->eta_jump = 0.0;
+    for (int k = 0; k + 1 < c->T.n_fine; ++k) {
+        const double h0 = static_cast<double>(k) / c->T.inv_dh;
+        const double h1 = static_cast<double>(k + 1) / c->T.inv_dh;
+        bool straddle = false;
+        for (int l = 0; l < 6; ++l)
+            straddle = straddle || (c->atm.h_bound[l] > h0 && c->atm.h_bound[l] <= h1);
+        if (straddle || !(c->T.eta[k] > 0.0)) continue;
+        c->eta_jump = std::max(c->eta_jump, std::fabs(c->T.eta[k + 1] - c->T.eta[k]) / c->T.eta[k]);
+    }
+    c->eta_jump *= 1.5;
 
     const int H = c->T.H, Z = c->T.Z;
     const size_t per = entry_values(c->T);
@@ -949,7 +964,8 @@ cher_status cher_set_fallback(cher_ctx *c, double zenith_max_deg, int64_t queue_
     return CHER_OK;
 }
 
-cher_status cher_round_to_float(const double *in, float *out, int64_t n, void *stream) {
+static cher_status round_or_split(const double *in, float *out, float *lo, int64_t n,
+                                  void *stream) {
     if (n < 0 || (n > 0 && (bad_ptr(in) || bad_ptr(out)))) return CHER_EINVAL;
     if (n == 0) return CHER_OK;
     int dev = 0, sms = 0;
@@ -958,8 +974,18 @@ cher_status cher_round_to_float(const double *in, float *out, int64_t n, void *s
         cudaGetLastError();
         return CHER_ECUDA;
     }
-    if (cher::round_to_float(in, out, n, sms, stream) != cudaSuccess) return CHER_ECUDA;
+    if (cher::round_to_float(in, out, lo, n, sms, stream) != cudaSuccess) return CHER_ECUDA;
     return CHER_OK;
+}
+
+cher_status cher_round_to_float(const double *in, float *out, int64_t n, void *stream) {
+    return round_or_split(in, out, nullptr, n, stream);
+}
+
+cher_status cher_split_to_float(const double *in, float *hi, float *lo, int64_t n,
+                                void *stream) {
+    if (n > 0 && bad_ptr(lo)) return CHER_EINVAL;
+    return round_or_split(in, hi, lo, n, stream);
 }
 
 cher_status cher_sync_status(cher_ctx *c, const cher_output *out, unsigned long long *stats_host,
@@ -1431,6 +1457,10 @@ extern "C" cher_status cher_generate_propagate_noalloc(cher_ctx *c, const cher_t
         return CHER_EINVAL;
     if (reinterpret_cast<uintptr_t>(out->pos) % 16 || reinterpret_cast<uintptr_t>(out->tim) % 16)
         return CHER_EINVAL;
+    // the beyond-table fallback queues its bunches in memory the context
+    // allocates: with it active this call would drop them where the regular
+    // entry point propagates them, so it refuses instead
+    if (c->fb_deg > c->tab_zen && c->earth_radius == 0.0) return CHER_EINVAL;
     unsigned long long *scratch = nullptr;
     cher_status s = static_scratch(c->device, &scratch);
     if (s != CHER_OK) return s;
@@ -1443,8 +1473,6 @@ extern "C" cher_status cher_generate_propagate_noalloc(cher_ctx *c, const cher_t
             cudaSuccess)
         return CHER_ECUDA;
     cher::KParams p = base_params(c, t, seed, fp32);
-    p.fb_q = 0.0;                         // no fallback queue here (it needs scratch)
-    cher::fill_float_constants(p);
     p.pos = out->pos;
     p.tim = out->tim;
     p.key = out->key;

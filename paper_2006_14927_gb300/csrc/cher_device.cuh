@@ -81,6 +81,31 @@ __device__ __forceinline__ float d2f_rn(double d) {
     return __uint_as_float(r | sign);
 }
 
+// A double as an unevaluated float pair, hi + lo, on the integer pipes:
+// hi = d2f_rn(d), and lo the float nearest to d - hi, which is the 29
+// fraction bits hi dropped minus the rounding carry, R = rem - up 2^29,
+// times 2^(E - 52) for the double's exponent E: R is converted to float and
+// E - 52 added to its exponent field (|lo| <= ulp(hi) / 2, so hi + lo
+// carries 48 bits).  lo is 0 where it would not be a normal float, and for
+// zero, subnormal, infinite or NaN d.
+__device__ __forceinline__ void d2f_split(double d, float &hi, float &lo) {
+    hi = d2f_rn(d);
+    const unsigned h = static_cast<unsigned>(__double2hiint(d));
+    const unsigned l = static_cast<unsigned>(__double2loint(d));
+    const unsigned ex = (h >> 20) & 0x7ffu;
+    const unsigned m = ((h & 0xfffffu) << 3) | (l >> 29);
+    const unsigned rem = l & 0x1fffffffu;
+    const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    const int R = static_cast<int>(rem) - static_cast<int>(up << 29);
+    const unsigned vb = __float_as_uint(static_cast<float>(R));
+    const int ve = static_cast<int>((vb >> 23) & 0xffu);
+    const int ne = ve + static_cast<int>(ex) - (1023 + 52);
+    const bool ok = ve != 0 && ne > 0 && ne < 255 && ex != 0u && ex != 0x7ffu;
+    const float a = ok ? __uint_as_float((vb & 0x807fffffu) | (static_cast<unsigned>(ne) << 23))
+                       : 0.0f;
+    lo = (h & 0x80000000u) ? -a : a;
+}
+
 __device__ __forceinline__ double eta_exact_lookup(const KParams &p, double h) {
     double hc = h;
     if (hc < 0.0) hc = 0.0;

@@ -89,6 +89,8 @@ struct KParams {
     const double *eta64;
     const float *eta32;
     double eta_slope;                     // max |eta[k+1] - eta[k]| / dh
+    double eta_jump;                      // 1.5 x max |eta[k+1] - eta[k]| / eta[k] over
+                                          // the cells that hold no layer boundary
     // observation level
     double h_obs, eta_obs;
     // refraction tables, pair-interleaved: entry (j, k), k < Z-1, holds
@@ -184,7 +186,7 @@ struct KParams {
         float h_obs, dH_max, eta_o, inv_np1o, np1o, q_max, inv_dht, inv_dq, inv_dh;
         float lam_inv1, lam_dinv, rcut2, q_band;
         // FP32 screen of the yield: constants and the table's largest slope
-        float inv_me, K, inv_B, h_max, dh, eta_slope;
+        float inv_me, K, inv_B, h_max, dh, eta_slope, eta_jump;
         float gx0[2], gy0[2], inv_gcs[2];
         float prof_dx, prof_inv_dx;
         float trans_l0, trans_lscale, trans_h0, trans_hscale;
@@ -281,7 +283,8 @@ cudaError_t pack_records(bool fp32, const void *pos, const void *tim, const uint
                          void *stream);
 
 // The FP32 path's double -> float rounding over an array (grid-stride).
-cudaError_t round_to_float(const double *in, float *out, int64_t n, int num_sms, void *stream);
+cudaError_t round_to_float(const double *in, float *out, float *lo, int64_t n, int num_sms,
+                           void *stream);
 cudaError_t kernel_prepare(bool fp32, int block, int mode, size_t smem);
 cudaError_t kernel_launch(bool fp32, int block, int mode, int grid, size_t smem,
                           const KParams &p, void *stream);

@@ -43,7 +43,10 @@ struct alignas(16) Seg {
     R e2z, cosc, sinc, inv_nb;
     R x0, y0, dz0, tseg;   // dz0 = z0 - h_obs, tseg = t0 - t_ref (FP64 differences)
     R inv_bc, w;
-    int nb, pad;
+    // FP32 path: the low parts of tseg and dz0 (tseg + tseg_lo and dz0 +
+    // dz0_lo are their FP64 values to ~2^-48), for the arrival time's
+    // float-float sum (unused in FP64)
+    float tseg_lo, dz0_lo;
     // the parts of the first two Philox rounds that depend on the step only
     // (philox_bunch)
     uint32_t ph_a, ph_b, ph_c, ph_d;
@@ -61,6 +64,18 @@ struct YieldF {
     bool valid;
     float g, eta, s2, N;
 };
+
+// The FP32 screen keeps its photon count only where the Cherenkov-threshold
+// cancellation in the numerator loses at most a factor ~10 (num >= 0.1 of
+// its terms) and the midpoint's cell of the fine table holds no layer
+// boundary (there the density jumps, and the FP32 height's rounding would
+// move eta by up to the jump times ~1e-4): its rounding then leaves the
+// photons per bunch within ~5e-6 of the FP64 chain (a few 1e-7 of eta times
+// A / num <= 11, plus the FP32 operations); elsewhere the FP64 chain
+// computes them.  (Deferring only the photons of those steps to the hit
+// path, with the count kept from the screen, measured slower: the FP64 chain
+// there made the bunch loop spill.)
+constexpr float kMildCancel = 0.1f;
 
 // sign and zero tests on the bit pattern (no FP64 instruction)
 __device__ __forceinline__ bool d_negative(double v) {
@@ -131,7 +146,8 @@ __device__ __forceinline__ void step_yield_screened(const KParams &p, bool other
     const float E = 4.0f * (KL * p.f.inv_B * d_s2 + fabsf(q) * 8.0f * u) + 1e-30f;
     const float lo = q - E, hi = q + E;
     if (hi <= 0.0f) return;                              // below threshold for sure
-    if (lo > 0.0f && ceilf(lo) == ceilf(hi) && num >= 0.01f * (A + np1sq) && hi < 4.0e6f) {
+    if (lo > 0.0f && ceilf(lo) == ceilf(hi) && num >= kMildCancel * (A + np1sq) &&
+        fabsf(t1 - t0) <= p.f.eta_jump * t0 && hi < 4.0e6f) {
         y.nb = static_cast<int>(ceilf(hi));
         y.g = g;
         y.eta = eta;
@@ -309,7 +325,7 @@ __device__ __forceinline__ void step_yield_screened_disp(const KParams &p, bool 
                 const float d_B = d_e + 3.0f * u * B;
                 const float d_num = d_A + d_B + u * (A + B);
                 dsum += d_num / den + fabsf(S) * (12.0f * u + 2.0f * d_eta);
-                mild = mild && num >= 0.01f * (A + B);
+                mild = mild && num >= kMildCancel * (A + B);
                 sum += S;
                 D.cdf[m] = sum;
             }
@@ -319,7 +335,8 @@ __device__ __forceinline__ void step_yield_screened_disp(const KParams &p, bool 
         const float E = 4.0f * (KL * p.f.inv_B * dsum +
                                 fabsf(q) * (8.0f + static_cast<float>(K)) * u) + 1e-30f;
         const float lo = q - E, hi = q + E;
-        if (lo > 0.0f && ceilf(lo) == ceilf(hi) && mild && hi < 4.0e6f) {
+        if (lo > 0.0f && ceilf(lo) == ceilf(hi) && mild && fabsf(t1 - t0) <= p.f.eta_jump * t0 &&
+            hi < 4.0e6f) {
             y.nb = static_cast<int>(ceilf(hi));
             y.g = g;
             y.eta = eta;
@@ -422,8 +439,6 @@ __device__ __forceinline__ void prep_step(const KParams &p, int64_t i, const Y &
         const uint32_t sh = p.shower ? __ldg(p.shower + i) : 0u;
         if (static_cast<int32_t>(sh) < p.n_showers) t_ref = __ldg(p.t_ref + sh);
     }
-    S.nb = y.nb;
-    S.pad = 0;
     {
         // counter (lo(g), hi(g), j, 0): round 1 multiplies word 0 (the step's)
         // and word 2 (j); round 2 multiplies round 1's word 2, which is the
@@ -448,14 +463,15 @@ __device__ __forceinline__ void prep_step(const KParams &p, int64_t i, const Y &
         S.L = d2f_rn(__ldg(p.len + i));
         S.x0 = d2f_rn(__ldg(p.x0 + i));
         S.y0 = d2f_rn(__ldg(p.y0 + i));
-        S.dz0 = d2f_rn(__ldg(p.z0 + i) - p.h_obs);
-        S.tseg = d2f_rn(__ldg(p.t0 + i) - t_ref);
+        d2f_split(__ldg(p.z0 + i) - p.h_obs, S.dz0, S.dz0_lo);
+        d2f_split(__ldg(p.t0 + i) - t_ref, S.tseg, S.tseg_lo);
     } else {
         S.L = __ldg(p.len + i);
         S.x0 = __ldg(p.x0 + i);
         S.y0 = __ldg(p.y0 + i);
         S.dz0 = __ldg(p.z0 + i) - p.h_obs;
         S.tseg = __ldg(p.t0 + i) - t_ref;
+        S.tseg_lo = S.dz0_lo = 0.0f;
     }
     // azimuth basis around the step: e1 horizontal, e2 = d x e1
     R e1x, e1y;
@@ -635,8 +651,40 @@ struct BunchOut {
     R kap;               // (n - 1) scale at the bunch's wavelength
     R c2;                // cos^2 of the arrival zenith (queued fallback bunches)
     R zg;                // arrival z - h_obs (curved atmosphere; 0 in flat layers)
+    R tsec;              // FP32 hits path: 1 / cos(theta_obs), t holds the time's
+                         // small part (the float-float sum is formed on the hit path)
     int status;
 };
+
+// The FP32 arrival time at h_obs minus t_ref, summed in float-float.  With
+// Lp = sec (dz0 + m) the optical path (m = fl u_z + A_l sec^2, the part
+// beyond the step's own height above h_obs) the time is
+//     t = tseg + fl / (beta c) + Lp / c
+//       = [tseg + (sec dz0) / c] + [fl / (beta c) + sec m / c],
+// two large terms of opposite sign (tens of km of path against the step's
+// time before the shower front, ~1e5 ns each) and a small one r.  The large
+// ones are formed exactly: tseg and dz0 come as float pairs split from their
+// FP64 values (prep_step), 1/c as a float pair, the products sec dz0 and
+// (sec dz0) (1/c) with their FMA-exact rounding errors, their sum with tseg
+// by Knuth's two-sum; the rounding errors, the low parts and r are added
+// last.  r is formed where the bunch is propagated.  (Explicitly rounded
+// operations: no contraction into FMAs may touch the error-free
+// transforms.)
+constexpr double kInvC = 1.0 / kC;
+constexpr float kInvC_hi = static_cast<float>(kInvC);
+constexpr float kInvC_lo = static_cast<float>(kInvC - static_cast<double>(kInvC_hi));
+
+__device__ __forceinline__ float arrival_time_ff(const Seg<float> &S, float sec, float r) {
+    const float P = __fmul_rn(sec, S.dz0);
+    const float Pe = fmaf(sec, S.dz0, -P);
+    const float Q = __fmul_rn(P, kInvC_hi);
+    const float Qe = fmaf(P, kInvC_hi, -Q);
+    const float s = __fadd_rn(S.tseg, Q);
+    const float bb = __fsub_rn(s, S.tseg);
+    const float se = __fadd_rn(__fsub_rn(S.tseg, __fsub_rn(s, bb)), __fsub_rn(Q, bb));
+    const float lo = (P * kInvC_lo + (Pe + sec * S.dz0_lo) * kInvC_hi) + S.tseg_lo;
+    return s + (((se + Qe) + lo) + r);
+}
 
 template <class R>
 struct Consts {
@@ -1189,10 +1237,22 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
     const R hx = px * rse, hy = py * rse, so = se2 * rse * rat;
     const R tn = so * sec;
     const R D = tn * (dH + Ax * sec2);              // horizontal offset
-    const R Lp = sec * (dH + Al * sec2);            // optical path
     o.X = S.x0 + fl * S.ux + D * hx;
     o.Y = S.y0 + fl * S.uy + D * hy;
-    o.t = S.tseg + fl * S.inv_bc + Lp * R(1.0 / kC);
+    if constexpr (std::is_same<R, float>::value) {
+        // the time's small part here, its float-float sum on the hit path
+        // (LAZY) or now
+        const float r = fl * S.inv_bc + (sec * (fl * S.uz + Al * sec2)) * static_cast<float>(1.0 / kC);
+        if constexpr (LAZY) {
+            o.t = r;
+            o.tsec = sec;
+        } else {
+            o.t = arrival_time_ff(S, sec, r);
+        }
+    } else {
+        const R Lp = sec * (dH + Al * sec2);        // optical path
+        o.t = S.tseg + fl * S.inv_bc + Lp * R(1.0 / kC);
+    }
     o.cx = so * hx;
     o.cy = so * hy;
     o.cz = -co;
@@ -1331,10 +1391,11 @@ __device__ __forceinline__ void flush_stat_signed(unsigned long long *stats, int
 // telescope) one atomicAdd reserves the slots; the record is the crossing
 // of the arrival line with the horizontal plane through the sphere centre.
 // All 32 lanes call it (hm = 0 on lanes without a crossing).  The photon
-// weight, record key and wavelength come from weight_key(w, key, lambda),
-// called on the hit path only (about 2 % of bunches need them; in the plain
-// hits instantiation the bunch carries the spectrum's deviate and lambda is
-// formed there).
+// weight, record key, wavelength and arrival time at h_obs come from
+// weight_key(w, key, lambda, t), called on the hit path only (about 2 % of
+// bunches need them; in the plain hits instantiation the bunch carries the
+// spectrum's deviate and the time's small part, and lambda and the
+// float-float time are formed there).
 template <class R, class KW>
 __device__ __forceinline__ void record_hits(const KParams &p, const BunchOut<R> &o, unsigned hm,
                                             int s0, int gsel, KW weight_key, R np1o, int lane,
@@ -1359,13 +1420,13 @@ __device__ __forceinline__ void record_hits(const KParams &p, const BunchOut<R> 
             slot0 = __shfl_sync(grp, slot0, leader);
             const unsigned long long slot = slot0 + rank;
             if (slot < static_cast<unsigned long long>(p.cap)) {
-                R w, lam;
+                R w, lam, tg;
                 uint64_t key;
-                weight_key(w, key, lam);     // only on the (rare) hit path
+                weight_key(w, key, lam, tg);   // only on the (rare) hit path
                 const R sl = (tz - o.zg) / o.cz;   // to the plane through the centre
                 const int64_t r = static_cast<int64_t>(tel) * p.cap + static_cast<int64_t>(slot);
                 store4<R>(p.pos, r, o.X + sl * o.cx - tx, o.Y + sl * o.cy - ty, o.cx, o.cy);
-                store4<R>(p.tim, r, o.t + sl * np1o * R(1.0 / kC), o.he, w, lam);
+                store4<R>(p.tim, r, tg + sl * np1o * R(1.0 / kC), o.he, w, lam);
                 p.key[r] = key;
             } else {
                 ++st_over;
@@ -1655,11 +1716,17 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                 const Seg<R> *sp = seg + s;
                 constexpr bool kLazy = MODE == MODE_HITS && !TR && FB == 0 && !DS && !CV;
                 const R lam_o = o.lam, li1 = c.lam_inv1, ldi = c.lam_dinv;
+                const R t_o = o.t, sec_o = o.tsec;
                 record_hits<R>(p, o, hm, s0, gsel,
-                               [sp, gstep, j, lam_o, li1, ldi](R &w_, uint64_t &k_, R &l_) {
+                               [sp, gstep, j, lam_o, li1, ldi, t_o, sec_o](R &w_, uint64_t &k_,
+                                                                           R &l_, R &t_) {
                                    w_ = sp->w;
                                    k_ = (static_cast<uint64_t>(gstep) << 32) | static_cast<uint32_t>(j);
                                    l_ = kLazy ? R(1) / (li1 - lam_o * ldi) : lam_o;
+                                   if constexpr (kLazy && std::is_same<R, float>::value)
+                                       t_ = arrival_time_ff(*sp, sec_o, t_o);
+                                   else
+                                       t_ = t_o;
                                },
                                np1, lane, st_hits, st_over);
             }
@@ -1764,9 +1831,14 @@ __global__ void __launch_bounds__(128) k_fallback(const KParams p) {
         int s0 = 0, gsel = 0;
         unsigned hm = live ? sphere_hits<R>(p, c, o, s0, gsel) : 0u;
         const R np1 = DS ? R(1) + o.kap * c.eta_o : np1o;
-        const R lam_o = o.lam;
+        const R lam_o = o.lam, t_o = o.t;
         record_hits<R>(p, o, hm, s0, gsel,
-                       [w, key, lam_o](R &w_, uint64_t &k_, R &l_) { w_ = w; k_ = key; l_ = lam_o; },
+                       [w, key, lam_o, t_o](R &w_, uint64_t &k_, R &l_, R &t_) {
+                           w_ = w;
+                           k_ = key;
+                           l_ = lam_o;
+                           t_ = t_o;
+                       },
                        np1, lane, st_hits, st_over);
     }
     unsigned long long *S = p.stats;
@@ -1894,6 +1966,7 @@ void fill_float_constants(KParams &p) {
     p.f.h_max = static_cast<float>(p.h_max);
     p.f.dh = static_cast<float>(1.0 / p.inv_dh);
     p.f.eta_slope = static_cast<float>(p.eta_slope * 1.01);
+    p.f.eta_jump = static_cast<float>(p.eta_jump);
     p.f.rcut2 = static_cast<float>(p.rcut2);
     p.f.fb_q = static_cast<float>(p.fb_q);
     p.f.trans_l0 = static_cast<float>(p.trans_l0);
@@ -1928,10 +2001,14 @@ void fill_float_constants(KParams &p) {
 }
 
 namespace {
-__global__ void k_round_to_float(const double *in, float *out, int64_t n) {
+__global__ void k_round_to_float(const double *in, float *out, float *lo, int64_t n) {
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
-         i += int64_t(gridDim.x) * blockDim.x)
-        out[i] = d2f_rn(in[i]);
+         i += int64_t(gridDim.x) * blockDim.x) {
+        if (lo)
+            d2f_split(in[i], out[i], lo[i]);
+        else
+            out[i] = d2f_rn(in[i]);
+    }
 }
 }  // namespace
 
@@ -1961,11 +2038,12 @@ cudaError_t launch_fallback(bool fp32, bool tr, bool disp, const KParams &p, int
     return cudaGetLastError();
 }
 
-cudaError_t round_to_float(const double *in, float *out, int64_t n, int num_sms, void *stream) {
+cudaError_t round_to_float(const double *in, float *out, float *lo, int64_t n, int num_sms,
+                           void *stream) {
     if (n <= 0) return cudaSuccess;
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, int64_t(num_sms) * 8);
     k_round_to_float<<<static_cast<int>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        in, out, n);
+        in, out, lo, n);
     return cudaGetLastError();
 }
 

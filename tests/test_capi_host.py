@@ -112,6 +112,8 @@ def test_round_to_float_rejects_bad_arguments(L):
     assert L.cher_round_to_float(None, None, 5, None) == 1
     assert L.cher_round_to_float(None, None, -1, None) == 1
     assert L.cher_round_to_float(None, None, 0, None) == 0
+    assert L.cher_split_to_float(None, None, None, 5, None) == 1
+    assert L.cher_split_to_float(None, None, None, 0, None) == 0
 
 
 def test_dispersion_setter_rejects_a_missing_context(L):

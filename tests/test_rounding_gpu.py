@@ -54,3 +54,30 @@ def test_rounding_flushes_below_the_smallest_normal_and_keeps_nan():
     assert y[0] == 0.0 and y[1] == 0.0 and y[2] == 0.0
     assert np.signbit(y[1]) and not np.signbit(y[0])
     assert np.isnan(y[3]) and y[4] == np.inf and y[5] == -np.inf
+
+
+def test_split_is_the_nearest_float_pair():
+    """hi is the rounding above; lo is the float nearest to x - hi (computed
+    here in FP64, where x - hi is exact), so hi + lo holds x to ~2^-48."""
+    import torch
+    from paper_2006_14927_gb300._binding import split_to_float
+    rng = np.random.default_rng(11)
+    # the magnitudes the FP32 path splits (heights above h_obs, times before
+    # the front), exact ties, and values whose hi rounds up across a power of two
+    x = np.concatenate([rng.uniform(-1e5, 1e5, 200_000), rng.uniform(0, 6e4, 200_000),
+                        rng.normal(0, 1, 100_000) * 10.0 ** rng.uniform(-20, 20, 100_000),
+                        np.nextafter(np.float64(2.0) ** np.arange(-30, 30), 0.0),
+                        np.array([0.0, -0.0, 1.0, 3.0, -1e-30])])
+    xt = torch.as_tensor(x, device="cuda")
+    hi, lo = split_to_float(xt)
+    hi, lo = hi.cpu().numpy(), lo.cpu().numpy()
+    assert np.array_equal(hi.view(np.int32), xt.to(torch.float32).cpu().numpy().view(np.int32))
+    r = x - hi.astype(np.float64)
+    want = r.astype(np.float32)
+    normal = (np.abs(want) >= np.float32(2.0 ** -126)) | (want == 0)
+    assert normal.sum() > 490_000
+    bad = np.nonzero((lo != want) & normal)[0]
+    assert bad.size == 0, (x[bad[:5]], lo[bad[:5]], want[bad[:5]])
+    big = np.abs(x) > 1.0
+    err = np.abs(x - (hi.astype(np.float64) + lo.astype(np.float64)))
+    assert np.all(err[big] <= np.abs(x[big]) * 2.0 ** -47)

@@ -96,3 +96,38 @@ def test_noalloc_refuses_oversized_input():
                                                    ctypes.byref(o), None)
     assert code == 5                        # CHER_ERANGE
     ctx.close()
+
+
+def test_noalloc_refuses_an_active_fallback():
+    """With the beyond-table fallback active the regular entry point queues
+    the bunches past the tables' zenith range in memory the context
+    allocates and integrates them; the allocation-free call cannot, so it
+    refuses the context (CHER_EINVAL) before anything is launched, and
+    serves it again once the fallback is switched off."""
+    import torch
+    P.build()
+    sc = workloads.inclined_20tev(n=20_011)
+    sc["H"], sc["Z"], sc["theta_max_deg"] = 200, 32, 61.0
+    ctx = context(sc)
+    prec = FP32
+    dev = P.device_tracks(host_tracks(sc, prec), prec, t_ref=sc["t_ref"])
+    ctx.set_fallback(80.0)
+    ref_stats, _ = _run(ctx, dev, prec, 200_000, noalloc=False)
+    assert ref_stats[12] > 0                # the fallback propagated some bunches
+    out = ctx.alloc_hits(200_000, prec)
+    out.stats.fill_(7)                      # a launch would clear these
+    out.count.fill_(7)
+    t = ctx.tracks_struct(dev)
+    o = out.struct()
+    code = P.lib().cher_generate_propagate_noalloc(
+        ctx._h, ctypes.byref(t), ctypes.c_uint64(SEED), int(prec), ctypes.byref(o),
+        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert code == 1                        # CHER_EINVAL
+    torch.cuda.synchronize()
+    assert bool((out.stats == 7).all()) and bool((out.count == 7).all())
+    ctx.set_fallback(0.0)                   # off: served again, same as the regular call
+    ref_stats, ref = _run(ctx, dev, prec, 200_000, noalloc=False)
+    stats, rec = _run(ctx, dev, prec, 200_000, noalloc=True)
+    assert np.array_equal(stats, ref_stats)
+    assert np.array_equal(rec["key"], ref["key"])
+    ctx.close()
