@@ -206,3 +206,54 @@ def test_autograd_function(case):
         np.testing.assert_allclose(tracks[k].grad.cpu().numpy(), g, rtol=1e-9,
                                    atol=1e-12 * np.abs(g).max())
     ctx.close()
+
+
+# the largest deviations from the oracle's dual-number gradient, per
+# precision (read by a script that runs this file; pytest checks the bounds)
+MEASURED = {}
+# bounds on those deviations, relative to the largest gradient of each kind:
+# the FP64 recomputation is the oracle's arithmetic to rounding (measured
+# ~1e-13); the FP32 recomputation keeps FP32 directions and ground points,
+# whose rounding (~1e-7 rad over ~6 km, ~1e-3 m against a 1 m Gaussian)
+# leaves ~1e-5 of the largest gradient (measured 1.2e-5 for the atmosphere,
+# 4.4e-5 for the steps), inside the 1e-4 the adjoint is held to.  Finite
+# differences cannot check either that tightly (their own error is ~1e-4 at
+# steps that keep the azimuth basis and table cells smooth).
+DUAL_TOL = {FP64: dict(atm=1e-10, steps=1e-10), FP32: dict(atm=1e-4, steps=1e-4)}
+
+
+@pytest.fixture(scope="module")
+def dual_reference(case):
+    """The oracle's forward-mode dual-number gradient of the whole workload
+    (FP64, the table variant), for each precision's own track values."""
+    sc, gD, gT, M = case
+    ref = {}
+    for prec in (FP64, FP32):
+        ctx, tr, dev, nb = _gpu(sc, prec)
+        nbh = nb.cpu().numpy()
+        ref[prec] = (M.density_grad(tr, SEED, nbh, SIGMA, gD, gT), nbh)
+        ctx.close()
+    return ref
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_adjoint_vs_oracle_dual_gradient(case, dual_reference, prec):
+    """Every gradient of the adjoint against the oracle's dual numbers: the
+    15 atmosphere entries, and all six gradients of every step, each kind
+    relative to its largest entry."""
+    sc, gD, gT, M = case
+    (S_o, U_o, ga_o, gs_o), nbh = dual_reference[prec]
+    ctx, tr, dev, nb = _gpu(sc, prec)
+    assert np.array_equal(nb.cpu().numpy(), nbh)
+    ga, gt = ctx.adjoint(dev, SEED, prec, gD, gT, SIGMA, nb)
+    ga, gt = ga.cpu().numpy(), gt.cpu().numpy()
+    ctx.close()
+    assert np.all(ga[0:5] == 0.0) and np.all(ga_o[0:5] == 0.0)
+    e_atm = float(np.max(np.abs(ga - ga_o)) / np.max(np.abs(ga_o)))
+    e_steps = [float(np.max(np.abs(gt[m] - gs_o[m])) / np.max(np.abs(gs_o[m])))
+               for m in range(6)]
+    MEASURED[prec] = dict(atm=e_atm, steps=e_steps,
+                          atm_each=((ga - ga_o) / np.where(ga_o != 0, np.abs(ga_o), 1)).tolist())
+    tol = DUAL_TOL[prec]
+    assert e_atm <= tol["atm"], e_atm
+    assert max(e_steps) <= tol["steps"], e_steps

@@ -12,12 +12,15 @@ import pytest
 import oracle
 import paper_2006_14927_gb300 as P
 import workloads
-from parity import (FP32, FP64, compare_hits, compare_trace, compare_yield, context, gpu_hits,
-                    gpu_trace, host_tracks, oracle_model)
+from parity import (FP32, FP64, borderline_status, compare_hits, compare_trace, compare_yield,
+                    context, gpu_hits, gpu_trace, host_tracks, oracle_model, sphere_distance,
+                    trace_blocks)
 
 pytestmark = pytest.mark.gpu
 
 SEED = 0x5EED_1234_ABCD
+# the largest errors of the full-size run (read by a script that runs it)
+MEASURED = {}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -189,7 +192,7 @@ def test_full_size_vertical_shower_sampled():
     dev = P.device_tracks(tr, FP32, t_ref=sc["t_ref"])
     nb_g, w_g = ctx.segment_yield(dev, FP32)
     nb_o, w_o, _, _ = M.segment_yield(tr)
-    compare_yield(nb_o, nb_g.cpu().numpy(), w_o, w_g.cpu().numpy(), FP32)
+    dw_max = compare_yield(nb_o, nb_g.cpu().numpy(), w_o, w_g.cpu().numpy(), FP32)
     out = ctx.alloc_hits(2_000_000, FP32)
     ctx.generate_propagate(dev, SEED, FP32, out)
     code, stats = ctx.sync_status(out)
@@ -219,6 +222,9 @@ def test_full_size_vertical_shower_sampled():
         got += r["n_common"]
     assert got > 0
     torch.cuda.synchronize()
+    tb = trace_blocks(M, ctx, tr, sc["t_ref"], SEED, FP32, rng)
+    assert tb["n"] > 100_000
+    MEASURED["vertical_1tev"] = dict(tb, max_dw_yield_all_steps=dw_max)
     ctx.close()
 
 
@@ -292,4 +298,91 @@ def test_fp32_yield_screen_exact_at_integer_and_threshold_edges():
     # and the fused kernel generates exactly that many bunches
     code, stats, _ = gpu_hits(ctx, tr, sc["t_ref"], SEED, FP32, 16)
     assert int(stats[3]) == int(nb_o.sum())
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_overflow_writes_nothing_past_the_buffers(prec):
+    """Capacity overflow with canary words: every record buffer sits inside a
+    larger allocation filled with a canary pattern.  After a launch whose
+    telescopes overflow, the slots past each telescope's stored count and
+    the words after the last telescope still hold the canary, and every
+    stored record is a crossing of its own telescope in the oracle (a write
+    past telescope k's capacity would land in telescope k + 1's slots with a
+    key that does not cross k + 1)."""
+    import torch
+    sc = _reduced(workloads.vertical_1tev(n=4_001), 4_001)
+    M = oracle_model(sc)
+    ctx = context(sc)
+    tr = host_tracks(sc, prec)
+    o = M.bunches(tr, SEED)
+    orec = oracle.hit_records(o)
+    dist = sphere_distance(M, o)
+    tol = 0.05 if prec == FP32 else 1e-6
+    near = np.any(np.abs(dist) < tol, axis=1) | borderline_status(M, o, prec)
+    seg_key = (o["seg"].astype(np.uint64) << np.uint64(32)) | o["j"].astype(np.uint64)
+    near_keys = set(seg_key[near].tolist())
+    crossing = set(zip(orec["tel"].tolist(), orec["key"].tolist()))
+    # a capacity between the telescopes' counts: some overflow, some do not
+    _, _, full = gpu_hits(ctx, tr, sc["t_ref"], SEED, prec, 100_000)
+    c_full = np.sort(full.count.cpu().numpy())
+    n_tel, tail = ctx.n_tel, 4096
+    cap = int(max(1, c_full[n_tel // 2]))
+    dt = torch.float32 if prec == FP32 else torch.float64
+    CAN = -12345.0
+    big = {k: torch.full((n_tel * cap + tail, 4), CAN, dtype=dt, device="cuda")
+           for k in ("pos", "tim")}
+    bigkey = torch.full((n_tel * cap + tail,), -7, dtype=torch.int64, device="cuda")
+    out = P.HitBuffers(pos=big["pos"][:n_tel * cap].view(n_tel, cap, 4),
+                       tim=big["tim"][:n_tel * cap].view(n_tel, cap, 4),
+                       key=bigkey[:n_tel * cap].view(n_tel, cap),
+                       count=torch.zeros(n_tel, dtype=torch.int64, device="cuda"),
+                       stats=torch.zeros(P.NSTATS, dtype=torch.int64, device="cuda"),
+                       cap=cap, precision=prec)
+    dev = P.device_tracks(tr, prec, t_ref=sc["t_ref"])
+    ctx.generate_propagate(dev, SEED, prec, out)
+    code, stats = ctx.sync_status(out)
+    cnt = out.count.cpu().numpy()
+    assert code == 6 and stats[10] == np.maximum(cnt - cap, 0).sum() > 0
+    assert (cnt > cap).sum() >= 3 and (cnt < cap).sum() >= 3   # both kinds present
+    pos = big["pos"].cpu().numpy()
+    tim = big["tim"].cpu().numpy()
+    key = bigkey.cpu().numpy()
+    assert np.all(pos[n_tel * cap:] == CAN) and np.all(tim[n_tel * cap:] == CAN)
+    assert np.all(key[n_tel * cap:] == -7)
+    for k in range(n_tel):
+        stored = int(min(cnt[k], cap))
+        sl = slice(k * cap + stored, (k + 1) * cap)
+        assert np.all(pos[sl] == CAN) and np.all(tim[sl] == CAN) and np.all(key[sl] == -7)
+        for r in range(k * cap, k * cap + stored):
+            kk = int(key[r]) & 0xFFFFFFFFFFFFFFFF
+            assert (k, kk) in crossing or kk in near_keys, (k, hex(kk))
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_library_refuses_steps_past_its_bunch_limit(prec):
+    """The per-tile bunch scan runs in 32-bit integers, so the library counts
+    a step of 2^22 bunches or more as invalid (stats[INVALID]) and emits
+    nothing for it.  The oracle has no such limit: it gives that step
+    ceil(N / B) bunches; every other step still matches it exactly."""
+    sc = workloads.plain_fp64(n=300)
+    ctx = context(sc)
+    M = oracle_model(sc)
+    tr = host_tracks(sc, prec)
+    tr["len"][17] = 3.0e6                   # ~1.3e8 photons: past 2^22 bunches
+    tr["z0"][17] = 1.0e4 + 1.5e6 * 1e-6     # midpoint at 10 km
+    tr["uz"][17] = -1e-6 if prec == FP64 else float(np.float32(-1e-6))
+    tr["ekin"][17] = 1000.0
+    nb_o, w_o, _, valid_o = M.segment_yield(tr)
+    assert valid_o[17] and nb_o[17] >= 2 ** 22
+    dev = P.device_tracks(tr, prec, t_ref=sc["t_ref"])
+    nb_g, w_g = ctx.segment_yield(dev, prec)
+    nb_g = nb_g.cpu().numpy()
+    assert nb_g[17] == 0
+    keep = np.arange(len(nb_o)) != 17
+    compare_yield(nb_o[keep], nb_g[keep], w_o[keep], w_g.cpu().numpy()[keep], prec)
+    code, stats, _ = gpu_hits(ctx, tr, sc["t_ref"], SEED, prec, 4096)
+    assert code == 0
+    assert stats[2] == 1 and stats[3] == nb_o[keep].sum()
     ctx.close()
