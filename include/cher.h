@@ -54,7 +54,9 @@ typedef enum cher_status {
     CHER_ESTATE = 4,     /* refraction tables not built yet                 */
     CHER_ERANGE = 5,     /* a size exceeds what the library supports        */
     CHER_EOVERFLOW = 6,  /* a telescope buffer ran out of capacity          */
-    CHER_ETIMEOUT = 7    /* a bounded device-side wait gave up              */
+    CHER_ETIMEOUT = 7,   /* a bounded device-side wait gave up              */
+    CHER_EBOUNDS = 8     /* bounds-checked build only: a kernel index check
+                            failed (stats[CHER_STAT_DEBUG] says which)      */
 } cher_status;
 
 /* Text for a status code (static storage, never NULL). */
@@ -163,8 +165,17 @@ enum {
     CHER_STAT_OVERFLOW = 10,    /* crossings not stored (buffer full)       */
     CHER_STAT_ABSORBED = 11,    /* reached h_obs, lost to the transmission  */
     CHER_STAT_FALLBACK = 12,    /* propagated by the beyond-table fallback  */
-    CHER_STAT_FB_LOST = 13      /* past the tables' range, the fallback     */
+    CHER_STAT_FB_LOST = 13,     /* past the tables' range, the fallback     */
                                 /* queue full: not propagated              */
+    CHER_STAT_DEBUG = 14        /* bounds-checked build (compiled with      */
+                                /* CHER_DEBUG) only: bit mask of the index  */
+                                /* checks that failed (1 fine eta table, 2  */
+                                /* refraction tables, 4 grid and candidates, */
+                                /* 8 record buffers, 16 trace arrays, 32    */
+                                /* shared step constants and offsets, 64    */
+                                /* fallback queue); the access is skipped   */
+                                /* (index 0 taken instead), nothing traps.  */
+                                /* Always 0 in the regular build.           */
 };
 
 /* Per-telescope output buffers (device).  Telescope k owns records
@@ -347,7 +358,8 @@ cher_status cher_graph_launch(cher_graph *graph, void *stream);
 /* Release the graph (NULL is accepted). */
 cher_status cher_graph_destroy(cher_graph *graph);
 
-/* Synchronise `stream`, read out->stats and report CHER_EOVERFLOW if a
+/* Synchronise `stream`, read out->stats and report CHER_EBOUNDS if an index
+ * check of the bounds-checked build failed, else CHER_EOVERFLOW if a
  * telescope buffer overflowed during the last call, else CHER_OK (or
  * CHER_ECUDA if the stream reports an error).  stats_host (optional,
  * CHER_NSTATS entries) receives the counters. */

@@ -14,13 +14,15 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libcher.so")
+# CHER_DEBUG=1 selects the bounds-checked build (libcher_debug.so)
+LIB_PATH = os.path.join(_HERE, "libcher_debug.so" if os.environ.get("CHER_DEBUG", "") == "1"
+                        else "libcher.so")
 
 CHER_FP64 = 0
 CHER_FP32_BULK = 1
 NSTATS = 16
 STAT_NAMES = ["steps", "emitting", "invalid", "bunches", "upward", "below_obs", "above_max",
-              "angle", "ground", "hits", "overflow", "absorbed", "fallback", "fb_lost"]
+              "angle", "ground", "hits", "overflow", "absorbed", "fallback", "fb_lost", "debug"]
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
                 4: "tables not built", 5: "out of range", 6: "overflow", 7: "timeout"}
 

@@ -422,6 +422,7 @@ const char *cher_status_string(cher_status s) {
     case CHER_ERANGE: return "size out of supported range";
     case CHER_EOVERFLOW: return "telescope buffer overflow";
     case CHER_ETIMEOUT: return "device wait timed out";
+    case CHER_EBOUNDS: return "a device index check failed (bounds-checked build)";
     }
     return "unknown status";
 }
@@ -997,6 +998,7 @@ cher_status cher_sync_status(cher_ctx *c, const cher_output *out, unsigned long 
     if (cudaMemcpy(st, out->stats, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess)
         return CHER_ECUDA;
     if (stats_host) std::memcpy(stats_host, st, sizeof(st));
+    if (st[CHER_STAT_DEBUG]) return CHER_EBOUNDS;
     return st[CHER_STAT_OVERFLOW] ? CHER_EOVERFLOW : CHER_OK;
 }
 
@@ -1029,6 +1031,7 @@ cher_status cher_trace_bunches(cher_ctx *c, const cher_tracks *t, uint64_t seed,
     p.tim = out->tim;
     p.bunch_off = bunch_off;
     p.t_status = out->status;
+    p.t_nbunch = out->n_bunches;
     p.t_nhit = out->nhit;
     p.t_first = out->first_hit;
     return launch(c, p, fp32, cher::MODE_TRACE, false, stream);

@@ -106,6 +106,27 @@ __device__ __forceinline__ void d2f_split(double d, float &hi, float &lo) {
     lo = (h & 0x80000000u) ? -a : a;
 }
 
+// The bounds-checked build (compiled with CHER_DEBUG): an index about to be
+// used is checked against its array; a bad one sets `bit` in
+// stats[CHER_STAT_DEBUG] and is replaced by 0, so the access stays inside
+// the array and nothing traps.  The regular build compiles the check away.
+template <class I>
+__device__ __forceinline__ I dbg_index(const KParams &p, I i, int64_t n, unsigned bit) {
+#ifdef CHER_DEBUG
+    if (i < 0 || static_cast<int64_t>(i) >= n) {
+        if (p.stats) atomicOr(p.stats + CHER_STAT_DEBUG, static_cast<unsigned long long>(bit));
+        return I(0);
+    }
+#else
+    (void)p;
+    (void)n;
+    (void)bit;
+#endif
+    return i;
+}
+enum : unsigned { DBG_ETA = 1u, DBG_TAB = 2u, DBG_GRID = 4u, DBG_OUT = 8u, DBG_TRACE = 16u,
+                  DBG_SMEM = 32u, DBG_FB = 64u };
+
 __device__ __forceinline__ double eta_exact_lookup(const KParams &p, double h) {
     double hc = h;
     if (hc < 0.0) hc = 0.0;
@@ -114,6 +135,7 @@ __device__ __forceinline__ double eta_exact_lookup(const KParams &p, double h) {
     int k = static_cast<int>(x);
     if (k > p.n_fine - 2) k = p.n_fine - 2;
     const double f = __dsub_rn(x, static_cast<double>(k));
+    k = dbg_index(p, k, p.n_fine - 1, DBG_ETA);
     const double t0 = __ldg(p.eta64 + k), t1 = __ldg(p.eta64 + k + 1);
     const double d = __dsub_rn(t1, t0);
     const double fd = __dmul_rn(f, d);

@@ -122,6 +122,7 @@ struct KParams {
     // trace mode
     const int64_t *bunch_off;
     int32_t *t_status, *t_nhit, *t_first;
+    int64_t t_nbunch;                     // entries of the trace arrays
     // yield-only mode
     int32_t *y_nb;
     double *y_w;

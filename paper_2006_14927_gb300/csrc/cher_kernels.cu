@@ -123,6 +123,7 @@ __device__ __forceinline__ void step_yield_screened(const KParams &p, bool other
     const float x = hc * p.f.inv_dh;
     int k = static_cast<int>(x);
     k = k > p.n_fine - 2 ? p.n_fine - 2 : k;
+    k = dbg_index(p, k, p.n_fine - 1, DBG_ETA);
     const float f = x - static_cast<float>(k);
     const float t0 = __ldg(p.eta32 + k), t1 = __ldg(p.eta32 + k + 1);
     const float eta = t0 + f * (t1 - t0);
@@ -296,6 +297,7 @@ __device__ __forceinline__ void step_yield_screened_disp(const KParams &p, bool 
     const float x = hc * p.f.inv_dh;
     int k = static_cast<int>(x);
     k = k > p.n_fine - 2 ? p.n_fine - 2 : k;
+    k = dbg_index(p, k, p.n_fine - 1, DBG_ETA);
     const float f = x - static_cast<float>(k);
     const float t0 = __ldg(p.eta32 + k), t1 = __ldg(p.eta32 + k + 1);
     const float eta = t0 + f * (t1 - t0);
@@ -699,6 +701,7 @@ __device__ __forceinline__ R eta_at(const KParams &p, const Consts<R> &c, R h) {
     x = x < R(0) ? R(0) : x;
     int k = static_cast<int>(x);
     k = k > c.n_fine - 2 ? c.n_fine - 2 : k;
+    k = dbg_index(p, k, p.n_fine - 1, DBG_ETA);
     const R f = x - static_cast<R>(k);
     R t0, t1;
     if constexpr (std::is_same<R, float>::value) {
@@ -929,8 +932,9 @@ __device__ __forceinline__ void propagate_curved(const KParams &p, const Consts<
     int kk = static_cast<int>(fk);
     kk = kk > c.Z - 2 ? c.Z - 2 : kk;
     const R b = fk - static_cast<R>(kk);
-    const size_t e0 = static_cast<size_t>(jj) * (c.Z - 1) + kk;
-    const size_t e1 = e0 + (c.Z - 1);
+    const size_t e0 = dbg_index(p, static_cast<size_t>(jj) * (c.Z - 1) + kk,
+                                int64_t(c.H - 1) * (c.Z - 1), DBG_TAB);
+    const size_t e1 = dbg_index(p, e0 + (c.Z - 1), int64_t(c.H) * (c.Z - 1), DBG_TAB);
     R v[2][6];                  // rows jj, jj + 1: ax_k, al_k, ax_k1, al_k1, ag_k, ag_k1
     if constexpr (std::is_same<R, float>::value) {
         const float4 *T = static_cast<const float4 *>(DS ? p.tabd : p.tab);
@@ -1175,8 +1179,9 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
     R Ax, Al;
     if constexpr (DS) {
         // the tables of the band's two ends, linear in kappa
-        const size_t e0 = static_cast<size_t>(jj) * (c.Z - 1) + kk;
-        const size_t e1 = e0 + (c.Z - 1);
+        const size_t e0 = dbg_index(p, static_cast<size_t>(jj) * (c.Z - 1) + kk,
+                                    int64_t(c.H - 1) * (c.Z - 1), DBG_TAB);
+        const size_t e1 = dbg_index(p, e0 + (c.Z - 1), int64_t(c.H) * (c.Z - 1), DBG_TAB);
         if constexpr (std::is_same<R, float>::value) {
             const float wk = (o.kap - p.f.kap_lo) * p.f.kap_winv;
             const float4 *T = static_cast<const float4 *>(p.tabd);
@@ -1211,8 +1216,8 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
         }
     } else {
         // (H <= 65536, Z <= 4096: the entry index fits 32 bits)
-        const int e0 = jj * (c.Z - 1) + kk;
-        const int e1 = e0 + (c.Z - 1);
+        const int e0 = dbg_index(p, jj * (c.Z - 1) + kk, int64_t(c.H - 1) * (c.Z - 1), DBG_TAB);
+        const int e1 = dbg_index(p, e0 + (c.Z - 1), int64_t(c.H) * (c.Z - 1), DBG_TAB);
         if constexpr (std::is_same<R, float>::value) {
             const float4 *T = static_cast<const float4 *>(p.tab);
             const float4 t0 = __ldg(T + e0), t1 = __ldg(T + e1);
@@ -1297,15 +1302,18 @@ __device__ __forceinline__ unsigned sphere_hits(const KParams &p, const Consts<R
     if (static_cast<unsigned>(ix) >= static_cast<unsigned>(nx) ||
         static_cast<unsigned>(iy) >= static_cast<unsigned>(ny))
         return 0u;
-    const int cell = iy * nx + ix;
+    const int cell = dbg_index(p, iy * nx + ix, int64_t(nx) * ny, DBG_GRID);
     unsigned mask = 0u;
     if constexpr (std::is_same<R, float>::value) {
+        // (the first entry and the count packed in one word measured slower
+        // than the two neighbouring starts)
         const int32_t *cs = g ? p.grid[1].cell_start : p.grid[0].cell_start;
         const float4 *cd = static_cast<const float4 *>(g ? p.grid[1].cand32 : p.grid[0].cand32);
         s0 = __ldg(cs + cell);
         const int s1 = __ldg(cs + cell + 1);
         for (int m = s0; m < s1; ++m) {
-            const float4 T = __ldg(cd + m);
+            const float4 T = __ldg(cd + dbg_index(p, m, g ? p.grid[1].n_cand : p.grid[0].n_cand,
+                                                  DBG_GRID));
             const float dx = T.x - o.X, dy = T.y - o.Y, dz = CV ? T.z - o.zg : T.z;
             const float q0 = dy * o.cz - dz * o.cy;
             const float q1 = dz * o.cx - dx * o.cz;
@@ -1318,7 +1326,8 @@ __device__ __forceinline__ unsigned sphere_hits(const KParams &p, const Consts<R
         const int s1 = __ldg(cs + cell + 1);
         const double2 *T = static_cast<const double2 *>(g ? p.grid[1].cand64 : p.grid[0].cand64);
         for (int m = s0; m < s1; ++m) {
-            const double2 A = __ldg(T + 2 * m), B = __ldg(T + 2 * m + 1);
+            const int mc = dbg_index(p, m, g ? p.grid[1].n_cand : p.grid[0].n_cand, DBG_GRID);
+            const double2 A = __ldg(T + 2 * mc), B = __ldg(T + 2 * mc + 1);
             const double dx = A.x - o.X, dy = A.y - o.Y, dz = CV ? B.x - o.zg : B.x;
             const double q0 = dy * o.cz - dz * o.cy;
             const double q1 = dz * o.cx - dx * o.cz;
@@ -1407,7 +1416,10 @@ __device__ __forceinline__ void record_hits(const KParams &p, const BunchOut<R> 
         if (hm) {
             const int bit = __ffs(hm) - 1;
             hm &= hm - 1u;
-            tel = cand_info<R>(p, gsel, s0 + bit, tx, ty, tz);
+            tel = cand_info<R>(p, gsel,
+                               dbg_index(p, s0 + bit, gsel ? p.grid[1].n_cand : p.grid[0].n_cand,
+                                         DBG_GRID),
+                               tx, ty, tz);
             ++st_hits;
         }
         const unsigned grp = __match_any_sync(kFull, tel);
@@ -1424,7 +1436,9 @@ __device__ __forceinline__ void record_hits(const KParams &p, const BunchOut<R> 
                 uint64_t key;
                 weight_key(w, key, lam, tg);   // only on the (rare) hit path
                 const R sl = (tz - o.zg) / o.cz;   // to the plane through the centre
-                const int64_t r = static_cast<int64_t>(tel) * p.cap + static_cast<int64_t>(slot);
+                const int64_t r = dbg_index(p, static_cast<int64_t>(tel) * p.cap +
+                                                   static_cast<int64_t>(slot),
+                                            int64_t(p.n_tel) * p.cap, DBG_OUT);
                 store4<R>(p.pos, r, o.X + sl * o.cx - tx, o.Y + sl * o.cy - ty, o.cx, o.cy);
                 store4<R>(p.tim, r, tg + sl * np1o * R(1.0 / kC), o.he, w, lam);
                 p.key[r] = key;
@@ -1632,6 +1646,7 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             o.zg = R(0);
             int j = 0;
             if (live) {
+                s = dbg_index(p, s, BLOCK, DBG_SMEM);
                 j = bidx - off[s];
                 constexpr bool kLazy = MODE == MODE_HITS && !TR && FB == 0 && !DS && !CV;
                 bunch<R, TR, FB, DS, CV, kLazy>(p, c, seg[s], DS ? segd + s : nullptr, j, o);
@@ -1682,7 +1697,8 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
                         const int64_t gstep = p.track_base + base + s;
                         e.key = (static_cast<uint64_t>(gstep) << 32) | static_cast<uint32_t>(j);
                         e.step_hi = static_cast<uint32_t>(static_cast<uint64_t>(gstep) >> 32);
-                        static_cast<FbEntry<R> *>(p.fb_list)[at] = e;
+                        static_cast<FbEntry<R> *>(p.fb_list)[dbg_index(
+                            p, static_cast<int64_t>(at), p.fb_cap, DBG_FB)] = e;
                     }
                 }
             }
@@ -1691,7 +1707,8 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
             if constexpr (MODE == MODE_TRACE) {
                 st_hits += __popc(hm);
                 if (live) {
-                    const int64_t gb = __ldg(p.bunch_off + base + s) + j;
+                    const int64_t gb =
+                        dbg_index(p, __ldg(p.bunch_off + base + s) + j, p.t_nbunch, DBG_TRACE);
                     const R w = seg[s].w;
                     if (o.status == ST_GROUND) {
                         store4<R>(p.pos, gb, o.X, o.Y, o.cx, o.cy);
@@ -1786,7 +1803,8 @@ __global__ void __launch_bounds__(128) k_fallback(const KParams p) {
         R w = R(0);
         uint64_t key = 0;
         if (live) {
-            const FbEntry<R> E = static_cast<const FbEntry<R> *>(p.fb_list)[e];
+            const FbEntry<R> E =
+                static_cast<const FbEntry<R> *>(p.fb_list)[dbg_index(p, e, p.fb_cap, DBG_FB)];
             R D, L;
             if constexpr (std::is_same<R, float>::value)
                 ray_integrals_f(p, E.dh, E.s_obs, E.c2, DS ? E.kap : 1.0f, D, L);
