@@ -96,9 +96,9 @@ FP64_FMA_PER_SM_CLK = 2         # GB300: 1/64 of the FP32 rate (ncu: 2 DFMA/cycl
 # by its steps (the inputs, 64 B per step, dominate and scale with them).
 # Reported only while the kernel sources hash to what was profiled.
 TRAFFIC_PER_STEP = {
-    "vertical_1tev": (76.72, "efb7faad3856229f"),      # 128.51 + 24.93 MB at 2e6 steps
-    "inclined_20tev": (70.28, "efb7faad3856229f"),     # 129.73 + 10.84 MB at 2e6 steps
-    "batched_256": (72.04, "efb7faad3856229f"),        # 128.75 + 15.32 MB at 2e6 steps
+    "vertical_1tev": (76.72, "7320173fe4ca0c8a"),      # 128.51 + 24.93 MB at 2e6 steps
+    "inclined_20tev": (70.28, "7320173fe4ca0c8a"),     # 129.73 + 10.84 MB at 2e6 steps
+    "batched_256": (72.04, "7320173fe4ca0c8a"),        # 128.75 + 15.32 MB at 2e6 steps
 }
 KERNEL_SOURCES = ("cher_kernels.cu", "cher_device.cuh", "cher_internal.h")
 

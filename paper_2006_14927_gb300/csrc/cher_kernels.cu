@@ -2,8 +2,10 @@
 // of track steps, in FP64 and in FP32-bulk precision.
 //
 // A CTA owns a tile of `BLOCK` consecutive steps:
-//   phase A  one thread per step: Cherenkov yield in FP64 (CERENK, paper
-//            section 3.2), bunch count nb = ceil(N / B), per-step constants
+//   phase A  one thread per step: Cherenkov yield (CERENK, paper section
+//            3.2; the FP32 path screens it in FP32 and takes the FP64 chain
+//            wherever the count or the photons per bunch would not be
+//            certain), bunch count nb = ceil(N / B), per-step constants
 //            staged in shared memory; a CTA-wide exclusive scan of nb gives
 //            every bunch of the tile a slot;
 //   phase B  the CTA's threads stride over the tile's bunches (the paper's
