@@ -377,15 +377,21 @@ class Bench:
         return dict(ms=ms, wall=wall, stats=stats, code=code)
 
 
-def workload_leg(P, dev, wl, scale, cap_arg, steps, warmup, launch, sm_count, mhz, barrier):
-    """One more workload in the same run: FP32 (the autotuned shape of the
-    main workload, regular launches) and FP64, each with its roofline."""
+def workload_leg(P, dev, wl, scale, cap_arg, steps, warmup, launch, main_launch, sm_count, mhz,
+                 barrier):
+    """One more workload in the same run: FP32 (its own autotuned launch
+    shape, or the one given; regular launches) and FP64 (the main workload's
+    shape), each with its roofline."""
     import torch
     sc, tb = _make_workload(wl, scale, 0)
     B = Bench(P, dev, sc, wl, scale, _cap(wl, scale, cap_arg), tb, barrier)
-    r32 = B.measure(P.CHER_FP32_BULK, steps, warmup, launch=launch)
+    if launch is None:
+        dtr, out = B.buffers(P.CHER_FP32_BULK)
+        B.ctx.autotune(dtr, 11, P.CHER_FP32_BULK, out)
+    own = launch if launch is not None else B.ctx.get_launch()
+    r32 = B.measure(P.CHER_FP32_BULK, steps, warmup, launch=own)
     B.release(P.CHER_FP32_BULK)
-    r64 = B.measure(P.CHER_FP64, max(3, steps // 4), 3, launch=launch)
+    r64 = B.measure(P.CHER_FP64, max(3, steps // 4), 3, launch=main_launch)
     B.release(P.CHER_FP64)
     n = B.n
     b32, b64 = float(r32["stats"][3]), float(r64["stats"][3])
@@ -398,6 +404,7 @@ def workload_leg(P, dev, wl, scale, cap_arg, steps, warmup, launch, sm_count, mh
                     "roofline": fp64_roofline(b64, n, ms64, sm_count, mhz)},
            "fp32_over_fp64": (b32 / ms32) / (b64 / ms64),
            "overflowed_records": int(r32["stats"][10]), "table_build_s": B.table_s,
+           "launch": {"block": own[0], "ctas_per_sm": own[1]},
            "workload": WORKLOAD_TEXT.get(wl, wl)}
     B.ctx.close()
     del B
@@ -512,7 +519,8 @@ def run_ours(args):
         del B, ctx
         torch.cuda.empty_cache()
         for other in ("inclined_20tev", "vertical_1tev"):
-            legs[other] = workload_leg(P, dev, other, 1.0, None, steps, warmup, launch,
+            given = tuple(int(v) for v in args.launch.split(",")) if args.launch else None
+            legs[other] = workload_leg(P, dev, other, 1.0, None, steps, warmup, given, launch,
                                        sm_count, mhz, barrier)
     if rank != 0:
         if world > 1:

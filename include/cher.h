@@ -367,10 +367,12 @@ cher_status cher_sync_status(cher_ctx *ctx, const cher_output *out,
                              unsigned long long *stats_host, void *stream);
 
 /* Launch shape of cher_generate_propagate.  block_threads in {128, 256,
- * 512} is also the number of steps per tile; ctas_per_sm in 1..8 sets the
- * persistent grid (0 = one CTA per tile, no persistence).  A new context
- * starts at 128 / 8 (the shape cher_autotune settles on for the FP32 path on
- * GB300: 32 resident warps per SM); cher_autotune replaces it.  Errors:
+ * 512} is also the number of steps per tile; ctas_per_sm in 0..10 sets the
+ * persistent grid (0 = one CTA per tile, no persistence; above 8 only with
+ * 128-step tiles in the FP32 path, which has builds for 9 and 10 CTAs per SM
+ * with fewer registers per thread; other launches cap at what fits).  A
+ * new context starts at 128 / 8 (32 resident warps per SM); cher_autotune
+ * measures the shapes on the caller's input and keeps the fastest.  Errors:
  * CHER_EINVAL. */
 cher_status cher_set_launch(cher_ctx *ctx, int32_t block_threads,
                             int32_t ctas_per_sm);

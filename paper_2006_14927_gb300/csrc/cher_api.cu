@@ -377,7 +377,8 @@ cher_status launch(cher_ctx *c, cher::KParams &p, bool fp32, int mode, bool pers
     p.n_tiles = (p.n + block - 1) / block;
     if (p.n_tiles == 0) return CHER_OK;
     const size_t smem = cher::kernel_smem_bytes(fp32, block, p);
-    const int kmode = cher::kernel_mode(mode, p);
+    const int kmode = cher::kernel_mode(mode, p) |
+                      (persistent ? cher::occupancy_bits(fp32, block, c->ctas_per_sm) : 0);
     if (cher::kernel_prepare(fp32, block, kmode, smem) != cudaSuccess) {
         cudaGetLastError();
         return CHER_ERANGE;
@@ -855,7 +856,7 @@ cher_status cher_destroy(cher_ctx *c) {
 cher_status cher_set_launch(cher_ctx *c, int32_t block_threads, int32_t ctas_per_sm) {
     if (!c) return CHER_EINVAL;
     if (block_threads != 128 && block_threads != 256 && block_threads != 512) return CHER_EINVAL;
-    if (ctas_per_sm < 0 || ctas_per_sm > 8) return CHER_EINVAL;
+    if (ctas_per_sm < 0 || ctas_per_sm > 10) return CHER_EINVAL;
     c->block = block_threads;
     c->ctas_per_sm = ctas_per_sm;
     return CHER_OK;
@@ -1105,7 +1106,7 @@ cher_status cher_autotune(cher_ctx *c, const cher_tracks *t, uint64_t seed, cher
         }
     }
     const int blocks[] = {128, 256, 512};
-    const int ctas[] = {0, 1, 2, 3, 4, 6, 8};
+    const int ctas[] = {0, 1, 2, 3, 4, 6, 8, 9, 10};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return CHER_ECUDA;
@@ -1115,7 +1116,10 @@ cher_status cher_autotune(cher_ctx *c, const cher_tracks *t, uint64_t seed, cher
     cher_status rc = CHER_OK;
     for (int b : blocks)
         for (int cps : ctas) {
-            if (b == 512 && cps > 4) continue;
+            if ((b == 512 && cps > 4) || (b == 256 && cps > 8)) continue;
+            // more than 8 CTAs per SM: the FP32 hits kernel's builds for 9 and
+            // 10 (other precisions and modes cap at what fits)
+            if (cps > 8 && (b != 128 || prec != CHER_FP32_BULK)) continue;
             c->block = b;
             c->ctas_per_sm = cps;
             float tsum = 0.0f;
@@ -1486,7 +1490,8 @@ extern "C" cher_status cher_generate_propagate_noalloc(cher_ctx *c, const cher_t
     p.n_tiles = (p.n + block - 1) / block;
     if (p.n_tiles == 0) return CHER_OK;
     const size_t smem = cher::kernel_smem_bytes(fp32, block, p);
-    const int kmode = cher::kernel_mode(cher::MODE_HITS, p);
+    const int kmode = cher::kernel_mode(cher::MODE_HITS, p) |
+                      cher::occupancy_bits(fp32, block, c->ctas_per_sm);
     if (cher::kernel_prepare(fp32, block, kmode, smem) != cudaSuccess) {
         cudaGetLastError();
         return CHER_ERANGE;

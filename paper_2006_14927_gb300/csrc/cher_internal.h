@@ -233,6 +233,15 @@ constexpr int kFbBit = 8;
 // only; the curved atmosphere without the beyond-table fallback)
 constexpr int kDispBit = 16;
 constexpr int kCurvBit = 32;
+// The plain FP32 hits kernel also comes in builds for more resident CTAs per
+// SM (128 threads each, fewer registers per thread): 9 or 10; the launch
+// shape's CTAs per SM picks one (kOccShift: 2 bits of the mode word).
+constexpr int kOccShift = 6;
+constexpr int kOccMask = 3 << kOccShift;
+inline int occupancy_bits(bool fp32, int block, int ctas_per_sm) {
+    if (!fp32 || block != 128 || ctas_per_sm <= 8) return 0;
+    return (ctas_per_sm <= 9 ? 1 : 2) << kOccShift;
+}
 constexpr int kDispBlock = 128;
 inline int kernel_mode(int mode, const KParams &p) {
     int m = mode;

@@ -1466,8 +1466,7 @@ __host__ __device__ constexpr size_t segd_offset() {
 
 // CV: a curved atmosphere (radial heights, spherical shells).
 template <class R, int BLOCK, int MODE, bool TR, int FB, bool DS, bool CV>
-__global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / BLOCK : 1)
-    k_gen_prop(const KParams p) {
+__device__ __forceinline__ void gen_prop(const KParams &p) {
     extern __shared__ __align__(16) unsigned char smem[];
     Seg<R> *seg = reinterpret_cast<Seg<R> *>(smem);
     int *off = reinterpret_cast<int *>(seg + BLOCK);          // BLOCK + 1
@@ -1780,6 +1779,23 @@ __global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / 
     }
 }
 
+// The kernels: every instantiation at the register budget of 1024 / BLOCK
+// threads per SM (FP32) or of one CTA (FP64), and the plain FP32 hits
+// instantiation also at 9 and 10 CTAs of 128 threads per SM (56 and 48
+// registers): more resident warps hide more of the table and grid load
+// latency, at the cost of a few spilled values (measured on GB300: -0.5 to
+// -3 % by workload; 12 CTAs at 40 registers spilled too much, +2 to +5 %).
+template <class R, int BLOCK, int MODE, bool TR, int FB, bool DS, bool CV>
+__global__ void __launch_bounds__(BLOCK, std::is_same<R, float>::value ? 1024 / BLOCK : 1)
+    k_gen_prop(const KParams p) {
+    gen_prop<R, BLOCK, MODE, TR, FB, DS, CV>(p);
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) k_gen_prop_occ(const KParams p) {
+    gen_prop<float, 128, MODE_HITS, false, 0, false, false>(p);
+}
+
 // ------------------------------------------------------------------------
 // The fallback pass: one thread per queued bunch (warps walk the queue 32
 // entries at a time so that the compaction stays warp-synchronous).
@@ -1937,6 +1953,12 @@ const void *pick(int block, bool tr, bool fb, bool ds, bool cv) {
 // instantiations with the transmission draw / the beyond-table fallback /
 // the wavelength-dependent index / the curved atmosphere
 const void *pick_kernel(bool fp32, int block, int mode) {
+    const int occ = (mode & kOccMask) >> kOccShift;
+    mode &= ~kOccMask;
+    if (occ && fp32 && block == 128 && mode == MODE_HITS) {
+        return occ == 1 ? reinterpret_cast<const void *>(&k_gen_prop_occ<9>)
+                        : reinterpret_cast<const void *>(&k_gen_prop_occ<10>);
+    }
     const bool tr = (mode & kTransBit) != 0;
     const bool fb = (mode & kFbBit) != 0;
     const bool ds = (mode & kDispBit) != 0;

@@ -88,13 +88,14 @@ def test_batched_showers_reduced():
 
 
 def test_launch_shapes_agree():
-    """Persistent and one-CTA-per-tile launches, every block size: the same
-    records (order inside a telescope aside)."""
+    """Persistent and one-CTA-per-tile launches, every block size and the
+    builds for 9 and 10 CTAs per SM: the same records (order inside a
+    telescope aside)."""
     sc = _reduced(workloads.vertical_1tev(n=5_000), 5_000)
     ctx = context(sc)
     tr = host_tracks(sc, FP32)
     ref = None
-    for launch in [(256, 3), (128, 0), (512, 1), (256, 8), (128, 5)]:
+    for launch in [(256, 3), (128, 0), (512, 1), (256, 8), (128, 5), (128, 9), (128, 10)]:
         code, stats, out = gpu_hits(ctx, tr, sc["t_ref"], SEED, FP32, 50_000, launch=launch)
         assert code == 0
         rec = out.records()
