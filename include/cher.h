@@ -316,9 +316,8 @@ cher_status cher_split_to_float(const double *in, float *hi, float *lo, int64_t 
                                 void *stream);
 
 /* The same hot path as cher_generate_propagate (same kernel, same results;
- * see below for the one configuration it refuses) for callers that must not allocate device memory when they run it: code
- * that runs while a stream of the process is being captured into a CUDA
- * graph in global mode (where cudaMalloc is refused), pipelines whose device
+ * see below for the one configuration it refuses) for callers that must
+ * not allocate device memory when they run it: pipelines whose device
  * memory is all held by another allocator (a framework's caching pool), and
  * real-time loops that forbid allocation after start-up.  The paper has no
  * counterpart.  The context must have been created and its tables built
@@ -327,7 +326,7 @@ cher_status cher_split_to_float(const double *in, float *hi, float *lo, int64_t 
  * counter, lives in a fixed 256-byte device array compiled into the library,
  * which every GPU that loads the library holds until the process exits.
  * The first call on each device looks the array's device address up (with
- * that device current), so make that first call before any stream capture.
+ * that device current).
  * Every call shares the array and clears the counter before its launch:
  * calls that overlap on the GPU (different streams, or several contexts)
  * race on it and must be serialised by the caller.  A step count above

@@ -1,8 +1,7 @@
 """cher_generate_propagate_noalloc against cher_generate_propagate.
 
 The no-alloc entry point serves callers that must not allocate device memory
-while they run the hot path (a stream of the process in global-mode graph
-capture, where cudaMalloc is refused; device memory held entirely by another
+while they run the hot path (device memory held entirely by another
 allocator; real-time loops that forbid allocation after start-up).  It runs
 the same kernel with its tile counter in a fixed array compiled into the
 library, so its records must equal the regular entry point's, on two calls in
