@@ -91,14 +91,14 @@ FP32_LANES_PER_SM = 128
 FP64_FMA_PER_SM_CLK = 2         # GB300: 1/64 of the FP32 rate (ncu: 2 DFMA/cycle/SM)
 
 # DRAM bytes (read + write) per step of one FP32 launch, from ncu captures
-# (dram__bytes_read.sum + dram__bytes_write.sum of the fused kernel, 128
-# threads x 8 CTAs per SM) of each workload at 2e6 steps, scaled to a launch
+# (dram__bytes_read.sum + dram__bytes_write.sum of the fused kernel, in the
+# launch shape the autotuner picks for the workload) at 2e6 steps, scaled to a launch
 # by its steps (the inputs, 64 B per step, dominate and scale with them).
 # Reported only while the kernel sources hash to what was profiled.
 TRAFFIC_PER_STEP = {
-    "vertical_1tev": (76.72, "7320173fe4ca0c8a"),      # 128.51 + 24.93 MB at 2e6 steps
-    "inclined_20tev": (70.28, "7320173fe4ca0c8a"),     # 129.73 + 10.84 MB at 2e6 steps
-    "batched_256": (72.04, "7320173fe4ca0c8a"),        # 128.75 + 15.32 MB at 2e6 steps
+    "vertical_1tev": (76.48, "edbec2f1e89f4e47"),      # 128.21 + 24.75 MB at 2e6 steps, 128 x 9
+    "inclined_20tev": (70.50, "edbec2f1e89f4e47"),     # 129.76 + 11.24 MB at 2e6 steps, 128 x 10
+    "batched_256": (72.33, "edbec2f1e89f4e47"),        # 128.75 + 15.91 MB at 2e6 steps, 128 x 10
 }
 KERNEL_SOURCES = ("cher_kernels.cu", "cher_device.cuh", "cher_internal.h")
 
