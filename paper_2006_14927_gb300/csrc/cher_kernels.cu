@@ -17,7 +17,9 @@
 //            single-search refactor of section 3.3.1 and the repeated-call
 //            hoisting of Algorithm 3), the ground point and arrival time
 //            (RAYBND, Appendix B listing), candidate spheres from the ground
-//            grid, and warp-aggregated compaction of the crossings (TELOUT).
+//            grid, and warp-aggregated compaction of the crossings (TELOUT;
+//            the plain FP32 path queues its crossings per warp and records
+//            them 32 at a time, see flush_ring).
 // In the persistent variant CTAs pull tiles from an atomic queue, so showers
 // of very uneven size share one launch (the paper's independent-shower
 // parallelism, section 2, inside one GPU).
@@ -1451,6 +1453,68 @@ __device__ __forceinline__ void record_hits(const KParams &p, const BunchOut<R> 
     }
 }
 
+// The plain FP32 hits path records its crossings from a per-warp queue
+// instead of in the window where they are found.  About 1-2 % of bunches
+// cross a sphere, so a window usually holds none or one, and recording it
+// there keeps 31 of 32 lanes idle through the record's ~70 instructions.
+// The window queues each (bunch, candidate) pair as 8 bytes (step in tile
+// and bunch index; grid and candidate entry) in a ring of 64 in shared
+// memory; once 32 are queued, and at the end of the tile while its step
+// constants are still in shared memory, each lane takes one pair, computes
+// its bunch again (the same function on the same inputs, so the same
+// values) and writes the record with the per-(warp, telescope) atomics of
+// record_hits.  Measured on GB300: 4-7 % less time per launch.
+constexpr int kRing = 64;
+
+template <int BLOCK>
+__device__ __forceinline__ void flush_ring(const KParams &p, const Consts<float> &c, float np1o,
+                                           const Seg<float> *seg, const uint2 *ring, int head,
+                                           int n, int64_t base, int lane, unsigned &st_over) {
+    int tel = -1;
+    float tx = 0.0f, ty = 0.0f, tz = 0.0f;
+    BunchOut<float> o;
+    o.status = -1;
+    o.zg = 0.0f;
+    int s = 0, j = 0;
+    if (lane < n) {
+        const uint2 e = ring[(head + lane) & (kRing - 1)];
+        s = dbg_index(p, static_cast<int>(e.x >> 22), BLOCK, DBG_SMEM);
+        j = static_cast<int>(e.x & 0x3fffffu);
+        bunch<float, false, 0, false, false, true>(p, c, seg[s], nullptr, j, o);
+        const int g = static_cast<int>(e.y >> 31);
+        const int m = static_cast<int>(e.y & 0x7fffffffu);
+        tel = cand_info<float>(p, g, dbg_index(p, m, g ? p.grid[1].n_cand : p.grid[0].n_cand,
+                                               DBG_GRID), tx, ty, tz);
+    }
+    // from here on as record_hits, one crossing per lane
+    const unsigned grp = __match_any_sync(kFull, tel);
+    if (tel >= 0) {
+        const int leader = __ffs(grp) - 1;
+        const unsigned rank = __popc(grp & ((1u << lane) - 1u));
+        unsigned long long slot0 = 0;
+        if (lane == leader)
+            slot0 = atomicAdd(p.count + tel, static_cast<unsigned long long>(__popc(grp)));
+        slot0 = __shfl_sync(grp, slot0, leader);
+        const unsigned long long slot = slot0 + rank;
+        if (slot < static_cast<unsigned long long>(p.cap)) {
+            const Seg<float> &S = seg[s];
+            const int64_t gstep = p.track_base + base + s;
+            const uint64_t key = (static_cast<uint64_t>(gstep) << 32) | static_cast<uint32_t>(j);
+            const float lam = 1.0f / (c.lam_inv1 - o.lam * c.lam_dinv);
+            const float tg = arrival_time_ff(S, o.tsec, o.t);
+            const float sl = (tz - o.zg) / o.cz;   // to the plane through the centre
+            const int64_t r = dbg_index(p, static_cast<int64_t>(tel) * p.cap +
+                                               static_cast<int64_t>(slot),
+                                        int64_t(p.n_tel) * p.cap, DBG_OUT);
+            store4<float>(p.pos, r, o.X + sl * o.cx - tx, o.Y + sl * o.cy - ty, o.cx, o.cy);
+            store4<float>(p.tim, r, tg + sl * np1o * static_cast<float>(1.0 / kC), o.he, S.w, lam);
+            p.key[r] = key;
+        } else {
+            ++st_over;
+        }
+    }
+}
+
 // ------------------------------------------------------------------------
 // The fused kernel.
 // ------------------------------------------------------------------------
@@ -1472,8 +1536,17 @@ __device__ __forceinline__ void gen_prop(const KParams &p) {
     int *off = reinterpret_cast<int *>(seg + BLOCK);          // BLOCK + 1
     int *wsum = off + BLOCK + 1;                                // BLOCK / 32
     SegD<R> *segd = reinterpret_cast<SegD<R> *>(smem + segd_offset<R, BLOCK>());   // DS only
+    // the plain FP32 hits path queues its crossings (flush_ring); the ring
+    // takes the place of the spectra, which that path does not have (the
+    // entry packs the step in the tile in 10 bits above the bunch index in
+    // 22: a step has at most 2^22 bunches)
+    constexpr bool kQueue = MODE == MODE_HITS && !TR && FB == 0 && !DS && !CV &&
+                            std::is_same<R, float>::value;
+    static_assert(BLOCK <= 1024, "the queue entry holds the step in the tile in 10 bits");
     __shared__ unsigned long long s_tile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint2 *ring = reinterpret_cast<uint2 *>(smem + segd_offset<R, BLOCK>()) + warp * kRing;
+    int q_tail = 0, q_cnt = 0;       // (warp-uniform)
     // the candidate grids (a few KB) are read through L1; their sizes and
     // pointers come straight from the kernel parameters (selects, nothing
     // held in registers across the bunch loop)
@@ -1728,6 +1801,32 @@ __device__ __forceinline__ void gen_prop(const KParams &p) {
                     }
                     p.t_first[gb] = first;
                 }
+            } else if constexpr (kQueue) {
+                // one pair per lane and round (a lane with several crossings
+                // takes several rounds), so at most 32 join a ring of < 32
+                for (;;) {
+                    const unsigned has = __ballot_sync(kFull, hm != 0u);
+                    if (!has) break;
+                    if (hm) {
+                        const int bit = __ffs(hm) - 1;
+                        hm &= hm - 1u;
+                        const int slot =
+                            (q_tail + __popc(has & ((1u << lane) - 1u))) & (kRing - 1);
+                        ring[slot] = make_uint2(
+                            (static_cast<uint32_t>(s) << 22) | static_cast<uint32_t>(j),
+                            (static_cast<uint32_t>(gsel) << 31) | static_cast<uint32_t>(s0 + bit));
+                        ++st_hits;
+                    }
+                    q_tail = (q_tail + __popc(has)) & (kRing - 1);
+                    q_cnt += __popc(has);
+                    if (q_cnt >= 32) {
+                        __syncwarp();
+                        flush_ring<BLOCK>(p, c, np1o, seg, ring, (q_tail - q_cnt) & (kRing - 1),
+                                          32, base, lane, st_over);
+                        q_cnt -= 32;
+                        __syncwarp();
+                    }
+                }
             } else {
                 const R np1 = DS ? R(1) + o.kap * c.eta_o : np1o;
                 const int64_t gstep = p.track_base + base + s;
@@ -1748,6 +1847,16 @@ __device__ __forceinline__ void gen_prop(const KParams &p) {
                                },
                                np1, lane, st_hits, st_over);
             }
+        }
+        if constexpr (kQueue) {
+            // the rest of the queue, while the tile's step constants are there
+            __syncwarp();
+            if (q_cnt > 0) {
+                flush_ring<BLOCK>(p, c, np1o, seg, ring, (q_tail - q_cnt) & (kRing - 1), q_cnt,
+                                  base, lane, st_over);
+                q_cnt = 0;
+            }
+            __syncwarp();
         }
         if (!p.tile_counter) break;
         // every warp is done with this tile's step constants and offsets
@@ -1896,6 +2005,9 @@ template <class R, int BLOCK>
 size_t smem_bytes(const KParams &p) {
     size_t b = segd_offset<R, BLOCK>();
     if (p.disp_k > 0) b += sizeof(SegD<R>) * BLOCK;
+    // every FP32 launch without spectra reserves the crossing queue (only
+    // the plain hits kernel uses it; 2 KB per 128 threads)
+    else if (std::is_same<R, float>::value) b += sizeof(uint2) * kRing * (BLOCK / 32);
     return b;
 }
 
