@@ -18,7 +18,7 @@
 //            hoisting of Algorithm 3), the ground point and arrival time
 //            (RAYBND, Appendix B listing), candidate spheres from the ground
 //            grid, and warp-aggregated compaction of the crossings (TELOUT;
-//            the plain FP32 path queues its crossings per warp and records
+//            the hits kernels queue their crossings per warp and record
 //            them 32 at a time, see flush_ring).
 // In the persistent variant CTAs pull tiles from an atomic queue, so showers
 // of very uneven size share one launch (the paper's independent-shower
@@ -1405,10 +1405,9 @@ __device__ __forceinline__ void flush_stat_signed(unsigned long long *stats, int
 // of the arrival line with the horizontal plane through the sphere centre.
 // All 32 lanes call it (hm = 0 on lanes without a crossing).  The photon
 // weight, record key, wavelength and arrival time at h_obs come from
-// weight_key(w, key, lambda, t), called on the hit path only (about 2 % of
-// bunches need them; in the plain hits instantiation the bunch carries the
-// spectrum's deviate and the time's small part, and lambda and the
-// float-float time are formed there).
+// weight_key(w, key, lambda, t), called on the hit path only.  The fallback
+// pass records through it; the fused kernel queues its crossings and
+// records them with flush_ring, the same steps one crossing per lane.
 template <class R, class KW>
 __device__ __forceinline__ void record_hits(const KParams &p, const BunchOut<R> &o, unsigned hm,
                                             int s0, int gsel, KW weight_key, R np1o, int lane,
@@ -1453,38 +1452,43 @@ __device__ __forceinline__ void record_hits(const KParams &p, const BunchOut<R> 
     }
 }
 
-// The plain FP32 hits path records its crossings from a per-warp queue
-// instead of in the window where they are found.  About 1-2 % of bunches
-// cross a sphere, so a window usually holds none or one, and recording it
-// there keeps 31 of 32 lanes idle through the record's ~70 instructions.
-// The window queues each (bunch, candidate) pair as 8 bytes (step in tile
-// and bunch index; grid and candidate entry) in a ring of 64 in shared
-// memory; once 32 are queued, and at the end of the tile while its step
-// constants are still in shared memory, each lane takes one pair, computes
-// its bunch again (the same function on the same inputs, so the same
-// values) and writes the record with the per-(warp, telescope) atomics of
-// record_hits.  Measured on GB300: 4-7 % less time per launch.
+// The hits kernels record their crossings from a per-warp queue instead of
+// in the window where they are found.  About 1-2 % of bunches cross a
+// sphere, so a window usually holds none or one, and recording it there
+// keeps 31 of 32 lanes idle through the record's ~70 instructions.  The
+// window queues each (bunch, candidate) pair as 8 bytes (step in tile and
+// bunch index; grid and candidate entry) in a ring of 64 in shared memory;
+// once 32 are queued, and at the end of the tile while its step constants
+// are still in shared memory, each lane takes one pair, computes its bunch
+// again (the same function on the same inputs, so the same values) and
+// writes the record with the per-(warp, telescope) atomics of record_hits.
+// Measured on GB300: 4-8 % less time per launch of the plain FP32 path,
+// 5-7 % with the transmission draw, 1-2 % with spectra, 12-14 % in FP64
+// (where the record's division and products run on the FP64 pipe).
 constexpr int kRing = 64;
 
-template <int BLOCK>
-__device__ __forceinline__ void flush_ring(const KParams &p, const Consts<float> &c, float np1o,
-                                           const Seg<float> *seg, const uint2 *ring, int head,
-                                           int n, int64_t base, int lane, unsigned &st_over) {
+template <class R, int BLOCK, bool TR, int FB, bool DS, bool CV>
+__device__ __forceinline__ void flush_ring(const KParams &p, const Consts<R> &c, R np1o,
+                                           const Seg<R> *seg, const SegD<R> *segd,
+                                           const uint2 *ring, int head, int n, int64_t base,
+                                           int lane, unsigned &st_over) {
+    // the plain instantiation leaves wavelength and time's large part to here
+    constexpr bool kLazy = !TR && FB == 0 && !DS && !CV;
     int tel = -1;
-    float tx = 0.0f, ty = 0.0f, tz = 0.0f;
-    BunchOut<float> o;
+    R tx = R(0), ty = R(0), tz = R(0);
+    BunchOut<R> o;
     o.status = -1;
-    o.zg = 0.0f;
+    o.zg = R(0);
     int s = 0, j = 0;
     if (lane < n) {
         const uint2 e = ring[(head + lane) & (kRing - 1)];
         s = dbg_index(p, static_cast<int>(e.x >> 22), BLOCK, DBG_SMEM);
         j = static_cast<int>(e.x & 0x3fffffu);
-        bunch<float, false, 0, false, false, true>(p, c, seg[s], nullptr, j, o);
+        bunch<R, TR, FB, DS, CV, kLazy>(p, c, seg[s], DS ? segd + s : nullptr, j, o);
         const int g = static_cast<int>(e.y >> 31);
         const int m = static_cast<int>(e.y & 0x7fffffffu);
-        tel = cand_info<float>(p, g, dbg_index(p, m, g ? p.grid[1].n_cand : p.grid[0].n_cand,
-                                               DBG_GRID), tx, ty, tz);
+        tel = cand_info<R>(p, g, dbg_index(p, m, g ? p.grid[1].n_cand : p.grid[0].n_cand,
+                                           DBG_GRID), tx, ty, tz);
     }
     // from here on as record_hits, one crossing per lane
     const unsigned grp = __match_any_sync(kFull, tel);
@@ -1497,17 +1501,27 @@ __device__ __forceinline__ void flush_ring(const KParams &p, const Consts<float>
         slot0 = __shfl_sync(grp, slot0, leader);
         const unsigned long long slot = slot0 + rank;
         if (slot < static_cast<unsigned long long>(p.cap)) {
-            const Seg<float> &S = seg[s];
+            const Seg<R> &S = seg[s];
             const int64_t gstep = p.track_base + base + s;
             const uint64_t key = (static_cast<uint64_t>(gstep) << 32) | static_cast<uint32_t>(j);
-            const float lam = 1.0f / (c.lam_inv1 - o.lam * c.lam_dinv);
-            const float tg = arrival_time_ff(S, o.tsec, o.t);
-            const float sl = (tz - o.zg) / o.cz;   // to the plane through the centre
+            R lam, tg;
+            if constexpr (kLazy) {
+                lam = R(1) / (c.lam_inv1 - o.lam * c.lam_dinv);
+                if constexpr (std::is_same<R, float>::value)
+                    tg = arrival_time_ff(S, o.tsec, o.t);
+                else
+                    tg = o.t;
+            } else {
+                lam = o.lam;
+                tg = o.t;
+            }
+            const R np1 = DS ? R(1) + o.kap * c.eta_o : np1o;
+            const R sl = (tz - o.zg) / o.cz;   // to the plane through the centre
             const int64_t r = dbg_index(p, static_cast<int64_t>(tel) * p.cap +
                                                static_cast<int64_t>(slot),
                                         int64_t(p.n_tel) * p.cap, DBG_OUT);
-            store4<float>(p.pos, r, o.X + sl * o.cx - tx, o.Y + sl * o.cy - ty, o.cx, o.cy);
-            store4<float>(p.tim, r, tg + sl * np1o * static_cast<float>(1.0 / kC), o.he, S.w, lam);
+            store4<R>(p.pos, r, o.X + sl * o.cx - tx, o.Y + sl * o.cy - ty, o.cx, o.cy);
+            store4<R>(p.tim, r, tg + sl * np1 * R(1.0 / kC), o.he, S.w, lam);
             p.key[r] = key;
         } else {
             ++st_over;
@@ -1528,6 +1542,12 @@ __host__ __device__ constexpr size_t segd_offset() {
     return (sizeof(Seg<R>) * BLOCK + sizeof(int) * (BLOCK + 1 + 32) + 15) & ~size_t(15);
 }
 
+// the crossing queue of the hits kernels, after the spectra (DS)
+template <class R, int BLOCK, bool DS>
+__host__ __device__ constexpr size_t ring_offset() {
+    return segd_offset<R, BLOCK>() + (DS ? sizeof(SegD<R>) * BLOCK : 0);
+}
+
 // CV: a curved atmosphere (radial heights, spherical shells).
 template <class R, int BLOCK, int MODE, bool TR, int FB, bool DS, bool CV>
 __device__ __forceinline__ void gen_prop(const KParams &p) {
@@ -1536,16 +1556,14 @@ __device__ __forceinline__ void gen_prop(const KParams &p) {
     int *off = reinterpret_cast<int *>(seg + BLOCK);          // BLOCK + 1
     int *wsum = off + BLOCK + 1;                                // BLOCK / 32
     SegD<R> *segd = reinterpret_cast<SegD<R> *>(smem + segd_offset<R, BLOCK>());   // DS only
-    // the plain FP32 hits path queues its crossings (flush_ring); the ring
-    // takes the place of the spectra, which that path does not have (the
-    // entry packs the step in the tile in 10 bits above the bunch index in
-    // 22: a step has at most 2^22 bunches)
-    constexpr bool kQueue = MODE == MODE_HITS && !TR && FB == 0 && !DS && !CV &&
-                            std::is_same<R, float>::value;
+    // the hits kernels queue their crossings (flush_ring) in a ring after
+    // the spectra (the entry packs the step in the tile in 10 bits above the
+    // bunch index in 22: a step has at most 2^22 bunches)
+    constexpr bool kQueue = MODE == MODE_HITS;
     static_assert(BLOCK <= 1024, "the queue entry holds the step in the tile in 10 bits");
     __shared__ unsigned long long s_tile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint2 *ring = reinterpret_cast<uint2 *>(smem + segd_offset<R, BLOCK>()) + warp * kRing;
+    uint2 *ring = reinterpret_cast<uint2 *>(smem + ring_offset<R, BLOCK, DS>()) + warp * kRing;
     int q_tail = 0, q_cnt = 0;       // (warp-uniform)
     // the candidate grids (a few KB) are read through L1; their sizes and
     // pointers come straight from the kernel parameters (selects, nothing
@@ -1821,39 +1839,22 @@ __device__ __forceinline__ void gen_prop(const KParams &p) {
                     q_cnt += __popc(has);
                     if (q_cnt >= 32) {
                         __syncwarp();
-                        flush_ring<BLOCK>(p, c, np1o, seg, ring, (q_tail - q_cnt) & (kRing - 1),
-                                          32, base, lane, st_over);
+                        flush_ring<R, BLOCK, TR, FB, DS, CV>(p, c, np1o, seg, segd, ring,
+                                                             (q_tail - q_cnt) & (kRing - 1), 32,
+                                                             base, lane, st_over);
                         q_cnt -= 32;
                         __syncwarp();
                     }
                 }
-            } else {
-                const R np1 = DS ? R(1) + o.kap * c.eta_o : np1o;
-                const int64_t gstep = p.track_base + base + s;
-                const Seg<R> *sp = seg + s;
-                constexpr bool kLazy = MODE == MODE_HITS && !TR && FB == 0 && !DS && !CV;
-                const R lam_o = o.lam, li1 = c.lam_inv1, ldi = c.lam_dinv;
-                const R t_o = o.t, sec_o = o.tsec;
-                record_hits<R>(p, o, hm, s0, gsel,
-                               [sp, gstep, j, lam_o, li1, ldi, t_o, sec_o](R &w_, uint64_t &k_,
-                                                                           R &l_, R &t_) {
-                                   w_ = sp->w;
-                                   k_ = (static_cast<uint64_t>(gstep) << 32) | static_cast<uint32_t>(j);
-                                   l_ = kLazy ? R(1) / (li1 - lam_o * ldi) : lam_o;
-                                   if constexpr (kLazy && std::is_same<R, float>::value)
-                                       t_ = arrival_time_ff(*sp, sec_o, t_o);
-                                   else
-                                       t_ = t_o;
-                               },
-                               np1, lane, st_hits, st_over);
             }
         }
         if constexpr (kQueue) {
             // the rest of the queue, while the tile's step constants are there
             __syncwarp();
             if (q_cnt > 0) {
-                flush_ring<BLOCK>(p, c, np1o, seg, ring, (q_tail - q_cnt) & (kRing - 1), q_cnt,
-                                  base, lane, st_over);
+                flush_ring<R, BLOCK, TR, FB, DS, CV>(p, c, np1o, seg, segd, ring,
+                                                     (q_tail - q_cnt) & (kRing - 1), q_cnt, base,
+                                                     lane, st_over);
                 q_cnt = 0;
             }
             __syncwarp();
@@ -2005,9 +2006,9 @@ template <class R, int BLOCK>
 size_t smem_bytes(const KParams &p) {
     size_t b = segd_offset<R, BLOCK>();
     if (p.disp_k > 0) b += sizeof(SegD<R>) * BLOCK;
-    // every FP32 launch without spectra reserves the crossing queue (only
-    // the plain hits kernel uses it; 2 KB per 128 threads)
-    else if (std::is_same<R, float>::value) b += sizeof(uint2) * kRing * (BLOCK / 32);
+    // every launch reserves the crossing queue (the hits kernels use it;
+    // 2 KB per 128 threads)
+    b += sizeof(uint2) * kRing * (BLOCK / 32);
     return b;
 }
 

@@ -87,6 +87,27 @@ def test_batched_showers_reduced():
     assert rt["n"] > 50_000
 
 
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_dense_overlapping_spheres(prec):
+    """Large, overlapping and stacked spheres around the core of a reduced
+    vertical shower: most bunches cross one sphere or more, so nearly every
+    window holds crossings, lanes hold several, and the per-warp crossing
+    queue fills, wraps and is flushed many times per tile."""
+    sc = _reduced(workloads.vertical_1tev(n=3_001), 3_001)
+    sc["telescopes"] = np.array([
+        (0.0, 0.0, 0.0, 150.0),        # at the core
+        (120.0, 0.0, 0.0, 150.0),      # overlapping the first
+        (0.0, 0.0, 200.0, 100.0),      # above the first (centre 200 m up)
+        (-60.0, 80.0, 40.0, 60.0),     # inside the first's reach
+        (300.0, 300.0, 0.0, 12.0),     # a small one off to the side
+    ])
+    rt, rh, stats = _full_compare(sc, prec, cap=400_000)
+    n_cross = int(stats[9])
+    assert n_cross > int(stats[8])          # more crossings than bunches on the ground
+    assert rh["n_common"] > 0.99 * n_cross
+    assert rt["edge_status"] + rt["edge_hit"] < 0.02 * rt["n"]
+
+
 def test_launch_shapes_agree():
     """Persistent and one-CTA-per-tile launches, every block size and the
     builds for 9 and 10 CTAs per SM: the same records (order inside a
