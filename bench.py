@@ -590,7 +590,8 @@ def run_ours(args):
 
 def run_leg(args):
     """One secondary leg alone: the step generator (2e6 steps of the 1 TeV
-    vertical shower) or the adjoint (300 GeV shower, both precisions)."""
+    vertical shower), the adjoint (300 GeV shower, both precisions), the
+    beyond-table fallback or the end to end from shower parameters."""
     import torch
 
     import paper_2006_14927_gb300 as P
@@ -602,6 +603,10 @@ def run_leg(args):
         return
     if args.leg == "fallback":
         print(json.dumps({"leg": "fallback", **fallback_leg(dev, args)}), flush=True)
+        return
+    if args.leg == "e2e_generated":
+        print(json.dumps({"leg": "e2e_generated",
+                          **generated_leg(P, dev, args.steps, args.warmup)}), flush=True)
         return
     sc = workloads.vertical_1tev(n=10)
     ctx = P.Context(sc["atm"], sc["h_obs"], sc["telescopes"])
@@ -782,7 +787,11 @@ def generated_leg(P, dev, steps, warmup):
     """End to end from shower parameters: the 1 TeV vertical shower's 2e6
     steps come from the device generator (cher_generate_steps), only the
     shower parameters and its depth table go up, the packed records come
-    down; and the generator alone (64 B of steps written per step)."""
+    down; and the generator alone (64 B of steps written per step).  Two
+    stages over steps: step k's generator, kernel and packing run on the
+    compute stream while step k-1's records come down on a copy stream (each
+    download starts once the next step's work has); two step buffers, two
+    output buffers and two host record buffers."""
     import torch
 
     import workloads
@@ -792,46 +801,74 @@ def generated_leg(P, dev, steps, warmup):
     prec = P.CHER_FP32_BULK
     n = 2_000_000
     showers = [dict(e0_mev=1.0e6, zenith=0.0, azimuth=0.0, core_x=0.0, core_y=0.0, n=n)]
-    out = ctx.alloc_hits(600_000, prec, device=dev)
-    gen_buf = ctx.generate_steps(showers, 11, prec)
-    n_rec = 19 * 600_000
-    pk = dict(pos=torch.empty((n_rec, 4), dtype=torch.float32, device=dev),
-              tim=torch.empty((n_rec, 4), dtype=torch.float32, device=dev),
-              key=torch.empty(n_rec, dtype=torch.int64, device=dev),
-              offset=torch.empty(20, dtype=torch.int64, device=dev))
-    h_pos = torch.empty((n_rec, 4), dtype=torch.float32).pin_memory()
-    h_tim = torch.empty((n_rec, 4), dtype=torch.float32).pin_memory()
-    h_key = torch.empty(n_rec, dtype=torch.int64).pin_memory()
-    h_cnt = torch.empty(19, dtype=torch.int64).pin_memory()
-    h_st = torch.empty(P.NSTATS, dtype=torch.int64).pin_memory()
-    h_off = torch.empty(20, dtype=torch.int64).pin_memory()
+    n_tel = ctx.n_tel
+    outs = [ctx.alloc_hits(600_000, prec, device=dev) for _ in range(2)]
+    gens = [ctx.generate_steps(showers, 11, prec) for _ in range(2)]
+    n_rec = n_tel * 600_000
+    pk = [dict(pos=torch.empty((n_rec, 4), dtype=torch.float32, device=dev),
+               tim=torch.empty((n_rec, 4), dtype=torch.float32, device=dev),
+               key=torch.empty(n_rec, dtype=torch.int64, device=dev),
+               offset=torch.empty(n_tel + 1, dtype=torch.int64, device=dev))
+          for _ in range(2)]
+    hrec = [tuple(torch.empty(shape, dtype=dt).pin_memory()
+                  for shape, dt in (((n_rec, 4), torch.float32), ((n_rec, 4), torch.float32),
+                                    (n_rec, torch.int64)))
+            for _ in range(2)]
+    h_cnts = [torch.empty(n_tel, dtype=torch.int64).pin_memory() for _ in range(2)]
+    h_sts = [torch.empty(P.NSTATS, dtype=torch.int64).pin_memory() for _ in range(2)]
+    h_offs = [torch.empty(n_tel + 1, dtype=torch.int64).pin_memory() for _ in range(2)]
+    down = torch.cuda.Stream(device=dev)
+    comp = torch.cuda.current_stream()
+    ev = {k: [torch.cuda.Event(), torch.cuda.Event()] for k in ("cnt", "down", "start")}
 
-    def gen_step():
-        dg = ctx.generate_steps(showers, 11, prec, out=gen_buf)
-        ctx.generate_propagate(dg, 11, prec, out)
-        ctx.pack_records(out, pk)
-        h_cnt.copy_(out.count, non_blocking=True)
-        h_st.copy_(out.stats, non_blocking=True)
-        h_off.copy_(pk["offset"], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        nbytes = (h_cnt.numel() + h_st.numel() + h_off.numel()) * 8
-        total = min(int(h_off[-1]), n_rec)
-        if total > 0:
-            h_pos[:total].copy_(pk["pos"][:total], non_blocking=True)
-            h_tim[:total].copy_(pk["tim"][:total], non_blocking=True)
-            h_key[:total].copy_(pk["key"][:total], non_blocking=True)
-        nbytes += total * 40
-        torch.cuda.current_stream().synchronize()
-        return nbytes, int(h_st[3])
+    def launch_step(b):
+        comp.wait_event(ev["down"][b])             # out b's records are down
+        ev["start"][b].record(comp)
+        dg = ctx.generate_steps(showers, 11, prec, out=gens[b])
+        ctx.generate_propagate(dg, 11, prec, outs[b])
+        ctx.pack_records(outs[b], pk[b], stream=comp)
+        h_cnts[b].copy_(outs[b].count, non_blocking=True)
+        h_sts[b].copy_(outs[b].stats, non_blocking=True)
+        h_offs[b].copy_(pk[b]["offset"], non_blocking=True)
+        ev["cnt"][b].record(comp)
 
-    for _ in range(max(1, warmup // 2)):
-        gen_step()
+    def download(b):
+        ev["cnt"][b].synchronize()                  # this step's counts on the host
+        nbytes = (h_cnts[b].numel() + h_sts[b].numel() + h_offs[b].numel()) * 8
+        total = int(h_offs[b][-1])
+        if total > n_rec:
+            raise RuntimeError("host record buffer too small")
+        with torch.cuda.stream(down):
+            down.wait_event(ev["cnt"][b])           # the packed records are written
+            down.wait_event(ev["start"][1 - b])     # the next step's work has started
+            hp, ht, hk = hrec[b]
+            if total > 0:
+                hp[:total].copy_(pk[b]["pos"][:total], non_blocking=True)
+                ht[:total].copy_(pk[b]["tim"][:total], non_blocking=True)
+                hk[:total].copy_(pk[b]["key"][:total], non_blocking=True)
+            nbytes += total * 40
+            ev["down"][b].record(down)
+        return nbytes, int(h_sts[b][3])
+
+    def run(n_steps):
+        nbytes, nb = 0, 0
+        for k in range(n_steps):
+            b = k % 2
+            launch_step(b)
+            if k >= 1:
+                nbytes, got = download(1 - b)
+                nb += got
+        nbytes, got = download((n_steps - 1) % 2)
+        nb += got
+        down.synchronize()
+        comp.synchronize()
+        return nbytes, nb
+
+    run(max(2, warmup // 2))
     g0 = time.perf_counter()
-    gb = 0
-    for _ in range(steps):
-        gd2h, gbunch = gen_step()
-        gb += gbunch
+    gd2h, gb = run(steps)
     tg = time.perf_counter() - g0
+    gen_buf = gens[0]
     gms = []
     for _ in range(steps):
         a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -847,6 +884,7 @@ def generated_leg(P, dev, steps, warmup):
     return {"value": gb / tg, "unit": UNIT, "h2d_bytes_per_step": 64 + 16 + 4 * 1024 + 8,
             "d2h_bytes_per_step": int(gd2h), "steps_generated": n,
             "bunches_per_step": gb // steps,
+            "pipelined": "step k-1's records down during step k's generator and kernel",
             "generator": {"ms_per_call": g_ms, "steps_per_s": n / (g_ms / 1e3),
                           "roofline": {"bound": "hbm", "achieved": g_gbs,
                                        "peak": float(peaks_.get("hbm_gbs", 6800.0)),
@@ -973,7 +1011,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the other workloads, the adjoint and the generator legs")
-    ap.add_argument("--leg", choices=["all", "generator", "adjoint", "fallback"], default="all",
+    ap.add_argument("--leg", choices=["all", "generator", "adjoint", "fallback", "e2e_generated"],
+                    default="all",
                     help="run one secondary leg alone (for profiling captures)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
