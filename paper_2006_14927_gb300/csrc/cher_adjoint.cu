@@ -287,10 +287,13 @@ __device__ bool bunch_dual(const AdjParams &A, int64_t i, int j, BunchDual<T> &o
     {
         const int e0 = jj * (p.Z - 1) + kk, e1 = e0 + (p.Z - 1);
         if constexpr (std::is_same<T, float>::value) {
-            const float4 *Tb = static_cast<const float4 *>(p.tab);
-            const float4 t0 = __ldg(Tb + e0), t1 = __ldg(Tb + e1);
-            c00x = t0.x; c00l = t0.y; c01x = t0.z; c01l = t0.w;
-            c10x = t1.x; c10l = t1.y; c11x = t1.z; c11l = t1.w;
+            // (flat layers: one float2 (ax, al) per node)
+            const float2 *Tb = static_cast<const float2 *>(p.tab);
+            const int n0 = jj * p.Z + kk;
+            const float2 a0 = __ldg(Tb + n0), a1 = __ldg(Tb + n0 + 1);
+            const float2 b0 = __ldg(Tb + n0 + p.Z), b1 = __ldg(Tb + n0 + p.Z + 1);
+            c00x = a0.x; c00l = a0.y; c01x = a1.x; c01l = a1.y;
+            c10x = b0.x; c10l = b0.y; c11x = b1.x; c11l = b1.y;
         } else {
             const double2 *Tb = static_cast<const double2 *>(p.tab);
             const double2 a0 = __ldg(Tb + 2 * e0), a1 = __ldg(Tb + 2 * e0 + 1);

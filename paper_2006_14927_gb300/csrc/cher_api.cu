@@ -539,13 +539,24 @@ cher_status cher_build_refraction_tables(cher_ctx *c, int32_t n_heights, int32_t
     const int H = c->T.H, Z = c->T.Z;
     const size_t per = entry_values(c->T);
     std::vector<double> t64(static_cast<size_t>(H) * (Z - 1) * per);
-    std::vector<float> t32(t64.size());
     for (int j = 0; j < H; ++j)
-        for (int k = 0; k < Z - 1; ++k) {
-            const size_t e = (static_cast<size_t>(j) * (Z - 1) + k) * per;
-            pack_entry(c->T, j, k, &t64[e]);
-            for (size_t q = 0; q < per; ++q) t32[e + q] = static_cast<float>(t64[e + q]);
+        for (int k = 0; k < Z - 1; ++k)
+            pack_entry(c->T, j, k, &t64[(static_cast<size_t>(j) * (Z - 1) + k) * per]);
+    // FP32: in flat layers one (ax, al) pair per node, [H][Z] (half the bytes
+    // of the pair-interleaved entries: the bunch loop reads the cell's four
+    // nodes as four 8-byte loads, and more of a large table stays in L1);
+    // in a curved atmosphere the FP64 entries rounded
+    std::vector<float> t32;
+    if (per == 4) {
+        t32.resize(static_cast<size_t>(H) * Z * 2);
+        for (size_t a = 0; a < static_cast<size_t>(H) * Z; ++a) {
+            t32[2 * a] = static_cast<float>(c->T.ax[a]);
+            t32[2 * a + 1] = static_cast<float>(c->T.al[a]);
         }
+    } else {
+        t32.resize(t64.size());
+        for (size_t q = 0; q < t64.size(); ++q) t32[q] = static_cast<float>(t64[q]);
+    }
     std::vector<float> e32(c->T.eta.begin(), c->T.eta.end());
     const size_t nt = c->tel.size();
     std::vector<double> tel64(nt * 4);

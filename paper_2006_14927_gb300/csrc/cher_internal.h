@@ -97,7 +97,11 @@ struct KParams {
     // {ax[j][k], al[j][k], ax[j][k+1], al[j][k+1]}
     int32_t H, Z;
     double inv_dht, inv_dq, q_max;
-    const void *tab;                      // float4 or double4 [H][Z-1]
+    // FP64: entry (j, k < Z-1) = {ax_k, al_k, ax_k+1, al_k+1} (and, in a
+    // curved atmosphere, {ag_k, ag_k+1, 0, 0}); FP32 in flat layers one
+    // float2 (ax, al) per node [H][Z], in a curved atmosphere the FP64
+    // entries rounded
+    const void *tab;
     // wavelength band in 1/nm
     double lam_inv1, lam_dinv;
     // telescopes and two ground grids of candidate spheres: grid 0 serves
