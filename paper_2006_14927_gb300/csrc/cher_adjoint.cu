@@ -285,7 +285,6 @@ __device__ bool bunch_dual(const AdjParams &A, int64_t i, int j, BunchDual<T> &o
     const T b = fk - static_cast<T>(kk);
     T c00x, c01x, c10x, c11x, c00l, c01l, c10l, c11l;
     {
-        const int e0 = jj * (p.Z - 1) + kk, e1 = e0 + (p.Z - 1);
         if constexpr (std::is_same<T, float>::value) {
             // (flat layers: one float2 (ax, al) per node)
             const float2 *Tb = static_cast<const float2 *>(p.tab);
@@ -296,8 +295,9 @@ __device__ bool bunch_dual(const AdjParams &A, int64_t i, int j, BunchDual<T> &o
             c10x = b0.x; c10l = b0.y; c11x = b1.x; c11l = b1.y;
         } else {
             const double2 *Tb = static_cast<const double2 *>(p.tab);
-            const double2 a0 = __ldg(Tb + 2 * e0), a1 = __ldg(Tb + 2 * e0 + 1);
-            const double2 b0 = __ldg(Tb + 2 * e1), b1 = __ldg(Tb + 2 * e1 + 1);
+            const int n0 = jj * p.Z + kk;
+            const double2 a0 = __ldg(Tb + n0), a1 = __ldg(Tb + n0 + 1);
+            const double2 b0 = __ldg(Tb + n0 + p.Z), b1 = __ldg(Tb + n0 + p.Z + 1);
             c00x = a0.x; c00l = a0.y; c01x = a1.x; c01l = a1.y;
             c10x = b0.x; c10l = b0.y; c11x = b1.x; c11l = b1.y;
         }

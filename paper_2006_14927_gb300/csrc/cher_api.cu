@@ -192,8 +192,9 @@ cher_status upload_grid(cher_ctx *c, int g) {
     return CHER_OK;
 }
 
-// Device layout of one table set: per entry (j, k < Z-1) the pair
-// {ax_k, al_k, ax_k+1, al_k+1} and, in a curved atmosphere, {ag_k, ag_k+1, 0, 0}.
+// Pair-interleaved entries (the dispersion tables, and the main tables in a
+// curved atmosphere): per entry (j, k < Z-1) the pair {ax_k, al_k, ax_k+1,
+// al_k+1} and, in a curved atmosphere, {ag_k, ag_k+1, 0, 0}.
 size_t entry_values(const cher::HostTables &T) { return T.earth_radius > 0.0 ? 8 : 4; }
 
 void pack_entry(const cher::HostTables &T, int j, int k, double *out) {
@@ -538,14 +539,24 @@ cher_status cher_build_refraction_tables(cher_ctx *c, int32_t n_heights, int32_t
 
     const int H = c->T.H, Z = c->T.Z;
     const size_t per = entry_values(c->T);
-    std::vector<double> t64(static_cast<size_t>(H) * (Z - 1) * per);
-    for (int j = 0; j < H; ++j)
-        for (int k = 0; k < Z - 1; ++k)
-            pack_entry(c->T, j, k, &t64[(static_cast<size_t>(j) * (Z - 1) + k) * per]);
-    // FP32: in flat layers one (ax, al) pair per node, [H][Z] (half the bytes
-    // of the pair-interleaved entries: the bunch loop reads the cell's four
-    // nodes as four 8-byte loads, and more of a large table stays in L1);
-    // in a curved atmosphere the FP64 entries rounded
+    std::vector<double> t64;
+    if (per == 4) {
+        // FP64 in flat layers: one (ax, al) pair per node, [H][Z]
+        t64.resize(static_cast<size_t>(H) * Z * 2);
+        for (size_t a = 0; a < static_cast<size_t>(H) * Z; ++a) {
+            t64[2 * a] = c->T.ax[a];
+            t64[2 * a + 1] = c->T.al[a];
+        }
+    } else {
+        t64.resize(static_cast<size_t>(H) * (Z - 1) * per);
+        for (int j = 0; j < H; ++j)
+            for (int k = 0; k < Z - 1; ++k)
+                pack_entry(c->T, j, k, &t64[(static_cast<size_t>(j) * (Z - 1) + k) * per]);
+    }
+    // FP32 likewise: in flat layers one (ax, al) pair per node (half the
+    // bytes of pair-interleaved entries: the bunch loop reads the cell's four
+    // nodes as four 8-byte loads, and more of a large table stays in L1); in
+    // a curved atmosphere the FP64 entries rounded
     std::vector<float> t32;
     if (per == 4) {
         t32.resize(static_cast<size_t>(H) * Z * 2);

@@ -97,10 +97,9 @@ struct KParams {
     // {ax[j][k], al[j][k], ax[j][k+1], al[j][k+1]}
     int32_t H, Z;
     double inv_dht, inv_dq, q_max;
-    // FP64: entry (j, k < Z-1) = {ax_k, al_k, ax_k+1, al_k+1} (and, in a
-    // curved atmosphere, {ag_k, ag_k+1, 0, 0}); FP32 in flat layers one
-    // float2 (ax, al) per node [H][Z], in a curved atmosphere the FP64
-    // entries rounded
+    // flat layers: one (ax, al) pair per node [H][Z] (double2 or float2);
+    // curved atmosphere: entry (j, k < Z-1) = {ax_k, al_k, ax_k+1, al_k+1},
+    // {ag_k, ag_k+1, 0, 0} (double, or rounded to float)
     const void *tab;
     // wavelength band in 1/nm
     double lam_inv1, lam_dinv;

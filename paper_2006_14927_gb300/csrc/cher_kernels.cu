@@ -1231,13 +1231,12 @@ __device__ __forceinline__ void bunch(const KParams &p, const Consts<R> &c, cons
         Ax = x0 + b * (x1 - x0);
         Al = l0 + b * (l1 - l0);
     } else {
-        const int e0 = dbg_index(p, jj * (c.Z - 1) + kk, int64_t(c.H - 1) * (c.Z - 1), DBG_TAB);
-        const int e1 = dbg_index(p, e0 + (c.Z - 1), int64_t(c.H) * (c.Z - 1), DBG_TAB);
+        const int n0 = dbg_index(p, jj * c.Z + kk, int64_t(c.H - 1) * c.Z - 1, DBG_TAB);
         const double2 *T = static_cast<const double2 *>(p.tab);
-        const double2 t0a = __ldg(T + 2 * e0), t0b = __ldg(T + 2 * e0 + 1);
-        const double2 t1a = __ldg(T + 2 * e1), t1b = __ldg(T + 2 * e1 + 1);
-        const double x0 = t0a.x + a * (t1a.x - t0a.x), x1 = t0b.x + a * (t1b.x - t0b.x);
-        const double l0 = t0a.y + a * (t1a.y - t0a.y), l1 = t0b.y + a * (t1b.y - t0b.y);
+        const double2 a0 = __ldg(T + n0), a1 = __ldg(T + n0 + 1);
+        const double2 b0 = __ldg(T + n0 + c.Z), b1 = __ldg(T + n0 + c.Z + 1);
+        const double x0 = a0.x + a * (b0.x - a0.x), x1 = a1.x + a * (b1.x - a1.x);
+        const double l0 = a0.y + a * (b0.y - a0.y), l1 = a1.y + a * (b1.y - a1.y);
         Ax = x0 + b * (x1 - x0);
         Al = l0 + b * (l1 - l0);
     }
