@@ -96,9 +96,9 @@ FP64_FMA_PER_SM_CLK = 2         # GB300: 1/64 of the FP32 rate (ncu: 2 DFMA/cycl
 # by its steps (the inputs, 64 B per step, dominate and scale with them).
 # Reported only while the kernel sources hash to what was profiled.
 TRAFFIC_PER_STEP = {
-    "vertical_1tev": (77.43, "4ff101747fbfdfa1"),      # 129.37 + 25.49 MB at 2e6 steps, 128 x 9
-    "inclined_20tev": (74.45, "4ff101747fbfdfa1"),     # 135.39 + 13.52 MB at 2e6 steps, 128 x 10
-    "batched_256": (75.50, "4ff101747fbfdfa1"),        # 132.57 + 18.44 MB at 2e6 steps, 128 x 10
+    "vertical_1tev": (77.26, "e12d0db1d7ddc53f"),      # 128.74 + 25.79 MB at 2e6 steps, 128 x 8
+    "inclined_20tev": (74.38, "e12d0db1d7ddc53f"),     # 135.36 + 13.40 MB at 2e6 steps, 128 x 10
+    "batched_256": (75.45, "e12d0db1d7ddc53f"),        # 132.56 + 18.35 MB at 2e6 steps, 128 x 10
 }
 KERNEL_SOURCES = ("cher_kernels.cu", "cher_device.cuh", "cher_internal.h")
 
