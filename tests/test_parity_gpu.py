@@ -88,6 +88,38 @@ def test_batched_showers_reduced():
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
+def test_refraction_table_edges(prec):
+    """Bunches in the refraction tables' last height row (emitted within the
+    top 400 m below h_max) and last zenith column (steps at 66-70.5 degrees,
+    the tables reaching 70), and some just past both (emitted above h_max,
+    arriving beyond the zenith range): the lookups clamped into the last
+    cell, the drops counted."""
+    import math
+    sc = workloads.plain_fp64(n=1_500)
+    n = 1_500
+    rng = np.random.default_rng(31)
+    tr = {k: np.array(v, dtype=float) for k, v in sc["tracks"].items()}
+    top = np.arange(n) < n // 2
+    h_max = sc["h_max"]
+    tr["z0"] = np.where(top, rng.uniform(h_max - 400.0, h_max + 30.0, n),
+                        rng.uniform(3000.0, 5000.0, n))
+    zen = np.where(top, rng.uniform(0.0, math.radians(5.0), n),
+                   rng.uniform(math.radians(66.0), math.radians(70.5), n))
+    ph = rng.uniform(0.0, 2.0 * math.pi, n)
+    tr["ux"], tr["uy"], tr["uz"] = np.sin(zen) * np.cos(ph), np.sin(zen) * np.sin(ph), -np.cos(zen)
+    # (near h_max the threshold is above 1 GeV)
+    tr["ekin"] = np.where(top, np.exp(rng.uniform(math.log(5e3), math.log(5e4), n)),
+                          np.exp(rng.uniform(math.log(200.0), math.log(2000.0), n)))
+    tr["t0"] = (workloads.H_START - tr["z0"]) / workloads.C_LIGHT
+    sc["tracks"] = tr
+    rt, rh, stats = _full_compare(sc, prec)
+    assert rt["n"] > 10_000
+    assert stats[6] > 0                     # emitted above h_max
+    assert stats[7] > 0                     # beyond the tables' zenith range
+    assert rt["edge_status"] + rt["edge_hit"] < 0.02 * rt["n"]
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
 def test_dense_overlapping_spheres(prec):
     """Large, overlapping and stacked spheres around the core of a reduced
     vertical shower: most bunches cross one sphere or more, so nearly every
