@@ -412,6 +412,16 @@ def workload_leg(P, dev, wl, scale, cap_arg, steps, warmup, launch, main_launch,
     return res
 
 
+def _leg(fn, *a):
+    """A secondary leg of the line: its result, or the error it raised (the
+    headline and the other legs are still reported)."""
+    try:
+        return fn(*a)
+    except Exception as e:  # noqa: BLE001 - reported in the line, not swallowed
+        print(f"leg {fn.__name__} failed: {e!r}", file=sys.stderr, flush=True)
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
+
+
 def run_ours(args):
     import torch
 
@@ -507,7 +517,11 @@ def run_ours(args):
     vg, v32, v64 = bg / tg, b32 / t32, b64 / t64
 
     # ---- end to end: host buffers through the C ABI ---------------------
-    e2e = None if args.no_e2e else e2e_leg(P, B, r32, steps, warmup, world, dev)
+    # (one process: a failure is reported in the line; several: every rank
+    # must reach the same barriers, so an error ends the run)
+    e2e = None if args.no_e2e else (
+        _leg(e2e_leg, P, B, r32, steps, warmup, world, dev) if world == 1
+        else e2e_leg(P, B, r32, steps, warmup, world, dev))
     B.release(FP32)
 
     peaks, src = _peaks()
@@ -520,8 +534,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
         for other in ("inclined_20tev", "vertical_1tev"):
             given = tuple(int(v) for v in args.launch.split(",")) if args.launch else None
-            legs[other] = workload_leg(P, dev, other, 1.0, None, steps, warmup, given, launch,
-                                       sm_count, mhz, barrier)
+            legs[other] = _leg(workload_leg, P, dev, other, 1.0, None, steps, warmup, given,
+                               launch, sm_count, mhz, barrier)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -537,7 +551,7 @@ def run_ours(args):
     rl64 = fp64_roofline(float(r64["stats"][3]), steps_n, ms64, sm_count, mhz)
     # the FP64 path beside the FP32 one inside the roofline object as well
     rl["fp64_path"] = {"value": v64, "frac": rl64["frac"], "fp32_over_fp64": vg / v64}
-    cpu = cpu_baseline(wl) if world == 1 else None
+    cpu = _leg(cpu_baseline, wl) if world == 1 else None
     line = {
         "metric": METRIC, "value": vg, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": warmup, "ms_per_step": 1e3 * tg / len(rg["ms"]),
@@ -575,14 +589,17 @@ def run_ours(args):
     for k, v in legs.items():
         line[k] = v
     if world == 1 and not args.no_legs and wl == "batched_256" and args.scale == 1.0:
-        line["adjoint"] = adjoint_leg(dev, steps)
-        line["adjoint"]["cpu_baseline"] = cpu_baseline_readout()
-        line["e2e_generated"] = generated_leg(P, dev, steps, warmup)
+        line["adjoint"] = _leg(adjoint_leg, dev, steps)
+        if "error" not in line["adjoint"]:
+            line["adjoint"]["cpu_baseline"] = _leg(cpu_baseline_readout)
+        line["e2e_generated"] = _leg(generated_leg, P, dev, steps, warmup)
     # the headline figures once more at the end of the line
     line["summary"] = {"fp32": vg, "fp32_frac": rl["frac"], "fp64": v64,
                        "fp64_frac": rl64["frac"], "fp32_over_fp64": vg / v64,
-                       **{f"{k}_fp32_frac": v["roofline"]["frac"] for k, v in legs.items()},
-                       **{f"{k}_fp64_frac": v["fp64"]["roofline"]["frac"] for k, v in legs.items()}}
+                       **{f"{k}_fp32_frac": v["roofline"]["frac"] for k, v in legs.items()
+                          if "error" not in v},
+                       **{f"{k}_fp64_frac": v["fp64"]["roofline"]["frac"] for k, v in legs.items()
+                          if "error" not in v}}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
